@@ -1,0 +1,443 @@
+#!/usr/bin/env python
+"""Throughput of the fisheye Gaussian-splatting hot path on GB300.
+
+Workload: 500,000 Gaussians (shell of radius 1-5 around the camera, log-scales N(-3, 0.5),
+SH degree 3), one equidistant fisheye view of 1752x1168 at 180 degrees with a random pose,
+dL/dimage ~ N(0, 1e-2). One step = forward (preprocess -> bin/sort -> rasterize) + backward
+(rasterize backward -> preprocess backward) of one view, every stage in the sm_103a kernels.
+
+Prints one JSON line (rank 0). `value` = views/s of the whole job (fwd+bwd); the forward-only
+rate, per-stage times, the roofline of the dominant kernel, the end-to-end rate through host
+buffers and the CPU oracle's rate on a bounded sample are reported beside it.
+
+--impl reference times the FP64 CPU oracle (the slow program the GPU path is checked
+against) on the same workload, a bounded sample of pixels per step.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "fisheye views/s fwd and fwd+bwd at 1752×1168; served p50/p99 latency"
+WORKLOAD = "fisheye-GS 500k Gaussians SH3, 1752x1168 @180deg, random pose, fwd+bwd"
+L2_FLUSH_BYTES = 256 << 20
+# FP32 flops per (pixel, Gaussian) pair in the rasterizer's formulation (FMA = 2):
+FLOPS_FWD_EVAL = 10    # dx, dy, the quadratic form and the log-opacity offset
+FLOPS_FWD_BLEND = 10   # min, 1-alpha, T(1-alpha), alpha T, three colour FMAs
+FLOPS_BWD_EVAL = 10
+FLOPS_BWD_CONTRIB = 58  # transmittance recovery, dL/dalpha, colour suffix, 9 gradients + sum
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=d.get("hbm_gbs", 6800.0), sm_max_mhz=d.get("sm_max_mhz", 2070.0),
+                    source="measured")
+    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), hw=parts[5], hwt=parts[6],
+                                 swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                            ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[k].lower().startswith("active"):
+                    reasons.add(name)
+        return dict(sm_mhz=statistics.median(r["sm"] for r in rows),
+                    sm_max_mhz=max(r["smax"] for r in rows), reasons=sorted(reasons),
+                    samples=len(rows))
+
+
+def _traffic(kernel_name):
+    """DRAM bytes per launch of `kernel_name` from the committed ncu summary, if it was taken
+    on the current source (sha256 of the kernel's .cu file); else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if f.get("kernel") != kernel_name:
+            continue
+        src = os.path.join(ROOT, "paper_2409_04751_gb300", "csrc", f.get("source", ""))
+        if not os.path.exists(src):
+            return None
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if sha != f.get("sha"):
+            return None
+        return float(f["dram_bytes_per_launch"])
+    return None
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle (cpu_baseline leg and --impl reference)
+
+def _oracle_sample_rate(scene, cam, target_s, rng_seed=0):
+    """Time the FP64 oracle's fwd+bwd on a pixel sample sized for about target_s seconds and
+    extrapolate to views/s for the full view. Returns (views_per_s, seconds, sample_desc,
+    threads)."""
+    import oracle
+    w, h = cam["width"], cam["height"]
+    P = w * h
+    rng = np.random.default_rng(rng_seed)
+    t0 = time.perf_counter()
+    G = oracle.project(scene, cam)
+    t_proj = time.perf_counter() - t0
+    n_pix = 256
+    spent = 0.0
+    per_pix = None
+    while True:
+        idx = rng.choice(P, n_pix, replace=False)
+        pix = np.stack([idx % w, idx // w], 1).astype(np.int32)
+        g = rng.normal(0, 1e-2, (n_pix, 3))
+        t0 = time.perf_counter()
+        oracle.render(G, pix)
+        oracle.backward(G, scene, cam, pix, g)
+        dt = time.perf_counter() - t0
+        spent += dt
+        per_pix = dt / n_pix
+        if spent >= target_s or n_pix >= P:
+            break
+        n_pix = int(min(P, max(n_pix * 2, (target_s - spent) / max(per_pix, 1e-9))))
+    est = t_proj + per_pix * P
+    desc = (f"oracle fwd+bwd on {n_pix} random pixels of the 1752x1168 view "
+            f"(+ projection of all Gaussians), extrapolated to the full view")
+    return 1.0 / est, spent + t_proj, desc, oracle.num_threads()
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    from paper_2409_04751_gb300 import scenes
+    scene, cams = scenes.config1()
+    cam = cams[0]
+    import oracle
+    G = oracle.project(scene, cam)
+    w, h = cam["width"], cam["height"]
+    rng = np.random.default_rng(5)
+    n_pix = 512
+    times = []
+    for step in range(args.warmup + args.steps):
+        idx = rng.choice(w * h, n_pix, replace=False)
+        pix = np.stack([idx % w, idx // w], 1).astype(np.int32)
+        g = rng.normal(0, 1e-2, (n_pix, 3))
+        t0 = time.perf_counter()
+        Gs = oracle.project(scene, cam)
+        t1 = time.perf_counter()
+        oracle.render(Gs, pix)
+        oracle.backward(Gs, scene, cam, pix, g)
+        t2 = time.perf_counter()
+        if step >= args.warmup:
+            times.append((t1 - t0) + (t2 - t1) * (w * h) / n_pix)
+    per_view = sum(times) / len(times)
+    value = 1.0 / per_view
+    line = dict(metric=METRIC, value=value, unit="views/s", n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=per_view * 1e3, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                impl="reference",
+                config=dict(workload=WORKLOAD, n_gaussians=500000, width=1752, height=1168,
+                            fov_deg=180.0, sh_degree=3),
+                cpu_baseline=dict(value=value, unit="views/s", cores=oracle.num_threads(),
+                                  kind="oracle",
+                                  sample=f"per step: projection of all Gaussians + fwd+bwd of "
+                                         f"{n_pix} random pixels, extrapolated to 1752x1168"),
+                e2e=dict(value=value, unit="views/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0),
+                gpu_launches=0)
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    from paper_2409_04751_gb300 import fgs, scenes
+    from paper_2409_04751_gb300.renderer import FisheyeRenderer, gaussians_of, scene_to_device
+
+    rank, world, local = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    scene, cams = scenes.config1()
+    if rank > 0:  # weak scaling: each rank renders its own pose of the same scene
+        cams = [scenes.pose_camera(1752, 1168, 180.0, seed=1000 + 1 + rank)]
+    gs = scene_to_device(scene, dev)
+    n = scene["means"].shape[0]
+    P = 1752 * 1168
+    dL = torch.as_tensor(scenes.upstream_grad((3 * P,), 1e-2, seed=7 + rank)).to(dev)
+    r = FisheyeRenderer(dev, capacity=20_000_000)
+    fr = r.forward(gs, cams, check=True)  # sizes the key buffers
+    m = int(fr.n_intersections.item())
+    cam_c = fr.cams
+    g = gaussians_of(gs)
+    grads = {k: torch.empty_like(gs[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
+    ws = r._bufs["ws"]
+    cap = r.capacity
+    wsb = fgs.fgs_workspace_size(n, cam_c, cap)
+    tiles = fgs.fgs_total_tiles(cam_c)
+    passes = (32 + max(1, math.ceil(math.log2(tiles))) + 7) // 8
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def stages(ev, with_bwd=True):
+        ev[0].record(stream)
+        fgs.fgs_preprocess(g, cam_c, fr.records, fr.tiles_touched)
+        ev[1].record(stream)
+        fgs.fgs_bin_sort(fr.records, fr.tiles_touched, n, cam_c, fr.keys, fr.vals, cap,
+                         fr.tile_ranges, fr.n_intersections, ws, wsb)
+        ev[2].record(stream)
+        fgs.fgs_rasterize(fr.records, fr.vals, fr.tile_ranges, cam_c, None, fr.images,
+                          fr.final_T, fr.n_processed, ws, wsb)
+        ev[3].record(stream)
+        if with_bwd:
+            fgs.fgs_backward_raster(fr.records, fr.vals, fr.tile_ranges, n, cam_c, None,
+                                    fr.final_T, fr.n_processed, dL, ws, wsb)
+            ev[4].record(stream)
+            fgs.fgs_backward_preprocess(g, cam_c, fr.records, fr.tiles_touched, grads["means"],
+                                        grads["scales"], grads["quats"], grads["opacities"],
+                                        grads["sh"], ws, wsb)
+            ev[5].record(stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # instrumented pass (untimed): algorithmic work of the rasterizer
+    fgs.fgs_set_instrumentation(True)
+    stages([torch.cuda.Event(enable_timing=True) for _ in range(6)])
+    counters = fgs.fgs_read_counters(ws)
+    fgs.fgs_set_instrumentation(False)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        stages([torch.cuda.Event(enable_timing=True) for _ in range(6)])
+    st = fgs.fgs_read_status(ws)
+    if st != fgs.FGS_OK:
+        raise fgs.FgsError(st, "warm-up")
+
+    vis_dev = os.environ.get("CUDA_VISIBLE_DEVICES")
+    smi_id = vis_dev.split(",")[local].strip() if vis_dev else str(local)
+    sampler = ClockSampler(smi_id)
+    barrier()
+    sampler.start()
+    time.sleep(0.3)
+    evs = []
+    barrier()
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        stages(ev)
+        evs.append(ev)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    stage_ms = np.zeros(5)
+    step_ms = []
+    for ev in evs:
+        d = [ev[i].elapsed_time(ev[i + 1]) for i in range(5)]
+        stage_ms += np.array(d)
+        step_ms.append(sum(d))
+    stage_ms /= args.steps
+    total_s = sum(step_ms) / 1e3
+
+    # forward only
+    fevs = []
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        stages(ev, with_bwd=False)
+        fevs.append(ev)
+    barrier()
+    fwd_s = sum(ev[0].elapsed_time(ev[3]) for ev in fevs) / 1e3
+    clocks = sampler.stop()
+    st = fgs.fgs_read_status(ws)
+    if st != fgs.FGS_OK:
+        raise fgs.FgsError(st, "timed run")
+
+    # end to end through host buffers: pinned inputs -> device, the five calls, image and
+    # gradients -> pinned host memory, every step
+    host_in = {k: gs[k].cpu().pin_memory() for k in ("means", "scales", "quats", "opacities", "sh")}
+    host_dL = dL.cpu().pin_memory()
+    host_img = torch.empty(3 * P, dtype=torch.float32).pin_memory()
+    host_g = {k: torch.empty_like(host_in[k]).pin_memory() for k in host_in}
+    h2d = sum(t.numel() * 4 for t in host_in.values()) + host_dL.numel() * 4
+    d2h = host_img.numel() * 4 + sum(t.numel() * 4 for t in host_g.values())
+    eevs = []
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in host_in:
+            gs[k].copy_(host_in[k], non_blocking=True)
+        dL.copy_(host_dL, non_blocking=True)
+        stages([torch.cuda.Event(enable_timing=True) for _ in range(6)])
+        host_img.copy_(fr.images[:3 * P], non_blocking=True)
+        for k in host_g:
+            host_g[k].copy_(grads[k], non_blocking=True)
+        e1.record(stream)
+        eevs.append((e0, e1))
+    barrier()
+    e2e_s = sum(a.elapsed_time(b) for a, b in eevs) / 1e3
+
+    def gmax(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    total_s, fwd_s, e2e_s = gmax(total_s), gmax(fwd_s), gmax(e2e_s)
+    value = world * args.steps / total_s
+
+    # roofline of the dominant kernel
+    peaks = _peaks()
+    names = ["preprocess_fwd", "bin_sort", "raster_fwd", "raster_bwd", "preprocess_bwd"]
+    dom = int(np.argmax(stage_ms))
+    fp32_peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12  # TFLOP/s
+    kern = {}
+    fwd_flops = counters[0] * FLOPS_FWD_EVAL + counters[1] * FLOPS_FWD_BLEND
+    bwd_flops = counters[2] * FLOPS_BWD_EVAL + counters[3] * FLOPS_BWD_CONTRIB
+    kern["raster_fwd"] = dict(bound="alu", achieved=fwd_flops / (stage_ms[2] * 1e-3) / 1e12,
+                              peak=fp32_peak, unit="TFLOP/s")
+    kern["raster_bwd"] = dict(bound="alu", achieved=bwd_flops / (stage_ms[3] * 1e-3) / 1e12,
+                              peak=fp32_peak, unit="TFLOP/s")
+    sort_bytes = m * (12 + 12 + passes * 24) + n * 4
+    kern["bin_sort"] = dict(bound="hbm", achieved=sort_bytes / (stage_ms[1] * 1e-3) / 1e9,
+                            peak=peaks["hbm_gbs"], unit="GB/s")
+    vis = int((fr.tiles_touched > 0).sum().item())
+    pre_bytes = n * 16 + vis * (12 + 16 + 4 * 48 + 48) + n * 4
+    kern["preprocess_fwd"] = dict(bound="hbm", achieved=pre_bytes / (stage_ms[0] * 1e-3) / 1e9,
+                                  peak=peaks["hbm_gbs"], unit="GB/s")
+    bwdp_bytes = n * 4 + vis * (12 + 12 + 16 + 4 * 48 + 48 + 36) + n * 59 * 4
+    kern["preprocess_bwd"] = dict(bound="hbm", achieved=bwdp_bytes / (stage_ms[4] * 1e-3) / 1e9,
+                                  peak=peaks["hbm_gbs"], unit="GB/s")
+    for k in kern:
+        kern[k]["frac"] = kern[k]["achieved"] / kern[k]["peak"]
+    roof = dict(kern[names[dom]])
+    roof["kernel"] = names[dom]
+    roof["traffic"] = _traffic({"raster_bwd": "raster_bwd_kernel",
+                                "raster_fwd": "raster_fwd_kernel",
+                                "bin_sort": "onesweep_kernel",
+                                "preprocess_fwd": "preprocess_fwd_kernel",
+                                "preprocess_bwd": "preprocess_bwd_kernel"}[names[dom]])
+    roof["peak_source"] = ("FP32: 152 SMs x 128 lanes x 2 x max SM clock "
+                           f"({peaks['sm_max_mhz']:.0f} MHz, {peaks['source']})"
+                           if roof["bound"] == "alu" else f"HBM copy, {peaks['source']}")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, secs, desc, thr = _oracle_sample_rate(scene, cams[0], args.cpu_seconds)
+        cpu = dict(value=v, unit="views/s", cores=thr, kind="oracle", sample=desc,
+                   seconds=round(secs, 2))
+
+    launches_per_step = 1 + (1 + passes + 1) + 1 + 1 + 1
+    line = dict(
+        metric=METRIC, value=value, unit="views/s", n_gpus=world, steps=args.steps,
+        warmup=args.warmup, ms_per_step=1e3 * total_s / args.steps, higher_is_better=True,
+        scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+        config=dict(workload=WORKLOAD, n_gaussians=n, width=1752, height=1168, fov_deg=180.0,
+                    sh_degree=3, l2="flushed between steps (256 MiB write, untimed)",
+                    parallelism=f"views x{world} (replicas)"),
+        fwd_views_per_s=world * args.steps / fwd_s,
+        mpix_per_s_fwd_bwd=value * P / 1e6,
+        stage_ms=dict(zip(names, [round(float(x), 4) for x in stage_ms])),
+        intersections=m, visible=vis, pair_counters=counters,
+        roofline=roof, kernels=kern,
+        cpu_baseline=cpu,
+        e2e=dict(value=world * args.steps / e2e_s, unit="views/s", h2d_bytes_per_step=h2d,
+                 d2h_bytes_per_step=d2h),
+        gpu_launches=launches_per_step * args.steps,
+        clocks=clocks, wall_s=round(t_wall, 3))
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fgs", choices=["fgs", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

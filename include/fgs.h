@@ -1,0 +1,195 @@
+/*
+ * fgs.h - C ABI of the GB300 (sm_103a) fisheye Gaussian-splatting hot path.
+ *
+ * The method is Fisheye-GS (arXiv 2409.04751): 3D Gaussian splatting in which the pinhole
+ * projection is replaced by the equidistant fisheye model r_d = f * theta (Sec. 3.2). The
+ * path is the renderer's four stages (Sec. 4.1: preprocess, tile binning, sort, rasterize)
+ * and their backward (Sec. 4.2, 4.3). Every stage runs in hand-written CUDA kernels.
+ *
+ * Conventions shared by every call:
+ *  - All array pointers are DEVICE pointers unless stated otherwise; the caller allocates and
+ *    owns every buffer (this library never allocates or frees device memory). Camera arrays
+ *    and the background colour are HOST pointers, read during the call.
+ *  - Every call is asynchronous and ordered on `stream` (a cudaStream_t; NULL = the legacy
+ *    default stream). No call synchronises the host, so a sequence of calls can be captured
+ *    in a CUDA graph.
+ *  - A call returns FGS_ERR_INVALID_ARG before launching anything if an argument is wrong
+ *    (null pointer with a non-zero size, negative size, sh_degree outside 0..3, no views or
+ *    more than FGS_MAX_VIEWS, a non-positive image size, a workspace that is too small, a
+ *    record buffer not 16-byte aligned). FGS_ERR_CUDA reports a failed launch.
+ *  - Errors found on the device (more intersections than `capacity`; a bounded wait that ran
+ *    out) are written to a status word in the workspace; fgs_bin_sort resets it and
+ *    fgs_read_status reads it. Outputs are then undefined but every access stays in bounds.
+ *  - Gradients are overwritten, not accumulated.
+ *  - Calls on distinct workspaces are independent; calls sharing a workspace must not
+ *    overlap in time (they share its counters).
+ */
+#ifndef FGS_H
+#define FGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *fgs_stream; /* == cudaStream_t */
+
+typedef enum {
+  FGS_OK = 0,
+  FGS_ERR_INVALID_ARG = 1,
+  FGS_ERR_CAPACITY = 2, /* more (Gaussian, tile) intersections than the key buffers hold */
+  FGS_ERR_TIMEOUT = 3,  /* a bounded device-side wait gave up */
+  FGS_ERR_CUDA = 4
+} fgs_status;
+
+#define FGS_TILE 16        /* tiles are 16 x 16 pixels (Sec. 3.1 "Rendering") */
+#define FGS_MAX_VIEWS 128  /* views per call */
+
+/* An equidistant fisheye camera (Sec. 3.1 "Transformation", Sec. 3.2):
+ *   mu_c = W mu + b (W row-major, world -> camera; camera x right, y down, z forward),
+ *   theta = atan2(|(x_c, y_c)|, z_c), x_p = cx + fx theta x_c / l_z, y_p = cy + fy theta y_c / l_z.
+ * Pixel (i, j) is sampled at (i + 0.5, j + 0.5). */
+typedef struct {
+  float W[9];
+  float b[3];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+} fgs_camera;
+
+/* The Gaussian set (Sec. 3.1 "Definition"): device pointers, FP32, contiguous.
+ *   means [n,3]; scales [n,3] (activated, > 0; S = diag(scales)); quats [n,4] (w, x, y, z,
+ *   any non-zero norm: normalised inside); opacities [n] (activated, in (0, 1));
+ *   sh [n, (sh_degree+1)^2, 3] real spherical-harmonic coefficients (Condon-Shortley phase,
+ *   order l = 0..3, m = -l..l), colour = max(0, sum_k sh_k Y_k(dir) + 0.5). */
+typedef struct {
+  const float *means;
+  const float *scales;
+  const float *quats;
+  const float *opacities;
+  const float *sh;
+  int64_t n;
+  int32_t sh_degree;
+} fgs_gaussians;
+
+/* Per-(view, Gaussian) record written by fgs_preprocess, 48 bytes, 16-byte aligned.
+ * Record r = v * n + i belongs to Gaussian i in view v.
+ *   xy      projected mean mu_p (pixels)
+ *   conic   (A, B, C) = inverse of Sigma_p + 0.3 I; alpha(p) = min(0.99, opacity *
+ *           exp(-0.5 (A dx^2 + 2 B dx dy + C dy^2))), d = p - xy
+ *   depth   |mu_c| (distance along the ray; the sort key's low 32 bits are its FP32 bits)
+ *   rect    x0, y0, x1, y1: inclusive tile rectangle in the view's tile grid; it contains
+ *           every pixel centre where alpha >= 1/255. Empty (tiles_touched = 0) if the
+ *           Gaussian is culled: |mu_c| <= 0.2, theta >= pi - 0.05, opacity < 1/255, or the
+ *           footprint misses the image. Other fields are unspecified then. */
+typedef struct {
+  float xy[2];
+  float conic[3];
+  float opacity;
+  float rgb[3];
+  float depth;
+  uint16_t rect[4];
+} fgs_record;
+
+/* Bytes of workspace needed by fgs_bin_sort, fgs_rasterize and fgs_backward for this set of
+ * views, n Gaussians and a key capacity (0 < capacity < 2^32). */
+fgs_status fgs_workspace_size(int64_t n, const fgs_camera *cams, int n_views, int64_t capacity,
+                              size_t *bytes);
+
+/* Number of 16x16 tiles over all views (global tile ids are view-major, row-major inside a
+ * view) and number of pixels over all views. Host-only helpers. */
+int64_t fgs_total_tiles(const fgs_camera *cams, int n_views);
+int64_t fgs_total_pixels(const fgs_camera *cams, int n_views);
+
+/* Stage 1, per-Gaussian preprocess (Sec. 4.1 preprocessCUDA, modified by Sec. 4.2 / 4.3):
+ * view transform, equidistant projection of the mean, fisheye Jacobian J, covariance
+ * Sigma = R S S^T R^T, Sigma_p = (J W) Sigma (J W)^T + 0.3 I, conic, colour from SH along
+ * (mu - camera centre), depth and tile rectangle.
+ * Outputs: records [n_views * n] (fgs_record), tiles_touched [n_views * n] (rect area, 0 if
+ * culled). */
+fgs_status fgs_preprocess(const fgs_gaussians *g, const fgs_camera *cams, int n_views,
+                          fgs_record *records, uint32_t *tiles_touched, fgs_stream stream);
+
+/* Stages 2-4, tile binning + sort (Sec. 3.1 "Rendering", Sec. 4.1 duplicateWithKeys and
+ * radixSort): for every record r with a non-empty rect and every tile t of the rect,
+ * one pair (key = t << 32 | bits(depth_r), value = r), t the global tile id; the pairs are
+ * sorted by key, equal keys in increasing r (a stable sort of the emission in record order).
+ * Inputs: records, tiles_touched [n_views * n] (as written by fgs_preprocess, or any records
+ * whose rect and depth fields are set and tiles_touched = rect area).
+ * Outputs: keys [capacity] u64, vals [capacity] u32 (first *n_intersections entries valid),
+ * tile_ranges [fgs_total_tiles * 2] u32 = [start, end) of each global tile,
+ * n_intersections (device int64, the true count even when it exceeds capacity).
+ * Resets the workspace status word; sets FGS_ERR_CAPACITY there if the count exceeds
+ * capacity. */
+fgs_status fgs_bin_sort(const fgs_record *records, const uint32_t *tiles_touched, int64_t n,
+                        const fgs_camera *cams, int n_views, uint64_t *keys, uint32_t *vals,
+                        int64_t capacity, uint32_t *tile_ranges, int64_t *n_intersections,
+                        void *workspace, size_t workspace_bytes, fgs_stream stream);
+
+/* Stage 5, rasterize (Sec. 3.1 "Rendering", Sec. 4.1 renderCUDA): per pixel, front to back
+ * over its tile's sorted list: skip alpha < 1/255, stop before a Gaussian whose blend would
+ * take T below 1e-4, C += rgb alpha T, T *= 1 - alpha; finally C += T bg.
+ * bg: HOST float[3] (NULL = black).
+ * Outputs: images (planar [3][H][W] per view, views packed in order), final_T [pixels],
+ * n_processed [pixels] u32 = 1 + position in the tile list of the last blended Gaussian
+ * (0 if none); the backward reads final_T and n_processed. */
+fgs_status fgs_rasterize(const fgs_record *records, const uint32_t *vals,
+                         const uint32_t *tile_ranges, const fgs_camera *cams, int n_views,
+                         const float *bg, float *images, float *final_T,
+                         uint32_t *n_processed, void *workspace, size_t workspace_bytes,
+                         fgs_stream stream);
+
+/* Stages 5-1 backward (Sec. 4.2 / 4.3 backward and the blend derivative): gradients of
+ * L = <dL_dimages, images> with respect to the fgs_gaussians inputs, summed over views.
+ * The blend state per pixel is recomputed from the records, final_T and n_processed;
+ * J and dJ/dmu_c are recomputed from the inputs; the gradient of mu is the sum of its
+ * mean-projection and covariance paths.
+ * Outputs (overwritten): d_means [n,3], d_scales [n,3], d_quats [n,4], d_opacities [n],
+ * d_sh [n,(d+1)^2,3]. bg: HOST float[3] or NULL (as given to fgs_rasterize). */
+fgs_status fgs_backward(const fgs_gaussians *g, const fgs_camera *cams, int n_views,
+                        const fgs_record *records, const uint32_t *tiles_touched,
+                        const uint32_t *vals, const uint32_t *tile_ranges, const float *bg,
+                        const float *final_T, const uint32_t *n_processed,
+                        const float *dL_dimages, float *d_means, float *d_scales,
+                        float *d_quats, float *d_opacities, float *d_sh, void *workspace,
+                        size_t workspace_bytes, fgs_stream stream);
+
+/* The two halves of fgs_backward, for callers that time or reuse them separately:
+ * fgs_backward_raster replays the blend and accumulates per-record screen-space gradients
+ * (dL/d xy, dL/d conic, dL/d opacity, dL/d rgb) into the workspace; fgs_backward_preprocess
+ * pulls them back to the Gaussian inputs (overwriting the d_* outputs). Called in this order
+ * on one workspace they equal fgs_backward. n = Gaussians per view. */
+fgs_status fgs_backward_raster(const fgs_record *records, const uint32_t *vals,
+                               const uint32_t *tile_ranges, int64_t n, const fgs_camera *cams,
+                               int n_views, const float *bg, const float *final_T,
+                               const uint32_t *n_processed, const float *dL_dimages,
+                               void *workspace, size_t workspace_bytes, fgs_stream stream);
+fgs_status fgs_backward_preprocess(const fgs_gaussians *g, const fgs_camera *cams, int n_views,
+                                   const fgs_record *records, const uint32_t *tiles_touched,
+                                   float *d_means, float *d_scales, float *d_quats,
+                                   float *d_opacities, float *d_sh, void *workspace,
+                                   size_t workspace_bytes, fgs_stream stream);
+
+/* Synchronises `stream` and returns the device status word of `workspace` in *status
+ * (an fgs_status value). */
+fgs_status fgs_read_status(const void *workspace, fgs_stream stream, int *status);
+
+/* Measurement hooks (not part of the rendering path). While instrumentation is on (process
+ * wide), fgs_rasterize and fgs_backward launch variants of their kernels that also count
+ * work into the workspace: counters[0] = forward (pixel, Gaussian) evaluations, [1] = forward
+ * blends, [2] = backward evaluations, [3] = backward contributions. The counters are reset by
+ * fgs_bin_sort. Instrumented launches are slower; they exist to size the algorithmic work of
+ * a timed (uninstrumented) run. fgs_read_counters synchronises `stream` and copies the four
+ * counters to host memory. */
+void fgs_set_instrumentation(int on);
+fgs_status fgs_read_counters(const void *workspace, fgs_stream stream, uint64_t *counters);
+
+/* Static description of a status code. */
+const char *fgs_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FGS_H */

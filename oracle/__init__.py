@@ -46,7 +46,7 @@ def _lib_handle():
         lib = ctypes.CDLL(path)
         lib.orc_project.argtypes = [ctypes.c_int64, _D, _D, _D, _D, _D, ctypes.c_int, _D, _D]
         lib.orc_render.argtypes = [ctypes.c_int64, _D, ctypes.c_int64, _I32, _D, ctypes.c_int,
-                                   ctypes.c_double, _D, _D, _I64, _I32, _D]
+                                   ctypes.c_double, ctypes.c_double, _D, _D, _I64, _I32, _D]
         lib.orc_backward.argtypes = [ctypes.c_int64, _D, _D, _D, _D, _D, _D, ctypes.c_int, _D,
                                      ctypes.c_int64, _I32, _D, _D, ctypes.c_int, _D, _D, _D, _D,
                                      _D, _D]
@@ -106,9 +106,10 @@ def all_pixels(cam) -> np.ndarray:
     return np.ascontiguousarray(np.stack([ii.reshape(-1), jj.reshape(-1)], 1))
 
 
-def render(G, pixels, bg=(0.0, 0.0, 0.0), use_bbox=True, band=2e-3):
+def render(G, pixels, bg=(0.0, 0.0, 0.0), use_bbox=True, band=2e-3, impact_min=0.0):
     """Render the given pixels [(col, row)]. band: log-alpha half width of the decision band
-    whose Gaussians are kept only to measure the alpha-threshold margin."""
+    whose Gaussians are kept only to measure the alpha-threshold margin. impact_min: decisions
+    whose flip could not move the colour by that much are left out of the margins."""
     lib = _lib_handle()
     G = _f64(G)
     pix = np.ascontiguousarray(pixels, dtype=np.int32).reshape(-1, 2)
@@ -120,14 +121,14 @@ def render(G, pixels, bg=(0.0, 0.0, 0.0), use_bbox=True, band=2e-3):
     nc = np.zeros(npx, np.int32)
     marg = np.zeros((npx, 3))
     lib.orc_render(G.shape[0], _p(G), npx, _p(pix, _I32), _p(bgv), int(use_bbox), float(band),
-                   _p(color), _p(T), _p(last, _I64), _p(nc, _I32), _p(marg))
+                   float(impact_min), _p(color), _p(T), _p(last, _I64), _p(nc, _I32), _p(marg))
     return dict(color=color, T_final=T, last_g=last, n_contrib=nc, margins=marg)
 
 
-def render_image(G, cam, bg=(0.0, 0.0, 0.0), use_bbox=True, band=2e-3):
+def render_image(G, cam, bg=(0.0, 0.0, 0.0), use_bbox=True, band=2e-3, impact_min=0.0):
     """Whole image: color [3, H, W] (planar), T_final [H, W], last_g, n_contrib, margins."""
     w, h = int(cam["width"]), int(cam["height"])
-    r = render(G, all_pixels(cam), bg, use_bbox, band)
+    r = render(G, all_pixels(cam), bg, use_bbox, band, impact_min)
     return dict(color=r["color"].reshape(h, w, 3).transpose(2, 0, 1).copy(),
                 T_final=r["T_final"].reshape(h, w), last_g=r["last_g"].reshape(h, w),
                 n_contrib=r["n_contrib"].reshape(h, w), margins=r["margins"].reshape(h, w, 3))

@@ -393,10 +393,16 @@ static int64_t orc_collect(int64_t n, const double *G, double px, double py, int
 /* Blend one pixel's sorted candidates. Returns the number blended; fills C, T_final, last
  * and the decision margins (relative distance of every alpha / T test that decided the
  * result from its threshold, and the relative depth gap of consecutive blended entries). */
+/* Margins: each decision's relative distance from its threshold (log ratio for the alpha
+ * and T tests, relative gap for the depth order), counted only when flipping that decision
+ * could move the pixel's colour by at least impact_min: an alpha-threshold flip at
+ * transmittance T changes the colour by about 2 T / 255 (its own term plus the dimming of
+ * everything behind), a stop flip by about alpha T + 1e-4, a swap of two consecutive
+ * Gaussians by about alpha_1 alpha_2 T. */
 static int orc_blend(const double *G, const orc_cand *cand, int64_t m, const double *bg,
-                     double *C, double *Tout, int64_t *last, double *m_alpha, double *m_T,
-                     double *m_depth, double *Tbefore, int64_t *pos) {
-  double T = 1.0, prev_depth = -1.0;
+                     double impact_min, double *C, double *Tout, int64_t *last, double *m_alpha,
+                     double *m_T, double *m_depth, double *Tbefore, int64_t *pos) {
+  double T = 1.0, prev_depth = -1.0, prev_alpha = 0.0;
   int nb = 0;
   *m_alpha = *m_T = *m_depth = INFINITY;
   C[0] = C[1] = C[2] = 0;
@@ -404,16 +410,17 @@ static int orc_blend(const double *G, const orc_cand *cand, int64_t m, const dou
   for (int64_t k = 0; k < m; ++k) {
     const orc_cand *c = cand + k;
     double ma = fabs(log(c->araw / ORC_ALPHA_MIN));
-    if (ma < *m_alpha) *m_alpha = ma;
+    if (ma < *m_alpha && 2.0 * T / 255.0 >= impact_min) *m_alpha = ma;
     if (!c->contributes) continue;
     double Tn = T * (1.0 - c->alpha);
     double mt = fabs(log(Tn / ORC_T_MIN));
-    if (mt < *m_T) *m_T = mt;
+    if (mt < *m_T && c->alpha * T + 1e-4 >= impact_min) *m_T = mt;
     if (prev_depth >= 0) {
       double md = (c->depth - prev_depth) / c->depth;
-      if (md < *m_depth) *m_depth = md;
+      if (md < *m_depth && prev_alpha * c->alpha * T >= impact_min) *m_depth = md;
     }
     prev_depth = c->depth;
+    prev_alpha = c->alpha;
     if (Tn < ORC_T_MIN) break;
     const double *o = G + c->idx * ORC_NF;
     for (int ch = 0; ch < 3; ++ch) C[ch] += o[F_RGB + ch] * c->alpha * T;
@@ -430,10 +437,10 @@ static int orc_blend(const double *G, const orc_cand *cand, int64_t m, const dou
 /* Render pixels pix[npix][2] = (column i, row j), sampled at (i + 0.5, j + 0.5).
  * Outputs: color [npix,3], T_final [npix], last_g [npix] (index of the last blended
  * Gaussian, -1 if none), n_contrib [npix], margins [npix,3] (alpha, T, depth; log-ratio /
- * relative units; +inf when no decision of that kind was taken). */
+ * relative units; +inf when no decision of that kind, with impact >= impact_min, was taken). */
 void orc_render(int64_t n, const double *G, int64_t npix, const int32_t *pix, const double *bg,
-                int use_bbox, double band, double *color, double *T_final, int64_t *last_g,
-                int32_t *n_contrib, double *margins) {
+                int use_bbox, double band, double impact_min, double *color, double *T_final,
+                int64_t *last_g, int32_t *n_contrib, double *margins) {
 #pragma omp parallel
   {
     orc_cand *buf = NULL;
@@ -443,7 +450,8 @@ void orc_render(int64_t n, const double *G, int64_t npix, const int32_t *pix, co
       double px = pix[2 * p] + 0.5, py = pix[2 * p + 1] + 0.5;
       int64_t m = orc_collect(n, G, px, py, use_bbox, band, &buf, &cap);
       double ma, mt, md;
-      n_contrib[p] = orc_blend(G, buf, m, bg, color + 3 * p, T_final + p, last_g + p, &ma, &mt, &md, NULL, NULL);
+      n_contrib[p] = orc_blend(G, buf, m, bg, impact_min, color + 3 * p, T_final + p, last_g + p,
+                               &ma, &mt, &md, NULL, NULL);
       margins[3 * p] = ma; margins[3 * p + 1] = mt; margins[3 * p + 2] = md;
     }
     free(buf);
@@ -484,7 +492,7 @@ void orc_backward(int64_t n, const double *G, const double *means, const double 
       }
       double C[3], Tf, ma, mt, md;
       int64_t last;
-      int nb = orc_blend(G, buf, m, bg, C, &Tf, &last, &ma, &mt, &md, Tb, pos);
+      int nb = orc_blend(G, buf, m, bg, 0.0, C, &Tf, &last, &ma, &mt, &md, Tb, pos);
       /* S = colour behind blended entry k: sum_{j>k} rgb_j a_j T_j + T_final bg */
       double S[3] = {Tf * bg[0], Tf * bg[1], Tf * bg[2]};
       for (int k = nb - 1; k >= 0; --k) {

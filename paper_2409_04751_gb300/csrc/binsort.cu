@@ -1,0 +1,385 @@
+// binsort.cu - tile binning and key sort (Sec. 3.1 "Rendering"; Sec. 4.1 duplicateWithKeys and
+// radixSort), sm_103a.
+//
+//  1. emit_kernel: single-pass scan of tiles_touched with decoupled look-back (partitions of
+//     1024 records claimed in order through an atomic counter), then CTA-cooperative key
+//     emission: the CTA's (record, tile) pairs are spread evenly over its threads by a binary
+//     search of the record offsets held in shared memory, so a Gaussian covering thousands of
+//     tiles does not stall one thread, and the writes are coalesced. The same pass counts the
+//     8-bit digit histograms of every radix pass (warp-aggregated shared atomics), so the sort
+//     needs no separate histogram read of the keys.
+//  2. onesweep_kernel (one launch per 8-bit digit): Adinets & Merrill's single-pass LSD radix
+//     sort: each partition of 4096 keys is ranked in shared memory (warp multi-split with
+//     match_any, stable), publishes its per-digit counts, resolves its global digit offsets by
+//     decoupled look-back over earlier partitions (bounded waits), and scatters through shared
+//     memory so that runs of equal digits are written contiguously.
+//  3. ranges_kernel: [start, end) of every tile in the sorted keys.
+// The number of valid pairs is read on the device, so nothing here needs a host sync.
+#include "fgs_internal.cuh"
+
+namespace fgs {
+
+namespace {
+
+constexpr uint64_t LB_AGG = 1ull << 62;
+constexpr uint64_t LB_INC = 2ull << 62;
+constexpr uint64_t LB_VAL = (1ull << 62) - 1;
+
+// exclusive scan over a block of 256 threads; returns the block total in *total
+__device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *s_warp,
+                                                        uint32_t *total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t t = lane < 8 ? s_warp[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < 8) s_warp[lane] = t;  // inclusive warp totals
+  }
+  __syncthreads();
+  const uint32_t before = w > 0 ? s_warp[w - 1] : 0u;
+  *total = s_warp[7];
+  __syncthreads();
+  return before + x - v;
+}
+
+// Decoupled look-back: sums the values of partitions part-1, part-2, ... until an inclusive
+// entry is found. Bounded: gives up (FGS_ERR_TIMEOUT) after SPIN_LIMIT empty polls.
+__device__ __forceinline__ uint64_t look_back(const uint64_t *lb, int64_t part, int64_t stride,
+                                              uint32_t *status) {
+  uint64_t prefix = 0;
+  uint32_t spins = 0;
+  int64_t j = part - 1;
+  while (j >= 0) {
+    const uint64_t st = ld_volatile_u64(lb + j * stride);
+    const uint64_t flag = st & ~LB_VAL;
+    if (flag == 0) {
+      if (++spins > SPIN_LIMIT) {
+        set_status(status, ST_TIMEOUT);
+        break;
+      }
+      continue;
+    }
+    prefix += st & LB_VAL;
+    if (flag == LB_INC) break;
+    --j;
+  }
+  return prefix;
+}
+
+__global__ void __launch_bounds__(EMIT_THREADS)
+    emit_kernel(const fgs_record *__restrict__ rec, const uint32_t *__restrict__ tt, int64_t R,
+                int64_t n_per_view, Views vs, uint64_t *__restrict__ keys,
+                uint32_t *__restrict__ vals, int64_t capacity, int64_t *n_int, uint64_t *lb,
+                uint32_t *part_counter, uint32_t *hist, int passes, uint32_t *status) {
+  __shared__ uint32_t s_off[EMIT_PART + 1];
+  __shared__ uint2 s_rect[EMIT_PART];
+  __shared__ uint32_t s_depth[EMIT_PART];
+  __shared__ uint32_t s_hist[SORT_MAX_PASSES * 256];
+  __shared__ uint32_t s_warp[8];
+  __shared__ uint64_t s_prefix;
+  __shared__ uint32_t s_part;
+  __shared__ int s_overflow;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_part = atomicAdd(part_counter, 1u);
+    s_overflow = 0;
+  }
+  for (int e = tid; e < passes * 256; e += EMIT_THREADS) s_hist[e] = 0u;
+  __syncthreads();
+  const int64_t part = s_part;
+  const int64_t base = part * EMIT_PART;
+
+  uint32_t c[EMIT_ITEMS];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < EMIT_ITEMS; ++k) {
+    const int64_t r = base + tid * EMIT_ITEMS + k;
+    c[k] = r < R ? tt[r] : 0u;
+    sum += c[k];
+  }
+  uint32_t cta_total;
+  uint32_t off = block_excl_scan_256(sum, s_warp, &cta_total);
+  if (tid == 0) {
+    uint64_t prefix = 0;
+    if (part == 0) {
+      st_volatile_u64(lb, LB_INC | (uint64_t)cta_total);
+    } else {
+      st_volatile_u64(lb + part, LB_AGG | (uint64_t)cta_total);
+      prefix = look_back(lb, part, 1, status);
+      st_volatile_u64(lb + part, LB_INC | (prefix + cta_total));
+    }
+    s_prefix = prefix;
+    if (base + EMIT_PART >= R) *n_int = (int64_t)(prefix + cta_total);
+  }
+#pragma unroll
+  for (int k = 0; k < EMIT_ITEMS; ++k) {
+    const int loc = tid * EMIT_ITEMS + k;
+    s_off[loc] = off;
+    if (c[k] > 0u) {
+      const uint4 w2 = __ldg(reinterpret_cast<const uint4 *>(rec + base + loc) + 2);
+      s_rect[loc] = make_uint2(w2.z, w2.w);
+      s_depth[loc] = w2.y;
+    }
+    off += c[k];
+  }
+  if (tid == 0) s_off[EMIT_PART] = cta_total;
+  __syncthreads();
+  const uint64_t prefix = s_prefix;
+
+  bool overflow = false;
+  for (uint32_t jb = 0; jb < cta_total; jb += EMIT_THREADS) {
+    const uint32_t j = jb + tid;
+    bool valid = j < cta_total;
+    uint64_t key = 0;
+    if (valid) {
+      int lo = 0, hi = EMIT_PART;  // s_off[lo] <= j < s_off[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_off[mid] <= j) lo = mid; else hi = mid;
+      }
+      const uint32_t local = j - s_off[lo];
+      const uint2 rc = s_rect[lo];
+      const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
+      const uint32_t w = x1 - x0 + 1u;
+      const uint32_t dy = local / w;
+      const uint32_t tx = x0 + (local - dy * w), ty = y0 + dy;
+      const int64_t r = base + lo;
+      const int v = (int)(r / n_per_view);
+      const uint64_t tile = (uint64_t)(vs.v[v].tile_offset + (int64_t)ty * vs.v[v].tiles_x + tx);
+      key = (tile << 32) | (uint64_t)s_depth[lo];
+      const uint64_t gpos = prefix + j;
+      if (gpos < (uint64_t)capacity) {
+        keys[gpos] = key;
+        vals[gpos] = (uint32_t)r;
+      } else {
+        overflow = true;
+        valid = false;
+      }
+    }
+    for (int p = 0; p < passes; ++p) {
+      const uint32_t d = valid ? (uint32_t)(key >> (8 * p)) & 255u : 0x100u + (threadIdx.x & 31);
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      if (valid && (peers & lanemask_lt()) == 0u) atomicAdd(&s_hist[p * 256 + d], __popc(peers));
+    }
+  }
+  if (overflow) s_overflow = 1;
+  __syncthreads();
+  if (tid == 0 && s_overflow) set_status(status, ST_CAPACITY);
+  for (int e = tid; e < passes * 256; e += EMIT_THREADS)
+    if (s_hist[e]) atomicAdd(hist + e, s_hist[e]);
+}
+
+struct SortSmem {
+  uint64_t keys[SORT_PART];
+  uint32_t vals[SORT_PART];
+  uint32_t wcnt[SORT_THREADS / 32][256];  // per-warp digit counts -> per-warp offsets
+  uint32_t local_start[256];               // digit start inside the partition
+  uint32_t global_base[256];               // digit base in the output for this partition
+  uint32_t hist_excl[256];                 // exclusive scan of this pass's global histogram
+  uint32_t warp_tmp[8];
+  uint32_t part;
+};
+
+__global__ void __launch_bounds__(SORT_THREADS)
+    onesweep_kernel(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                    uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                    const int64_t *n_int, int64_t capacity, int shift, const uint32_t *hist,
+                    uint64_t *lb, uint64_t *lb_next, uint32_t *part_counter, uint32_t *status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SortSmem &S = *reinterpret_cast<SortSmem *>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t n = min(*n_int, capacity);
+  const int64_t nparts = (n + SORT_PART - 1) / SORT_PART;
+
+  // clear the look-back entries the next pass will use (the previous pass is complete)
+  for (int64_t e = (int64_t)blockIdx.x * SORT_THREADS + tid; e < nparts * 256;
+       e += (int64_t)gridDim.x * SORT_THREADS)
+    lb_next[e] = 0ull;
+
+  uint32_t tot;
+  {
+    const uint32_t hx = block_excl_scan_256(hist[tid], S.warp_tmp, &tot);
+    S.hist_excl[tid] = hx;
+  }
+  const uint32_t lt = lanemask_lt();
+
+  for (;;) {
+    if (tid == 0) S.part = atomicAdd(part_counter, 1u);
+    __syncthreads();
+    const int64_t part = S.part;
+    if (part >= nparts) break;
+    const int64_t base = part * SORT_PART;
+
+    // load (warp-striped, order within a warp = k then lane = input order)
+    uint64_t key[SORT_ITEMS];
+    uint32_t val[SORT_ITEMS];
+    uint32_t rank[SORT_ITEMS];
+#pragma unroll
+    for (int k = 0; k < SORT_ITEMS; ++k) {
+      const int64_t idx = base + (int64_t)w * 32 * SORT_ITEMS + k * 32 + lane;
+      if (idx < n) {
+        key[k] = kin[idx];
+        val[k] = vin[idx];
+      } else {
+        key[k] = 0ull;
+        val[k] = 0u;
+      }
+    }
+    for (int e = tid; e < (SORT_THREADS / 32) * 256; e += SORT_THREADS) (&S.wcnt[0][0])[e] = 0u;
+    __syncthreads();
+    // warp multi-split ranking (stable)
+#pragma unroll
+    for (int k = 0; k < SORT_ITEMS; ++k) {
+      const int64_t idx = base + (int64_t)w * 32 * SORT_ITEMS + k * 32 + lane;
+      const bool valid = idx < n;
+      const uint32_t d = valid ? (uint32_t)(key[k] >> shift) & 255u : 0x100u + lane;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t before = __popc(peers & lt);
+      uint32_t cnt = 0;
+      if (valid) cnt = S.wcnt[w][d];
+      __syncwarp();
+      if (valid && before == 0u) S.wcnt[w][d] = cnt + __popc(peers);
+      __syncwarp();
+      rank[k] = cnt + before;
+    }
+    __syncthreads();
+    // per digit: per-warp exclusive offsets and the partition's count
+    const int d = tid;
+    uint32_t run = 0;
+#pragma unroll
+    for (int ww = 0; ww < SORT_THREADS / 32; ++ww) {
+      const uint32_t c = S.wcnt[ww][d];
+      S.wcnt[ww][d] = run;
+      run += c;
+    }
+    const uint32_t dcount = run;
+    uint64_t *my = lb + part * 256 + d;
+    if (part == 0) st_volatile_u64(my, LB_INC | dcount);
+    else st_volatile_u64(my, LB_AGG | dcount);
+    uint32_t ptot;
+    const uint32_t lstart = block_excl_scan_256(dcount, S.warp_tmp, &ptot);
+    S.local_start[d] = lstart;
+    uint64_t prefix = 0;
+    if (part > 0) {
+      prefix = look_back(lb + d, part, 256, status);
+      st_volatile_u64(my, LB_INC | (prefix + dcount));
+    }
+    S.global_base[d] = S.hist_excl[d] + (uint32_t)prefix;
+    __syncthreads();
+    // local scatter into shared memory, sorted by digit
+#pragma unroll
+    for (int k = 0; k < SORT_ITEMS; ++k) {
+      const int64_t idx = base + (int64_t)w * 32 * SORT_ITEMS + k * 32 + lane;
+      if (idx < n) {
+        const uint32_t dd = (uint32_t)(key[k] >> shift) & 255u;
+        const uint32_t pos = S.local_start[dd] + S.wcnt[w][dd] + rank[k];
+        S.keys[pos] = key[k];
+        S.vals[pos] = val[k];
+      }
+    }
+    __syncthreads();
+    // global scatter: consecutive shared positions of one digit go to consecutive addresses
+    const int cnt = (int)min((int64_t)SORT_PART, n - base);
+    for (int i = tid; i < cnt; i += SORT_THREADS) {
+      const uint64_t kk = S.keys[i];
+      const uint32_t dd = (uint32_t)(kk >> shift) & 255u;
+      const uint64_t gpos = (uint64_t)S.global_base[dd] + (uint32_t)(i - S.local_start[dd]);
+      if (gpos < (uint64_t)n) {
+        kout[gpos] = kk;
+        vout[gpos] = S.vals[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void ranges_kernel(const uint64_t *__restrict__ keys, const int64_t *n_int,
+                              int64_t capacity, uint32_t *__restrict__ ranges) {
+  const int64_t n = min(*n_int, capacity);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t t = keys[i] >> 32;
+    if (i == 0 || (keys[i - 1] >> 32) != t) ranges[2 * t] = (uint32_t)i;
+    if (i == n - 1 || (keys[i + 1] >> 32) != t) ranges[2 * t + 1] = (uint32_t)(i + 1);
+  }
+}
+
+int g_sort_occ = 0;
+
+}  // namespace
+
+cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_touched,
+                            int64_t n, const Views &vs, uint64_t *keys, uint32_t *vals,
+                            int64_t capacity, uint32_t *tile_ranges, int64_t *n_int,
+                            char *ws, const WsLayout &L, cudaStream_t st) {
+  cudaError_t e;
+  WsHeader *hdr = reinterpret_cast<WsHeader *>(ws + L.header);
+  uint64_t *scan_lb = reinterpret_cast<uint64_t *>(ws + L.scan_lb);
+  uint32_t *hist = reinterpret_cast<uint32_t *>(ws + L.hist);
+  uint64_t *sort_lb = reinterpret_cast<uint64_t *>(ws + L.sort_lb);
+  uint64_t *alt_keys = reinterpret_cast<uint64_t *>(ws + L.alt_keys);
+  uint32_t *alt_vals = reinterpret_cast<uint32_t *>(ws + L.alt_vals);
+  const int64_t R = (int64_t)vs.n * n;
+  const int passes = (32 + vs.tile_bits + 7) / 8;
+
+  if ((e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * SORT_MAX_PASSES * 256, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)vs.total_tiles, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(sort_lb, 0, sizeof(uint64_t) * 256 * (size_t)L.sort_parts, st)) != cudaSuccess) return e;
+  if (R == 0) return cudaMemsetAsync(n_int, 0, sizeof(int64_t), st);
+  if ((e = cudaMemsetAsync(scan_lb, 0, sizeof(uint64_t) * (size_t)L.scan_parts, st)) != cudaSuccess) return e;
+
+  // emission target: the passes ping-pong, the last one must land in the caller's buffers
+  uint64_t *k0 = (passes & 1) ? alt_keys : keys;
+  uint32_t *v0 = (passes & 1) ? alt_vals : vals;
+  uint64_t *k1 = (passes & 1) ? keys : alt_keys;
+  uint32_t *v1 = (passes & 1) ? vals : alt_vals;
+
+  emit_kernel<<<(unsigned)L.scan_parts, EMIT_THREADS, 0, st>>>(
+      records, tiles_touched, R, n, vs, k0, v0, capacity, n_int, scan_lb, &hdr->scan_parts, hist,
+      passes, &hdr->status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+  const size_t smem = sizeof(SortSmem);
+  if (g_sort_occ == 0) {
+    if ((e = cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+      return e;
+    int occ = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, onesweep_kernel, SORT_THREADS,
+                                                           smem)) != cudaSuccess)
+      return e;
+    g_sort_occ = occ > 0 ? occ : 1;
+  }
+  int64_t grid = (int64_t)sm_count() * g_sort_occ;
+  if (grid > L.sort_parts) grid = L.sort_parts;
+  if (grid < 1) grid = 1;
+  for (int p = 0; p < passes; ++p) {
+    const uint64_t *kin = (p & 1) ? k1 : k0;
+    const uint32_t *vin = (p & 1) ? v1 : v0;
+    uint64_t *kout = (p & 1) ? k0 : k1;
+    uint32_t *vout = (p & 1) ? v0 : v1;
+    uint64_t *lb = sort_lb + (size_t)(p & 1) * 256 * (size_t)L.sort_parts;
+    uint64_t *lbn = sort_lb + (size_t)((p + 1) & 1) * 256 * (size_t)L.sort_parts;
+    onesweep_kernel<<<(unsigned)grid, SORT_THREADS, smem, st>>>(
+        kin, vin, kout, vout, n_int, capacity, 8 * p, hist + p * 256, lb, lbn,
+        &hdr->sort_parts[p], &hdr->status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const int64_t rgrid = (int64_t)sm_count() * 8;
+  ranges_kernel<<<(unsigned)rgrid, 256, 0, st>>>(keys, n_int, capacity, tile_ranges);
+  return cudaGetLastError();
+}
+
+}  // namespace fgs

@@ -1,0 +1,370 @@
+// fgs_internal.cuh - shared device code of the fisheye Gaussian-splatting kernels (sm_103a).
+//
+// Everything here is written from the method's mathematics (Fisheye-GS, arXiv 2409.04751):
+// the equidistant projection (Sec. 3.2), its Jacobian (Sec. 4.2, with f on the theta terms)
+// and the derivative of the Jacobian (Sec. 4.3), in a form that stays accurate near the
+// optical axis.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fgs.h"
+
+namespace fgs {
+
+// ------------------------------------------------------------------------------------------
+// Renderer conventions (the paper inherits them from the 3DGS rasteriser and fixes none):
+constexpr int TILE = FGS_TILE;
+constexpr float NEAR_DIST = 0.2f;                         // cull |mu_c| <= 0.2
+constexpr float THETA_MAX = 3.14159265358979f - 0.05f;    // cull the singular cone theta -> pi
+constexpr float ALPHA_MIN = 1.0f / 255.0f;                // contribution threshold
+constexpr float ALPHA_MAX = 0.99f;                        // alpha cap
+constexpr float T_MIN = 1e-4f;                            // transmittance stop
+constexpr float DILATION = 0.3f;                          // added to Sigma_p's diagonal
+constexpr float LOG2E = 1.4426950408889634f;
+constexpr float LOG2_ALPHA_MIN = -7.994353436858858f;     // log2(1/255)
+constexpr float SERIES_T = 0.3f;                          // near-axis series below t = l_z/z
+
+// Device status codes (same values as fgs_status).
+constexpr uint32_t ST_CAPACITY = FGS_ERR_CAPACITY;
+constexpr uint32_t ST_TIMEOUT = FGS_ERR_TIMEOUT;
+
+// Bounded waits: polls before a wait gives up and reports FGS_ERR_TIMEOUT. A 48-byte bulk copy
+// lands within microseconds and a look-back predecessor publishes within one partition's work,
+// so these limits (about a second of polling) are only reached if something is broken.
+constexpr uint32_t SPIN_LIMIT = 1u << 20;
+
+// ------------------------------------------------------------------------------------------
+// Per-view parameters, passed by value in the kernel parameter space (no device copy).
+struct View {
+  float W[9];
+  float b[3];
+  float fx, fy, cx, cy;
+  float cam_pos[3];  // camera centre -W^T b
+  int32_t width, height, tiles_x, tiles_y;
+  int64_t tile_offset, pixel_offset;
+};
+
+struct Views {
+  int32_t n;
+  int32_t tile_bits;
+  int64_t total_tiles, total_pixels;
+  View v[FGS_MAX_VIEWS];
+};
+
+// global tile -> view (views are few; binary search over the tile offsets)
+__device__ __forceinline__ int view_of_tile(const Views &vs, int64_t t) {
+  int lo = 0, hi = vs.n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (vs.v[mid].tile_offset <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------------------------------------
+// Workspace layout (bytes from the workspace base; every region 256-byte aligned).
+struct WsHeader {
+  uint32_t status;            // fgs_status of device-detected errors (first one wins)
+  uint32_t scan_parts;        // partition counter of the key-emission scan
+  uint32_t sort_parts[8];     // partition counters of the radix-sort passes
+  uint32_t raster_tiles;      // tile queue of the forward rasterizer
+  uint32_t backward_tiles;    // tile queue of the backward rasterizer
+  // measurement counters, written only by instrumented launches (fgs_set_instrumentation):
+  // [0] forward (pixel, Gaussian) evaluations, [1] forward blends,
+  // [2] backward evaluations, [3] backward contributions
+  unsigned long long counters[4];
+  uint32_t pad[44];
+};
+static_assert(sizeof(WsHeader) == 256, "header size");
+
+constexpr int EMIT_THREADS = 256;
+constexpr int EMIT_ITEMS = 4;
+constexpr int EMIT_PART = EMIT_THREADS * EMIT_ITEMS;  // records per scan partition
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_PART = SORT_THREADS * SORT_ITEMS;  // keys per sort partition
+constexpr int SORT_MAX_PASSES = 8;
+constexpr int G2D_STRIDE = 12;                        // floats per record of screen-space grads
+
+struct WsLayout {
+  size_t header, scan_lb, hist, sort_lb, alt_keys, alt_vals, g2d, total;
+  int64_t scan_parts, sort_parts;
+};
+
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+inline WsLayout ws_layout(int64_t n_records, int64_t capacity) {
+  WsLayout L;
+  L.scan_parts = (n_records + EMIT_PART - 1) / EMIT_PART;
+  L.sort_parts = (capacity + SORT_PART - 1) / SORT_PART;
+  size_t o = 0;
+  // regions that depend on the record count only come first, so the rasterizer and the
+  // backward can locate them without knowing the key capacity
+  L.header = o; o += align256(sizeof(WsHeader));
+  L.scan_lb = o; o += align256(sizeof(uint64_t) * (size_t)(L.scan_parts > 0 ? L.scan_parts : 1));
+  L.g2d = o; o += align256(sizeof(float) * G2D_STRIDE * (size_t)(n_records > 0 ? n_records : 1));
+  L.hist = o; o += align256(sizeof(uint32_t) * SORT_MAX_PASSES * 256);
+  L.sort_lb = o; o += align256(sizeof(uint64_t) * 256 * 2 * (size_t)(L.sort_parts > 0 ? L.sort_parts : 1));
+  L.alt_keys = o; o += align256(sizeof(uint64_t) * (size_t)capacity);
+  L.alt_vals = o; o += align256(sizeof(uint32_t) * ((size_t)capacity + 4));
+  L.total = o;
+  return L;
+}
+
+__device__ __forceinline__ void set_status(uint32_t *status, uint32_t code) {
+  atomicCAS(status, 0u, code);
+}
+
+// ------------------------------------------------------------------------------------------
+// PTX helpers: mbarrier + TMA bulk copy (cp.async.bulk), sm_90+ forms used on sm_103a.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; returns false (and records FGS_ERR_TIMEOUT) on give-up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t *status) {
+  for (uint32_t it = 0; it < SPIN_LIMIT; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+  }
+  set_status(status, ST_TIMEOUT);
+  return false;
+}
+
+// One TMA bulk copy global -> shared of `bytes` (multiple of 16, both addresses 16-aligned),
+// completing `bytes` transactions on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, uint32_t bytes,
+                                         uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst_smem)),
+      "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_volatile_u64(uint64_t *p, uint64_t v) {
+  asm volatile("st.volatile.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// ------------------------------------------------------------------------------------------
+// Equidistant projection pieces. With u = l_z = |(x, y)|, l2 = |mu_c|^2, theta = atan2(u, z):
+//   g   = theta / u                       (x_p = cx + fx g x, y_p = cy + fy g y)
+//   h   = dg/du / u = (z u / l2 - theta) / u^3
+//   huu = dh/du / u = -(2 z / l2^2 + 3 h) / u^2
+// so that J = [[fx (g + x^2 h), fx x y h, -fx x / l2], [fy x y h, fy (g + y^2 h), -fy y / l2]].
+// Near the axis (0 < t = u / z < SERIES_T) h and huu cancel catastrophically; there the
+// Taylor series in t (from atan t = sum (-1)^k t^(2k+1) / (2k+1)) are used:
+//   g   = z^-1 sum_{k>=0} (-1)^k t^2k / (2k+1)
+//   h   = z^-3 sum_{k>=1} (-1)^k 2k/(2k+1) t^(2k-2)
+//   huu = z^-5 sum_{k>=2} (-1)^k 2k (2k-2)/(2k+1) t^(2k-4)
+struct FishG {
+  float theta, g, h, huu;
+};
+
+template <bool NEED_HUU>
+__device__ __forceinline__ FishG fisheye_g(float x, float y, float z) {
+  FishG r;
+  float u2 = x * x + y * y;
+  float u = sqrtf(u2);
+  float l2 = u2 + z * z;
+  r.theta = atan2f(u, z);
+  if (z > 0.f && u < SERIES_T * z) {
+    float iz = 1.0f / z;
+    float t2 = u2 * iz * iz;
+    // Horner in t2; coefficients (-1)^k / (2k+1), k = 0..9
+    float sg = -1.f / 19.f;
+    sg = fmaf(sg, t2, 1.f / 17.f); sg = fmaf(sg, t2, -1.f / 15.f); sg = fmaf(sg, t2, 1.f / 13.f);
+    sg = fmaf(sg, t2, -1.f / 11.f); sg = fmaf(sg, t2, 1.f / 9.f); sg = fmaf(sg, t2, -1.f / 7.f);
+    sg = fmaf(sg, t2, 1.f / 5.f); sg = fmaf(sg, t2, -1.f / 3.f); sg = fmaf(sg, t2, 1.f);
+    // (-1)^k 2k/(2k+1), k = 1..9
+    float sh = -18.f / 19.f;
+    sh = fmaf(sh, t2, 16.f / 17.f); sh = fmaf(sh, t2, -14.f / 15.f); sh = fmaf(sh, t2, 12.f / 13.f);
+    sh = fmaf(sh, t2, -10.f / 11.f); sh = fmaf(sh, t2, 8.f / 9.f); sh = fmaf(sh, t2, -6.f / 7.f);
+    sh = fmaf(sh, t2, 4.f / 5.f); sh = fmaf(sh, t2, -2.f / 3.f);
+    float iz3 = iz * iz * iz;
+    r.g = sg * iz;
+    r.h = sh * iz3;
+    if (NEED_HUU) {
+      // (-1)^k 2k(2k-2)/(2k+1), k = 2..10
+      float s8 = 360.f / 21.f;
+      s8 = fmaf(s8, t2, -288.f / 19.f); s8 = fmaf(s8, t2, 224.f / 17.f);
+      s8 = fmaf(s8, t2, -168.f / 15.f); s8 = fmaf(s8, t2, 120.f / 13.f);
+      s8 = fmaf(s8, t2, -80.f / 11.f); s8 = fmaf(s8, t2, 48.f / 9.f);
+      s8 = fmaf(s8, t2, -24.f / 7.f); s8 = fmaf(s8, t2, 8.f / 5.f);
+      r.huu = s8 * iz3 * iz * iz;
+    } else {
+      r.huu = 0.f;
+    }
+  } else {
+    r.g = r.theta / u;
+    r.h = (z * u / l2 - r.theta) / (u2 * u);
+    r.huu = NEED_HUU ? -(2.f * z / (l2 * l2) + 3.f * r.h) / u2 : 0.f;
+  }
+  return r;
+}
+
+// ------------------------------------------------------------------------------------------
+// Real spherical harmonics up to degree 3 (Condon-Shortley phase, order m = -l..l) as
+// polynomials of the unit direction (x, y, z). Constants are the normalisations
+//   c0 = 1/(2 sqrt(pi)); c1 = sqrt(3/(4 pi));
+//   c2a = sqrt(15/pi)/2, c2b = sqrt(5/pi)/4, c2c = sqrt(15/pi)/4;
+//   c3a = sqrt(35/(2 pi))/4, c3b = sqrt(105/pi)/2, c3c = sqrt(21/(2 pi))/4,
+//   c3d = sqrt(7/pi)/4, c3e = sqrt(105/pi)/4.
+constexpr float SH_C0 = 0.28209479177387814f;
+constexpr float SH_C1 = 0.48860251190291992f;
+constexpr float SH_C2A = 1.0925484305920792f;
+constexpr float SH_C2B = 0.31539156525252005f;
+constexpr float SH_C2C = 0.54627421529603959f;
+constexpr float SH_C3A = 0.59004358992664352f;
+constexpr float SH_C3B = 2.8906114426405538f;
+constexpr float SH_C3C = 0.45704579946446572f;
+constexpr float SH_C3D = 0.37317633259011540f;
+constexpr float SH_C3E = 1.4453057213202769f;
+
+template <int D>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y) {
+  Y[0] = SH_C0;
+  if (D >= 1) {
+    Y[1] = -SH_C1 * y; Y[2] = SH_C1 * z; Y[3] = -SH_C1 * x;
+  }
+  if (D >= 2) {
+    float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = SH_C2A * x * y;
+    Y[5] = -SH_C2A * y * z;
+    Y[6] = SH_C2B * (2.f * zz - xx - yy);
+    Y[7] = -SH_C2A * x * z;
+    Y[8] = SH_C2C * (xx - yy);
+    if (D >= 3) {
+      Y[9] = -SH_C3A * y * (3.f * xx - yy);
+      Y[10] = SH_C3B * x * y * z;
+      Y[11] = -SH_C3C * y * (4.f * zz - xx - yy);
+      Y[12] = SH_C3D * z * (2.f * zz - 3.f * xx - 3.f * yy);
+      Y[13] = -SH_C3C * x * (4.f * zz - xx - yy);
+      Y[14] = SH_C3E * z * (xx - yy);
+      Y[15] = -SH_C3A * x * (xx - 3.f * yy);
+    }
+  }
+}
+
+// d Y_k / d(x, y, z) of the polynomials above (their tangential part is the derivative on
+// the sphere, which is all the backward uses).
+template <int D>
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float (*dY)[3]) {
+  dY[0][0] = dY[0][1] = dY[0][2] = 0.f;
+  if (D >= 1) {
+    dY[1][0] = 0.f; dY[1][1] = -SH_C1; dY[1][2] = 0.f;
+    dY[2][0] = 0.f; dY[2][1] = 0.f; dY[2][2] = SH_C1;
+    dY[3][0] = -SH_C1; dY[3][1] = 0.f; dY[3][2] = 0.f;
+  }
+  if (D >= 2) {
+    float xx = x * x, yy = y * y, zz = z * z;
+    dY[4][0] = SH_C2A * y; dY[4][1] = SH_C2A * x; dY[4][2] = 0.f;
+    dY[5][0] = 0.f; dY[5][1] = -SH_C2A * z; dY[5][2] = -SH_C2A * y;
+    dY[6][0] = -2.f * SH_C2B * x; dY[6][1] = -2.f * SH_C2B * y; dY[6][2] = 4.f * SH_C2B * z;
+    dY[7][0] = -SH_C2A * z; dY[7][1] = 0.f; dY[7][2] = -SH_C2A * x;
+    dY[8][0] = 2.f * SH_C2C * x; dY[8][1] = -2.f * SH_C2C * y; dY[8][2] = 0.f;
+    if (D >= 3) {
+      dY[9][0] = -6.f * SH_C3A * x * y; dY[9][1] = -SH_C3A * (3.f * xx - 3.f * yy); dY[9][2] = 0.f;
+      dY[10][0] = SH_C3B * y * z; dY[10][1] = SH_C3B * x * z; dY[10][2] = SH_C3B * x * y;
+      dY[11][0] = 2.f * SH_C3C * x * y; dY[11][1] = -SH_C3C * (4.f * zz - xx - 3.f * yy);
+      dY[11][2] = -8.f * SH_C3C * y * z;
+      dY[12][0] = -6.f * SH_C3D * x * z; dY[12][1] = -6.f * SH_C3D * y * z;
+      dY[12][2] = SH_C3D * (6.f * zz - 3.f * xx - 3.f * yy);
+      dY[13][0] = -SH_C3C * (4.f * zz - 3.f * xx - yy); dY[13][1] = 2.f * SH_C3C * x * y;
+      dY[13][2] = -8.f * SH_C3C * x * z;
+      dY[14][0] = 2.f * SH_C3E * x * z; dY[14][1] = -2.f * SH_C3E * y * z;
+      dY[14][2] = SH_C3E * (xx - yy);
+      dY[15][0] = -SH_C3A * (3.f * xx - 3.f * yy); dY[15][1] = 6.f * SH_C3A * x * y;
+      dY[15][2] = 0.f;
+    }
+  }
+}
+
+// Rotation from a quaternion (w, x, y, z) already normalised; row-major.
+__device__ __forceinline__ void quat_to_rot(float w, float x, float y, float z, float *R) {
+  R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// ------------------------------------------------------------------------------------------
+// Launchers (one per stage), implemented in the .cu files.
+struct GaussPtrs {
+  const float *means, *scales, *quats, *opacities, *sh;
+  int64_t n;
+  int32_t sh_degree;
+};
+
+int sm_count();
+bool instrumented();
+
+cudaError_t launch_preprocess_fwd(const GaussPtrs &g, const Views &vs, fgs_record *records,
+                                  uint32_t *tiles_touched, cudaStream_t st);
+cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_touched,
+                            int64_t n, const Views &vs, uint64_t *keys, uint32_t *vals,
+                            int64_t capacity, uint32_t *tile_ranges, int64_t *n_int,
+                            char *ws, const WsLayout &L, cudaStream_t st);
+cudaError_t launch_raster_fwd(const fgs_record *records, const uint32_t *vals,
+                              const uint32_t *tile_ranges, const Views &vs, float bg0, float bg1,
+                              float bg2, float *images, float *final_T, uint32_t *n_processed,
+                              char *ws, const WsLayout &L, cudaStream_t st);
+cudaError_t launch_raster_bwd(const fgs_record *records, const uint32_t *vals,
+                              const uint32_t *tile_ranges, const Views &vs, float bg0, float bg1,
+                              float bg2, const float *final_T, const uint32_t *n_processed,
+                              const float *dL_dimages, int64_t n_records, char *ws,
+                              const WsLayout &L, cudaStream_t st);
+cudaError_t launch_preprocess_bwd(const GaussPtrs &g, const Views &vs, const fgs_record *records,
+                                  const uint32_t *tiles_touched, const float *g2d,
+                                  float *d_means, float *d_scales, float *d_quats,
+                                  float *d_opacities, float *d_sh, uint32_t *status,
+                                  cudaStream_t st);
+
+}  // namespace fgs

@@ -1,0 +1,407 @@
+// preprocess.cu - per-Gaussian preprocess (forward) and its backward, sm_103a.
+//
+// Forward (Sec. 4.1 preprocessCUDA with the fisheye projection of Sec. 4.2 / 4.3): one thread
+// per Gaussian, looping over the views of the call, so each Gaussian's parameters (236 B at SH
+// degree 3) are read from HBM once however many views there are. Quaternions and SH rows are
+// read with 16-byte vector loads when their rows are 16-byte aligned.
+//
+// Backward (Sec. 4.2 / 4.3 backward): one thread per Gaussian; the per-view screen-space
+// gradients (written by the rasterizer backward) are pulled back through the conic,
+// Sigma_p = T Sigma T^T, T = J W, J(mu_c) and the SH colour, summed over views, then through
+// Sigma = R S S^T R^T to scales and quaternions.
+#include "fgs_internal.cuh"
+
+namespace fgs {
+
+namespace {
+
+template <int D, bool VEC>
+__device__ __forceinline__ void load_sh(const float *__restrict__ sh, int64_t i, float *c) {
+  constexpr int K3 = (D + 1) * (D + 1) * 3;
+  const float *p = sh + (size_t)i * K3;
+  if (VEC && (K3 % 4) == 0) {
+    const float4 *p4 = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int k = 0; k < K3 / 4; ++k) {
+      float4 v = __ldg(p4 + k);
+      c[4 * k] = v.x; c[4 * k + 1] = v.y; c[4 * k + 2] = v.z; c[4 * k + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < K3; ++k) c[k] = __ldg(p + k);
+  }
+}
+
+template <bool VEC>
+__device__ __forceinline__ float4 load_quat(const float *__restrict__ q, int64_t i) {
+  if (VEC) return __ldg(reinterpret_cast<const float4 *>(q) + i);
+  return make_float4(__ldg(q + 4 * i), __ldg(q + 4 * i + 1), __ldg(q + 4 * i + 2), __ldg(q + 4 * i + 3));
+}
+
+// Sigma = M M^T, M = R diag(s): upper triangle (xx, xy, xz, yy, yz, zz)
+__device__ __forceinline__ void covariance(const float *R, float sx, float sy, float sz, float *S) {
+  float M[9] = {R[0] * sx, R[1] * sy, R[2] * sz, R[3] * sx, R[4] * sy, R[5] * sz,
+                R[6] * sx, R[7] * sy, R[8] * sz};
+  S[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+  S[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+  S[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+  S[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+  S[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+  S[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+}
+
+template <int D, bool VEC>
+__global__ void __launch_bounds__(256)
+    preprocess_fwd_kernel(GaussPtrs g, Views vs, fgs_record *__restrict__ rec,
+                          uint32_t *__restrict__ tt) {
+  constexpr int K = (D + 1) * (D + 1);
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  const float mx = __ldg(g.means + 3 * i), my = __ldg(g.means + 3 * i + 1),
+              mz = __ldg(g.means + 3 * i + 2);
+  const float op = __ldg(g.opacities + i);
+  const bool op_ok = op >= ALPHA_MIN;
+
+  // view-independent: Sigma and the footprint level q* = 2 ln(255 opacity)
+  float S[6] = {0, 0, 0, 0, 0, 0};
+  float qs = 0.f;
+  if (op_ok) {
+    float4 q = load_quat<VEC>(g.quats, i);
+    float qn = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    float R[9];
+    quat_to_rot(q.x * qn, q.y * qn, q.z * qn, q.w * qn, R);
+    covariance(R, __ldg(g.scales + 3 * i), __ldg(g.scales + 3 * i + 1),
+               __ldg(g.scales + 3 * i + 2), S);
+    qs = fmaxf(2.f * logf(255.f * op), 0.f);
+  }
+  float shc[K * 3];
+  bool sh_loaded = false;
+
+  for (int v = 0; v < vs.n; ++v) {
+    const View &V = vs.v[v];
+    const int64_t r = (int64_t)v * g.n + i;
+    const float x = fmaf(V.W[0], mx, fmaf(V.W[1], my, fmaf(V.W[2], mz, V.b[0])));
+    const float y = fmaf(V.W[3], mx, fmaf(V.W[4], my, fmaf(V.W[5], mz, V.b[1])));
+    const float z = fmaf(V.W[6], mx, fmaf(V.W[7], my, fmaf(V.W[8], mz, V.b[2])));
+    const float l2 = x * x + y * y + z * z;
+    const float dist = sqrtf(l2);
+    const FishG fg = fisheye_g<false>(x, y, z);
+    if (!(op_ok && dist > NEAR_DIST && fg.theta < THETA_MAX)) {
+      tt[r] = 0u;
+      continue;
+    }
+    // mean (Sec. 3.2) and Jacobian (Sec. 4.2)
+    const float px = fmaf(V.fx * fg.g, x, V.cx);
+    const float py = fmaf(V.fy * fg.g, y, V.cy);
+    const float il2 = 1.f / l2;
+    const float J00 = V.fx * fmaf(x * x, fg.h, fg.g), J01 = V.fx * x * y * fg.h, J02 = -V.fx * x * il2;
+    const float J10 = V.fy * x * y * fg.h, J11 = V.fy * fmaf(y * y, fg.h, fg.g), J12 = -V.fy * y * il2;
+    // T = J W
+    float T0[3], T1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T0[c] = J00 * V.W[c] + J01 * V.W[3 + c] + J02 * V.W[6 + c];
+      T1[c] = J10 * V.W[c] + J11 * V.W[3 + c] + J12 * V.W[6 + c];
+    }
+    // Sigma_p = T Sigma T^T + 0.3 I (Sec. 4.3)
+    const float u0 = T0[0] * S[0] + T0[1] * S[1] + T0[2] * S[2];
+    const float u1 = T0[0] * S[1] + T0[1] * S[3] + T0[2] * S[4];
+    const float u2 = T0[0] * S[2] + T0[1] * S[4] + T0[2] * S[5];
+    const float w0 = T1[0] * S[0] + T1[1] * S[1] + T1[2] * S[2];
+    const float w1 = T1[0] * S[1] + T1[1] * S[3] + T1[2] * S[4];
+    const float w2 = T1[0] * S[2] + T1[1] * S[4] + T1[2] * S[5];
+    const float a = u0 * T0[0] + u1 * T0[1] + u2 * T0[2] + DILATION;
+    const float b = u0 * T1[0] + u1 * T1[1] + u2 * T1[2];
+    const float c = w0 * T1[0] + w1 * T1[1] + w2 * T1[2] + DILATION;
+    const float det = a * c - b * b;
+    const float idet = 1.f / det;
+    // footprint: AABB of the alpha >= 1/255 ellipse, padded, as an inclusive tile rect
+    const float ex = fmaf(sqrtf(qs * a), 1.00001f, 1e-3f);
+    const float ey = fmaf(sqrtf(qs * c), 1.00001f, 1e-3f);
+    const float lx = (px - ex) * (1.f / TILE), hx = (px + ex) * (1.f / TILE);
+    const float ly = (py - ey) * (1.f / TILE), hy = (py + ey) * (1.f / TILE);
+    if (!(hx >= 0.f && hy >= 0.f && lx < (float)V.tiles_x && ly < (float)V.tiles_y)) {
+      tt[r] = 0u;
+      continue;
+    }
+    const int x0 = lx < 0.f ? 0 : (int)floorf(lx);
+    const int y0 = ly < 0.f ? 0 : (int)floorf(ly);
+    const int x1 = (int)floorf(fminf(hx, (float)(V.tiles_x - 1)));
+    const int y1 = (int)floorf(fminf(hy, (float)(V.tiles_y - 1)));
+    // colour from SH along (mu - camera centre)
+    if (!sh_loaded) {
+      load_sh<D, VEC>(g.sh, i, shc);
+      sh_loaded = true;
+    }
+    float dx = mx - V.cam_pos[0], dy = my - V.cam_pos[1], dz = mz - V.cam_pos[2];
+    const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= dn; dy *= dn; dz *= dn;
+    float Y[K];
+    sh_basis<D>(dx, dy, dz, Y);
+    float rgb[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float s = 0.5f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) s = fmaf(shc[3 * k + ch], Y[k], s);
+      rgb[ch] = fmaxf(s, 0.f);
+    }
+    float4 *o = reinterpret_cast<float4 *>(rec + r);
+    o[0] = make_float4(px, py, c * idet, -b * idet);
+    o[1] = make_float4(a * idet, op, rgb[0], rgb[1]);
+    const uint32_t r01 = (uint32_t)x0 | ((uint32_t)y0 << 16);
+    const uint32_t r23 = (uint32_t)x1 | ((uint32_t)y1 << 16);
+    o[2] = make_float4(rgb[2], dist, __uint_as_float(r01), __uint_as_float(r23));
+    tt[r] = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+  }
+}
+
+template <int D, bool VEC>
+__global__ void __launch_bounds__(128)
+    preprocess_bwd_kernel(GaussPtrs g, Views vs, const fgs_record *__restrict__ rec,
+                          const uint32_t *__restrict__ tt, const float *__restrict__ g2d,
+                          float *__restrict__ d_means, float *__restrict__ d_scales,
+                          float *__restrict__ d_quats, float *__restrict__ d_opac,
+                          float *__restrict__ d_sh) {
+  constexpr int K = (D + 1) * (D + 1);
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  const float mx = __ldg(g.means + 3 * i), my = __ldg(g.means + 3 * i + 1),
+              mz = __ldg(g.means + 3 * i + 2);
+  float dmu[3] = {0.f, 0.f, 0.f};
+  float dS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma (symmetric, xx xy xz yy yz zz)
+  float dsh[K * 3];
+#pragma unroll
+  for (int k = 0; k < K * 3; ++k) dsh[k] = 0.f;
+  float dop = 0.f;
+  bool any = false;
+  float S[6], R[9], qnv[4], qnorm = 1.f;
+  float shc[K * 3];
+
+  for (int v = 0; v < vs.n; ++v) {
+    const int64_t r = (int64_t)v * g.n + i;
+    if (tt[r] == 0u) continue;
+    const View &V = vs.v[v];
+    if (!any) {
+      any = true;
+      float4 q = load_quat<VEC>(g.quats, i);
+      qnorm = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+      const float iq = 1.f / qnorm;
+      qnv[0] = q.x * iq; qnv[1] = q.y * iq; qnv[2] = q.z * iq; qnv[3] = q.w * iq;
+      quat_to_rot(qnv[0], qnv[1], qnv[2], qnv[3], R);
+      covariance(R, __ldg(g.scales + 3 * i), __ldg(g.scales + 3 * i + 1),
+                 __ldg(g.scales + 3 * i + 2), S);
+      load_sh<D, VEC>(g.sh, i, shc);
+    }
+    const float4 g0 = __ldg(reinterpret_cast<const float4 *>(g2d + (size_t)r * G2D_STRIDE));
+    const float4 g1 = __ldg(reinterpret_cast<const float4 *>(g2d + (size_t)r * G2D_STRIDE) + 1);
+    const float gb = __ldg(g2d + (size_t)r * G2D_STRIDE + 8);
+    const float4 rc0 = __ldg(reinterpret_cast<const float4 *>(rec + r));
+    const float4 rc1 = __ldg(reinterpret_cast<const float4 *>(rec + r) + 1);
+    const float rgb2 = __ldg(reinterpret_cast<const float *>(rec + r) + 8);
+    dop += g1.y;
+
+    const float x = fmaf(V.W[0], mx, fmaf(V.W[1], my, fmaf(V.W[2], mz, V.b[0])));
+    const float y = fmaf(V.W[3], mx, fmaf(V.W[4], my, fmaf(V.W[5], mz, V.b[1])));
+    const float z = fmaf(V.W[6], mx, fmaf(V.W[7], my, fmaf(V.W[8], mz, V.b[2])));
+    const float l2 = x * x + y * y + z * z;
+    const float il2 = 1.f / l2;
+    const FishG fg = fisheye_g<true>(x, y, z);
+    const float J00 = V.fx * fmaf(x * x, fg.h, fg.g), J01 = V.fx * x * y * fg.h, J02 = -V.fx * x * il2;
+    const float J10 = V.fy * x * y * fg.h, J11 = V.fy * fmaf(y * y, fg.h, fg.g), J12 = -V.fy * y * il2;
+    float T0[3], T1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T0[c] = J00 * V.W[c] + J01 * V.W[3 + c] + J02 * V.W[6 + c];
+      T1[c] = J10 * V.W[c] + J11 * V.W[3 + c] + J12 * V.W[6 + c];
+    }
+    // conic -> Sigma_p: dL/dSigma_p = -M Gc M with M the conic matrix and Gc the symmetric
+    // gradient [[gA, gB/2], [gB/2, gC]] (B is the off-diagonal entry, counted twice).
+    const float cA = rc0.z, cB = rc0.w, cC = rc1.x;
+    const float gA = g0.z, gBh = 0.5f * g0.w, gC = g1.x;
+    const float t00 = gA * cA + gBh * cB, t01 = gA * cB + gBh * cC;
+    const float t10 = gBh * cA + gC * cB, t11 = gBh * cB + gC * cC;
+    const float Gs00 = -(cA * t00 + cB * t10);
+    const float Gs01 = -(cA * t01 + cB * t11);
+    const float Gs11 = -(cB * t01 + cC * t11);
+    // dL/dSigma += T^T Gs T ; dL/dT = 2 Gs T Sigma
+    float GsT0[3], GsT1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      GsT0[c] = Gs00 * T0[c] + Gs01 * T1[c];
+      GsT1[c] = Gs01 * T0[c] + Gs11 * T1[c];
+    }
+    dS[0] += T0[0] * GsT0[0] + T1[0] * GsT1[0];
+    dS[1] += T0[0] * GsT0[1] + T1[0] * GsT1[1];
+    dS[2] += T0[0] * GsT0[2] + T1[0] * GsT1[2];
+    dS[3] += T0[1] * GsT0[1] + T1[1] * GsT1[1];
+    dS[4] += T0[1] * GsT0[2] + T1[1] * GsT1[2];
+    dS[5] += T0[2] * GsT0[2] + T1[2] * GsT1[2];
+    // GT = 2 (Gs T) Sigma
+    float GT0[3], GT1[3];
+    GT0[0] = 2.f * (GsT0[0] * S[0] + GsT0[1] * S[1] + GsT0[2] * S[2]);
+    GT0[1] = 2.f * (GsT0[0] * S[1] + GsT0[1] * S[3] + GsT0[2] * S[4]);
+    GT0[2] = 2.f * (GsT0[0] * S[2] + GsT0[1] * S[4] + GsT0[2] * S[5]);
+    GT1[0] = 2.f * (GsT1[0] * S[0] + GsT1[1] * S[1] + GsT1[2] * S[2]);
+    GT1[1] = 2.f * (GsT1[0] * S[1] + GsT1[1] * S[3] + GsT1[2] * S[4]);
+    GT1[2] = 2.f * (GsT1[0] * S[2] + GsT1[1] * S[4] + GsT1[2] * S[5]);
+    // dL/dJ = dL/dT W^T
+    float GJ0[3], GJ1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      GJ0[k] = GT0[0] * V.W[3 * k] + GT0[1] * V.W[3 * k + 1] + GT0[2] * V.W[3 * k + 2];
+      GJ1[k] = GT1[0] * V.W[3 * k] + GT1[1] * V.W[3 * k + 1] + GT1[2] * V.W[3 * k + 2];
+    }
+    // J -> mu_c (Sec. 4.3): with A..F the f-scaled dL/dJ entries,
+    //   L_J = (A + E) g + Q h - P / l2,  Q = A x^2 + (B + D) x y + E y^2,  P = C x + F y,
+    // dg/dx = x h, dg/dy = y h, dg/dz = -1/l2, dh/dx = x huu, dh/dy = y huu, dh/dz = 2/l2^2.
+    const float A = V.fx * GJ0[0], B = V.fx * GJ0[1], Cc = V.fx * GJ0[2];
+    const float Dd = V.fy * GJ1[0], E = V.fy * GJ1[1], F = V.fy * GJ1[2];
+    const float AE = A + E, BD = B + Dd;
+    const float Q = A * x * x + BD * x * y + E * y * y;
+    const float P = Cc * x + F * y;
+    const float il22 = il2 * il2;
+    float dmc0 = AE * x * fg.h + (2.f * A * x + BD * y) * fg.h + Q * fg.huu * x - Cc * il2 + 2.f * P * x * il22;
+    float dmc1 = AE * y * fg.h + (BD * x + 2.f * E * y) * fg.h + Q * fg.huu * y - F * il2 + 2.f * P * y * il22;
+    float dmc2 = -AE * il2 + 2.f * Q * il22 + 2.f * P * z * il22;
+    // mu_p -> mu_c (Sec. 4.2): J^T dL/dmu_p
+    dmc0 += J00 * g0.x + J10 * g0.y;
+    dmc1 += J01 * g0.x + J11 * g0.y;
+    dmc2 += J02 * g0.x + J12 * g0.y;
+    // mu_c = W mu + b
+    dmu[0] += V.W[0] * dmc0 + V.W[3] * dmc1 + V.W[6] * dmc2;
+    dmu[1] += V.W[1] * dmc0 + V.W[4] * dmc1 + V.W[7] * dmc2;
+    dmu[2] += V.W[2] * dmc0 + V.W[5] * dmc1 + V.W[8] * dmc2;
+    // colour -> SH and view direction (clamped channels pass no gradient)
+    const float grgb[3] = {rc1.z > 0.f ? g1.z : 0.f, rc1.w > 0.f ? g1.w : 0.f,
+                           rgb2 > 0.f ? gb : 0.f};
+    float ux = mx - V.cam_pos[0], uy = my - V.cam_pos[1], uz = mz - V.cam_pos[2];
+    const float un = rsqrtf(ux * ux + uy * uy + uz * uz);
+    ux *= un; uy *= un; uz *= un;
+    float Y[K], dY[K][3];
+    sh_basis<D>(ux, uy, uz, Y);
+    sh_basis_grad<D>(ux, uy, uz, dY);
+    float dd0 = 0.f, dd1 = 0.f, dd2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      float s = 0.f;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        dsh[3 * k + ch] = fmaf(Y[k], grgb[ch], dsh[3 * k + ch]);
+        s = fmaf(shc[3 * k + ch], grgb[ch], s);
+      }
+      dd0 = fmaf(s, dY[k][0], dd0);
+      dd1 = fmaf(s, dY[k][1], dd1);
+      dd2 = fmaf(s, dY[k][2], dd2);
+    }
+    const float dot = ux * dd0 + uy * dd1 + uz * dd2;
+    dmu[0] += (dd0 - ux * dot) * un;
+    dmu[1] += (dd1 - uy * dot) * un;
+    dmu[2] += (dd2 - uz * dot) * un;
+  }
+
+  float dsc[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
+  if (any) {
+    // Sigma = M M^T, M = R diag(s): dL/dM = 2 dS M
+    const float sx = __ldg(g.scales + 3 * i), sy = __ldg(g.scales + 3 * i + 1),
+                sz = __ldg(g.scales + 3 * i + 2);
+    const float sc[3] = {sx, sy, sz};
+    const float dSf[9] = {dS[0], dS[1], dS[2], dS[1], dS[3], dS[4], dS[2], dS[4], dS[5]};
+    float GR[9];
+#pragma unroll
+    for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        // (dS M)[rr][cc] = sum_k dS[rr][k] R[k][cc] s_cc
+        const float gm = 2.f * (dSf[3 * rr] * R[cc] + dSf[3 * rr + 1] * R[3 + cc] +
+                                dSf[3 * rr + 2] * R[6 + cc]) * sc[cc];
+        dsc[cc] += gm * R[3 * rr + cc];
+        GR[3 * rr + cc] = gm * sc[cc];
+      }
+    const float w = qnv[0], x = qnv[1], y = qnv[2], z = qnv[3];
+    // dL/dq_n from R(q_n), entry by entry
+    const float gw = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
+    const float gx = 2.f * (y * GR[1] + z * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] +
+                            z * GR[6] + w * GR[7] - 2.f * x * GR[8]);
+    const float gy = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + z * GR[5] -
+                            w * GR[6] + z * GR[7] - 2.f * y * GR[8]);
+    const float gz = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4] +
+                            y * GR[5] + x * GR[6] + y * GR[7]);
+    // through q_n = q / |q|
+    const float dot = gw * w + gx * x + gy * y + gz * z;
+    const float iq = 1.f / qnorm;
+    dq[0] = (gw - w * dot) * iq; dq[1] = (gx - x * dot) * iq;
+    dq[2] = (gy - y * dot) * iq; dq[3] = (gz - z * dot) * iq;
+  }
+  d_means[3 * i] = dmu[0]; d_means[3 * i + 1] = dmu[1]; d_means[3 * i + 2] = dmu[2];
+  d_scales[3 * i] = dsc[0]; d_scales[3 * i + 1] = dsc[1]; d_scales[3 * i + 2] = dsc[2];
+  d_quats[4 * i] = dq[0]; d_quats[4 * i + 1] = dq[1]; d_quats[4 * i + 2] = dq[2]; d_quats[4 * i + 3] = dq[3];
+  d_opac[i] = dop;
+  float *o = d_sh + (size_t)i * K * 3;
+  if (VEC && ((K * 3) % 4) == 0) {
+    float4 *o4 = reinterpret_cast<float4 *>(o);
+#pragma unroll
+    for (int k = 0; k < K * 3 / 4; ++k)
+      o4[k] = make_float4(dsh[4 * k], dsh[4 * k + 1], dsh[4 * k + 2], dsh[4 * k + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < K * 3; ++k) o[k] = dsh[k];
+  }
+}
+
+template <int D>
+cudaError_t fwd_dispatch(const GaussPtrs &g, const Views &vs, fgs_record *rec, uint32_t *tt,
+                         bool vec, cudaStream_t st) {
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((g.n + threads - 1) / threads);
+  if (vec) preprocess_fwd_kernel<D, true><<<blocks, threads, 0, st>>>(g, vs, rec, tt);
+  else preprocess_fwd_kernel<D, false><<<blocks, threads, 0, st>>>(g, vs, rec, tt);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t bwd_dispatch(const GaussPtrs &g, const Views &vs, const fgs_record *rec,
+                         const uint32_t *tt, const float *g2d, float *dm, float *ds, float *dq,
+                         float *dop, float *dsh, bool vec, cudaStream_t st) {
+  const int threads = 128;
+  const unsigned blocks = (unsigned)((g.n + threads - 1) / threads);
+  if (vec)
+    preprocess_bwd_kernel<D, true><<<blocks, threads, 0, st>>>(g, vs, rec, tt, g2d, dm, ds, dq, dop, dsh);
+  else
+    preprocess_bwd_kernel<D, false><<<blocks, threads, 0, st>>>(g, vs, rec, tt, g2d, dm, ds, dq, dop, dsh);
+  return cudaGetLastError();
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+}  // namespace
+
+cudaError_t launch_preprocess_fwd(const GaussPtrs &g, const Views &vs, fgs_record *records,
+                                  uint32_t *tiles_touched, cudaStream_t st) {
+  if (g.n == 0) return cudaSuccess;
+  const bool vec = aligned16(g.quats) && aligned16(g.sh);
+  switch (g.sh_degree) {
+    case 0: return fwd_dispatch<0>(g, vs, records, tiles_touched, vec, st);
+    case 1: return fwd_dispatch<1>(g, vs, records, tiles_touched, vec, st);
+    case 2: return fwd_dispatch<2>(g, vs, records, tiles_touched, vec, st);
+    default: return fwd_dispatch<3>(g, vs, records, tiles_touched, vec, st);
+  }
+}
+
+cudaError_t launch_preprocess_bwd(const GaussPtrs &g, const Views &vs, const fgs_record *records,
+                                  const uint32_t *tiles_touched, const float *g2d,
+                                  float *d_means, float *d_scales, float *d_quats,
+                                  float *d_opacities, float *d_sh, uint32_t *status,
+                                  cudaStream_t st) {
+  (void)status;
+  if (g.n == 0) return cudaSuccess;
+  const bool vec = aligned16(g.quats) && aligned16(g.sh) && aligned16(d_sh);
+  switch (g.sh_degree) {
+    case 0: return bwd_dispatch<0>(g, vs, records, tiles_touched, g2d, d_means, d_scales, d_quats, d_opacities, d_sh, vec, st);
+    case 1: return bwd_dispatch<1>(g, vs, records, tiles_touched, g2d, d_means, d_scales, d_quats, d_opacities, d_sh, vec, st);
+    case 2: return bwd_dispatch<2>(g, vs, records, tiles_touched, g2d, d_means, d_scales, d_quats, d_opacities, d_sh, vec, st);
+    default: return bwd_dispatch<3>(g, vs, records, tiles_touched, g2d, d_means, d_scales, d_quats, d_opacities, d_sh, vec, st);
+  }
+}
+
+}  // namespace fgs

@@ -1,0 +1,229 @@
+"""Thin Python binding of the C ABI in include/fgs.h (libfgs.so, sm_103a).
+
+Argument marshalling only: every function here passes device pointers and sizes to the
+library function of the same name and turns a non-OK status into an exception. Device memory
+comes from torch; streams are torch's current stream unless given. There is no fallback: if the
+library is not built the first call raises.
+"""
+import ctypes
+import os
+
+import torch
+
+from .build import LIB_PATH
+
+RECORD_BYTES = 48
+TILE = 16
+MAX_VIEWS = 128
+
+FGS_OK = 0
+FGS_ERR_INVALID_ARG = 1
+FGS_ERR_CAPACITY = 2
+FGS_ERR_TIMEOUT = 3
+FGS_ERR_CUDA = 4
+
+EXPORTS = ["fgs_workspace_size", "fgs_total_tiles", "fgs_total_pixels", "fgs_preprocess",
+           "fgs_bin_sort", "fgs_rasterize", "fgs_backward", "fgs_backward_raster",
+           "fgs_backward_preprocess", "fgs_read_status",
+           "fgs_set_instrumentation", "fgs_read_counters", "fgs_status_string"]
+
+
+class FgsCamera(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_float * 9), ("b", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class FgsGaussians(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("scales", ctypes.c_void_p),
+                ("quats", ctypes.c_void_p), ("opacities", ctypes.c_void_p),
+                ("sh", ctypes.c_void_p), ("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32)]
+
+
+class FgsError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+_lib = None
+
+
+def lib():
+    """Load libfgs.so (built by __graft_entry__.build() / paper_2409_04751_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing; "
+                               "run `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        cam_p, g_p = ctypes.POINTER(FgsCamera), ctypes.POINTER(FgsGaussians)
+        L.fgs_workspace_size.argtypes = [i64, cam_p, i32, i64, ctypes.POINTER(ctypes.c_size_t)]
+        L.fgs_total_tiles.argtypes = [cam_p, i32]
+        L.fgs_total_tiles.restype = i64
+        L.fgs_total_pixels.argtypes = [cam_p, i32]
+        L.fgs_total_pixels.restype = i64
+        L.fgs_preprocess.argtypes = [g_p, cam_p, i32, vp, vp, vp]
+        L.fgs_bin_sort.argtypes = [vp, vp, i64, cam_p, i32, vp, vp, i64, vp, vp, vp,
+                                   ctypes.c_size_t, vp]
+        L.fgs_rasterize.argtypes = [vp, vp, vp, cam_p, i32, vp, vp, vp, vp, vp,
+                                    ctypes.c_size_t, vp]
+        L.fgs_backward.argtypes = [g_p, cam_p, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                   vp, vp, vp, ctypes.c_size_t, vp]
+        L.fgs_backward_raster.argtypes = [vp, vp, vp, i64, cam_p, i32, vp, vp, vp, vp, vp,
+                                          ctypes.c_size_t, vp]
+        L.fgs_backward_preprocess.argtypes = [g_p, cam_p, i32, vp, vp, vp, vp, vp, vp, vp, vp,
+                                              ctypes.c_size_t, vp]
+        L.fgs_read_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int)]
+        L.fgs_set_instrumentation.argtypes = [ctypes.c_int]
+        L.fgs_set_instrumentation.restype = None
+        L.fgs_read_counters.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.fgs_status_string.argtypes = [ctypes.c_int]
+        L.fgs_status_string.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name not in ("fgs_total_tiles", "fgs_total_pixels", "fgs_status_string",
+                            "fgs_set_instrumentation"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().fgs_status_string(int(status)).decode()
+
+
+def _check(status, where):
+    if status != FGS_OK:
+        raise FgsError(status, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def cameras(cams):
+    """ctypes array of FgsCamera from camera dicts (W, b, fx, fy, cx, cy, width, height)."""
+    arr = (FgsCamera * len(cams))()
+    for k, c in enumerate(cams):
+        W = [float(v) for v in torch.as_tensor(c["W"]).reshape(9).tolist()]
+        b = [float(v) for v in torch.as_tensor(c["b"]).reshape(3).tolist()]
+        arr[k].W[:] = W
+        arr[k].b[:] = b
+        arr[k].fx, arr[k].fy = float(c["fx"]), float(c["fy"])
+        arr[k].cx, arr[k].cy = float(c["cx"]), float(c["cy"])
+        arr[k].width, arr[k].height = int(c["width"]), int(c["height"])
+    return arr
+
+
+def gaussians(means, scales, quats, opacities, sh, sh_degree):
+    """FgsGaussians over contiguous FP32 device tensors (kept alive by the caller)."""
+    n = int(means.shape[0])
+    for t in (means, scales, quats, opacities, sh):
+        assert t.dtype == torch.float32 and t.is_contiguous(), "FP32 contiguous tensors expected"
+    return FgsGaussians(_ptr(means), _ptr(scales), _ptr(quats), _ptr(opacities), _ptr(sh), n,
+                        int(sh_degree))
+
+
+def fgs_workspace_size(n, cams, capacity) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().fgs_workspace_size(int(n), cams, len(cams), int(capacity), ctypes.byref(out)),
+           "fgs_workspace_size")
+    return int(out.value)
+
+
+def fgs_total_tiles(cams) -> int:
+    return int(lib().fgs_total_tiles(cams, len(cams)))
+
+
+def fgs_total_pixels(cams) -> int:
+    return int(lib().fgs_total_pixels(cams, len(cams)))
+
+
+def fgs_preprocess(g, cams, records, tiles_touched, stream=None):
+    _check(lib().fgs_preprocess(ctypes.byref(g), cams, len(cams), _ptr(records),
+                                _ptr(tiles_touched), _stream(stream)), "fgs_preprocess")
+
+
+def fgs_bin_sort(records, tiles_touched, n, cams, keys, vals, capacity, tile_ranges,
+                 n_intersections, workspace, workspace_bytes, stream=None):
+    _check(lib().fgs_bin_sort(_ptr(records), _ptr(tiles_touched), int(n), cams, len(cams),
+                              _ptr(keys), _ptr(vals), int(capacity), _ptr(tile_ranges),
+                              _ptr(n_intersections), _ptr(workspace), int(workspace_bytes),
+                              _stream(stream)), "fgs_bin_sort")
+
+
+def _bg_arg(bg):
+    if bg is None:
+        return None, None
+    arr = (ctypes.c_float * 3)(*[float(v) for v in bg])
+    return ctypes.cast(arr, ctypes.c_void_p).value, arr
+
+
+def fgs_rasterize(records, vals, tile_ranges, cams, bg, images, final_T, n_processed,
+                  workspace, workspace_bytes, stream=None):
+    bgp, keep = _bg_arg(bg)
+    _check(lib().fgs_rasterize(_ptr(records), _ptr(vals), _ptr(tile_ranges), cams, len(cams),
+                               bgp, _ptr(images), _ptr(final_T), _ptr(n_processed),
+                               _ptr(workspace), int(workspace_bytes), _stream(stream)),
+           "fgs_rasterize")
+    del keep
+
+
+def fgs_backward(g, cams, records, tiles_touched, vals, tile_ranges, bg, final_T, n_processed,
+                 dL_dimages, d_means, d_scales, d_quats, d_opacities, d_sh, workspace,
+                 workspace_bytes, stream=None):
+    bgp, keep = _bg_arg(bg)
+    _check(lib().fgs_backward(ctypes.byref(g), cams, len(cams), _ptr(records),
+                              _ptr(tiles_touched), _ptr(vals), _ptr(tile_ranges), bgp,
+                              _ptr(final_T), _ptr(n_processed), _ptr(dL_dimages),
+                              _ptr(d_means), _ptr(d_scales), _ptr(d_quats), _ptr(d_opacities),
+                              _ptr(d_sh), _ptr(workspace), int(workspace_bytes),
+                              _stream(stream)), "fgs_backward")
+    del keep
+
+
+def fgs_backward_raster(records, vals, tile_ranges, n, cams, bg, final_T, n_processed,
+                        dL_dimages, workspace, workspace_bytes, stream=None):
+    bgp, keep = _bg_arg(bg)
+    _check(lib().fgs_backward_raster(_ptr(records), _ptr(vals), _ptr(tile_ranges), int(n), cams,
+                                     len(cams), bgp, _ptr(final_T), _ptr(n_processed),
+                                     _ptr(dL_dimages), _ptr(workspace), int(workspace_bytes),
+                                     _stream(stream)), "fgs_backward_raster")
+    del keep
+
+
+def fgs_backward_preprocess(g, cams, records, tiles_touched, d_means, d_scales, d_quats,
+                            d_opacities, d_sh, workspace, workspace_bytes, stream=None):
+    _check(lib().fgs_backward_preprocess(ctypes.byref(g), cams, len(cams), _ptr(records),
+                                         _ptr(tiles_touched), _ptr(d_means), _ptr(d_scales),
+                                         _ptr(d_quats), _ptr(d_opacities), _ptr(d_sh),
+                                         _ptr(workspace), int(workspace_bytes), _stream(stream)),
+           "fgs_backward_preprocess")
+
+
+def fgs_read_status(workspace, stream=None) -> int:
+    out = ctypes.c_int(0)
+    _check(lib().fgs_read_status(_ptr(workspace), _stream(stream), ctypes.byref(out)),
+           "fgs_read_status")
+    return int(out.value)
+
+
+def fgs_set_instrumentation(on: bool):
+    lib().fgs_set_instrumentation(1 if on else 0)
+
+
+def fgs_read_counters(workspace, stream=None):
+    out = (ctypes.c_uint64 * 4)()
+    _check(lib().fgs_read_counters(_ptr(workspace), _stream(stream), out), "fgs_read_counters")
+    return [int(v) for v in out]

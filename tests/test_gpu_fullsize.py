@@ -1,0 +1,91 @@
+"""Parity at the full benchmark workload (500k Gaussians, SH degree 3, one 1752x1168 view at
+180 degrees, random pose), in the launch configuration the benchmark times: sampled pixels
+rendered one by one by the oracle, the gradient of the loss restricted to those pixels, and
+properties of the sorted keys that hold at any size."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2409_04751_gb300 import scenes
+from paper_2409_04751_gb300.renderer import FisheyeRenderer, scene_to_device
+from tests import parity
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    scene, cams = scenes.config1()
+    dev = torch.device("cuda:0")
+    gs = scene_to_device(scene, dev)
+    r = FisheyeRenderer(dev, capacity=24_000_000)
+    fr = r.forward(gs, cams)
+    G = oracle.project(scene, cams[0])
+    return scene, cams, gs, r, fr, G
+
+
+def test_config1_sampled_pixels(cfg1):
+    scene, cams, gs, r, fr, G = cfg1
+    cam = cams[0]
+    w, h = cam["width"], cam["height"]
+    rng = np.random.default_rng(123)
+    pix = np.stack([rng.integers(0, w, 3000), rng.integers(0, h, 3000)], 1).astype(np.int32)
+    ref = oracle.render(G, pix, impact_min=parity.IMPACT_MIN)
+    img = fr.view_images(cams)[0].cpu().numpy()
+    got = img[:, pix[:, 1], pix[:, 0]].T
+    d = np.abs(got - ref["color"])
+    fl = parity.flagged(ref["margins"])
+    assert fl.mean() < 0.08, (fl.mean(), d[~fl].max(), d.mean(0))
+    assert d[~fl].max() <= parity.IMG_MAX
+    assert np.all(d.mean(0) <= parity.IMG_MEAN)
+
+
+def test_config1_keys_properties(cfg1):
+    """Sorted keys are non-decreasing, each tile's range holds exactly its keys, and the
+    (key, value) multiset is the one the records define (count per record = rect area, tile
+    ids inside the rect, low word = the record's depth bits)."""
+    scene, cams, gs, r, fr, G = cfg1
+    n = scene["means"].shape[0]
+    m = int(fr.n_intersections.item())
+    keys = parity.u64(fr.keys)[:m]
+    vals = parity.u32(fr.vals)[:m]
+    assert m > 5_000_000
+    assert np.all(keys[1:] >= keys[:-1])
+    same = keys[1:] == keys[:-1]
+    assert np.all(vals[1:][same] > vals[:-1][same])  # stable: equal keys in record order
+    rec = parity.records_np(fr.records, n)
+    tt = fr.tiles_touched.cpu().numpy().astype(np.int64)
+    assert np.array_equal(np.bincount(vals, minlength=n), tt)
+    assert np.array_equal((keys & np.uint64(0xFFFFFFFF)).astype(np.uint32), rec["depth_bits"][vals])
+    tile = (keys >> np.uint64(32)).astype(np.int64)
+    tx, ty = tile % 110, tile // 110
+    rc = rec["rect"][vals]
+    assert np.all((tx >= rc[:, 0]) & (tx <= rc[:, 2]) & (ty >= rc[:, 1]) & (ty <= rc[:, 3]))
+    ranges = parity.u32(fr.tile_ranges).reshape(-1, 2).astype(np.int64)
+    cnt = np.bincount(tile, minlength=ranges.shape[0])
+    assert np.array_equal(ranges[:, 1] - ranges[:, 0], cnt)
+    # GPU rects against the oracle's FP64 rects, except rounding-near boundaries
+    F = oracle.F
+    vis = G[:, F["vis"]] > 0
+    near = G[:, F["rmargin"]] < 1e-4
+    ok = vis & (tt > 0) & ~near
+    assert np.array_equal(rec["rect"][ok], G[ok][:, F["rect"]:F["rect"] + 4].astype(np.int32))
+    assert np.array_equal(vis[~near], (tt > 0)[~near])
+
+
+def test_config1_sampled_gradient(cfg1):
+    """dL/dimage nonzero only on sampled pixels: every gradient tensor against the oracle's
+    gradient of the same restricted loss."""
+    scene, cams, gs, r, fr, G = cfg1
+    cam = cams[0]
+    w, h = cam["width"], cam["height"]
+    rng = np.random.default_rng(321)
+    idx = rng.choice(w * h, 1500, replace=False)
+    pix = np.stack([idx % w, idx // w], 1).astype(np.int32)
+    gvals = rng.normal(0, 1e-2, (1500, 3))
+    dL = np.zeros((3, h * w), np.float32)
+    dL[:, idx] = gvals.T.astype(np.float32)
+    ref = oracle.backward(G, scene, cam, pix, dL[:, idx].T.astype(np.float64))
+    g = r.backward(gs, fr, torch.as_tensor(dL.reshape(-1)).cuda())
+    parity.check_grads(g, ref, "config1 sampled")

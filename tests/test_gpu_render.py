@@ -1,0 +1,197 @@
+"""GPU forward (fgs_preprocess -> fgs_bin_sort -> fgs_rasterize) and backward (fgs_backward)
+against the FP64 oracle on seeded synthetic scenes small enough for the oracle to render every
+pixel in seconds: per-record projection, whole images, and every gradient."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2409_04751_gb300 import scenes
+from paper_2409_04751_gb300.renderer import FisheyeRenderer, scene_to_device
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+def _render(scene, cams, bg=None, capacity=1 << 16):
+    dev = torch.device("cuda:0")
+    gs = scene_to_device(scene, dev)
+    r = FisheyeRenderer(dev, capacity=capacity)
+    fr = r.forward(gs, cams, bg=bg)
+    return r, gs, fr
+
+
+def _mid_scene(seed=11, n=20_000):
+    return scenes.shell_scene(n, seed=seed, sh_degree=3)
+
+
+def test_preprocess_matches_oracle(cuda_device):
+    scene = _mid_scene()
+    cam = scenes.pose_camera(640, 480, 190.0, seed=12)
+    r, gs, fr = _render(scene, [cam])
+    n = scene["means"].shape[0]
+    rec = parity.records_np(fr.records, n)
+    tt = fr.tiles_touched.cpu().numpy()
+    G = oracle.project(scene, cam)
+    F = oracle.F
+    vis_o = G[:, F["vis"]] > 0
+    vis_g = tt > 0
+    # decisions on the rect / culling within rounding of their threshold may differ
+    near = G[:, F["rmargin"]] < 1e-4
+    assert np.array_equal(vis_o[~near], vis_g[~near])
+    both = vis_o & vis_g
+    xy = G[both][:, F["xy"]:F["xy"] + 2]
+    assert np.abs(rec["xy"][both] - xy).max() < 2e-3
+    con = G[both][:, F["conic"]:F["conic"] + 3]
+    scale = np.abs(con).max(1)
+    # FP32 inversion of Sigma_p loses about cond(Sigma_p) ulps
+    a, b, c = (G[both][:, F["cov"] + k] for k in range(3))
+    tr, det = a + c, a * c - b * b
+    disc = np.sqrt(np.maximum(tr * tr - 4 * det, 0))
+    cond = (tr + disc) / (tr - disc)
+    err = np.abs(rec["conic"][both] - con).max(1) / scale
+    assert np.all(err <= 1e-6 * cond + 1e-5), (err / (1e-6 * cond + 1e-5)).max()
+    assert np.array_equal(rec["opacity"][both], scene["opacities"][both])
+    assert np.abs(rec["rgb"][both] - G[both][:, F["rgb"]:F["rgb"] + 3]).max() < 2e-5
+    assert (np.abs(rec["depth"][both] - G[both][:, F["depth"]]) / G[both][:, F["depth"]]).max() < 2e-6
+    ok = both & ~near
+    assert np.array_equal(rec["rect"][ok], G[ok][:, F["rect"]:F["rect"] + 4].astype(np.int32))
+    area = (rec["rect"][:, 2] - rec["rect"][:, 0] + 1) * (rec["rect"][:, 3] - rec["rect"][:, 1] + 1)
+    assert np.array_equal(tt[vis_g], area[vis_g])
+    assert int(fr.n_intersections.item()) == int(tt.astype(np.int64).sum())
+
+
+def test_config0_image_matches_oracle(cuda_device):
+    scene, cams = scenes.config0()
+    r, gs, fr = _render(scene, cams)
+    img = fr.view_images(cams)[0].cpu().numpy()
+    ref = oracle.render_image(oracle.project(scene, cams[0]), cams[0], impact_min=parity.IMPACT_MIN)
+    st = parity.check_image(img, ref, "config0")
+    assert st["flagged"] < 0.02 * st["pixels"]
+    # the stop and contributor bookkeeping: final T and the last blended Gaussian
+    T = fr.final_T.cpu().numpy().reshape(256, 256)
+    ok = ~parity.flagged(ref["margins"])
+    assert np.abs(T - ref["T_final"])[ok].max() < 1e-4
+    nproc = parity.u32(fr.n_processed).reshape(256, 256)
+    vals = parity.u32(fr.vals)
+    ranges = parity.u32(fr.tile_ranges).reshape(-1, 2)
+    jj, ii = np.nonzero(nproc > 0)
+    tile = (jj // 16) * 16 + ii // 16
+    last_g = vals[ranges[tile, 0] + nproc[jj, ii] - 1]
+    assert np.array_equal(last_g[ok[jj, ii]], ref["last_g"][jj, ii][ok[jj, ii]])
+    assert np.all(ref["last_g"][ok & (nproc == 0)] == -1)
+
+
+@pytest.mark.parametrize("w,h,fov,deg,seed,bg", [
+    (320, 224, 180.0, 3, 21, (0.0, 0.0, 0.0)),
+    (333, 201, 200.0, 1, 22, (0.25, 0.5, 0.75)),   # ragged tiles, behind-camera Gaussians
+    (200, 200, 150.0, 2, 23, (1.0, 1.0, 1.0)),
+])
+def test_images_match_oracle(cuda_device, w, h, fov, deg, seed, bg):
+    scene = scenes.shell_scene(30_000, seed=seed, sh_degree=deg)
+    cam = scenes.pose_camera(w, h, fov, seed=seed + 100)
+    r, gs, fr = _render(scene, [cam], bg=bg)
+    img = fr.view_images([cam])[0].cpu().numpy()
+    ref = oracle.render_image(oracle.project(scene, cam), cam, bg=bg, impact_min=parity.IMPACT_MIN)
+    parity.check_image(img, ref, f"{w}x{h}@{fov}")
+
+
+def test_dense_scene_exercises_stop(cuda_device):
+    """Many large opaque Gaussians: most pixels reach the 1e-4 stop."""
+    scene = scenes.shell_scene(20_000, seed=31, log_scale=(-1.8, 0.3), sh_degree=0)
+    scene["opacities"] = np.full_like(scene["opacities"], 0.97)
+    cam = scenes.fisheye_camera(160, 128, 180.0)
+    r, gs, fr = _render(scene, [cam], capacity=1 << 20)
+    ref = oracle.render_image(oracle.project(scene, cam), cam, impact_min=parity.IMPACT_MIN)
+    assert (ref["T_final"] < 1e-3).mean() > 0.5
+    parity.check_image(fr.view_images([cam])[0].cpu().numpy(), ref, "dense")
+
+
+def test_empty_and_culled(cuda_device):
+    cam = scenes.fisheye_camera(48, 40, 180.0)
+    bg = (0.1, 0.2, 0.3)
+    empty = dict(means=np.zeros((0, 3)), scales=np.zeros((0, 3)), quats=np.zeros((0, 4)),
+                 opacities=np.zeros(0), sh=np.zeros((0, 1, 3)), sh_degree=0)
+    # near, on the singular cone, inside the cone, below the opacity cut, and visible but
+    # projected 45 px outside the image (theta = 170 deg)
+    culled = dict(means=np.array([[0, 0, 0.1], [0, 0, -3.0], [0.01, 0, -2.0], [0, 0, 2.0],
+                                  [0.5, 0, -3.0]]),
+                  scales=np.full((5, 3), 0.1), quats=np.tile([1.0, 0, 0, 0], (5, 1)),
+                  opacities=np.array([0.9, 0.9, 0.9, 1.0 / 256, 0.9]), sh=np.zeros((5, 1, 3)),
+                  sh_degree=0)
+    for sc in (empty, culled):
+        r, gs, fr = _render(sc, [cam], bg=bg)
+        img = fr.view_images([cam])[0].cpu().numpy()
+        for ch in range(3):
+            assert np.all(img[ch] == np.float32(bg[ch]))
+        assert np.all(fr.final_T.cpu().numpy() == 1.0)
+        assert int(fr.n_intersections.item()) == 0
+        if sc["means"].shape[0]:
+            g = r.backward(gs, fr, torch.ones(3 * 48 * 40, device="cuda"))
+            for k in g:
+                assert torch.all(g[k] == 0)
+
+
+def test_multiview_call_equals_single_view_calls(cuda_device):
+    """One call over several views of uneven size gives each view's image bit for bit."""
+    scene = scenes.shell_scene(15_000, seed=41, sh_degree=3)
+    cams = [scenes.pose_camera(w, h, f, seed=410 + k)
+            for k, (w, h, f) in enumerate([(128, 96, 180.0), (200, 200, 150.0), (64, 300, 200.0),
+                                           (96, 96, 190.0)])]
+    r, gs, fr = _render(scene, cams, capacity=1 << 20)
+    multi = [x.cpu().numpy().copy() for x in fr.view_images(cams)]
+    for k, c in enumerate(cams):
+        r1, gs1, f1 = _render(scene, [c])
+        assert np.array_equal(f1.view_images([c])[0].cpu().numpy(), multi[k])
+
+
+def _grad_case(scene, cams, seed, bg=None, mask=None):
+    dev = torch.device("cuda:0")
+    r, gs, fr = _render(scene, cams, bg=bg, capacity=1 << 20)
+    P = sum(c["width"] * c["height"] for c in cams)
+    dL = scenes.upstream_grad((3 * P,), 1.0, seed)
+    g = r.backward(gs, fr, torch.as_tensor(dL).to(dev))
+    ref = None
+    off = 0
+    for c in cams:
+        w, h = c["width"], c["height"]
+        dv = dL[3 * off:3 * (off + w * h)].reshape(3, h * w).T
+        G = oracle.project(scene, c)
+        rv = oracle.backward(G, scene, c, oracle.all_pixels(c), dv, bg or (0, 0, 0))
+        ref = rv if ref is None else {k: ref[k] + rv[k] for k in ref}
+        off += w * h
+    return g, ref
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2, 3])
+def test_gradients_match_oracle(cuda_device, deg):
+    scene = scenes.shell_scene(6000, seed=50 + deg, sh_degree=deg)
+    scene["quats"] = scene["quats"] * np.float32(1.7)  # non-unit quaternions
+    cam = scenes.pose_camera(160, 120, 190.0, seed=500 + deg)
+    g, ref = _grad_case(scene, [cam], seed=5 + deg, bg=(0.2, 0.3, 0.4))
+    parity.check_grads(g, ref, f"deg {deg}")
+
+
+def test_gradients_multiview_sum(cuda_device):
+    scene = scenes.shell_scene(5000, seed=60, sh_degree=3)
+    cams = [scenes.pose_camera(w, h, 180.0, seed=600 + k) for k, (w, h) in enumerate([(96, 80), (128, 64), (50, 70)])]
+    g, ref = _grad_case(scene, cams, seed=61)
+    parity.check_grads(g, ref, "multiview")
+
+
+def test_gradients_near_axis_series_region(cuda_device):
+    """Gaussians within t = l_z / z < 0.3 of the optical axis (the near-axis series of h and
+    dh/dl_z) and on it."""
+    rng = np.random.default_rng(70)
+    n = 400
+    z = rng.uniform(1.0, 3.0, n)
+    t = np.concatenate([rng.uniform(0, 0.3, n - 4), [0.0, 1e-7, 0.299, 0.301]])
+    a = rng.uniform(0, 2 * math.pi, n)
+    means = np.stack([t * z * np.cos(a), t * z * np.sin(a), z], 1).astype(np.float32)
+    scene = scenes.shell_scene(n, seed=71, sh_degree=1)
+    scene["means"] = means
+    cam = scenes.fisheye_camera(128, 128, 180.0)
+    g, ref = _grad_case(scene, [cam], seed=72)
+    parity.check_grads(g, ref, "near-axis")
