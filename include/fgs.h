@@ -155,6 +155,27 @@ fgs_status fgs_backward(const fgs_gaussians *g, const fgs_camera *cams, int n_vi
                         float *d_quats, float *d_opacities, float *d_sh, void *workspace,
                         size_t workspace_bytes, fgs_stream stream);
 
+/* fgs_bin_sort for callers that cannot allocate device memory (the paper has no counterpart:
+ * this is a deployment variant). Plugins running inside a host application that owns the GPU
+ * memory budget, and real-time loops that must never call cudaMalloc / cudaFree (which can
+ * synchronise the device), have no workspace to pass; this entry point keeps the sort's scratch
+ * in a fixed array inside the library instead, and the caller passes only inputs and outputs.
+ * Results are the same as fgs_bin_sort's for the same inputs.
+ *  - Limits: n_views * n <= 2^20 records and capacity <= 2^19 key slots; larger sizes return
+ *    FGS_ERR_INVALID_ARG before anything is launched. Every GPU that loads the library holds
+ *    the array (about 6.8 MB) until the process exits.
+ *  - status: DEVICE pointer to one uint32 the call fills, in stream order, with the device
+ *    status word (FGS_OK, FGS_ERR_CAPACITY or FGS_ERR_TIMEOUT) once the sort has run.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ *    make that first call before any stream capture on that device.
+ *  - All calls share the one array and leave their contents in it (each call clears what must
+ *    start at zero): calls whose work overlaps on the GPU race; calls ordered on one stream
+ *    are safe. */
+fgs_status fgs_bin_sort_noalloc(const fgs_record *records, const uint32_t *tiles_touched,
+                                int64_t n, const fgs_camera *cams, int n_views, uint64_t *keys,
+                                uint32_t *vals, int64_t capacity, uint32_t *tile_ranges,
+                                int64_t *n_intersections, uint32_t *status, fgs_stream stream);
+
 /* The two halves of fgs_backward, for callers that time or reuse them separately:
  * fgs_backward_raster replays the blend and accumulates per-record screen-space gradients
  * (dL/d xy, dL/d conic, dL/d opacity, dL/d rgb) into the workspace; fgs_backward_preprocess

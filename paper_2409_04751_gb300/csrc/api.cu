@@ -23,8 +23,6 @@ int sm_count() {
 static int g_instrument = 0;
 bool instrumented() { return g_instrument != 0; }
 
-namespace {
-
 // Largest tile grid accepted per view: a view's tile count must fit 20 bits so that a
 // record's tile count and a 1024-record partition's sum stay well inside 32 bits.
 constexpr int64_t MAX_TILES_PER_VIEW = 1 << 20;
@@ -61,6 +59,8 @@ bool build_views(const fgs_camera *cams, int n_views, Views *vs) {
   vs->tile_bits = bits;
   return true;
 }
+
+namespace {
 
 bool gauss_ok(const fgs_gaussians *g) {
   if (g == nullptr || g->n < 0 || g->n > 0xffffffffLL || g->sh_degree < 0 || g->sh_degree > 3)

@@ -345,6 +345,8 @@ struct GaussPtrs {
 
 int sm_count();
 bool instrumented();
+// Per-view parameter table from the caller's cameras; false if any camera is invalid.
+bool build_views(const fgs_camera *cams, int n_views, Views *vs);
 
 cudaError_t launch_preprocess_fwd(const GaussPtrs &g, const Views &vs, fgs_record *records,
                                   uint32_t *tiles_touched, cudaStream_t st);

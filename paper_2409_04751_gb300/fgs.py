@@ -24,7 +24,7 @@ FGS_ERR_CUDA = 4
 
 EXPORTS = ["fgs_workspace_size", "fgs_total_tiles", "fgs_total_pixels", "fgs_preprocess",
            "fgs_bin_sort", "fgs_rasterize", "fgs_backward", "fgs_backward_raster",
-           "fgs_backward_preprocess", "fgs_read_status",
+           "fgs_backward_preprocess", "fgs_bin_sort_noalloc", "fgs_read_status",
            "fgs_set_instrumentation", "fgs_read_counters", "fgs_status_string"]
 
 
@@ -75,6 +75,7 @@ def lib():
                                           ctypes.c_size_t, vp]
         L.fgs_backward_preprocess.argtypes = [g_p, cam_p, i32, vp, vp, vp, vp, vp, vp, vp, vp,
                                               ctypes.c_size_t, vp]
+        L.fgs_bin_sort_noalloc.argtypes = [vp, vp, i64, cam_p, i32, vp, vp, i64, vp, vp, vp, vp]
         L.fgs_read_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int)]
         L.fgs_set_instrumentation.argtypes = [ctypes.c_int]
         L.fgs_set_instrumentation.restype = None
@@ -210,6 +211,16 @@ def fgs_backward_preprocess(g, cams, records, tiles_touched, d_means, d_scales, 
                                          _ptr(d_quats), _ptr(d_opacities), _ptr(d_sh),
                                          _ptr(workspace), int(workspace_bytes), _stream(stream)),
            "fgs_backward_preprocess")
+
+
+def fgs_bin_sort_noalloc(records, tiles_touched, n, cams, keys, vals, capacity, tile_ranges,
+                         n_intersections, status, stream=None):
+    """fgs_bin_sort without a workspace (fixed scratch inside the library); `status` is a
+    device uint32 buffer that receives the device status word."""
+    _check(lib().fgs_bin_sort_noalloc(_ptr(records), _ptr(tiles_touched), int(n), cams,
+                                      len(cams), _ptr(keys), _ptr(vals), int(capacity),
+                                      _ptr(tile_ranges), _ptr(n_intersections), _ptr(status),
+                                      _stream(stream)), "fgs_bin_sort_noalloc")
 
 
 def fgs_read_status(workspace, stream=None) -> int:
