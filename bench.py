@@ -268,6 +268,18 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # work shape of the rasterizers, chosen by the autotuner on this workload (untimed)
+    shape = {"fwd": 2, "bwd": 2}
+    if args.raster_shape:
+        f, b = (int(x) for x in args.raster_shape.split(","))
+        shape = {"fwd": f, "bwd": b}
+        fgs.fgs_set_raster_shape(f, b)
+    elif not args.no_tune:
+        from paper_2409_04751_gb300.autotune import tune_raster
+        shape = tune_raster(r, gs, fr, dL, use_cache=False)
+    else:
+        fgs.fgs_set_raster_shape(2, 2)
+
     # instrumented pass (untimed): algorithmic work of the rasterizer
     fgs.fgs_set_instrumentation(True)
     stages([torch.cuda.Event(enable_timing=True) for _ in range(6)])
@@ -405,10 +417,12 @@ def run_gpu(args):
         scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
         config=dict(workload=WORKLOAD, n_gaussians=n, width=1752, height=1168, fov_deg=180.0,
                     sh_degree=3, l2="flushed between steps (256 MiB write, untimed)",
-                    parallelism=f"views x{world} (replicas)"),
+                    parallelism=f"views x{world} (replicas)",
+                    raster_pixels_per_thread=dict(fwd=shape["fwd"], bwd=shape["bwd"])),
         fwd_views_per_s=world * args.steps / fwd_s,
         mpix_per_s_fwd_bwd=value * P / 1e6,
         stage_ms=dict(zip(names, [round(float(x), 4) for x in stage_ms])),
+        tuning_ms={k: round(v, 4) for k, v in shape.get("ms", {}).items()},
         intersections=m, visible=vis, pair_counters=counters,
         roofline=roof, kernels=kern,
         cpu_baseline=cpu,
@@ -431,6 +445,9 @@ def main():
     ap.add_argument("--impl", default="fgs", choices=["fgs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--raster-shape", default="",
+                    help="pixels per thread 'fwd,bwd' (1, 2 or 4); skips the autotuner")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

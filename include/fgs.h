@@ -161,9 +161,9 @@ fgs_status fgs_backward(const fgs_gaussians *g, const fgs_camera *cams, int n_vi
  * synchronise the device), have no workspace to pass; this entry point keeps the sort's scratch
  * in a fixed array inside the library instead, and the caller passes only inputs and outputs.
  * Results are the same as fgs_bin_sort's for the same inputs.
- *  - Limits: n_views * n <= 2^20 records and capacity <= 2^19 key slots; larger sizes return
+ *  - Limits: n_views * n <= 2^19 records and capacity <= 2^19 key slots; larger sizes return
  *    FGS_ERR_INVALID_ARG before anything is launched. Every GPU that loads the library holds
- *    the array (about 6.8 MB) until the process exits.
+ *    the array (about 13 MB) until the process exits.
  *  - status: DEVICE pointer to one uint32 the call fills, in stream order, with the device
  *    status word (FGS_OK, FGS_ERR_CAPACITY or FGS_ERR_TIMEOUT) once the sort has run.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
@@ -205,6 +205,13 @@ fgs_status fgs_read_status(const void *workspace, fgs_stream stream, int *status
  * counters to host memory. */
 void fgs_set_instrumentation(int on);
 fgs_status fgs_read_counters(const void *workspace, fgs_stream stream, uint64_t *counters);
+
+/* Work shape of the rasterizers (process wide): pixels per thread of the forward and the
+ * backward kernels, each 1, 2 or 4 (a 16x16 tile runs on 256 / that many threads). Images,
+ * final transmittances and processed counts do not depend on it, bit for bit; gradients only
+ * through the order of their floating-point sums. It trades parallelism against per-thread
+ * reuse, so a tuner may pick whichever is fastest. Default 2 and 2. */
+fgs_status fgs_set_raster_shape(int fwd_pixels_per_thread, int bwd_pixels_per_thread);
 
 /* Static description of a status code. */
 const char *fgs_status_string(int status);

@@ -23,6 +23,11 @@ int sm_count() {
 static int g_instrument = 0;
 bool instrumented() { return g_instrument != 0; }
 
+// Pixels per thread of the forward [0] and backward [1] rasterizers (1, 2 or 4). Any value
+// gives the same image and gradients; it only changes the work shape.
+static int g_raster_shape[2] = {2, 2};
+int raster_shape(int which) { return g_raster_shape[which & 1]; }
+
 // Largest tile grid accepted per view: a view's tile count must fit 20 bits so that a
 // record's tile count and a 1024-record partition's sum stay well inside 32 bits.
 constexpr int64_t MAX_TILES_PER_VIEW = 1 << 20;
@@ -235,6 +240,14 @@ fgs_status fgs_read_status(const void *workspace, fgs_stream stream, int *status
 }
 
 void fgs_set_instrumentation(int on) { g_instrument = on ? 1 : 0; }
+
+fgs_status fgs_set_raster_shape(int fwd_pixels_per_thread, int bwd_pixels_per_thread) {
+  auto ok = [](int v) { return v == 1 || v == 2 || v == 4; };
+  if (!ok(fwd_pixels_per_thread) || !ok(bwd_pixels_per_thread)) return FGS_ERR_INVALID_ARG;
+  g_raster_shape[0] = fwd_pixels_per_thread;
+  g_raster_shape[1] = bwd_pixels_per_thread;
+  return FGS_OK;
+}
 
 fgs_status fgs_read_counters(const void *workspace, fgs_stream stream, uint64_t *counters) {
   if (!workspace || !counters) return FGS_ERR_INVALID_ARG;

@@ -1,19 +1,22 @@
 // binsort.cu - tile binning and key sort (Sec. 3.1 "Rendering"; Sec. 4.1 duplicateWithKeys and
 // radixSort), sm_103a.
 //
-//  1. emit_kernel: single-pass scan of tiles_touched with decoupled look-back (partitions of
-//     1024 records claimed in order through an atomic counter), then CTA-cooperative key
-//     emission: the CTA's (record, tile) pairs are spread evenly over its threads by a binary
-//     search of the record offsets held in shared memory, so a Gaussian covering thousands of
-//     tiles does not stall one thread, and the writes are coalesced. The same pass counts the
-//     8-bit digit histograms of every radix pass (warp-aggregated shared atomics), so the sort
-//     needs no separate histogram read of the keys.
-//  2. onesweep_kernel (one launch per 8-bit digit): Adinets & Merrill's single-pass LSD radix
+//  1. scan_kernel: single-pass scan of tiles_touched with decoupled look-back (partitions of
+//     1024 records claimed in order through an atomic counter). For every record with pairs it
+//     writes its pair offset and its rank among such records (a compacted list), and for every
+//     2048-pair chunk the rank of the record holding the chunk's first pair.
+//  2. emit_kernel: one CTA per 2048-pair chunk, so the work per CTA is fixed however many
+//     tiles one Gaussian covers. The CTA loads the few records its chunk spans into shared
+//     memory; each pair finds its record by binary search there and writes
+//     key = tile << 32 | depth bits, value = record, coalesced. The same pass counts the 8-bit
+//     digit histograms of every radix pass (warp-aggregated shared atomics), so the sort needs
+//     no separate histogram read of the keys.
+//  3. onesweep_kernel (one launch per 8-bit digit): Adinets & Merrill's single-pass LSD radix
 //     sort: each partition of 4096 keys is ranked in shared memory (warp multi-split with
 //     match_any, stable), publishes its per-digit counts, resolves its global digit offsets by
 //     decoupled look-back over earlier partitions (bounded waits), and scatters through shared
 //     memory so that runs of equal digits are written contiguously.
-//  3. ranges_kernel: [start, end) of every tile in the sorted keys.
+//  4. ranges_kernel: [start, end) of every tile in the sorted keys.
 // The number of valid pairs is read on the device, so nothing here needs a host sync.
 #include "fgs_internal.cuh"
 
@@ -78,104 +81,138 @@ __device__ __forceinline__ uint64_t look_back(const uint64_t *lb, int64_t part, 
 }
 
 __global__ void __launch_bounds__(EMIT_THREADS)
-    emit_kernel(const fgs_record *__restrict__ rec, const uint32_t *__restrict__ tt, int64_t R,
-                int64_t n_per_view, Views vs, uint64_t *__restrict__ keys,
-                uint32_t *__restrict__ vals, int64_t capacity, int64_t *n_int, uint64_t *lb,
-                uint32_t *part_counter, uint32_t *hist, int passes, uint32_t *status) {
-  __shared__ uint32_t s_off[EMIT_PART + 1];
-  __shared__ uint2 s_rect[EMIT_PART];
-  __shared__ uint32_t s_depth[EMIT_PART];
-  __shared__ uint32_t s_hist[SORT_MAX_PASSES * 256];
+    scan_kernel(const uint32_t *__restrict__ tt, int64_t R, int64_t capacity, int64_t *n_int,
+                unsigned long long *n_vis, uint64_t *lb_pairs, uint64_t *lb_vis,
+                uint32_t *part_counter, uint32_t *__restrict__ vis_rec,
+                uint64_t *__restrict__ vis_off, uint32_t *__restrict__ chunk_first,
+                uint32_t *status) {
   __shared__ uint32_t s_warp[8];
-  __shared__ uint64_t s_prefix;
+  __shared__ uint64_t s_prefix[2];
   __shared__ uint32_t s_part;
-  __shared__ int s_overflow;
   const int tid = threadIdx.x;
-  if (tid == 0) {
-    s_part = atomicAdd(part_counter, 1u);
-    s_overflow = 0;
-  }
-  for (int e = tid; e < passes * 256; e += EMIT_THREADS) s_hist[e] = 0u;
+  if (tid == 0) s_part = atomicAdd(part_counter, 1u);
   __syncthreads();
   const int64_t part = s_part;
   const int64_t base = part * EMIT_PART;
 
   uint32_t c[EMIT_ITEMS];
-  uint32_t sum = 0;
+  uint32_t sum = 0, nv = 0;
 #pragma unroll
   for (int k = 0; k < EMIT_ITEMS; ++k) {
     const int64_t r = base + tid * EMIT_ITEMS + k;
     c[k] = r < R ? tt[r] : 0u;
     sum += c[k];
+    nv += c[k] > 0u ? 1u : 0u;
   }
-  uint32_t cta_total;
-  uint32_t off = block_excl_scan_256(sum, s_warp, &cta_total);
-  if (tid == 0) {
+  uint32_t cta_pairs, cta_vis;
+  uint32_t off = block_excl_scan_256(sum, s_warp, &cta_pairs);
+  uint32_t voff = block_excl_scan_256(nv, s_warp, &cta_vis);
+  // two look-backs at once: warp 0 for the pair offsets, warp 1 for the compacted ranks
+  if ((tid & 31) == 0 && tid < 64) {
+    uint64_t *lb = tid == 0 ? lb_pairs : lb_vis;
+    const uint64_t agg = tid == 0 ? cta_pairs : cta_vis;
     uint64_t prefix = 0;
     if (part == 0) {
-      st_volatile_u64(lb, LB_INC | (uint64_t)cta_total);
+      st_volatile_u64(lb, LB_INC | agg);
     } else {
-      st_volatile_u64(lb + part, LB_AGG | (uint64_t)cta_total);
+      st_volatile_u64(lb + part, LB_AGG | agg);
       prefix = look_back(lb, part, 1, status);
-      st_volatile_u64(lb + part, LB_INC | (prefix + cta_total));
+      st_volatile_u64(lb + part, LB_INC | (prefix + agg));
     }
-    s_prefix = prefix;
-    if (base + EMIT_PART >= R) *n_int = (int64_t)(prefix + cta_total);
+    s_prefix[tid == 0 ? 0 : 1] = prefix;
+    if (base + EMIT_PART >= R) {
+      if (tid == 0) *n_int = (int64_t)(prefix + agg);
+      else *n_vis = prefix + agg;
+    }
   }
+  __syncthreads();
+  const uint64_t pbase = s_prefix[0], vbase = s_prefix[1];
+  uint64_t o = pbase + off;
+  uint64_t v = vbase + voff;
 #pragma unroll
   for (int k = 0; k < EMIT_ITEMS; ++k) {
-    const int loc = tid * EMIT_ITEMS + k;
-    s_off[loc] = off;
     if (c[k] > 0u) {
-      const uint4 w2 = __ldg(reinterpret_cast<const uint4 *>(rec + base + loc) + 2);
-      s_rect[loc] = make_uint2(w2.z, w2.w);
-      s_depth[loc] = w2.y;
+      vis_rec[v] = (uint32_t)(base + tid * EMIT_ITEMS + k);
+      vis_off[v] = o;
+      // chunks whose first pair falls inside this record's pairs [o, o + c)
+      const uint64_t end = min(o + c[k], (uint64_t)capacity);
+      for (uint64_t ck = (o + EMIT_CHUNK - 1) / EMIT_CHUNK; ck * EMIT_CHUNK < end; ++ck)
+        chunk_first[ck] = (uint32_t)v;
+      ++v;
     }
-    off += c[k];
+    o += c[k];
   }
-  if (tid == 0) s_off[EMIT_PART] = cta_total;
-  __syncthreads();
-  const uint64_t prefix = s_prefix;
+}
 
-  bool overflow = false;
-  for (uint32_t jb = 0; jb < cta_total; jb += EMIT_THREADS) {
-    const uint32_t j = jb + tid;
-    bool valid = j < cta_total;
-    uint64_t key = 0;
-    if (valid) {
-      int lo = 0, hi = EMIT_PART;  // s_off[lo] <= j < s_off[hi]
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (s_off[mid] <= j) lo = mid; else hi = mid;
-      }
-      const uint32_t local = j - s_off[lo];
-      const uint2 rc = s_rect[lo];
-      const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
-      const uint32_t w = x1 - x0 + 1u;
-      const uint32_t dy = local / w;
-      const uint32_t tx = x0 + (local - dy * w), ty = y0 + dy;
-      const int64_t r = base + lo;
-      const int v = (int)(r / n_per_view);
-      const uint64_t tile = (uint64_t)(vs.v[v].tile_offset + (int64_t)ty * vs.v[v].tiles_x + tx);
-      key = (tile << 32) | (uint64_t)s_depth[lo];
-      const uint64_t gpos = prefix + j;
-      if (gpos < (uint64_t)capacity) {
-        keys[gpos] = key;
-        vals[gpos] = (uint32_t)r;
-      } else {
-        overflow = true;
-        valid = false;
-      }
+__global__ void __launch_bounds__(EMIT_THREADS)
+    emit_kernel(const fgs_record *__restrict__ rec, int64_t n_per_view, Views vs,
+                const uint32_t *__restrict__ vis_rec, const uint64_t *__restrict__ vis_off,
+                const uint32_t *__restrict__ chunk_first, const int64_t *n_int,
+                const unsigned long long *n_vis, uint64_t *__restrict__ keys,
+                uint32_t *__restrict__ vals, int64_t capacity, uint32_t *hist, int passes,
+                uint32_t *status) {
+  __shared__ uint64_t s_off[EMIT_CHUNK + 1];
+  __shared__ uint2 s_rect[EMIT_CHUNK + 1];
+  __shared__ uint32_t s_depth[EMIT_CHUNK + 1];
+  __shared__ uint32_t s_rec[EMIT_CHUNK + 1];
+  __shared__ uint32_t s_hist[SORT_MAX_PASSES * 256];
+  const int tid = threadIdx.x;
+  const int64_t total = *n_int;
+  if (tid == 0 && total > capacity) set_status(status, ST_CAPACITY);
+  const int64_t n = min(total, capacity);
+  const int64_t nchunks = (n + EMIT_CHUNK - 1) / EMIT_CHUNK;
+  const int64_t nv = (int64_t)*n_vis;
+  for (int e = tid; e < passes * 256; e += EMIT_THREADS) s_hist[e] = 0u;
+
+  for (int64_t ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
+    const int64_t lo = ck * EMIT_CHUNK;
+    const int64_t hi = min(lo + (int64_t)EMIT_CHUNK, n);
+    const int64_t v0 = chunk_first[ck];
+    const int64_t v1 = ck + 1 < nchunks ? (int64_t)chunk_first[ck + 1] : nv - 1;
+    // records spanned by the chunk: the owner of pair lo and at most EMIT_CHUNK more (the
+    // last chunk of a capacity-truncated emission may list more; they own no pair below hi)
+    const int nw = (int)min(v1 - v0 + 1, (int64_t)EMIT_CHUNK + 1);
+    __syncthreads();
+    for (int i = tid; i < nw; i += EMIT_THREADS) {
+      const uint32_t r = vis_rec[v0 + i];
+      const uint4 w2 = __ldg(reinterpret_cast<const uint4 *>(rec + r) + 2);
+      s_off[i] = vis_off[v0 + i];
+      s_rec[i] = r;
+      s_rect[i] = make_uint2(w2.z, w2.w);
+      s_depth[i] = w2.y;
     }
-    for (int p = 0; p < passes; ++p) {
-      const uint32_t d = valid ? (uint32_t)(key >> (8 * p)) & 255u : 0x100u + (threadIdx.x & 31);
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      if (valid && (peers & lanemask_lt()) == 0u) atomicAdd(&s_hist[p * 256 + d], __popc(peers));
+    __syncthreads();
+    for (int64_t jb = lo; jb < hi; jb += EMIT_THREADS) {
+      const int64_t j = jb + tid;
+      const bool valid = j < hi;
+      uint64_t key = 0;
+      if (valid) {
+        int a = 0, b = nw;  // s_off[a] <= j < s_off[b] (s_off[nw] taken as +inf)
+        while (b - a > 1) {
+          const int mid = (a + b) >> 1;
+          if (s_off[mid] <= (uint64_t)j) a = mid; else b = mid;
+        }
+        const uint32_t local = (uint32_t)((uint64_t)j - s_off[a]);
+        const uint2 rc = s_rect[a];
+        const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
+        const uint32_t w = x1 - x0 + 1u;
+        const uint32_t dy = local / w;
+        const uint32_t tx = x0 + (local - dy * w), ty = y0 + dy;
+        const uint32_t r = s_rec[a];
+        const int v = (int)((int64_t)r / n_per_view);
+        const uint64_t tile = (uint64_t)(vs.v[v].tile_offset + (int64_t)ty * vs.v[v].tiles_x + tx);
+        key = (tile << 32) | (uint64_t)s_depth[a];
+        keys[j] = key;
+        vals[j] = r;
+      }
+      for (int p = 0; p < passes; ++p) {
+        const uint32_t d = valid ? (uint32_t)(key >> (8 * p)) & 255u : 0x100u + (threadIdx.x & 31);
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (valid && (peers & lanemask_lt()) == 0u) atomicAdd(&s_hist[p * 256 + d], __popc(peers));
+      }
     }
   }
-  if (overflow) s_overflow = 1;
   __syncthreads();
-  if (tid == 0 && s_overflow) set_status(status, ST_CAPACITY);
   for (int e = tid; e < passes * 256; e += EMIT_THREADS)
     if (s_hist[e]) atomicAdd(hist + e, s_hist[e]);
 }
@@ -338,7 +375,7 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
   if ((e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)vs.total_tiles, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(sort_lb, 0, sizeof(uint64_t) * 256 * (size_t)L.sort_parts, st)) != cudaSuccess) return e;
   if (R == 0) return cudaMemsetAsync(n_int, 0, sizeof(int64_t), st);
-  if ((e = cudaMemsetAsync(scan_lb, 0, sizeof(uint64_t) * (size_t)L.scan_parts, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(scan_lb, 0, sizeof(uint64_t) * 2 * (size_t)L.scan_parts, st)) != cudaSuccess) return e;
 
   // emission target: the passes ping-pong, the last one must land in the caller's buffers
   uint64_t *k0 = (passes & 1) ? alt_keys : keys;
@@ -346,9 +383,19 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
   uint64_t *k1 = (passes & 1) ? keys : alt_keys;
   uint32_t *v1 = (passes & 1) ? vals : alt_vals;
 
-  emit_kernel<<<(unsigned)L.scan_parts, EMIT_THREADS, 0, st>>>(
-      records, tiles_touched, R, n, vs, k0, v0, capacity, n_int, scan_lb, &hdr->scan_parts, hist,
-      passes, &hdr->status);
+  uint32_t *vis_rec = reinterpret_cast<uint32_t *>(ws + L.vis_rec);
+  uint64_t *vis_off = reinterpret_cast<uint64_t *>(ws + L.vis_off);
+  uint32_t *chunk_first = reinterpret_cast<uint32_t *>(ws + L.chunk_first);
+  scan_kernel<<<(unsigned)L.scan_parts, EMIT_THREADS, 0, st>>>(
+      tiles_touched, R, capacity, n_int, &hdr->n_visible, scan_lb, scan_lb + L.scan_parts,
+      &hdr->scan_parts, vis_rec, vis_off, chunk_first, &hdr->status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  int64_t egrid = (int64_t)sm_count() * 4;
+  if (egrid > L.chunks) egrid = L.chunks;
+  if (egrid < 1) egrid = 1;
+  emit_kernel<<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
+      records, n, vs, vis_rec, vis_off, chunk_first, n_int, &hdr->n_visible, k0, v0, capacity,
+      hist, passes, &hdr->status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
   const size_t smem = sizeof(SortSmem);

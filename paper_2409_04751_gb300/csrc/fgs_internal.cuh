@@ -67,7 +67,7 @@ __device__ __forceinline__ int view_of_tile(const Views &vs, int64_t t) {
 // Workspace layout (bytes from the workspace base; every region 256-byte aligned).
 struct WsHeader {
   uint32_t status;            // fgs_status of device-detected errors (first one wins)
-  uint32_t scan_parts;        // partition counter of the key-emission scan
+  uint32_t scan_parts;        // partition counter of the tiles_touched scan
   uint32_t sort_parts[8];     // partition counters of the radix-sort passes
   uint32_t raster_tiles;      // tile queue of the forward rasterizer
   uint32_t backward_tiles;    // tile queue of the backward rasterizer
@@ -75,13 +75,15 @@ struct WsHeader {
   // [0] forward (pixel, Gaussian) evaluations, [1] forward blends,
   // [2] backward evaluations, [3] backward contributions
   unsigned long long counters[4];
-  uint32_t pad[44];
+  unsigned long long n_visible;  // records with a non-empty rect (written by the scan)
+  uint32_t pad[42];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
 
 constexpr int EMIT_THREADS = 256;
 constexpr int EMIT_ITEMS = 4;
 constexpr int EMIT_PART = EMIT_THREADS * EMIT_ITEMS;  // records per scan partition
+constexpr int EMIT_CHUNK = 2048;                      // (record, tile) pairs per emission CTA
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 16;
 constexpr int SORT_PART = SORT_THREADS * SORT_ITEMS;  // keys per sort partition
@@ -89,28 +91,39 @@ constexpr int SORT_MAX_PASSES = 8;
 constexpr int G2D_STRIDE = 12;                        // floats per record of screen-space grads
 
 struct WsLayout {
-  size_t header, scan_lb, hist, sort_lb, alt_keys, alt_vals, g2d, total;
-  int64_t scan_parts, sort_parts;
+  size_t header, scan_lb, g2d, vis_rec, vis_off, hist, sort_lb, alt_keys, alt_vals, chunk_first,
+      total;
+  int64_t scan_parts, sort_parts, chunks;
 };
 
-__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+__host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-inline WsLayout ws_layout(int64_t n_records, int64_t capacity) {
-  WsLayout L;
+// Workspace layout. Regions that depend on the record count only come first, so the
+// rasterizer and the backward can locate them without knowing the key capacity; with_g2d =
+// false leaves out the backward's accumulator (used by the sort-only variant).
+constexpr WsLayout ws_layout_ex(int64_t n_records, int64_t capacity, bool with_g2d) {
+  WsLayout L{};
+  const int64_t R = n_records > 0 ? n_records : 1;
   L.scan_parts = (n_records + EMIT_PART - 1) / EMIT_PART;
   L.sort_parts = (capacity + SORT_PART - 1) / SORT_PART;
+  L.chunks = (capacity + EMIT_CHUNK - 1) / EMIT_CHUNK;
   size_t o = 0;
-  // regions that depend on the record count only come first, so the rasterizer and the
-  // backward can locate them without knowing the key capacity
-  L.header = o; o += align256(sizeof(WsHeader));
-  L.scan_lb = o; o += align256(sizeof(uint64_t) * (size_t)(L.scan_parts > 0 ? L.scan_parts : 1));
-  L.g2d = o; o += align256(sizeof(float) * G2D_STRIDE * (size_t)(n_records > 0 ? n_records : 1));
+  L.header = o; o += align256(256);
+  L.scan_lb = o; o += align256(sizeof(uint64_t) * 2 * (size_t)(L.scan_parts > 0 ? L.scan_parts : 1));
+  L.g2d = o; if (with_g2d) o += align256(sizeof(float) * G2D_STRIDE * (size_t)R);
+  L.vis_rec = o; o += align256(sizeof(uint32_t) * (size_t)R);
+  L.vis_off = o; o += align256(sizeof(uint64_t) * (size_t)R);
   L.hist = o; o += align256(sizeof(uint32_t) * SORT_MAX_PASSES * 256);
   L.sort_lb = o; o += align256(sizeof(uint64_t) * 256 * 2 * (size_t)(L.sort_parts > 0 ? L.sort_parts : 1));
   L.alt_keys = o; o += align256(sizeof(uint64_t) * (size_t)capacity);
   L.alt_vals = o; o += align256(sizeof(uint32_t) * ((size_t)capacity + 4));
+  L.chunk_first = o; o += align256(sizeof(uint32_t) * ((size_t)L.chunks + 2));
   L.total = o;
   return L;
+}
+
+inline WsLayout ws_layout(int64_t n_records, int64_t capacity) {
+  return ws_layout_ex(n_records, capacity, true);
 }
 
 __device__ __forceinline__ void set_status(uint32_t *status, uint32_t code) {
@@ -176,6 +189,21 @@ __device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, u
           "r"(smem_addr(dst_smem)),
       "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
+}
+
+// Hardware approximations (single MUFU instructions): 2^x with relative error below 2^-22 and
+// 1/x with relative error below 2^-23, subnormals flushed. The blend's alpha >= 1/255 and the
+// transmittance >= 1e-4 never reach the subnormal range.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -345,6 +373,7 @@ struct GaussPtrs {
 
 int sm_count();
 bool instrumented();
+int raster_shape(int which);  // pixels per thread: 0 = forward, 1 = backward
 // Per-view parameter table from the caller's cameras; false if any camera is invalid.
 bool build_views(const fgs_camera *cams, int n_views, Views *vs);
 

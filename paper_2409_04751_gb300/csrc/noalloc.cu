@@ -8,7 +8,7 @@
 // histograms, sort look-back, alternate key and value buffers) in one file-scope device array of
 // fixed size, so the only memory the caller provides is the inputs and outputs.
 //
-// The array is part of the module: every GPU that loads the library holds it (about 6.8 MB)
+// The array is part of the module: every GPU that loads the library holds it (about 13 MB)
 // until the process exits. It supports at most NOALLOC_MAX_RECORDS records (views x Gaussians)
 // and NOALLOC_MAX_CAPACITY key slots; larger requests are rejected before anything is launched.
 // All calls share the one array, so calls whose work overlaps on the GPU (concurrent streams,
@@ -23,34 +23,11 @@
 namespace fgs {
 namespace {
 
-constexpr int64_t NOALLOC_MAX_RECORDS = 1 << 20;
+constexpr int64_t NOALLOC_MAX_RECORDS = 1 << 19;
 constexpr int64_t NOALLOC_MAX_CAPACITY = 1 << 19;
 
-// The scratch regions of fgs_bin_sort, in the order it uses them (no backward region).
-WsLayout noalloc_layout(int64_t n_records, int64_t capacity) {
-  WsLayout L;
-  L.scan_parts = (n_records + EMIT_PART - 1) / EMIT_PART;
-  L.sort_parts = (capacity + SORT_PART - 1) / SORT_PART;
-  size_t o = 0;
-  L.header = o; o += align256(sizeof(WsHeader));
-  L.scan_lb = o; o += align256(sizeof(uint64_t) * (size_t)(L.scan_parts > 0 ? L.scan_parts : 1));
-  L.g2d = o;  // unused by the sort
-  L.hist = o; o += align256(sizeof(uint32_t) * SORT_MAX_PASSES * 256);
-  L.sort_lb = o; o += align256(sizeof(uint64_t) * 256 * 2 * (size_t)(L.sort_parts > 0 ? L.sort_parts : 1));
-  L.alt_keys = o; o += align256(sizeof(uint64_t) * (size_t)capacity);
-  L.alt_vals = o; o += align256(sizeof(uint32_t) * ((size_t)capacity + 4));
-  L.total = o;
-  return L;
-}
-
-constexpr size_t align256c(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t NOALLOC_BYTES =
-    align256c(sizeof(WsHeader)) +
-    align256c(sizeof(uint64_t) * (size_t)((NOALLOC_MAX_RECORDS + EMIT_PART - 1) / EMIT_PART)) +
-    align256c(sizeof(uint32_t) * SORT_MAX_PASSES * 256) +
-    align256c(sizeof(uint64_t) * 256 * 2 * (size_t)((NOALLOC_MAX_CAPACITY + SORT_PART - 1) / SORT_PART)) +
-    align256c(sizeof(uint64_t) * (size_t)NOALLOC_MAX_CAPACITY) +
-    align256c(sizeof(uint32_t) * ((size_t)NOALLOC_MAX_CAPACITY + 4));
+    ws_layout_ex(NOALLOC_MAX_RECORDS, NOALLOC_MAX_CAPACITY, false).total;
 
 // The scratch itself. In host code `g_noalloc_scratch` is only a host-side stand-in for the
 // symbol, never a device address: the device address is looked up per device below.
@@ -93,7 +70,7 @@ extern "C" fgs_status fgs_bin_sort_noalloc(const fgs_record *records,
     return FGS_ERR_INVALID_ARG;
   Views vs;
   if (!build_views(cams, n_views, &vs)) return FGS_ERR_INVALID_ARG;
-  const WsLayout L = noalloc_layout(R, capacity);
+  const WsLayout L = ws_layout_ex(R, capacity, false);
   if (L.total > NOALLOC_BYTES) return FGS_ERR_INVALID_ARG;
   char *ws = scratch_on_current_device();
   if (ws == nullptr) return FGS_ERR_CUDA;

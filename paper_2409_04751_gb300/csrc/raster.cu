@@ -1,88 +1,102 @@
 // raster.cu - per-tile alpha blending (Sec. 3.1 "Rendering"; Sec. 4.1 renderCUDA) and its
 // backward, sm_103a.
 //
-// One CTA of 256 threads per 16x16 tile, one pixel per thread; CTAs are persistent and take
-// tiles from an atomic queue. Each tile's Gaussians are staged through shared memory in batches
-// of 256: every thread issues one TMA bulk copy (cp.async.bulk, 48 bytes) of its record,
-// completing on an mbarrier, and the next batch is in flight while the current one is blended
-// (two stages). The sorted indices of the batch after next are prefetched into registers. A
-// warp whose pixels have all stopped skips the batch (warp ballot); the CTA leaves the tile
-// when all 256 pixels have stopped.
+// One CTA per 16x16 tile with 256/PPT threads; each thread owns PPT vertically adjacent pixels
+// (PPT = 1, 2 or 4, the "work shape"; the image does not depend on it). CTAs are persistent and
+// take tiles from an atomic queue. Each tile's Gaussians are staged through shared memory in
+// batches of 256 records: every thread issues TMA bulk copies (cp.async.bulk, 48 bytes each) of
+// its share, completing on an mbarrier, and the next batch is in flight while the current one is
+// blended (two stages). The sorted indices of the batch after next are prefetched into registers.
+// A warp whose pixels have all stopped skips the batch (warp ballot); the CTA leaves the tile
+// when all its pixels have stopped.
 //
 // The backward replays each pixel's blend back to front from its final transmittance and the
 // number of list entries it processed (both written by the forward), recovering the
-// transmittance before each Gaussian by division; nothing per (pixel, Gaussian) is stored.
-// Screen-space gradients are summed over the warp with shuffles and added to the record's
-// accumulator with one vector atomic per warp.
+// transmittance before each Gaussian by division; nothing per (pixel, Gaussian) is stored. Each
+// thread first sums its own pixels' screen-space gradients of a Gaussian; the warp then reduces
+// the nine sums with a transpose reduction (each exchange halves the values a lane carries: 14
+// shuffles instead of 45) and eight lanes add their totals to the record's accumulator.
 #include "fgs_internal.cuh"
 
 namespace fgs {
 
 namespace {
 
-constexpr int RT = 256;     // threads per tile CTA (one per pixel)
-constexpr int BATCH = 256;  // Gaussians per staged batch
+constexpr int TILE_PIX = TILE * TILE;  // 256 pixels per tile
+constexpr int BATCH = 256;             // Gaussians per staged batch
 constexpr uint32_t REC_BYTES = sizeof(fgs_record);
 static_assert(REC_BYTES == 48, "record size");
 
 struct TileInfo {
-  int64_t t;
   int v;
-  int px, py;
-  bool inside;
+  int tx, ty;
   uint32_t start, count;
 };
 
 __device__ __forceinline__ TileInfo tile_info(const Views &vs, int64_t t,
                                               const uint32_t *__restrict__ ranges) {
   TileInfo ti;
-  ti.t = t;
   ti.v = view_of_tile(vs, t);
   const View &V = vs.v[ti.v];
   const int64_t local = t - V.tile_offset;
-  const int ty = (int)(local / V.tiles_x), tx = (int)(local - (int64_t)ty * V.tiles_x);
-  ti.px = tx * TILE + (threadIdx.x & (TILE - 1));
-  ti.py = ty * TILE + (threadIdx.x / TILE);
-  ti.inside = ti.px < V.width && ti.py < V.height;
+  ti.ty = (int)(local / V.tiles_x);
+  ti.tx = (int)(local - (int64_t)ti.ty * V.tiles_x);
   const uint2 rg = __ldg(reinterpret_cast<const uint2 *>(ranges) + t);
   ti.start = rg.x;
   ti.count = rg.y > rg.x ? rg.y - rg.x : 0u;
   return ti;
 }
 
-// Issue this thread's share of a batch: one 48-byte bulk copy of its record, or a plain
-// arrival when the batch has no entry for it. The barrier expects RT arrivals per phase.
+// Issue this thread's share of a batch: slots tid, tid + NT, ... below `cnt`, one 48-byte
+// bulk copy each, announced with one arrive.expect_tx (the barrier expects NT arrivals).
+template <int NT, int PER>
 __device__ __forceinline__ void issue_batch(fgs_record *stage, uint64_t *bar,
-                                            const fgs_record *__restrict__ rec, uint32_t idx,
-                                            bool has) {
-  if (has) {
-    mbar_arrive_expect_tx(bar, REC_BYTES);
-    bulk_g2s(stage + threadIdx.x, rec + idx, REC_BYTES, bar);
-  } else {
-    mbar_arrive(bar);
+                                            const fgs_record *__restrict__ rec,
+                                            const uint32_t (&idx)[PER], uint32_t cnt) {
+  uint32_t n = 0;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) n += (threadIdx.x + k * NT < cnt) ? 1u : 0u;
+  mbar_arrive_expect_tx(bar, n * REC_BYTES);
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const uint32_t slot = threadIdx.x + k * NT;
+    if (slot < cnt) bulk_g2s(stage + slot, rec + idx[k], REC_BYTES, bar);
   }
 }
 
-template <bool COUNT>
-__global__ void __launch_bounds__(RT)
+template <int NT, int PER>
+__device__ __forceinline__ void load_idx(const uint32_t *__restrict__ vals, uint32_t base,
+                                         uint32_t lo, uint32_t cnt, uint32_t (&idx)[PER]) {
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const uint32_t slot = threadIdx.x + k * NT;
+    idx[k] = slot < cnt ? __ldg(vals + base + lo + slot) : 0u;
+  }
+}
+
+template <int PPT, bool COUNT>
+__global__ void __launch_bounds__(TILE_PIX / PPT)
     raster_fwd_kernel(const fgs_record *__restrict__ rec, const uint32_t *__restrict__ vals,
                       const uint32_t *__restrict__ ranges, Views vs, float bg0, float bg1,
                       float bg2, float *__restrict__ images, float *__restrict__ final_T,
                       uint32_t *__restrict__ n_processed, uint32_t *tile_counter,
                       uint32_t *status, unsigned long long *counters) {
+  constexpr int NT = TILE_PIX / PPT;
+  constexpr int PER = BATCH / NT;  // copies each thread issues per batch
   __shared__ __align__(128) fgs_record raw[2][BATCH];
   __shared__ __align__(16) float4 xf[BATCH][3];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int64_t s_tile;
   const int tid = threadIdx.x;
   if (tid == 0) {
-    mbar_init(&bar[0], RT);
-    mbar_init(&bar[1], RT);
+    mbar_init(&bar[0], NT);
+    mbar_init(&bar[1], NT);
     fence_mbar_init();
   }
   __syncthreads();
   uint32_t phase0 = 0, phase1 = 0;
   uint32_t n_eval = 0, n_blend = 0;
+  const int lx = tid & (TILE - 1), ly0 = (tid / TILE) * PPT;
 
   for (;;) {
     if (tid == 0) s_tile = (int64_t)atomicAdd(tile_counter, 1u);
@@ -92,31 +106,41 @@ __global__ void __launch_bounds__(RT)
     if (t >= vs.total_tiles) break;
     const TileInfo ti = tile_info(vs, t, ranges);
     const View &V = vs.v[ti.v];
-    const float fpx = (float)ti.px + 0.5f, fpy = (float)ti.py + 0.5f;
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    uint32_t last = 0;
-    bool done = !ti.inside;
+    const int px = ti.tx * TILE + lx;
+    const float fpx = (float)px + 0.5f;
+    float fpy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
+    uint32_t last[PPT];
+    bool live[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int py = ti.ty * TILE + ly0 + k;
+      fpy[k] = (float)py + 0.5f;
+      T[k] = 1.f; C0[k] = C1[k] = C2[k] = 0.f;
+      last[k] = 0;
+      live[k] = px < V.width && py < V.height;
+    }
+    bool done = true;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) done = done && !live[k];
     const uint32_t count = ti.count;
     const uint32_t nb = (count + BATCH - 1) / BATCH;
 
     if (nb > 0) {
-      uint32_t idx_next = 0;
-      {
-        const bool has0 = (uint32_t)tid < count;
-        const uint32_t idx0 = has0 ? __ldg(vals + ti.start + tid) : 0u;
-        if (BATCH + (uint32_t)tid < count) idx_next = __ldg(vals + ti.start + BATCH + tid);
-        fence_proxy_async_smem();
-        issue_batch(raw[0], &bar[0], rec, idx0, has0);
-      }
+      uint32_t idx[PER], idx_next[PER];
+      load_idx<NT, PER>(vals, ti.start, 0, count, idx);
+      load_idx<NT, PER>(vals, ti.start, BATCH, count > BATCH ? count - BATCH : 0u, idx_next);
+      fence_proxy_async_smem();
+      issue_batch<NT, PER>(raw[0], &bar[0], rec, idx, min(count, (uint32_t)BATCH));
       for (uint32_t b = 0; b < nb; ++b) {
         const int s = b & 1;
-        const uint32_t cnt = min((uint32_t)BATCH, count - b * BATCH);
+        const uint32_t lo = b * BATCH;
+        const uint32_t cnt = min((uint32_t)BATCH, count - lo);
         if (b + 1 < nb) {
-          const bool has = (b + 1) * BATCH + (uint32_t)tid < count;
           fence_proxy_async_smem();
-          issue_batch(raw[s ^ 1], &bar[s ^ 1], rec, idx_next, has);
-          const uint32_t q = (b + 2) * BATCH + (uint32_t)tid;
-          idx_next = q < count ? __ldg(vals + ti.start + q) : 0u;
+          issue_batch<NT, PER>(raw[s ^ 1], &bar[s ^ 1], rec, idx_next,
+                               min((uint32_t)BATCH, count - lo - BATCH));
+          const uint32_t lo2 = lo + 2 * BATCH;
+          load_idx<NT, PER>(vals, ti.start, lo2, count > lo2 ? count - lo2 : 0u, idx_next);
         }
         const bool ok = mbar_wait(&bar[s], s ? phase1 : phase0, status);
         if (s) phase1 ^= 1u; else phase0 ^= 1u;
@@ -124,36 +148,76 @@ __global__ void __launch_bounds__(RT)
           if (b + 1 < nb) mbar_wait(&bar[s ^ 1], s ? phase0 : phase1, status);
           return;
         }
-        if ((uint32_t)tid < cnt) {
-          const fgs_record &g = raw[s][tid];
-          // exponent in base 2: e = A' dx^2 + B' dx dy + C' dy^2 + log2(opacity)
-          xf[tid][0] = make_float4(g.xy[0], g.xy[1], -0.5f * LOG2E * g.conic[0], -LOG2E * g.conic[1]);
-          xf[tid][1] = make_float4(-0.5f * LOG2E * g.conic[2], log2f(g.opacity), g.rgb[0], g.rgb[1]);
-          xf[tid][2] = make_float4(g.rgb[2], 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+          const uint32_t slot = tid + k * NT;
+          if (slot < cnt) {
+            const fgs_record &g = raw[s][slot];
+            // exponent in base 2: e = A' dx^2 + B' dx dy + C' dy^2 + log2(opacity)
+            xf[slot][0] = make_float4(g.xy[0], g.xy[1], -0.5f * LOG2E * g.conic[0], -LOG2E * g.conic[1]);
+            xf[slot][1] = make_float4(-0.5f * LOG2E * g.conic[2], log2f(g.opacity), g.rgb[0], g.rgb[1]);
+            xf[slot][2] = make_float4(g.rgb[2], 0.f, 0.f, 0.f);
+          }
         }
         __syncthreads();
         if (!__all_sync(0xffffffffu, done)) {
+          const uint32_t lo1 = lo + 1;
           for (uint32_t j = 0; j < cnt && !done; ++j) {
             const float4 a = xf[j][0];
             const float4 c = xf[j][1];
-            const float dx = fpx - a.x, dy = fpy - a.y;
-            const float e = fmaf(dx, fmaf(a.z, dx, a.w * dy), fmaf(c.x * dy, dy, c.y));
-            if (COUNT) ++n_eval;
-            if (e < LOG2_ALPHA_MIN) continue;
-            const float alpha = fminf(ALPHA_MAX, exp2f(e));
-            const float Tn = T * (1.f - alpha);
-            if (Tn < T_MIN) {
-              done = true;
-              break;
+            const float dx = fpx - a.x;
+            const float adx = a.z * dx;
+            if (PPT == 1) {
+              const float dy = fpy[0] - a.y;
+              const float e = fmaf(dx, fmaf(a.w, dy, adx), fmaf(c.x * dy, dy, c.y));
+              if (COUNT) ++n_eval;
+              if (e < LOG2_ALPHA_MIN) continue;
+              const float alpha = fminf(ALPHA_MAX, ex2_approx(e));
+              const float Tn = T[0] * (1.f - alpha);
+              if (Tn < T_MIN) {
+                live[0] = false;
+                break;
+              }
+              const float wgt = alpha * T[0];
+              C0[0] = fmaf(c.z, wgt, C0[0]);
+              C1[0] = fmaf(c.w, wgt, C1[0]);
+              C2[0] = fmaf(xf[j][2].x, wgt, C2[0]);
+              T[0] = Tn;
+              last[0] = lo1 + j;
+              if (COUNT) ++n_blend;
+            } else {
+              bool any_live = false;
+#pragma unroll
+              for (int k = 0; k < PPT; ++k) {
+                if (live[k]) {
+                  const float dy = fpy[k] - a.y;
+                  const float e = fmaf(dx, fmaf(a.w, dy, adx), fmaf(c.x * dy, dy, c.y));
+                  if (COUNT) ++n_eval;
+                  if (e >= LOG2_ALPHA_MIN) {
+                    const float alpha = fminf(ALPHA_MAX, ex2_approx(e));
+                    const float Tn = T[k] * (1.f - alpha);
+                    if (Tn < T_MIN) {
+                      live[k] = false;
+                    } else {
+                      const float wgt = alpha * T[k];
+                      C0[k] = fmaf(c.z, wgt, C0[k]);
+                      C1[k] = fmaf(c.w, wgt, C1[k]);
+                      C2[k] = fmaf(xf[j][2].x, wgt, C2[k]);
+                      T[k] = Tn;
+                      last[k] = lo1 + j;
+                      if (COUNT) ++n_blend;
+                    }
+                  }
+                }
+                any_live = any_live || live[k];
+              }
+              if (!any_live) break;
             }
-            const float wgt = alpha * T;
-            C0 = fmaf(c.z, wgt, C0);
-            C1 = fmaf(c.w, wgt, C1);
-            C2 = fmaf(xf[j][2].x, wgt, C2);
-            T = Tn;
-            last = b * BATCH + j + 1;
-            if (COUNT) ++n_blend;
           }
+          bool any_live = false;
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) any_live = any_live || live[k];
+          done = !any_live;
         }
         if (__syncthreads_count(!done) == 0) {
           if (b + 1 < nb) {  // drain the batch in flight before leaving the tile
@@ -164,15 +228,19 @@ __global__ void __launch_bounds__(RT)
         }
       }
     }
-    if (ti.inside) {
-      const int64_t p = V.pixel_offset + (int64_t)ti.py * V.width + ti.px;
-      const int64_t plane = (int64_t)V.width * V.height;
-      float *img = images + 3 * V.pixel_offset + (int64_t)ti.py * V.width + ti.px;
-      img[0] = fmaf(T, bg0, C0);
-      img[plane] = fmaf(T, bg1, C1);
-      img[2 * plane] = fmaf(T, bg2, C2);
-      final_T[p] = T;
-      n_processed[p] = last;
+    const int64_t plane = (int64_t)V.width * V.height;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int py = ti.ty * TILE + ly0 + k;
+      if (px < V.width && py < V.height) {
+        const int64_t off = (int64_t)py * V.width + px;
+        float *img = images + 3 * V.pixel_offset + off;
+        img[0] = fmaf(T[k], bg0, C0[k]);
+        img[plane] = fmaf(T[k], bg1, C1[k]);
+        img[2 * plane] = fmaf(T[k], bg2, C2[k]);
+        final_T[V.pixel_offset + off] = T[k];
+        n_processed[V.pixel_offset + off] = last[k];
+      }
     }
   }
   if (COUNT) {
@@ -181,20 +249,46 @@ __global__ void __launch_bounds__(RT)
   }
 }
 
+// Warp sum of eight values by transpose reduction: at each exchange a lane keeps half of its
+// values and sends the other half to its partner, so 4 + 2 + 1 + 1 + 1 shuffles reduce all
+// eight. On return lane l holds the total of value 4*b4 + 2*b3 + b2 (b_i = bit i of l).
+__device__ __forceinline__ float warp_transpose_sum8(const float (&a)[8], int lane) {
+  float b[4], c[2];
+  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float keep = h4 ? a[k + 4] : a[k];
+    const float send = h4 ? a[k] : a[k + 4];
+    b[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float keep = h3 ? b[k + 2] : b[k];
+    const float send = h3 ? b[k] : b[k + 2];
+    c[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float d = (h2 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, h2 ? c[0] : c[1], 4);
+  d += __shfl_xor_sync(0xffffffffu, d, 2);
+  d += __shfl_xor_sync(0xffffffffu, d, 1);
+  return d;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-template <bool COUNT>
-__global__ void __launch_bounds__(RT)
+template <int PPT, bool COUNT>
+__global__ void __launch_bounds__(TILE_PIX / PPT)
     raster_bwd_kernel(const fgs_record *__restrict__ rec, const uint32_t *__restrict__ vals,
                       const uint32_t *__restrict__ ranges, Views vs, float bg0, float bg1,
                       float bg2, const float *__restrict__ final_T,
                       const uint32_t *__restrict__ n_processed, const float *__restrict__ dLdimg,
                       float *__restrict__ g2d, uint32_t *tile_counter, uint32_t *status,
                       unsigned long long *counters) {
+  constexpr int NT = TILE_PIX / PPT;
+  constexpr int PER = BATCH / NT;
   __shared__ __align__(128) fgs_record raw[2][BATCH];
   __shared__ __align__(16) float4 xf[BATCH][4];
   __shared__ uint32_t xidx[BATCH];
@@ -203,13 +297,14 @@ __global__ void __launch_bounds__(RT)
   __shared__ uint32_t s_max;
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid == 0) {
-    mbar_init(&bar[0], RT);
-    mbar_init(&bar[1], RT);
+    mbar_init(&bar[0], NT);
+    mbar_init(&bar[1], NT);
     fence_mbar_init();
   }
   __syncthreads();
   uint32_t phase0 = 0, phase1 = 0;
   uint32_t n_eval = 0, n_contrib = 0;
+  const int lx = tid & (TILE - 1), ly0 = (tid / TILE) * PPT;
 
   for (;;) {
     if (tid == 0) {
@@ -221,47 +316,58 @@ __global__ void __launch_bounds__(RT)
     if (t >= vs.total_tiles) break;
     const TileInfo ti = tile_info(vs, t, ranges);
     const View &V = vs.v[ti.v];
-    const float fpx = (float)ti.px + 0.5f, fpy = (float)ti.py + 0.5f;
-    float T = 1.f, G0 = 0.f, G1 = 0.f, G2 = 0.f;
-    uint32_t last = 0;
-    if (ti.inside) {
-      const int64_t p = V.pixel_offset + (int64_t)ti.py * V.width + ti.px;
-      const int64_t plane = (int64_t)V.width * V.height;
-      const float *gi = dLdimg + 3 * V.pixel_offset + (int64_t)ti.py * V.width + ti.px;
-      T = final_T[p];
-      last = min(n_processed[p], ti.count);
-      G0 = gi[0]; G1 = gi[plane]; G2 = gi[2 * plane];
-      atomicMax(&s_max, last);
+    const int px = ti.tx * TILE + lx;
+    const float fpx = (float)px + 0.5f;
+    const int64_t plane = (int64_t)V.width * V.height;
+    float fpy[PPT], T[PPT], G0[PPT], G1[PPT], G2[PPT], S0[PPT], S1[PPT], S2[PPT];
+    uint32_t last[PPT];
+    uint32_t my_max = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int py = ti.ty * TILE + ly0 + k;
+      fpy[k] = (float)py + 0.5f;
+      T[k] = 1.f; G0[k] = G1[k] = G2[k] = 0.f;
+      last[k] = 0;
+      if (px < V.width && py < V.height) {
+        const int64_t off = (int64_t)py * V.width + px;
+        const float *gi = dLdimg + 3 * V.pixel_offset + off;
+        T[k] = final_T[V.pixel_offset + off];
+        last[k] = min(n_processed[V.pixel_offset + off], ti.count);
+        G0[k] = gi[0]; G1[k] = gi[plane]; G2[k] = gi[2 * plane];
+      }
+      // colour behind the current entry: sum over later blended entries + T_final bg
+      S0[k] = T[k] * bg0; S1[k] = T[k] * bg1; S2[k] = T[k] * bg2;
+      my_max = max(my_max, last[k]);
     }
-    // colour behind the current entry: sum over later blended entries + T_final bg
-    float S0 = T * bg0, S1 = T * bg1, S2 = T * bg2;
+    atomicMax(&s_max, my_max);
     __syncthreads();
     const uint32_t max_last = s_max;
     const uint32_t nb = (max_last + BATCH - 1) / BATCH;
 
     if (nb > 0) {
-      // batches from the back: it = 0 handles batch nb-1
-      uint32_t idx_next = 0;
+      // batches from the back: iteration it handles batch nb - 1 - it
+      uint32_t idx[PER], idx_next[PER];
       {
-        const uint32_t b0 = nb - 1;
-        const bool has0 = b0 * BATCH + (uint32_t)tid < max_last;
-        const uint32_t idx0 = has0 ? __ldg(vals + ti.start + b0 * BATCH + tid) : 0u;
-        if (nb >= 2) idx_next = __ldg(vals + ti.start + (nb - 2) * BATCH + tid);
+        const uint32_t lo0 = (nb - 1) * BATCH;
+        load_idx<NT, PER>(vals, ti.start, lo0, max_last - lo0, idx);
+        if (nb >= 2) load_idx<NT, PER>(vals, ti.start, lo0 - BATCH, BATCH, idx_next);
         fence_proxy_async_smem();
-        issue_batch(raw[0], &bar[0], rec, idx0, has0);
-        if (has0) xidx[tid] = idx0;
+        issue_batch<NT, PER>(raw[0], &bar[0], rec, idx, max_last - lo0);
+#pragma unroll
+        for (int k = 0; k < PER; ++k) xidx[tid + k * NT] = idx[k];
       }
       for (uint32_t it = 0; it < nb; ++it) {
         const uint32_t b = nb - 1 - it;
         const int s = it & 1;
         const uint32_t lo = b * BATCH;
         const uint32_t cnt = min((uint32_t)BATCH, max_last - lo);
-        uint32_t my_idx = 0;
+        uint32_t mine[PER];
         if (b >= 1) {
           fence_proxy_async_smem();
-          issue_batch(raw[s ^ 1], &bar[s ^ 1], rec, idx_next, true);
-          my_idx = idx_next;
-          idx_next = b >= 2 ? __ldg(vals + ti.start + (b - 2) * BATCH + tid) : 0u;
+          issue_batch<NT, PER>(raw[s ^ 1], &bar[s ^ 1], rec, idx_next, BATCH);
+#pragma unroll
+          for (int k = 0; k < PER; ++k) mine[k] = idx_next[k];
+          if (b >= 2) load_idx<NT, PER>(vals, ti.start, lo - 2 * BATCH, BATCH, idx_next);
         }
         const bool ok = mbar_wait(&bar[s], s ? phase1 : phase0, status);
         if (s) phase1 ^= 1u; else phase0 ^= 1u;
@@ -269,69 +375,82 @@ __global__ void __launch_bounds__(RT)
           if (b >= 1) mbar_wait(&bar[s ^ 1], s ? phase0 : phase1, status);
           return;
         }
-        if ((uint32_t)tid < cnt) {
-          const fgs_record &g = raw[s][tid];
-          xf[tid][0] = make_float4(g.xy[0], g.xy[1], -0.5f * LOG2E * g.conic[0], -LOG2E * g.conic[1]);
-          xf[tid][1] = make_float4(-0.5f * LOG2E * g.conic[2], log2f(g.opacity), g.rgb[0], g.rgb[1]);
-          xf[tid][2] = make_float4(g.rgb[2], g.conic[0], g.conic[1], g.conic[2]);
-          xf[tid][3] = make_float4(g.opacity, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+          const uint32_t slot = tid + k * NT;
+          if (slot < cnt) {
+            const fgs_record &g = raw[s][slot];
+            xf[slot][0] = make_float4(g.xy[0], g.xy[1], -0.5f * LOG2E * g.conic[0], -LOG2E * g.conic[1]);
+            xf[slot][1] = make_float4(-0.5f * LOG2E * g.conic[2], log2f(g.opacity), g.rgb[0], g.rgb[1]);
+            xf[slot][2] = make_float4(g.rgb[2], g.conic[0], g.conic[1], g.conic[2]);
+            xf[slot][3] = make_float4(rcp_approx(g.opacity), 0.f, 0.f, 0.f);
+          }
         }
         __syncthreads();
         for (int j = (int)cnt - 1; j >= 0; --j) {
           const uint32_t pos = lo + (uint32_t)j;
+          const bool any_pos = pos < my_max;
+          if (!__any_sync(0xffffffffu, any_pos)) continue;
           float v[9];
+#pragma unroll
+          for (int q = 0; q < 9; ++q) v[q] = 0.f;
           bool contrib = false;
-          if (pos < last) {
+          if (any_pos) {
             const float4 a = xf[j][0];
             const float4 c = xf[j][1];
-            const float dx = fpx - a.x, dy = fpy - a.y;
-            const float e = fmaf(dx, fmaf(a.z, dx, a.w * dy), fmaf(c.x * dy, dy, c.y));
-            if (COUNT) ++n_eval;
-            if (e >= LOG2_ALPHA_MIN) {
-              contrib = true;
-              if (COUNT) ++n_contrib;
-              const float4 r2 = xf[j][2];
-              const float araw = exp2f(e);
-              const float alpha = fminf(ALPHA_MAX, araw);
-              const float om = 1.f / (1.f - alpha);
-              T *= om;  // transmittance before this Gaussian
-              const float wgt = alpha * T;
-              const float dLda = G0 * (c.z * T - S0 * om) + G1 * (c.w * T - S1 * om) +
-                                 G2 * (r2.x * T - S2 * om);
-              S0 = fmaf(c.z, wgt, S0);
-              S1 = fmaf(c.w, wgt, S1);
-              S2 = fmaf(r2.x, wgt, S2);
-              v[6] = G0 * wgt; v[7] = G1 * wgt; v[8] = G2 * wgt;
-              if (araw < ALPHA_MAX) {
-                const float dLdp = dLda * alpha;  // p = -0.5 d^T conic d
-                v[0] = dLdp * (r2.y * dx + r2.z * dy);
-                v[1] = dLdp * (r2.z * dx + r2.w * dy);
-                v[2] = -0.5f * dx * dx * dLdp;
-                v[3] = -dx * dy * dLdp;
-                v[4] = -0.5f * dy * dy * dLdp;
-                v[5] = dLda * araw / xf[j][3].x;
-              } else {
-                v[0] = v[1] = v[2] = v[3] = v[4] = v[5] = 0.f;
+            const float dx = fpx - a.x;
+            const float adx = a.z * dx;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+              if (pos < last[k]) {
+                const float dy = fpy[k] - a.y;
+                const float e = fmaf(dx, fmaf(a.w, dy, adx), fmaf(c.x * dy, dy, c.y));
+                if (COUNT) ++n_eval;
+                if (e >= LOG2_ALPHA_MIN) {
+                  contrib = true;
+                  if (COUNT) ++n_contrib;
+                  const float4 r2 = xf[j][2];
+                  const float araw = ex2_approx(e);
+                  const float alpha = fminf(ALPHA_MAX, araw);
+                  const float om = rcp_approx(1.f - alpha);
+                  T[k] *= om;  // transmittance before this Gaussian
+                  const float wgt = alpha * T[k];
+                  const float dLda = G0[k] * (c.z * T[k] - S0[k] * om) +
+                                     G1[k] * (c.w * T[k] - S1[k] * om) +
+                                     G2[k] * (r2.x * T[k] - S2[k] * om);
+                  S0[k] = fmaf(c.z, wgt, S0[k]);
+                  S1[k] = fmaf(c.w, wgt, S1[k]);
+                  S2[k] = fmaf(r2.x, wgt, S2[k]);
+                  v[6] = fmaf(G0[k], wgt, v[6]);
+                  v[7] = fmaf(G1[k], wgt, v[7]);
+                  v[8] = fmaf(G2[k], wgt, v[8]);
+                  if (araw < ALPHA_MAX) {
+                    const float dLdp = dLda * alpha;  // p = -0.5 d^T conic d
+                    v[0] = fmaf(dLdp, r2.y * dx + r2.z * dy, v[0]);
+                    v[1] = fmaf(dLdp, r2.z * dx + r2.w * dy, v[1]);
+                    v[2] = fmaf(-0.5f * dx * dx, dLdp, v[2]);
+                    v[3] = fmaf(-dx * dy, dLdp, v[3]);
+                    v[4] = fmaf(-0.5f * dy * dy, dLdp, v[4]);
+                    v[5] = fmaf(dLda * araw, xf[j][3].x, v[5]);
+                  }
+                }
               }
             }
           }
           if (__any_sync(0xffffffffu, contrib)) {
-            if (!contrib) {
-#pragma unroll
-              for (int k = 0; k < 9; ++k) v[k] = 0.f;
-            }
-#pragma unroll
-            for (int k = 0; k < 9; ++k) v[k] = warp_sum(v[k]);
-            if (lane == 0) {
-              float *dst = g2d + (size_t)xidx[j] * G2D_STRIDE;
-              atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(v[0], v[1], v[2], v[3]));
-              atomicAdd(reinterpret_cast<float4 *>(dst) + 1, make_float4(v[4], v[5], v[6], v[7]));
-              atomicAdd(dst + 8, v[8]);
-            }
+            const float a8[8] = {v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7]};
+            const float tot = warp_transpose_sum8(a8, lane);
+            const float tot8 = warp_sum(v[8]);
+            float *dst = g2d + (size_t)xidx[j] * G2D_STRIDE;
+            if ((lane & 3) == 0) atomicAdd(dst + (lane >> 2), tot);
+            if (lane == 0) atomicAdd(dst + 8, tot8);
           }
         }
         __syncthreads();  // xf / xidx reused by the next batch
-        if (b >= 1) xidx[tid] = my_idx;
+        if (b >= 1) {
+#pragma unroll
+          for (int k = 0; k < PER; ++k) xidx[tid + k * NT] = mine[k];
+        }
       }
     }
     __syncthreads();
@@ -342,7 +461,55 @@ __global__ void __launch_bounds__(RT)
   }
 }
 
-int g_fwd_occ = 0, g_bwd_occ = 0;
+template <typename K>
+int occupancy_of(K kernel, int threads) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0) != cudaSuccess) return 1;
+  return occ > 0 ? occ : 1;
+}
+
+template <int PPT>
+cudaError_t fwd_launch(const fgs_record *records, const uint32_t *vals, const uint32_t *ranges,
+                       const Views &vs, float bg0, float bg1, float bg2, float *images,
+                       float *final_T, uint32_t *n_processed, WsHeader *hdr, cudaStream_t st) {
+  constexpr int NT = TILE_PIX / PPT;
+  static int occ = 0;
+  if (occ == 0) occ = occupancy_of(raster_fwd_kernel<PPT, false>, NT);
+  int64_t grid = (int64_t)sm_count() * occ;
+  if (grid > vs.total_tiles) grid = vs.total_tiles;
+  if (grid < 1) grid = 1;
+  if (instrumented())
+    raster_fwd_kernel<PPT, true><<<(unsigned)grid, NT, 0, st>>>(
+        records, vals, ranges, vs, bg0, bg1, bg2, images, final_T, n_processed,
+        &hdr->raster_tiles, &hdr->status, hdr->counters);
+  else
+    raster_fwd_kernel<PPT, false><<<(unsigned)grid, NT, 0, st>>>(
+        records, vals, ranges, vs, bg0, bg1, bg2, images, final_T, n_processed,
+        &hdr->raster_tiles, &hdr->status, hdr->counters);
+  return cudaGetLastError();
+}
+
+template <int PPT>
+cudaError_t bwd_launch(const fgs_record *records, const uint32_t *vals, const uint32_t *ranges,
+                       const Views &vs, float bg0, float bg1, float bg2, const float *final_T,
+                       const uint32_t *n_processed, const float *dL, float *g2d, WsHeader *hdr,
+                       cudaStream_t st) {
+  constexpr int NT = TILE_PIX / PPT;
+  static int occ = 0;
+  if (occ == 0) occ = occupancy_of(raster_bwd_kernel<PPT, false>, NT);
+  int64_t grid = (int64_t)sm_count() * occ;
+  if (grid > vs.total_tiles) grid = vs.total_tiles;
+  if (grid < 1) grid = 1;
+  if (instrumented())
+    raster_bwd_kernel<PPT, true><<<(unsigned)grid, NT, 0, st>>>(
+        records, vals, ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL, g2d,
+        &hdr->backward_tiles, &hdr->status, hdr->counters);
+  else
+    raster_bwd_kernel<PPT, false><<<(unsigned)grid, NT, 0, st>>>(
+        records, vals, ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL, g2d,
+        &hdr->backward_tiles, &hdr->status, hdr->counters);
+  return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -353,24 +520,11 @@ cudaError_t launch_raster_fwd(const fgs_record *records, const uint32_t *vals,
   WsHeader *hdr = reinterpret_cast<WsHeader *>(ws + L.header);
   cudaError_t e = cudaMemsetAsync(&hdr->raster_tiles, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
-  if (g_fwd_occ == 0) {
-    int occ = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, raster_fwd_kernel<false>, RT, 0)) != cudaSuccess)
-      return e;
-    g_fwd_occ = occ > 0 ? occ : 1;
+  switch (raster_shape(0)) {
+    case 1: return fwd_launch<1>(records, vals, tile_ranges, vs, bg0, bg1, bg2, images, final_T, n_processed, hdr, st);
+    case 4: return fwd_launch<4>(records, vals, tile_ranges, vs, bg0, bg1, bg2, images, final_T, n_processed, hdr, st);
+    default: return fwd_launch<2>(records, vals, tile_ranges, vs, bg0, bg1, bg2, images, final_T, n_processed, hdr, st);
   }
-  int64_t grid = (int64_t)sm_count() * g_fwd_occ;
-  if (grid > vs.total_tiles) grid = vs.total_tiles;
-  if (grid < 1) grid = 1;
-  if (instrumented())
-    raster_fwd_kernel<true><<<(unsigned)grid, RT, 0, st>>>(
-        records, vals, tile_ranges, vs, bg0, bg1, bg2, images, final_T, n_processed,
-        &hdr->raster_tiles, &hdr->status, hdr->counters);
-  else
-    raster_fwd_kernel<false><<<(unsigned)grid, RT, 0, st>>>(
-        records, vals, tile_ranges, vs, bg0, bg1, bg2, images, final_T, n_processed,
-        &hdr->raster_tiles, &hdr->status, hdr->counters);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_raster_bwd(const fgs_record *records, const uint32_t *vals,
@@ -384,24 +538,11 @@ cudaError_t launch_raster_bwd(const fgs_record *records, const uint32_t *vals,
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(g2d, 0, sizeof(float) * G2D_STRIDE * (size_t)n_records, st)) != cudaSuccess)
     return e;
-  if (g_bwd_occ == 0) {
-    int occ = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, raster_bwd_kernel<false>, RT, 0)) != cudaSuccess)
-      return e;
-    g_bwd_occ = occ > 0 ? occ : 1;
+  switch (raster_shape(1)) {
+    case 1: return bwd_launch<1>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, hdr, st);
+    case 4: return bwd_launch<4>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, hdr, st);
+    default: return bwd_launch<2>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, hdr, st);
   }
-  int64_t grid = (int64_t)sm_count() * g_bwd_occ;
-  if (grid > vs.total_tiles) grid = vs.total_tiles;
-  if (grid < 1) grid = 1;
-  if (instrumented())
-    raster_bwd_kernel<true><<<(unsigned)grid, RT, 0, st>>>(
-        records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d,
-        &hdr->backward_tiles, &hdr->status, hdr->counters);
-  else
-    raster_bwd_kernel<false><<<(unsigned)grid, RT, 0, st>>>(
-        records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d,
-        &hdr->backward_tiles, &hdr->status, hdr->counters);
-  return cudaGetLastError();
 }
 
 }  // namespace fgs

@@ -25,7 +25,8 @@ FGS_ERR_CUDA = 4
 EXPORTS = ["fgs_workspace_size", "fgs_total_tiles", "fgs_total_pixels", "fgs_preprocess",
            "fgs_bin_sort", "fgs_rasterize", "fgs_backward", "fgs_backward_raster",
            "fgs_backward_preprocess", "fgs_bin_sort_noalloc", "fgs_read_status",
-           "fgs_set_instrumentation", "fgs_read_counters", "fgs_status_string"]
+           "fgs_set_instrumentation", "fgs_read_counters", "fgs_set_raster_shape",
+           "fgs_status_string"]
 
 
 class FgsCamera(ctypes.Structure):
@@ -80,6 +81,7 @@ def lib():
         L.fgs_set_instrumentation.argtypes = [ctypes.c_int]
         L.fgs_set_instrumentation.restype = None
         L.fgs_read_counters.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.fgs_set_raster_shape.argtypes = [ctypes.c_int, ctypes.c_int]
         L.fgs_status_string.argtypes = [ctypes.c_int]
         L.fgs_status_string.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -238,3 +240,8 @@ def fgs_read_counters(workspace, stream=None):
     out = (ctypes.c_uint64 * 4)()
     _check(lib().fgs_read_counters(_ptr(workspace), _stream(stream), out), "fgs_read_counters")
     return [int(v) for v in out]
+
+
+def fgs_set_raster_shape(fwd_pixels_per_thread: int, bwd_pixels_per_thread: int):
+    _check(lib().fgs_set_raster_shape(int(fwd_pixels_per_thread), int(bwd_pixels_per_thread)),
+           "fgs_set_raster_shape")

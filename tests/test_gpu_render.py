@@ -8,7 +8,7 @@ import pytest
 import torch
 
 import oracle
-from paper_2409_04751_gb300 import scenes
+from paper_2409_04751_gb300 import fgs, scenes
 from paper_2409_04751_gb300.renderer import FisheyeRenderer, scene_to_device
 from tests import parity
 
@@ -195,3 +195,28 @@ def test_gradients_near_axis_series_region(cuda_device):
     cam = scenes.fisheye_camera(128, 128, 180.0)
     g, ref = _grad_case(scene, [cam], seed=72)
     parity.check_grads(g, ref, "near-axis")
+
+
+def test_work_shapes_agree(cuda_device):
+    """Every rasterizer work shape (pixels per thread 1, 2, 4) gives the same image, final T and
+    processed counts bit for bit, and the same gradients up to summation order."""
+    scene = scenes.shell_scene(20_000, seed=80, sh_degree=3)
+    cam = scenes.pose_camera(300, 200, 190.0, seed=81)
+    dL = torch.as_tensor(scenes.upstream_grad((3 * 300 * 200,), 1.0, 82)).cuda()
+    outs = []
+    try:
+        for s in (1, 2, 4):
+            fgs.fgs_set_raster_shape(s, s)
+            r, gs, fr = _render(scene, [cam], capacity=1 << 20)
+            g = r.backward(gs, fr, dL)
+            outs.append((fr.images.cpu().numpy().copy(), fr.final_T.cpu().numpy().copy(),
+                         fr.n_processed.cpu().numpy().copy(),
+                         {k: v.cpu().numpy().copy() for k, v in g.items()}))
+    finally:
+        fgs.fgs_set_raster_shape(2, 2)
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0])
+        assert np.array_equal(o[1], outs[0][1])
+        assert np.array_equal(o[2], outs[0][2])
+        for k in o[3]:
+            assert parity.rel_l2(o[3][k], outs[0][3][k]) < 1e-5, k

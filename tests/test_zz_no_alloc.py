@@ -97,7 +97,7 @@ def test_noalloc_refuses_sizes_beyond_its_limits(cuda_device):
     assert L.fgs_bin_sort_noalloc(p, p, 10, cams, 1, p, p, (1 << 19) + 1, p, p, p, None) == \
         fgs.FGS_ERR_INVALID_ARG
     # more records than the fixed scratch holds
-    assert L.fgs_bin_sort_noalloc(p, p, (1 << 20) + 1, cams, 1, p, p, 1024, p, p, p, None) == \
+    assert L.fgs_bin_sort_noalloc(p, p, (1 << 19) + 1, cams, 1, p, p, 1024, p, p, p, None) == \
         fgs.FGS_ERR_INVALID_ARG
     # a missing status buffer
     assert L.fgs_bin_sort_noalloc(p, p, 10, cams, 1, p, p, 1024, p, p, None, None) == \
