@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(EMIT_THREADS)
                 uint32_t *__restrict__ vals, int64_t capacity, uint32_t *hist, int passes,
                 uint32_t *status) {
   __shared__ uint64_t s_off[EMIT_CHUNK + 1];
-  __shared__ uint2 s_rect[EMIT_CHUNK + 1];
+  __shared__ uint32_t s_base[EMIT_CHUNK + 1];   // global tile id of the rect's corner (x0, y0)
+  __shared__ uint32_t s_geom[EMIT_CHUNK + 1];   // rect width | view tiles_x << 16
   __shared__ uint32_t s_depth[EMIT_CHUNK + 1];
   __shared__ uint32_t s_rec[EMIT_CHUNK + 1];
   __shared__ uint32_t s_hist[SORT_MAX_PASSES * 256];
@@ -176,12 +177,28 @@ __global__ void __launch_bounds__(EMIT_THREADS)
     for (int i = tid; i < nw; i += EMIT_THREADS) {
       const uint32_t r = vis_rec[v0 + i];
       const uint4 w2 = __ldg(reinterpret_cast<const uint4 *>(rec + r) + 2);
+      const uint32_t x0 = w2.z & 0xffffu, y0 = w2.z >> 16, x1 = w2.w & 0xffffu;
+      const int v = (int)(r / (uint32_t)n_per_view);
+      const uint32_t tiles_x = (uint32_t)vs.v[v].tiles_x;
       s_off[i] = vis_off[v0 + i];
       s_rec[i] = r;
-      s_rect[i] = make_uint2(w2.z, w2.w);
+      s_base[i] = (uint32_t)vs.v[v].tile_offset + y0 * tiles_x + x0;
+      s_geom[i] = (x1 - x0 + 1u) | (tiles_x << 16);
       s_depth[i] = w2.y;
     }
     __syncthreads();
+    // depth digits (passes 0-3) are the same for all pairs of a record: count them once per
+    // record with the number of its pairs inside this chunk
+    for (int i = tid; i < nw; i += EMIT_THREADS) {
+      const uint64_t a0 = s_off[i] > (uint64_t)lo ? s_off[i] : (uint64_t)lo;
+      const uint64_t a1 = i + 1 < nw ? (s_off[i + 1] < (uint64_t)hi ? s_off[i + 1] : (uint64_t)hi)
+                                     : (uint64_t)hi;
+      if (a1 > a0) {
+        const uint32_t cnt = (uint32_t)(a1 - a0), dep = s_depth[i];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p * 256 + ((dep >> (8 * p)) & 255u)], cnt);
+      }
+    }
     for (int64_t jb = lo; jb < hi; jb += EMIT_THREADS) {
       const int64_t j = jb + tid;
       const bool valid = j < hi;
@@ -193,19 +210,21 @@ __global__ void __launch_bounds__(EMIT_THREADS)
           if (s_off[mid] <= (uint64_t)j) a = mid; else b = mid;
         }
         const uint32_t local = (uint32_t)((uint64_t)j - s_off[a]);
-        const uint2 rc = s_rect[a];
-        const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
-        const uint32_t w = x1 - x0 + 1u;
-        const uint32_t dy = local / w;
-        const uint32_t tx = x0 + (local - dy * w), ty = y0 + dy;
-        const uint32_t r = s_rec[a];
-        const int v = (int)((int64_t)r / n_per_view);
-        const uint64_t tile = (uint64_t)(vs.v[v].tile_offset + (int64_t)ty * vs.v[v].tiles_x + tx);
-        key = (tile << 32) | (uint64_t)s_depth[a];
+        const uint32_t geom = s_geom[a];
+        const uint32_t w = geom & 0xffffu, tiles_x = geom >> 16;
+        // row inside the rect: float quotient (local < 2^22 is exact in FP32) corrected by one
+        uint32_t dy = (uint32_t)((float)local * rcp_approx((float)w));
+        if (dy * w > local) --dy;
+        if ((dy + 1u) * w <= local) ++dy;
+        const uint32_t tile = s_base[a] + dy * tiles_x + (local - dy * w);
+        key = ((uint64_t)tile << 32) | (uint64_t)s_depth[a];
         keys[j] = key;
-        vals[j] = r;
+        vals[j] = s_rec[a];
       }
-      for (int p = 0; p < passes; ++p) {
+      // tile digits: the lowest changes from pair to pair along a rect row (plain atomics
+      // rarely collide); higher ones are shared by runs of pairs (warp-aggregated)
+      if (passes > 4 && valid) atomicAdd(&s_hist[4 * 256 + ((uint32_t)(key >> 32) & 255u)], 1u);
+      for (int p = 5; p < passes; ++p) {
         const uint32_t d = valid ? (uint32_t)(key >> (8 * p)) & 255u : 0x100u + (threadIdx.x & 31);
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         if (valid && (peers & lanemask_lt()) == 0u) atomicAdd(&s_hist[p * 256 + d], __popc(peers));
@@ -228,7 +247,7 @@ struct SortSmem {
   uint32_t part;
 };
 
-__global__ void __launch_bounds__(SORT_THREADS)
+__global__ void __launch_bounds__(SORT_THREADS, 4)
     onesweep_kernel(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                     uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
                     const int64_t *n_int, int64_t capacity, int shift, const uint32_t *hist,
@@ -251,93 +270,92 @@ __global__ void __launch_bounds__(SORT_THREADS)
   }
   const uint32_t lt = lanemask_lt();
 
-  for (;;) {
-    if (tid == 0) S.part = atomicAdd(part_counter, 1u);
-    __syncthreads();
-    const int64_t part = S.part;
-    if (part >= nparts) break;
-    const int64_t base = part * SORT_PART;
+  // one partition per CTA, claimed in launch order so every partition a CTA waits on belongs
+  // to a CTA that is already running
+  if (tid == 0) S.part = atomicAdd(part_counter, 1u);
+  __syncthreads();
+  const int64_t part = S.part;
+  if (part >= nparts) return;
+  const int64_t base = part * SORT_PART;
 
-    // load (warp-striped, order within a warp = k then lane = input order)
-    uint64_t key[SORT_ITEMS];
-    uint32_t val[SORT_ITEMS];
-    uint32_t rank[SORT_ITEMS];
+  // load (warp-striped, order within a warp = k then lane = input order)
+  uint64_t key[SORT_ITEMS];
+  uint32_t val[SORT_ITEMS];
+  uint32_t rank[SORT_ITEMS];
 #pragma unroll
-    for (int k = 0; k < SORT_ITEMS; ++k) {
-      const int64_t idx = base + (int64_t)w * 32 * SORT_ITEMS + k * 32 + lane;
-      if (idx < n) {
-        key[k] = kin[idx];
-        val[k] = vin[idx];
-      } else {
-        key[k] = 0ull;
-        val[k] = 0u;
-      }
+  for (int k = 0; k < SORT_ITEMS; ++k) {
+    const int64_t idx = base + (int64_t)w * 32 * SORT_ITEMS + k * 32 + lane;
+    if (idx < n) {
+      key[k] = kin[idx];
+      val[k] = vin[idx];
+    } else {
+      key[k] = 0ull;
+      val[k] = 0u;
     }
-    for (int e = tid; e < (SORT_THREADS / 32) * 256; e += SORT_THREADS) (&S.wcnt[0][0])[e] = 0u;
-    __syncthreads();
-    // warp multi-split ranking (stable)
+  }
+  for (int e = tid; e < (SORT_THREADS / 32) * 256; e += SORT_THREADS) (&S.wcnt[0][0])[e] = 0u;
+  __syncthreads();
+  // warp multi-split ranking (stable)
 #pragma unroll
-    for (int k = 0; k < SORT_ITEMS; ++k) {
-      const int64_t idx = base + (int64_t)w * 32 * SORT_ITEMS + k * 32 + lane;
-      const bool valid = idx < n;
-      const uint32_t d = valid ? (uint32_t)(key[k] >> shift) & 255u : 0x100u + lane;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      const uint32_t before = __popc(peers & lt);
-      uint32_t cnt = 0;
-      if (valid) cnt = S.wcnt[w][d];
-      __syncwarp();
-      if (valid && before == 0u) S.wcnt[w][d] = cnt + __popc(peers);
-      __syncwarp();
-      rank[k] = cnt + before;
-    }
-    __syncthreads();
-    // per digit: per-warp exclusive offsets and the partition's count
-    const int d = tid;
-    uint32_t run = 0;
+  for (int k = 0; k < SORT_ITEMS; ++k) {
+    const int64_t idx = base + (int64_t)w * 32 * SORT_ITEMS + k * 32 + lane;
+    const bool valid = idx < n;
+    const uint32_t d = valid ? (uint32_t)(key[k] >> shift) & 255u : 0x100u + lane;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t before = __popc(peers & lt);
+    uint32_t cnt = 0;
+    if (valid) cnt = S.wcnt[w][d];
+    __syncwarp();
+    if (valid && before == 0u) S.wcnt[w][d] = cnt + __popc(peers);
+    __syncwarp();
+    rank[k] = cnt + before;
+  }
+  __syncthreads();
+  // per digit: per-warp exclusive offsets and the partition's count
+  const int d = tid;
+  uint32_t run = 0;
 #pragma unroll
-    for (int ww = 0; ww < SORT_THREADS / 32; ++ww) {
-      const uint32_t c = S.wcnt[ww][d];
-      S.wcnt[ww][d] = run;
-      run += c;
-    }
-    const uint32_t dcount = run;
-    uint64_t *my = lb + part * 256 + d;
-    if (part == 0) st_volatile_u64(my, LB_INC | dcount);
-    else st_volatile_u64(my, LB_AGG | dcount);
-    uint32_t ptot;
-    const uint32_t lstart = block_excl_scan_256(dcount, S.warp_tmp, &ptot);
-    S.local_start[d] = lstart;
-    uint64_t prefix = 0;
-    if (part > 0) {
-      prefix = look_back(lb + d, part, 256, status);
-      st_volatile_u64(my, LB_INC | (prefix + dcount));
-    }
-    S.global_base[d] = S.hist_excl[d] + (uint32_t)prefix;
-    __syncthreads();
-    // local scatter into shared memory, sorted by digit
+  for (int ww = 0; ww < SORT_THREADS / 32; ++ww) {
+    const uint32_t c = S.wcnt[ww][d];
+    S.wcnt[ww][d] = run;
+    run += c;
+  }
+  const uint32_t dcount = run;
+  uint64_t *my = lb + part * 256 + d;
+  if (part == 0) st_volatile_u64(my, LB_INC | dcount);
+  else st_volatile_u64(my, LB_AGG | dcount);
+  uint32_t ptot;
+  const uint32_t lstart = block_excl_scan_256(dcount, S.warp_tmp, &ptot);
+  S.local_start[d] = lstart;
+  uint64_t prefix = 0;
+  if (part > 0) {
+    prefix = look_back(lb + d, part, 256, status);
+    st_volatile_u64(my, LB_INC | (prefix + dcount));
+  }
+  S.global_base[d] = S.hist_excl[d] + (uint32_t)prefix;
+  __syncthreads();
+  // local scatter into shared memory, sorted by digit
 #pragma unroll
-    for (int k = 0; k < SORT_ITEMS; ++k) {
-      const int64_t idx = base + (int64_t)w * 32 * SORT_ITEMS + k * 32 + lane;
-      if (idx < n) {
-        const uint32_t dd = (uint32_t)(key[k] >> shift) & 255u;
-        const uint32_t pos = S.local_start[dd] + S.wcnt[w][dd] + rank[k];
-        S.keys[pos] = key[k];
-        S.vals[pos] = val[k];
-      }
+  for (int k = 0; k < SORT_ITEMS; ++k) {
+    const int64_t idx = base + (int64_t)w * 32 * SORT_ITEMS + k * 32 + lane;
+    if (idx < n) {
+      const uint32_t dd = (uint32_t)(key[k] >> shift) & 255u;
+      const uint32_t pos = S.local_start[dd] + S.wcnt[w][dd] + rank[k];
+      S.keys[pos] = key[k];
+      S.vals[pos] = val[k];
     }
-    __syncthreads();
-    // global scatter: consecutive shared positions of one digit go to consecutive addresses
-    const int cnt = (int)min((int64_t)SORT_PART, n - base);
-    for (int i = tid; i < cnt; i += SORT_THREADS) {
-      const uint64_t kk = S.keys[i];
-      const uint32_t dd = (uint32_t)(kk >> shift) & 255u;
-      const uint64_t gpos = (uint64_t)S.global_base[dd] + (uint32_t)(i - S.local_start[dd]);
-      if (gpos < (uint64_t)n) {
-        kout[gpos] = kk;
-        vout[gpos] = S.vals[i];
-      }
+  }
+  __syncthreads();
+  // global scatter: consecutive shared positions of one digit go to consecutive addresses
+  const int cnt = (int)min((int64_t)SORT_PART, n - base);
+  for (int i = tid; i < cnt; i += SORT_THREADS) {
+    const uint64_t kk = S.keys[i];
+    const uint32_t dd = (uint32_t)(kk >> shift) & 255u;
+    const uint64_t gpos = (uint64_t)S.global_base[dd] + (uint32_t)(i - S.local_start[dd]);
+    if (gpos < (uint64_t)n) {
+      kout[gpos] = kk;
+      vout[gpos] = S.vals[i];
     }
-    __syncthreads();
   }
 }
 
@@ -403,15 +421,10 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
     if ((e = cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
       return e;
-    int occ = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, onesweep_kernel, SORT_THREADS,
-                                                           smem)) != cudaSuccess)
-      return e;
-    g_sort_occ = occ > 0 ? occ : 1;
+    g_sort_occ = 1;
   }
-  int64_t grid = (int64_t)sm_count() * g_sort_occ;
-  if (grid > L.sort_parts) grid = L.sort_parts;
-  if (grid < 1) grid = 1;
+  // one CTA per possible partition; those beyond the device-side count return at once
+  const int64_t grid = L.sort_parts > 0 ? L.sort_parts : 1;
   for (int p = 0; p < passes; ++p) {
     const uint64_t *kin = (p & 1) ? k1 : k0;
     const uint32_t *vin = (p & 1) ? v1 : v0;
