@@ -57,25 +57,38 @@ __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *s_
 }
 
 // Decoupled look-back: sums the values of partitions part-1, part-2, ... until an inclusive
-// entry is found. Bounded: gives up (FGS_ERR_TIMEOUT) after SPIN_LIMIT empty polls.
+// entry is found, reading four predecessors per step so the walk costs a quarter of the L2
+// round trips, and backing off while a predecessor has not published yet. Bounded: gives up
+// (FGS_ERR_TIMEOUT) after SPIN_LIMIT empty polls.
 __device__ __forceinline__ uint64_t look_back(const uint64_t *lb, int64_t part, int64_t stride,
                                               uint32_t *status) {
   uint64_t prefix = 0;
   uint32_t spins = 0;
   int64_t j = part - 1;
   while (j >= 0) {
-    const uint64_t st = ld_volatile_u64(lb + j * stride);
-    const uint64_t flag = st & ~LB_VAL;
-    if (flag == 0) {
+    uint64_t st[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) st[q] = j - q >= 0 ? ld_volatile_u64(lb + (j - q) * stride) : LB_INC;
+    int used = 0;
+    bool done = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (done || used < q) break;
+      const uint64_t flag = st[q] & ~LB_VAL;
+      if (flag == 0) break;
+      prefix += st[q] & LB_VAL;
+      ++used;
+      if (flag == LB_INC) done = true;
+    }
+    if (done) break;
+    if (used == 0) {
       if (++spins > SPIN_LIMIT) {
         set_status(status, ST_TIMEOUT);
         break;
       }
-      continue;
+      __nanosleep(32);
     }
-    prefix += st & LB_VAL;
-    if (flag == LB_INC) break;
-    --j;
+    j -= used;
   }
   return prefix;
 }
@@ -150,7 +163,7 @@ __global__ void __launch_bounds__(EMIT_THREADS)
                 const uint32_t *__restrict__ chunk_first, const int64_t *n_int,
                 const unsigned long long *n_vis, uint64_t *__restrict__ keys,
                 uint32_t *__restrict__ vals, int64_t capacity, uint32_t *hist, int passes,
-                uint32_t *status) {
+                int idx_bits, int packed, uint32_t *status) {
   __shared__ uint64_t s_off[EMIT_CHUNK + 1];
   __shared__ uint32_t s_base[EMIT_CHUNK + 1];   // global tile id of the rect's corner (x0, y0)
   __shared__ uint32_t s_geom[EMIT_CHUNK + 1];   // rect width | view tiles_x << 16
@@ -218,8 +231,12 @@ __global__ void __launch_bounds__(EMIT_THREADS)
         if ((dy + 1u) * w <= local) ++dy;
         const uint32_t tile = s_base[a] + dy * tiles_x + (local - dy * w);
         key = ((uint64_t)tile << 32) | (uint64_t)s_depth[a];
-        keys[j] = key;
-        vals[j] = s_rec[a];
+        if (packed) {
+          keys[j] = (key << idx_bits) | (uint64_t)s_rec[a];
+        } else {
+          keys[j] = key;
+          vals[j] = s_rec[a];
+        }
       }
       // tile digits: the lowest changes from pair to pair along a rect row (plain atomics
       // rarely collide); higher ones are shared by runs of pairs (warp-aggregated)
@@ -236,24 +253,50 @@ __global__ void __launch_bounds__(EMIT_THREADS)
     if (s_hist[e]) atomicAdd(hist + e, s_hist[e]);
 }
 
+// Shared memory of one onesweep CTA: two input buffers filled by TMA bulk copies (the next
+// partition lands in one while the current one is ranked in the other, which then serves as
+// the exchange buffer of the local scatter), per-warp digit counters and digit offsets.
+template <bool KV>
 struct SortSmem {
-  uint64_t keys[SORT_PART];
-  uint32_t vals[SORT_PART];
+  uint64_t keys[2][SORT_PART];
+  uint32_t vals[KV ? 2 : 1][KV ? SORT_PART : 4];
   uint32_t wcnt[SORT_THREADS / 32][256];  // per-warp digit counts -> per-warp offsets
   uint32_t local_start[256];               // digit start inside the partition
   uint32_t global_base[256];               // digit base in the output for this partition
   uint32_t hist_excl[256];                 // exclusive scan of this pass's global histogram
   uint32_t warp_tmp[8];
-  uint32_t part;
+  uint32_t part[2];
+  uint64_t bar[2];
 };
 
-__global__ void __launch_bounds__(SORT_THREADS, 4)
+// Issue the TMA bulk copies of partition `part` into buffer `b`: the 16-byte-aligned prefix
+// of its keys (and values); the few trailing elements of a ragged last partition are loaded
+// with plain loads after the wait.
+template <bool KV>
+__device__ __forceinline__ void sort_issue(SortSmem<KV> &S, int b, const uint64_t *kin,
+                                           const uint32_t *vin, int64_t part, int64_t n) {
+  const int64_t base = part * SORT_PART;
+  const uint32_t cnt = (uint32_t)min((int64_t)SORT_PART, n - base);
+  const uint32_t kb = (cnt & ~1u) * 8u;
+  const uint32_t vb = KV ? (cnt & ~3u) * 4u : 0u;
+  mbar_arrive_expect_tx(&S.bar[b], kb + vb);
+  if (kb) bulk_g2s(S.keys[b], kin + base, kb, &S.bar[b]);
+  if (KV && vb) bulk_g2s(S.vals[b], vin + base, vb, &S.bar[b]);
+}
+
+// One LSD pass over the 8-bit digit at bit `shift` of the stored words. Persistent CTAs take
+// partitions of SORT_PART keys in claim order. KV: 64-bit keys with 32-bit values; otherwise
+// packed words (key << idx_bits | value) only, and with `unpack` the pass writes the caller's
+// keys (word >> idx_bits) and values (low idx_bits) instead of words.
+template <bool KV>
+__global__ void __launch_bounds__(SORT_THREADS, KV ? 2 : 3)
     onesweep_kernel(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                     uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
-                    const int64_t *n_int, int64_t capacity, int shift, const uint32_t *hist,
-                    uint64_t *lb, uint64_t *lb_next, uint32_t *part_counter, uint32_t *status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SortSmem &S = *reinterpret_cast<SortSmem *>(smem_raw);
+                    const int64_t *n_int, int64_t capacity, int shift, int idx_bits, int unpack,
+                    const uint32_t *hist, uint64_t *lb, uint64_t *lb_next,
+                    uint32_t *part_counter, uint32_t *status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  SortSmem<KV> &S = *reinterpret_cast<SortSmem<KV> *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int64_t n = min(*n_int, capacity);
   const int64_t nparts = (n + SORT_PART - 1) / SORT_PART;
@@ -269,93 +312,124 @@ __global__ void __launch_bounds__(SORT_THREADS, 4)
     S.hist_excl[tid] = hx;
   }
   const uint32_t lt = lanemask_lt();
+  const uint64_t vmask = (idx_bits >= 64) ? ~0ull : ((1ull << idx_bits) - 1ull);
+  // Partitions are dealt round-robin (CTA c takes c, c + G, c + 2G, ...); the launch is
+  // cooperative, so all CTAs are resident and a predecessor's CTA is always making progress.
+  const int64_t G = gridDim.x;
+  int64_t part = blockIdx.x;
+  if (tid == 0) {
+    mbar_init(&S.bar[0], 1);
+    mbar_init(&S.bar[1], 1);
+    fence_mbar_init();
+    if (part < nparts) sort_issue<KV>(S, 0, kin, vin, part, n);
+  }
+  __syncthreads();
+  uint32_t phase = 0u;  // bit b = parity of buffer b's next phase
+  int cur = 0;
+  (void)part_counter;
 
-  // one partition per CTA, claimed in launch order so every partition a CTA waits on belongs
-  // to a CTA that is already running
-  if (tid == 0) S.part = atomicAdd(part_counter, 1u);
-  __syncthreads();
-  const int64_t part = S.part;
-  if (part >= nparts) return;
-  const int64_t base = part * SORT_PART;
+  while (part < nparts) {
+    const int64_t next = part + G;
+    // prefetch this CTA's next partition into the other buffer
+    if (tid == 0 && next < nparts) {
+      fence_proxy_async_smem();
+      sort_issue<KV>(S, cur ^ 1, kin, vin, next, n);
+    }
+    const bool ok = mbar_wait(&S.bar[cur], (phase >> cur) & 1u, status);
+    phase ^= 1u << cur;
+    if (__syncthreads_or(!ok)) {  // a copy never landed: drain (bounded) and leave
+      if (next < nparts) mbar_wait(&S.bar[cur ^ 1], (phase >> (cur ^ 1)) & 1u, status);
+      return;
+    }
+    const int64_t base = part * SORT_PART;
+    const uint32_t cnt = (uint32_t)min((int64_t)SORT_PART, n - base);
+    // ragged tail of the last partition: plain loads
+    if (tid < 4) {
+      const uint32_t kt = (cnt & ~1u) + tid;
+      if (tid < 1 && kt < cnt) S.keys[cur][kt] = kin[base + kt];
+      const uint32_t vt = (cnt & ~3u) + tid;
+      if (KV && vt < cnt) S.vals[cur][vt] = vin[base + vt];
+    }
+    for (int e = tid; e < (SORT_THREADS / 32) * 256; e += SORT_THREADS) (&S.wcnt[0][0])[e] = 0u;
+    __syncthreads();
 
-  // load (warp-striped, order within a warp = k then lane = input order)
-  uint64_t key[SORT_ITEMS];
-  uint32_t val[SORT_ITEMS];
-  uint32_t rank[SORT_ITEMS];
+    // load (warp-striped, order within a warp = k then lane = input order) and rank: warp
+    // multi-split with match_any, stable
+    uint64_t key[SORT_ITEMS];
+    uint32_t val[SORT_ITEMS];
+    uint32_t rank[SORT_ITEMS];
 #pragma unroll
-  for (int k = 0; k < SORT_ITEMS; ++k) {
-    const int64_t idx = base + (int64_t)w * 32 * SORT_ITEMS + k * 32 + lane;
-    if (idx < n) {
-      key[k] = kin[idx];
-      val[k] = vin[idx];
-    } else {
-      key[k] = 0ull;
-      val[k] = 0u;
+    for (int k = 0; k < SORT_ITEMS; ++k) {
+      const uint32_t li = (uint32_t)(w * 32 * SORT_ITEMS + k * 32 + lane);
+      const bool valid = li < cnt;
+      key[k] = valid ? S.keys[cur][li] : 0ull;
+      val[k] = (KV && valid) ? S.vals[cur][li] : 0u;
+      const uint32_t d = valid ? (uint32_t)(key[k] >> shift) & 255u : 0x100u + lane;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t before = __popc(peers & lt);
+      uint32_t c = 0;
+      if (valid) c = S.wcnt[w][d];
+      __syncwarp();
+      if (valid && before == 0u) S.wcnt[w][d] = c + __popc(peers);
+      __syncwarp();
+      rank[k] = c + before;
     }
-  }
-  for (int e = tid; e < (SORT_THREADS / 32) * 256; e += SORT_THREADS) (&S.wcnt[0][0])[e] = 0u;
-  __syncthreads();
-  // warp multi-split ranking (stable)
+    __syncthreads();
+    // per digit: per-warp exclusive offsets and the partition's count
+    const int d = tid;
+    uint32_t run = 0;
 #pragma unroll
-  for (int k = 0; k < SORT_ITEMS; ++k) {
-    const int64_t idx = base + (int64_t)w * 32 * SORT_ITEMS + k * 32 + lane;
-    const bool valid = idx < n;
-    const uint32_t d = valid ? (uint32_t)(key[k] >> shift) & 255u : 0x100u + lane;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t before = __popc(peers & lt);
-    uint32_t cnt = 0;
-    if (valid) cnt = S.wcnt[w][d];
-    __syncwarp();
-    if (valid && before == 0u) S.wcnt[w][d] = cnt + __popc(peers);
-    __syncwarp();
-    rank[k] = cnt + before;
-  }
-  __syncthreads();
-  // per digit: per-warp exclusive offsets and the partition's count
-  const int d = tid;
-  uint32_t run = 0;
-#pragma unroll
-  for (int ww = 0; ww < SORT_THREADS / 32; ++ww) {
-    const uint32_t c = S.wcnt[ww][d];
-    S.wcnt[ww][d] = run;
-    run += c;
-  }
-  const uint32_t dcount = run;
-  uint64_t *my = lb + part * 256 + d;
-  if (part == 0) st_volatile_u64(my, LB_INC | dcount);
-  else st_volatile_u64(my, LB_AGG | dcount);
-  uint32_t ptot;
-  const uint32_t lstart = block_excl_scan_256(dcount, S.warp_tmp, &ptot);
-  S.local_start[d] = lstart;
-  uint64_t prefix = 0;
-  if (part > 0) {
-    prefix = look_back(lb + d, part, 256, status);
-    st_volatile_u64(my, LB_INC | (prefix + dcount));
-  }
-  S.global_base[d] = S.hist_excl[d] + (uint32_t)prefix;
-  __syncthreads();
-  // local scatter into shared memory, sorted by digit
-#pragma unroll
-  for (int k = 0; k < SORT_ITEMS; ++k) {
-    const int64_t idx = base + (int64_t)w * 32 * SORT_ITEMS + k * 32 + lane;
-    if (idx < n) {
-      const uint32_t dd = (uint32_t)(key[k] >> shift) & 255u;
-      const uint32_t pos = S.local_start[dd] + S.wcnt[w][dd] + rank[k];
-      S.keys[pos] = key[k];
-      S.vals[pos] = val[k];
+    for (int ww = 0; ww < SORT_THREADS / 32; ++ww) {
+      const uint32_t c = S.wcnt[ww][d];
+      S.wcnt[ww][d] = run;
+      run += c;
     }
-  }
-  __syncthreads();
-  // global scatter: consecutive shared positions of one digit go to consecutive addresses
-  const int cnt = (int)min((int64_t)SORT_PART, n - base);
-  for (int i = tid; i < cnt; i += SORT_THREADS) {
-    const uint64_t kk = S.keys[i];
-    const uint32_t dd = (uint32_t)(kk >> shift) & 255u;
-    const uint64_t gpos = (uint64_t)S.global_base[dd] + (uint32_t)(i - S.local_start[dd]);
-    if (gpos < (uint64_t)n) {
-      kout[gpos] = kk;
-      vout[gpos] = S.vals[i];
+    const uint32_t dcount = run;
+    uint64_t *my = lb + part * 256 + d;
+    if (part == 0) st_volatile_u64(my, LB_INC | dcount);
+    else st_volatile_u64(my, LB_AGG | dcount);
+    uint32_t ptot;
+    const uint32_t lstart = block_excl_scan_256(dcount, S.warp_tmp, &ptot);
+    S.local_start[d] = lstart;
+    uint64_t prefix = 0;
+    if (part > 0) {
+      prefix = look_back(lb + d, part, 256, status);
+      st_volatile_u64(my, LB_INC | (prefix + dcount));
     }
+    S.global_base[d] = S.hist_excl[d] + (uint32_t)prefix;
+    __syncthreads();
+    // local scatter into the partition's own buffer, sorted by digit
+#pragma unroll
+    for (int k = 0; k < SORT_ITEMS; ++k) {
+      const uint32_t li = (uint32_t)(w * 32 * SORT_ITEMS + k * 32 + lane);
+      if (li < cnt) {
+        const uint32_t dd = (uint32_t)(key[k] >> shift) & 255u;
+        const uint32_t pos = S.local_start[dd] + S.wcnt[w][dd] + rank[k];
+        S.keys[cur][pos] = key[k];
+        if (KV) S.vals[cur][pos] = val[k];
+      }
+    }
+    __syncthreads();
+    // global scatter: consecutive shared positions of one digit go to consecutive addresses
+    for (uint32_t i = tid; i < cnt; i += SORT_THREADS) {
+      const uint64_t kk = S.keys[cur][i];
+      const uint32_t dd = (uint32_t)(kk >> shift) & 255u;
+      const uint64_t gpos = (uint64_t)S.global_base[dd] + (i - S.local_start[dd]);
+      if (gpos < (uint64_t)n) {
+        if (KV) {
+          kout[gpos] = kk;
+          vout[gpos] = S.vals[cur][i];
+        } else if (unpack) {
+          kout[gpos] = kk >> idx_bits;
+          vout[gpos] = (uint32_t)(kk & vmask);
+        } else {
+          kout[gpos] = kk;
+        }
+      }
+    }
+    __syncthreads();  // buffer, counters and offsets are reused by the next partition
+    part = next;
+    cur ^= 1;
   }
 }
 
@@ -370,7 +444,6 @@ __global__ void ranges_kernel(const uint64_t *__restrict__ keys, const int64_t *
   }
 }
 
-int g_sort_occ = 0;
 
 }  // namespace
 
@@ -395,11 +468,25 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
   if (R == 0) return cudaMemsetAsync(n_int, 0, sizeof(int64_t), st);
   if ((e = cudaMemsetAsync(scan_lb, 0, sizeof(uint64_t) * 2 * (size_t)L.scan_parts, st)) != cudaSuccess) return e;
 
-  // emission target: the passes ping-pong, the last one must land in the caller's buffers
-  uint64_t *k0 = (passes & 1) ? alt_keys : keys;
-  uint32_t *v0 = (passes & 1) ? alt_vals : vals;
-  uint64_t *k1 = (passes & 1) ? keys : alt_keys;
-  uint32_t *v1 = (passes & 1) ? vals : alt_vals;
+  // Packed mode when (tile << 32 | depth) << idx_bits | record fits in 64 bits: the passes
+  // move 8-byte words instead of 12-byte pairs and the last pass unpacks into the caller's
+  // keys and values. The ping-pong is arranged so that the last pass never reads the buffer
+  // it writes.
+  int idx_bits = 0;
+  while (idx_bits < 32 && ((int64_t)1 << idx_bits) < R) ++idx_bits;
+  const bool packed = idx_bits + 32 + vs.tile_bits <= 64;
+  uint64_t *k0, *k1;
+  uint32_t *v0 = nullptr, *v1 = nullptr;
+  if (packed) {
+    const bool last_even = ((passes - 1) & 1) == 0;  // last pass reads k0 if even
+    k0 = last_even ? alt_keys : keys;
+    k1 = last_even ? keys : alt_keys;
+  } else {
+    k0 = (passes & 1) ? alt_keys : keys;
+    v0 = (passes & 1) ? alt_vals : vals;
+    k1 = (passes & 1) ? keys : alt_keys;
+    v1 = (passes & 1) ? vals : alt_vals;
+  }
 
   uint32_t *vis_rec = reinterpret_cast<uint32_t *>(ws + L.vis_rec);
   uint64_t *vis_off = reinterpret_cast<uint64_t *>(ws + L.vis_off);
@@ -413,28 +500,58 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
   if (egrid < 1) egrid = 1;
   emit_kernel<<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
       records, n, vs, vis_rec, vis_off, chunk_first, n_int, &hdr->n_visible, k0, v0, capacity,
-      hist, passes, &hdr->status);
+      hist, passes, idx_bits, packed ? 1 : 0, &hdr->status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
-  const size_t smem = sizeof(SortSmem);
-  if (g_sort_occ == 0) {
-    if ((e = cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) != cudaSuccess)
+  static int occ_kv = 0, occ_packed = 0;
+  const size_t smem_kv = sizeof(SortSmem<true>), smem_packed = sizeof(SortSmem<false>);
+  if (occ_kv == 0) {
+    if ((e = cudaFuncSetAttribute(onesweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_kv)) != cudaSuccess)
       return e;
-    g_sort_occ = 1;
+    if ((e = cudaFuncSetAttribute(onesweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_packed)) != cudaSuccess)
+      return e;
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, onesweep_kernel<true>, SORT_THREADS, smem_kv);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, onesweep_kernel<false>, SORT_THREADS, smem_packed);
+    occ_kv = a > 0 ? a : 1;
+    occ_packed = b > 0 ? b : 1;
   }
-  // one CTA per possible partition; those beyond the device-side count return at once
-  const int64_t grid = L.sort_parts > 0 ? L.sort_parts : 1;
+  int64_t grid = (int64_t)sm_count() * (packed ? occ_packed : occ_kv);
+  if (grid > L.sort_parts) grid = L.sort_parts;
+  if (grid < 1) grid = 1;
   for (int p = 0; p < passes; ++p) {
     const uint64_t *kin = (p & 1) ? k1 : k0;
-    const uint32_t *vin = (p & 1) ? v1 : v0;
     uint64_t *kout = (p & 1) ? k0 : k1;
-    uint32_t *vout = (p & 1) ? v0 : v1;
     uint64_t *lb = sort_lb + (size_t)(p & 1) * 256 * (size_t)L.sort_parts;
     uint64_t *lbn = sort_lb + (size_t)((p + 1) & 1) * 256 * (size_t)L.sort_parts;
-    onesweep_kernel<<<(unsigned)grid, SORT_THREADS, smem, st>>>(
-        kin, vin, kout, vout, n_int, capacity, 8 * p, hist + p * 256, lb, lbn,
-        &hdr->sort_parts[p], &hdr->status);
+    if (packed) {
+      const bool last = p == passes - 1;
+      const uint64_t *a0 = kin;
+      const uint32_t *a1 = nullptr;
+      uint64_t *a2 = last ? keys : kout;
+      uint32_t *a3 = last ? vals : nullptr;
+      int a6 = idx_bits + 8 * p, a7 = idx_bits, a8 = last ? 1 : 0;
+      const uint32_t *a9 = hist + p * 256;
+      uint32_t *a12 = &hdr->sort_parts[p], *a13 = &hdr->status;
+      void *args[] = {&a0, &a1, &a2, &a3, &n_int, &capacity, &a6, &a7, &a8, &a9, &lb, &lbn,
+                      &a12, &a13};
+      e = cudaLaunchCooperativeKernel((const void *)onesweep_kernel<false>, dim3((unsigned)grid),
+                                      dim3(SORT_THREADS), args, smem_packed, st);
+      if (e != cudaSuccess) return e;
+    } else {
+      const uint32_t *vin = (p & 1) ? v1 : v0;
+      uint32_t *vout = (p & 1) ? v0 : v1;
+      int a6 = 8 * p, a7 = 0, a8 = 0;
+      const uint32_t *a9 = hist + p * 256;
+      uint32_t *a12 = &hdr->sort_parts[p], *a13 = &hdr->status;
+      void *args[] = {&kin, &vin, &kout, &vout, &n_int, &capacity, &a6, &a7, &a8, &a9, &lb, &lbn,
+                      &a12, &a13};
+      e = cudaLaunchCooperativeKernel((const void *)onesweep_kernel<true>, dim3((unsigned)grid),
+                                      dim3(SORT_THREADS), args, smem_kv, st);
+      if (e != cudaSuccess) return e;
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const int64_t rgrid = (int64_t)sm_count() * 8;

@@ -85,7 +85,7 @@ constexpr int EMIT_ITEMS = 4;
 constexpr int EMIT_PART = EMIT_THREADS * EMIT_ITEMS;  // records per scan partition
 constexpr int EMIT_CHUNK = 2048;                      // (record, tile) pairs per emission CTA
 constexpr int SORT_THREADS = 256;
-constexpr int SORT_ITEMS = 8;
+constexpr int SORT_ITEMS = 16;
 constexpr int SORT_PART = SORT_THREADS * SORT_ITEMS;  // keys per sort partition
 constexpr int SORT_MAX_PASSES = 8;
 constexpr int G2D_STRIDE = 12;                        // floats per record of screen-space grads

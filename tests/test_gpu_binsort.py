@@ -82,6 +82,8 @@ def _oracle(rect, depth, n, cams_py):
     (20000, [(1752, 1168)], 4, dict(max_ext=10, big_frac=0.002)),  # ~1M pairs, huge rects
     (4000, [(16, 16)], 5, dict(tie_frac=0.9)),                     # one tile, heavy ties
     (3000, [(64, 64)], 6, dict(p_empty=1.0)),                      # nothing visible
+    # 10 views x 30k records and 80k tiles: 15 + 17 + 32 bits > 64, the key/value sort path
+    (30000, [(1752, 1168)] * 10, 9, dict(max_ext=3, p_empty=0.5)),
 ])
 def test_binsort_bit_exact(cuda_device, n, sizes, seed, kw):
     cams_py = _cams(sizes)
