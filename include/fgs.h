@@ -19,7 +19,9 @@
  *    record buffer not 16-byte aligned). FGS_ERR_CUDA reports a failed launch.
  *  - Errors found on the device (more intersections than `capacity`; a bounded wait that ran
  *    out) are written to a status word in the workspace; fgs_bin_sort resets it and
- *    fgs_read_status reads it. Outputs are then undefined but every access stays in bounds.
+ *    fgs_read_status reads it. Outputs are then undefined but every access stays in bounds:
+ *    while the word is set, fgs_rasterize draws the background only and fgs_backward's
+ *    screen-space pass adds nothing.
  *  - Gradients are overwritten, not accumulated.
  *  - Calls on distinct workspaces are independent; calls sharing a workspace must not
  *    overlap in time (they share its counters).

@@ -433,12 +433,16 @@ __global__ void __launch_bounds__(SORT_THREADS, KV ? 2 : 3)
   }
 }
 
+// Tile ids come from the sorted keys; they are checked against the tile count so that keys
+// left undefined by a device-side error cannot steer a write out of bounds.
 __global__ void ranges_kernel(const uint64_t *__restrict__ keys, const int64_t *n_int,
-                              int64_t capacity, uint32_t *__restrict__ ranges) {
+                              int64_t capacity, int64_t total_tiles,
+                              uint32_t *__restrict__ ranges) {
   const int64_t n = min(*n_int, capacity);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t t = keys[i] >> 32;
+    if (t >= (uint64_t)total_tiles) continue;
     if (i == 0 || (keys[i - 1] >> 32) != t) ranges[2 * t] = (uint32_t)i;
     if (i == n - 1 || (keys[i + 1] >> 32) != t) ranges[2 * t + 1] = (uint32_t)(i + 1);
   }
@@ -555,7 +559,8 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const int64_t rgrid = (int64_t)sm_count() * 8;
-  ranges_kernel<<<(unsigned)rgrid, 256, 0, st>>>(keys, n_int, capacity, tile_ranges);
+  ranges_kernel<<<(unsigned)rgrid, 256, 0, st>>>(keys, n_int, capacity, vs.total_tiles,
+                                                  tile_ranges);
   return cudaGetLastError();
 }
 

@@ -97,6 +97,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
   uint32_t phase0 = 0, phase1 = 0;
   uint32_t n_eval = 0, n_blend = 0;
   const int lx = tid & (TILE - 1), ly0 = (tid / TILE) * PPT;
+  // after a device-side error in the binning the lists are undefined: render background only
+  const bool lists_ok = *(volatile const uint32_t *)status == 0u;
 
   for (;;) {
     if (tid == 0) s_tile = (int64_t)atomicAdd(tile_counter, 1u);
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
     bool done = true;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) done = done && !live[k];
-    const uint32_t count = ti.count;
+    const uint32_t count = lists_ok ? ti.count : 0u;
     const uint32_t nb = (count + BATCH - 1) / BATCH;
 
     if (nb > 0) {
@@ -305,6 +307,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
   uint32_t phase0 = 0, phase1 = 0;
   uint32_t n_eval = 0, n_contrib = 0;
   const int lx = tid & (TILE - 1), ly0 = (tid / TILE) * PPT;
+  // after a device-side error in the binning the lists are undefined: no gradient flows
+  const bool lists_ok = *(volatile const uint32_t *)status == 0u;
 
   for (;;) {
     if (tid == 0) {
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
         const int64_t off = (int64_t)py * V.width + px;
         const float *gi = dLdimg + 3 * V.pixel_offset + off;
         T[k] = final_T[V.pixel_offset + off];
-        last[k] = min(n_processed[V.pixel_offset + off], ti.count);
+        last[k] = lists_ok ? min(n_processed[V.pixel_offset + off], ti.count) : 0u;
         G0[k] = gi[0]; G1[k] = gi[plane]; G2[k] = gi[2 * plane];
       }
       // colour behind the current entry: sum over later blended entries + T_final bg
