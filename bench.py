@@ -410,7 +410,11 @@ def run_gpu(args):
         cpu = dict(value=v, unit="views/s", cores=thr, kind="oracle", sample=desc,
                    seconds=round(secs, 2))
 
-    launches_per_step = 1 + (1 + passes + 1) + 1 + 1 + 1
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batched:
+        batched = run_batched_compare(args, dev)
+
+    launches_per_step = 1 + (2 + passes + 1) + 1 + 1 + 1
     line = dict(
         metric=METRIC, value=value, unit="views/s", n_gpus=world, steps=args.steps,
         warmup=args.warmup, ms_per_step=1e3 * total_s / args.steps, higher_is_better=True,
@@ -426,6 +430,7 @@ def run_gpu(args):
         intersections=m, visible=vis, pair_counters=counters,
         roofline=roof, kernels=kern,
         cpu_baseline=cpu,
+        batched=batched,
         e2e=dict(value=world * args.steps / e2e_s, unit="views/s", h2d_bytes_per_step=h2d,
                  d2h_bytes_per_step=d2h),
         gpu_launches=launches_per_step * args.steps,
@@ -437,6 +442,90 @@ def run_gpu(args):
     return 0
 
 
+def run_batched_compare(args, dev):
+    """Batched multi-view fwd+bwd in one CUDA graph vs the plain one-view-per-call path, on the
+    1M-Gaussian, 64-view mixed-resolution workload. Returns a dict for the JSON line."""
+    import torch
+    from paper_2409_04751_gb300 import fgs, scenes
+    from paper_2409_04751_gb300.batched import GraphBatch
+    from paper_2409_04751_gb300.renderer import FisheyeRenderer, gaussians_of, scene_to_device
+
+    scene, cams = scenes.config3(n_views=args.batch_views)
+    gs = scene_to_device(scene, dev)
+    n = scene["means"].shape[0]
+    P = sum(c["width"] * c["height"] for c in cams)
+    dL = torch.as_tensor(scenes.upstream_grad((3 * P,), 1e-2, seed=33)).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    # plain: one view per call, buffers sized for the largest view
+    r = FisheyeRenderer(dev, capacity=1 << 22)
+    caps = []
+    for c in cams:
+        fr = r.forward(gs, [c], check=True)
+        caps.append(int(fr.n_intersections.item()))
+    r.capacity = int(max(caps) * 1.1) + 4096
+    frames = []
+    for c in cams:
+        frames.append(r.forward(gs, [c], check=True))
+    cap = r.capacity
+    ws = r._bufs["ws"]
+    g = gaussians_of(gs)
+    grads = {k: torch.empty_like(gs[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
+    offs = []
+    o = 0
+    for c in cams:
+        offs.append(o)
+        o += c["width"] * c["height"]
+
+    def plain_step():
+        for k, fr in enumerate(frames):
+            wsb = fgs.fgs_workspace_size(n, fr.cams, cap)
+            fgs.fgs_preprocess(g, fr.cams, fr.records, fr.tiles_touched)
+            fgs.fgs_bin_sort(fr.records, fr.tiles_touched, n, fr.cams, fr.keys, fr.vals, cap,
+                             fr.tile_ranges, fr.n_intersections, ws, wsb)
+            fgs.fgs_rasterize(fr.records, fr.vals, fr.tile_ranges, fr.cams, None, fr.images,
+                              fr.final_T, fr.n_processed, ws, wsb)
+            w, h = cams[k]["width"], cams[k]["height"]
+            fgs.fgs_backward(g, fr.cams, fr.records, fr.tiles_touched, fr.vals, fr.tile_ranges,
+                             None, fr.final_T, fr.n_processed,
+                             dL[3 * offs[k]:3 * (offs[k] + w * h)], grads["means"],
+                             grads["scales"], grads["quats"], grads["opacities"], grads["sh"],
+                             ws, wsb)
+
+    gb = GraphBatch(gs, cams, backward=True, device=dev)
+    gb.dL_dimages.copy_(dL)
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts
+
+    timed(plain_step, 1)
+    timed(gb.replay, 1)
+    tp = timed(plain_step, args.batch_reps)
+    tb = timed(gb.replay, args.batch_reps)
+    st = gb.status()
+    if st != fgs.FGS_OK:
+        raise fgs.FgsError(st, "batched replay")
+    V = len(cams)
+    mp = float(np.median(tp)) / 1e3
+    mb = float(np.median(tb)) / 1e3
+    return dict(workload=f"fisheye-GS 1M Gaussians SH3, {V} views mixed "
+                         "{512^2, 1024^2, 1752x1168, 2048x1536} x {150, 180, 200} deg, fwd+bwd",
+                views=V, pixels=P, intersections=int(gb.frame.n_intersections.item()),
+                batched_views_per_s=V / mb, plain_views_per_s=V / mp,
+                batched_ms=mb * 1e3, plain_ms=mp * 1e3, speedup=mp / mb,
+                gpu_launches_batched=1, note="batched = one CUDA-graph replay of one launch per "
+                "stage over all views; plain = one call sequence per view")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -446,6 +535,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-views", type=int, default=64)
+    ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--raster-shape", default="",
                     help="pixels per thread 'fwd,bwd' (1, 2 or 4); skips the autotuner")
     args = ap.parse_args()
