@@ -413,6 +413,9 @@ def run_gpu(args):
     batched = None
     if rank == 0 and world == 1 and not args.no_batched:
         batched = run_batched_compare(args, dev)
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        serving = run_serving(args, dev)
 
     launches_per_step = 1 + (2 + passes + 1) + 1 + 1 + 1
     line = dict(
@@ -431,6 +434,7 @@ def run_gpu(args):
         roofline=roof, kernels=kern,
         cpu_baseline=cpu,
         batched=batched,
+        serving=serving,
         e2e=dict(value=world * args.steps / e2e_s, unit="views/s", h2d_bytes_per_step=h2d,
                  d2h_bytes_per_step=d2h),
         gpu_launches=launches_per_step * args.steps,
@@ -526,6 +530,38 @@ def run_batched_compare(args, dev):
                 "stage over all views; plain = one call sequence per view")
 
 
+def run_serving(args, dev):
+    """Continuous-batching server vs plain one-request-at-a-time serving: 4 resident scenes
+    (200k, 500k, 1M, 2M Gaussians, SH 3), Poisson arrivals, random pose, square resolution
+    U{512..2048 step 256}, FOV U(150, 200) deg, forward rendering."""
+    import copy
+    import torch
+    from paper_2409_04751_gb300 import scenes
+    from paper_2409_04751_gb300.renderer import scene_to_device
+    from paper_2409_04751_gb300.serving import Server, poisson_requests, serve_plain
+
+    scs = [scene_to_device(scenes.shell_scene(n, seed=40 + k, sh_degree=3), dev)
+           for k, n in enumerate((200_000, 500_000, 1_000_000, 2_000_000))]
+    out = {"workload": "fisheye-GS serving, 4 resident scenes (0.2M, 0.5M, 1M, 2M Gaussians, SH3), "
+                       "Poisson arrivals, random pose, square 512..2048 px, FOV U(150,200) deg, fwd",
+           "rates": {}}
+    calib = [[scenes.pose_camera(1024, 1024, 175.0, seed=7 + k)] for k in range(len(scs))]
+    for rate in args.serve_rates:
+        reqs = poisson_requests(float(rate), args.serve_seconds, len(scs), seed=int(rate))
+        srv = Server(scs, n_slots=args.serve_slots, max_batch_views=args.serve_batch,
+                     device=dev)
+        srv.calibrate(calib)
+        # warm both paths on a few requests (untimed)
+        Server(scs, n_slots=2, device=dev).run(copy.deepcopy(reqs[:8]))
+        serve_plain(scs, copy.deepcopy(reqs[:4]), device=dev)
+        torch.cuda.synchronize()
+        a = srv.run(copy.deepcopy(reqs)).summary()
+        torch.cuda.synchronize()
+        b = serve_plain(scs, copy.deepcopy(reqs), device=dev).summary()
+        out["rates"][str(rate)] = {"requests": len(reqs), "batched": a, "plain": b}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -536,6 +572,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-rates", type=int, nargs="*", default=[200, 500, 1000, 2000])
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-slots", type=int, default=3)
+    ap.add_argument("--serve-batch", type=int, default=16)
     ap.add_argument("--batch-views", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--raster-shape", default="",
