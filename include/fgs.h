@@ -179,8 +179,9 @@ fgs_status fgs_bin_sort_noalloc(const fgs_record *records, const uint32_t *tiles
                                 int64_t *n_intersections, uint32_t *status, fgs_stream stream);
 
 /* The two halves of fgs_backward, for callers that time or reuse them separately:
- * fgs_backward_raster replays the blend and accumulates per-record screen-space gradients
- * (dL/d xy, dL/d conic, dL/d opacity, dL/d rgb) into the workspace; fgs_backward_preprocess
+ * fgs_backward_raster replays the blend and accumulates per-record screen-space gradient sums
+ * (the moments of dL/d exponent over the pixel offsets, dL/d opacity and dL/d rgb terms) into
+ * the workspace; fgs_backward_preprocess
  * pulls them back to the Gaussian inputs (overwriting the d_* outputs). Called in this order
  * on one workspace they equal fgs_backward. n = Gaussians per view. */
 fgs_status fgs_backward_raster(const fgs_record *records, const uint32_t *vals,

@@ -193,12 +193,20 @@ __global__ void __launch_bounds__(128)
                  __ldg(g.scales + 3 * i + 2), S);
       load_sh<D, VEC>(g.sh, i, shc);
     }
-    const float4 g0 = __ldg(reinterpret_cast<const float4 *>(g2d + (size_t)r * G2D_STRIDE));
-    const float4 g1 = __ldg(reinterpret_cast<const float4 *>(g2d + (size_t)r * G2D_STRIDE) + 1);
+    // the rasterizer backward leaves, per record, the moments of dL/dp over the pixel offsets
+    // d = pixel - xy (p = -0.5 d^T conic d): m = sum dL/dp (dx, dy, dx^2, dx dy, dy^2), then
+    // sum dL/dalpha alpha_raw and dL/drgb. With the record's conic (A, B, C) and opacity:
+    //   dL/dxy = (A m_x + B m_y, B m_x + C m_y), dL/dA = -m_xx / 2, dL/dB = -m_xy,
+    //   dL/dC = -m_yy / 2, dL/dopacity = sum dL/dalpha alpha_raw / opacity.
+    const float4 m0 = __ldg(reinterpret_cast<const float4 *>(g2d + (size_t)r * G2D_STRIDE));
+    const float4 m1 = __ldg(reinterpret_cast<const float4 *>(g2d + (size_t)r * G2D_STRIDE) + 1);
     const float gb = __ldg(g2d + (size_t)r * G2D_STRIDE + 8);
     const float4 rc0 = __ldg(reinterpret_cast<const float4 *>(rec + r));
     const float4 rc1 = __ldg(reinterpret_cast<const float4 *>(rec + r) + 1);
     const float rgb2 = __ldg(reinterpret_cast<const float *>(rec + r) + 8);
+    const float4 g0 = make_float4(rc0.z * m0.x + rc0.w * m0.y, rc0.w * m0.x + rc1.x * m0.y,
+                                  -0.5f * m0.z, -m0.w);
+    const float4 g1 = make_float4(-0.5f * m1.x, m1.y / rc1.y, m1.z, m1.w);
     dop += g1.y;
 
     const float x = fmaf(V.W[0], mx, fmaf(V.W[1], my, fmaf(V.W[2], mz, V.b[0])));

@@ -12,10 +12,14 @@
 //
 // The backward replays each pixel's blend back to front from its final transmittance and the
 // number of list entries it processed (both written by the forward), recovering the
-// transmittance before each Gaussian by division; nothing per (pixel, Gaussian) is stored. Each
-// thread first sums its own pixels' screen-space gradients of a Gaussian; the warp then reduces
-// the nine sums with a transpose reduction (each exchange halves the values a lane carries: 14
-// shuffles instead of 45) and eight lanes add their totals to the record's accumulator.
+// transmittance before each Gaussian by division; nothing per (pixel, Gaussian) is stored. Per
+// contributing pair it accumulates nine sums that depend on the pixel only: the moments
+// sum dL/dp (dx, dy, dx^2, dx dy, dy^2) of the exponent p = -0.5 d^T conic d, sum dL/dalpha
+// alpha_raw, and dL/drgb. Each thread first sums its own pixels; the warp then reduces the nine
+// sums with a transpose reduction (each exchange halves the values a lane carries: 14 shuffles
+// instead of 45) and eight lanes add their totals to the record's accumulator. The preprocess
+// backward turns the moments into dL/dxy, dL/dconic and dL/dopacity with the record's conic and
+// opacity.
 #include "fgs_internal.cuh"
 
 namespace fgs {
@@ -292,7 +296,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
   constexpr int NT = TILE_PIX / PPT;
   constexpr int PER = BATCH / NT;
   __shared__ __align__(128) fgs_record raw[2][BATCH];
-  __shared__ __align__(16) float4 xf[BATCH][4];
+  __shared__ __align__(16) float4 xf[BATCH][3];
   __shared__ uint32_t xidx[BATCH];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int64_t s_tile;
@@ -323,7 +327,9 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
     const int px = ti.tx * TILE + lx;
     const float fpx = (float)px + 0.5f;
     const int64_t plane = (int64_t)V.width * V.height;
-    float fpy[PPT], T[PPT], G0[PPT], G1[PPT], G2[PPT], S0[PPT], S1[PPT], S2[PPT];
+    // per pixel: transmittance, dL/dC, and GS = <dL/dC, colour behind the current entry>
+    // (the sum over later blended entries plus T_final bg), kept as one scalar
+    float fpy[PPT], T[PPT], G0[PPT], G1[PPT], G2[PPT], GS[PPT];
     uint32_t last[PPT];
     uint32_t my_max = 0;
 #pragma unroll
@@ -339,8 +345,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
         last[k] = lists_ok ? min(n_processed[V.pixel_offset + off], ti.count) : 0u;
         G0[k] = gi[0]; G1[k] = gi[plane]; G2[k] = gi[2 * plane];
       }
-      // colour behind the current entry: sum over later blended entries + T_final bg
-      S0[k] = T[k] * bg0; S1[k] = T[k] * bg1; S2[k] = T[k] * bg2;
+      GS[k] = T[k] * (G0[k] * bg0 + G1[k] * bg1 + G2[k] * bg2);
       my_max = max(my_max, last[k]);
     }
     atomicMax(&s_max, my_max);
@@ -386,8 +391,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
             const fgs_record &g = raw[s][slot];
             xf[slot][0] = make_float4(g.xy[0], g.xy[1], -0.5f * LOG2E * g.conic[0], -LOG2E * g.conic[1]);
             xf[slot][1] = make_float4(-0.5f * LOG2E * g.conic[2], log2f(g.opacity), g.rgb[0], g.rgb[1]);
-            xf[slot][2] = make_float4(g.rgb[2], g.conic[0], g.conic[1], g.conic[2]);
-            xf[slot][3] = make_float4(rcp_approx(g.opacity), 0.f, 0.f, 0.f);
+            xf[slot][2] = make_float4(g.rgb[2], 0.f, 0.f, 0.f);
           }
         }
         __syncthreads();
@@ -413,29 +417,31 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
                 if (e >= LOG2_ALPHA_MIN) {
                   contrib = true;
                   if (COUNT) ++n_contrib;
-                  const float4 r2 = xf[j][2];
+                  const float cb = xf[j][2].x;
                   const float araw = ex2_approx(e);
                   const float alpha = fminf(ALPHA_MAX, araw);
                   const float om = rcp_approx(1.f - alpha);
                   T[k] *= om;  // transmittance before this Gaussian
                   const float wgt = alpha * T[k];
-                  const float dLda = G0[k] * (c.z * T[k] - S0[k] * om) +
-                                     G1[k] * (c.w * T[k] - S1[k] * om) +
-                                     G2[k] * (r2.x * T[k] - S2[k] * om);
-                  S0[k] = fmaf(c.z, wgt, S0[k]);
-                  S1[k] = fmaf(c.w, wgt, S1[k]);
-                  S2[k] = fmaf(r2.x, wgt, S2[k]);
+                  const float gc = G0[k] * c.z + G1[k] * c.w + G2[k] * cb;  // <dL/dC, colour>
+                  // dL/dalpha = <dL/dC, colour T - behind / (1 - alpha)>
+                  const float dLda = fmaf(T[k], gc, -om * GS[k]);
+                  GS[k] = fmaf(gc, wgt, GS[k]);
                   v[6] = fmaf(G0[k], wgt, v[6]);
                   v[7] = fmaf(G1[k], wgt, v[7]);
                   v[8] = fmaf(G2[k], wgt, v[8]);
                   if (araw < ALPHA_MAX) {
-                    const float dLdp = dLda * alpha;  // p = -0.5 d^T conic d
-                    v[0] = fmaf(dLdp, r2.y * dx + r2.z * dy, v[0]);
-                    v[1] = fmaf(dLdp, r2.z * dx + r2.w * dy, v[1]);
-                    v[2] = fmaf(-0.5f * dx * dx, dLdp, v[2]);
-                    v[3] = fmaf(-dx * dy, dLdp, v[3]);
-                    v[4] = fmaf(-0.5f * dy * dy, dLdp, v[4]);
-                    v[5] = fmaf(dLda * araw, xf[j][3].x, v[5]);
+                    // alpha = opacity exp(p), p = -0.5 d^T conic d: accumulate the moments of
+                    // dL/dp over the pixel offsets; the conic and opacity are applied once per
+                    // record in the preprocess backward
+                    const float dLdp = dLda * alpha;
+                    const float tx = dLdp * dx, ty = dLdp * dy;
+                    v[0] += tx;
+                    v[1] += ty;
+                    v[2] = fmaf(tx, dx, v[2]);
+                    v[3] = fmaf(tx, dy, v[3]);
+                    v[4] = fmaf(ty, dy, v[4]);
+                    v[5] = fmaf(dLda, araw, v[5]);
                   }
                 }
               }
