@@ -16,7 +16,6 @@ against) on the same workload, a bounded sample of pixels per step.
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -239,7 +238,6 @@ def run_gpu(args):
     cap = r.capacity
     wsb = fgs.fgs_workspace_size(n, cam_c, cap)
     tiles = fgs.fgs_total_tiles(cam_c)
-    passes = (32 + max(1, math.ceil(math.log2(tiles))) + 7) // 8
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -381,10 +379,13 @@ def run_gpu(args):
                               peak=fp32_peak, unit="TFLOP/s")
     kern["raster_bwd"] = dict(bound="alu", achieved=bwd_flops / (stage_ms[3] * 1e-3) / 1e12,
                               peak=fp32_peak, unit="TFLOP/s")
-    sort_bytes = m * (12 + 12 + passes * 24) + n * 4
+    vis = int((fr.tiles_touched > 0).sum().item())
+    # bin + sort: tiles_touched, two reads of each visible record's rect and depth (count and
+    # scatter walks), the bucket words written and read (8 + 8 B per pair), keys and values
+    # written (12 B per pair)
+    sort_bytes = n * 4 + vis * 2 * 16 + m * (8 + 8 + 12)
     kern["bin_sort"] = dict(bound="hbm", achieved=sort_bytes / (stage_ms[1] * 1e-3) / 1e9,
                             peak=peaks["hbm_gbs"], unit="GB/s")
-    vis = int((fr.tiles_touched > 0).sum().item())
     pre_bytes = n * 16 + vis * (12 + 16 + 4 * 48 + 48) + n * 4
     kern["preprocess_fwd"] = dict(bound="hbm", achieved=pre_bytes / (stage_ms[0] * 1e-3) / 1e9,
                                   peak=peaks["hbm_gbs"], unit="GB/s")
@@ -397,7 +398,7 @@ def run_gpu(args):
     roof["kernel"] = names[dom]
     roof["traffic"] = _traffic({"raster_bwd": "raster_bwd_kernel",
                                 "raster_fwd": "raster_fwd_kernel",
-                                "bin_sort": "onesweep_kernel",
+                                "bin_sort": "segsort_kernel",
                                 "preprocess_fwd": "preprocess_fwd_kernel",
                                 "preprocess_bwd": "preprocess_bwd_kernel"}[names[dom]])
     roof["peak_source"] = ("FP32: 152 SMs x 128 lanes x 2 x max SM clock "
@@ -417,7 +418,9 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_serving:
         serving = run_serving(args, dev)
 
-    launches_per_step = 1 + (2 + passes + 1) + 1 + 1 + 1
+    # preprocess; scan, count, tile scan, scatter, two segment-sort classes; raster fwd; raster
+    # bwd; preprocess bwd
+    launches_per_step = 1 + 6 + 1 + 1 + 1
     line = dict(
         metric=METRIC, value=value, unit="views/s", n_gpus=world, steps=args.steps,
         warmup=args.warmup, ms_per_step=1e3 * total_s / args.steps, higher_is_better=True,

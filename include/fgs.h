@@ -52,7 +52,9 @@ typedef enum {
 /* An equidistant fisheye camera (Sec. 3.1 "Transformation", Sec. 3.2):
  *   mu_c = W mu + b (W row-major, world -> camera; camera x right, y down, z forward),
  *   theta = atan2(|(x_c, y_c)|, z_c), x_p = cx + fx theta x_c / l_z, y_p = cy + fy theta y_c / l_z.
- * Pixel (i, j) is sampled at (i + 0.5, j + 0.5). */
+ * Pixel (i, j) is sampled at (i + 0.5, j + 0.5).
+ * A view holds at most 2^20 tiles and at most 65535 tile columns and rows (the record's tile
+ * rect is 16-bit); a call with a larger view returns FGS_ERR_INVALID_ARG. */
 typedef struct {
   float W[9];
   float b[3];
@@ -163,9 +165,9 @@ fgs_status fgs_backward(const fgs_gaussians *g, const fgs_camera *cams, int n_vi
  * synchronise the device), have no workspace to pass; this entry point keeps the sort's scratch
  * in a fixed array inside the library instead, and the caller passes only inputs and outputs.
  * Results are the same as fgs_bin_sort's for the same inputs.
- *  - Limits: n_views * n <= 2^19 records and capacity <= 2^19 key slots; larger sizes return
- *    FGS_ERR_INVALID_ARG before anything is launched. Every GPU that loads the library holds
- *    the array (about 13 MB) until the process exits.
+ *  - Limits: n_views * n <= 2^19 records, capacity <= 2^19 key slots and at most 2^17 tiles
+ *    over all views; larger sizes return FGS_ERR_INVALID_ARG before anything is launched.
+ *    Every GPU that loads the library holds the array (about 12 MB) until the process exits.
  *  - status: DEVICE pointer to one uint32 the call fills, in stream order, with the device
  *    status word (FGS_OK, FGS_ERR_CAPACITY or FGS_ERR_TIMEOUT) once the sort has run.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress);

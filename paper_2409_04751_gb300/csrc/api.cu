@@ -52,6 +52,8 @@ bool build_views(const fgs_camera *cams, int n_views, Views *vs) {
     V.tiles_x = (c.width + TILE - 1) / TILE;
     V.tiles_y = (c.height + TILE - 1) / TILE;
     if ((int64_t)V.tiles_x * V.tiles_y > MAX_TILES_PER_VIEW) return false;
+    // record rects hold 16-bit tile coordinates
+    if (V.tiles_x > 65535 || V.tiles_y > 65535) return false;
     V.tile_offset = tiles;
     V.pixel_offset = pixels;
     tiles += (int64_t)V.tiles_x * V.tiles_y;
@@ -98,7 +100,7 @@ fgs_status fgs_workspace_size(int64_t n, const fgs_camera *cams, int n_views, in
   if (bytes == nullptr || n < 0 || capacity <= 0 || capacity > 0xffffffffLL ||
       !build_views(cams, n_views, &vs))
     return FGS_ERR_INVALID_ARG;
-  *bytes = ws_layout((int64_t)n_views * n, capacity).total;
+  *bytes = ws_layout((int64_t)n_views * n, capacity, vs.total_tiles).total;
   return FGS_OK;
 }
 
@@ -135,7 +137,7 @@ fgs_status fgs_bin_sort(const fgs_record *records, const uint32_t *tiles_touched
   if (!keys || !vals || !tile_ranges || !n_intersections || !workspace) return FGS_ERR_INVALID_ARG;
   if (n > 0 && (!records || !tiles_touched || !aligned(records, 16))) return FGS_ERR_INVALID_ARG;
   if (!aligned(workspace, 256)) return FGS_ERR_INVALID_ARG;
-  const WsLayout L = ws_layout((int64_t)n_views * n, capacity);
+  const WsLayout L = ws_layout((int64_t)n_views * n, capacity, vs.total_tiles);
   if (workspace_bytes < L.total) return FGS_ERR_INVALID_ARG;
   return cuda_status(launch_bin_sort(records, tiles_touched, n, vs, keys, vals, capacity,
                                      tile_ranges, n_intersections,
@@ -175,8 +177,8 @@ fgs_status fgs_backward_raster(const fgs_record *records, const uint32_t *vals,
   if (R > 0 && (!records || !aligned(records, 16))) return FGS_ERR_INVALID_ARG;
   if (!aligned(workspace, 256)) return FGS_ERR_INVALID_ARG;
   // the header and the screen-space gradient region precede every capacity-dependent region
-  const WsLayout L = ws_layout(R, 1);
-  if (workspace_bytes < L.hist) return FGS_ERR_INVALID_ARG;
+  const WsLayout L = ws_layout(R, 1, 1);
+  if (workspace_bytes < L.vis_rec) return FGS_ERR_INVALID_ARG;
   const float b0 = bg ? bg[0] : 0.f, b1 = bg ? bg[1] : 0.f, b2 = bg ? bg[2] : 0.f;
   return cuda_status(launch_raster_bwd(records, vals, tile_ranges, vs, b0, b1, b2, final_T,
                                        n_processed, dL_dimages, R,
@@ -196,8 +198,8 @@ fgs_status fgs_backward_preprocess(const fgs_gaussians *g, const fgs_camera *cam
   if (g->n > 0 && (!records || !tiles_touched || !d_means || !d_scales || !d_quats ||
                    !d_opacities || !d_sh || !aligned(records, 16)))
     return FGS_ERR_INVALID_ARG;
-  const WsLayout L = ws_layout(R, 1);
-  if (workspace_bytes < L.hist) return FGS_ERR_INVALID_ARG;
+  const WsLayout L = ws_layout(R, 1, 1);
+  if (workspace_bytes < L.vis_rec) return FGS_ERR_INVALID_ARG;
   char *ws = reinterpret_cast<char *>(workspace);
   WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
   return cuda_status(launch_preprocess_bwd(to_ptrs(g), vs, records, tiles_touched,

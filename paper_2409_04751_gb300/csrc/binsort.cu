@@ -1,23 +1,27 @@
 // binsort.cu - tile binning and key sort (Sec. 3.1 "Rendering"; Sec. 4.1 duplicateWithKeys and
 // radixSort), sm_103a.
 //
+// The result is the one the method defines: for every (record, tile) pair of a record's tile
+// rect, key = tile << 32 | depth bits and value = record, stably sorted by key, and each tile's
+// [start, end) in the sorted arrays. Instead of a device-wide radix sort over all key bits, the
+// pairs are bucketed by tile first and each tile's bucket is sorted on its own:
+//
 //  1. scan_kernel: single-pass scan of tiles_touched with decoupled look-back (partitions of
 //     1024 records claimed in order through an atomic counter). For every record with pairs it
 //     writes its pair offset and its rank among such records (a compacted list), and for every
-//     2048-pair chunk the rank of the record holding the chunk's first pair.
-//  2. emit_kernel: one CTA per 2048-pair chunk, so the work per CTA is fixed however many
-//     tiles one Gaussian covers. The CTA loads the few records its chunk spans into shared
-//     memory; each pair finds its record by binary search there and writes
-//     key = tile << 32 | depth bits, value = record, coalesced. The same pass counts the 8-bit
-//     digit histograms of every radix pass (warp-aggregated shared atomics), so the sort needs
-//     no separate histogram read of the keys.
-//  3. onesweep_kernel (one launch per 8-bit digit): Adinets & Merrill's single-pass LSD radix
-//     sort: each partition of 4096 keys is ranked in shared memory (warp multi-split with
-//     match_any, stable), publishes its per-digit counts, resolves its global digit offsets by
-//     decoupled look-back over earlier partitions (bounded waits), and scatters through shared
-//     memory so that runs of equal digits are written contiguously.
-//  4. ranges_kernel: [start, end) of every tile in the sorted keys.
-// The number of valid pairs is read on the device, so nothing here needs a host sync.
+//     1024-pair chunk the rank of the record holding the chunk's first pair.
+//  2. pair_kernel<false>: one CTA per 1024-pair chunk (the work per CTA is fixed however many
+//     tiles one Gaussian covers) counts the pairs of every tile.
+//  3. tile_scan_kernel: exclusive scan of the tile counts (decoupled look-back) gives every
+//     tile's start; tiles are listed by segment size.
+//  4. pair_kernel<true>: the same walk over the pairs claims a slot in the pair's tile bucket and
+//     writes depth bits << 32 | record there.
+//  5. segsort_kernel (one launch per size class): each tile's bucket is sorted in shared memory
+//     (a one-pass bucket sort on the depth bits, or LSD radix passes when the depths are too
+//     clustered for it) and written out as keys and values.
+// Moving 8-byte words through memory twice (bucket write, bucket read) replaces the five to
+// seven passes of a device-wide radix sort over (tile, depth) keys. The number of valid pairs
+// is read on the device, so nothing here needs a host sync.
 #include "fgs_internal.cuh"
 
 namespace fgs {
@@ -157,26 +161,37 @@ __global__ void __launch_bounds__(EMIT_THREADS)
   }
 }
 
+
+// The (record, tile) pairs of one EMIT_CHUNK-pair chunk per CTA iteration, in pair order.
+// The CTA loads the few records its chunk spans into shared memory and marks the first pair of
+// each; a max-scan over the chunk then gives every pair its record. SCATTER = false: count the
+// pairs of every tile (tile_ranges[2t]). SCATTER = true: claim a slot in the tile's bucket
+// (tile_ranges[2t + 1] holds the bucket's next free slot) and write the word
+// depth_bits << 32 | record there. Both passes visit the same pairs in the same way, so every
+// bucket is filled exactly. Pairs whose tile falls outside their view's grid (a malformed
+// caller record) are skipped by both.
+template <bool SCATTER>
 __global__ void __launch_bounds__(EMIT_THREADS)
-    emit_kernel(const fgs_record *__restrict__ rec, int64_t n_per_view, Views vs,
+    pair_kernel(const fgs_record *__restrict__ rec, int64_t n_per_view, Views vs,
                 const uint32_t *__restrict__ vis_rec, const uint64_t *__restrict__ vis_off,
                 const uint32_t *__restrict__ chunk_first, const int64_t *n_int,
-                const unsigned long long *n_vis, uint64_t *__restrict__ keys,
-                uint32_t *__restrict__ vals, int64_t capacity, uint32_t *hist, int passes,
-                int idx_bits, int packed, uint32_t *status) {
-  __shared__ uint64_t s_off[EMIT_CHUNK + 1];
-  __shared__ uint32_t s_base[EMIT_CHUNK + 1];   // global tile id of the rect's corner (x0, y0)
-  __shared__ uint32_t s_geom[EMIT_CHUNK + 1];   // rect width | view tiles_x << 16
+                const unsigned long long *n_vis, uint32_t *ranges, uint64_t *__restrict__ words,
+                int64_t capacity, uint32_t *status) {
+  constexpr int PER = EMIT_CHUNK / EMIT_THREADS;  // pairs per thread and chunk
+  __shared__ uint32_t s_off[EMIT_CHUNK + 1];   // first pair of the record (clamped to hi)
+  __shared__ uint32_t s_base[EMIT_CHUNK + 1];  // global tile id of the rect's corner (x0, y0)
+  __shared__ uint32_t s_geom[EMIT_CHUNK + 1];  // rect width | rect height << 16 (0: skip)
+  __shared__ uint32_t s_tx[EMIT_CHUNK + 1];    // the view's tiles_x
   __shared__ uint32_t s_depth[EMIT_CHUNK + 1];
   __shared__ uint32_t s_rec[EMIT_CHUNK + 1];
-  __shared__ uint32_t s_hist[SORT_MAX_PASSES * 256];
-  const int tid = threadIdx.x;
+  __shared__ uint16_t s_own[EMIT_CHUNK];       // record (window slot) owning each pair
+  __shared__ uint32_t s_wmax[EMIT_THREADS / 32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int64_t total = *n_int;
-  if (tid == 0 && total > capacity) set_status(status, ST_CAPACITY);
+  if (!SCATTER && blockIdx.x == 0 && tid == 0 && total > capacity) set_status(status, ST_CAPACITY);
   const int64_t n = min(total, capacity);
   const int64_t nchunks = (n + EMIT_CHUNK - 1) / EMIT_CHUNK;
   const int64_t nv = (int64_t)*n_vis;
-  for (int e = tid; e < passes * 256; e += EMIT_THREADS) s_hist[e] = 0u;
 
   for (int64_t ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
     const int64_t lo = ck * EMIT_CHUNK;
@@ -187,267 +202,610 @@ __global__ void __launch_bounds__(EMIT_THREADS)
     // last chunk of a capacity-truncated emission may list more; they own no pair below hi)
     const int nw = (int)min(v1 - v0 + 1, (int64_t)EMIT_CHUNK + 1);
     __syncthreads();
+    for (int i = tid; i < EMIT_CHUNK; i += EMIT_THREADS) s_own[i] = 0;
+    __syncthreads();
     for (int i = tid; i < nw; i += EMIT_THREADS) {
       const uint32_t r = vis_rec[v0 + i];
       const uint4 w2 = __ldg(reinterpret_cast<const uint4 *>(rec + r) + 2);
-      const uint32_t x0 = w2.z & 0xffffu, y0 = w2.z >> 16, x1 = w2.w & 0xffffu;
+      const uint32_t x0 = w2.z & 0xffffu, y0 = w2.z >> 16, x1 = w2.w & 0xffffu, y1 = w2.w >> 16;
       const int v = (int)(r / (uint32_t)n_per_view);
-      const uint32_t tiles_x = (uint32_t)vs.v[v].tiles_x;
-      s_off[i] = vis_off[v0 + i];
+      const uint32_t tiles_x = (uint32_t)vs.v[v].tiles_x, tiles_y = (uint32_t)vs.v[v].tiles_y;
+      const bool ok = x0 <= x1 && y0 <= y1 && x1 < tiles_x && y1 < tiles_y;
+      const uint64_t off = vis_off[v0 + i];
+      s_off[i] = (uint32_t)min(off, (uint64_t)hi);
       s_rec[i] = r;
       s_base[i] = (uint32_t)vs.v[v].tile_offset + y0 * tiles_x + x0;
-      s_geom[i] = (x1 - x0 + 1u) | (tiles_x << 16);
+      s_geom[i] = ok ? (x1 - x0 + 1u) | ((y1 - y0 + 1u) << 16) : 0u;
+      s_tx[i] = tiles_x;
       s_depth[i] = w2.y;
+      if (i > 0 && off < (uint64_t)hi) s_own[off - (uint64_t)lo] = (uint16_t)i;
     }
     __syncthreads();
-    // depth digits (passes 0-3) are the same for all pairs of a record: count them once per
-    // record with the number of its pairs inside this chunk
-    for (int i = tid; i < nw; i += EMIT_THREADS) {
-      const uint64_t a0 = s_off[i] > (uint64_t)lo ? s_off[i] : (uint64_t)lo;
-      const uint64_t a1 = i + 1 < nw ? (s_off[i + 1] < (uint64_t)hi ? s_off[i + 1] : (uint64_t)hi)
-                                     : (uint64_t)hi;
-      if (a1 > a0) {
-        const uint32_t cnt = (uint32_t)(a1 - a0), dep = s_depth[i];
+    // inclusive max-scan of the marks: thread t owns slots [PER t, PER t + PER)
+    {
+      uint32_t m[PER];
+      uint32_t run = 0;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p * 256 + ((dep >> (8 * p)) & 255u)], cnt);
+      for (int k = 0; k < PER; ++k) {
+        run = max(run, (uint32_t)s_own[tid * PER + k]);
+        m[k] = run;
+      }
+      uint32_t x = run;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) x = max(x, __shfl_up_sync(0xffffffffu, x, o) * (lane >= o));
+      if (lane == 31) s_wmax[wid] = x;
+      uint32_t before = __shfl_up_sync(0xffffffffu, x, 1) * (lane >= 1);
+      __syncthreads();
+      for (int ww = 0; ww < wid; ++ww) before = max(before, s_wmax[ww]);
+#pragma unroll
+      for (int k = 0; k < PER; ++k) s_own[tid * PER + k] = (uint16_t)max(m[k], before);
+    }
+    __syncthreads();
+    // each thread takes pairs tid, tid + 256, ... of the chunk: all their tiles first, then
+    // all their atomics, so that a thread has several atomics in flight
+    uint32_t tile[PER], owner[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int64_t j = lo + tid + k * EMIT_THREADS;
+      tile[k] = 0xffffffffu;
+      owner[k] = 0u;
+      if (j < hi) {
+        const uint32_t a = s_own[j - lo];
+        const uint32_t geom = s_geom[a];
+        const uint32_t local = (uint32_t)(j - lo) + (uint32_t)lo - s_off[a];
+        const uint32_t w = geom & 0xffffu, h = geom >> 16;
+        if (w != 0u) {
+          // row inside the rect: float quotient (local < 2^22 is exact in FP32), corrected by one
+          uint32_t dy = (uint32_t)((float)local * rcp_approx((float)w));
+          if (dy * w > local) --dy;
+          if ((dy + 1u) * w <= local) ++dy;
+          const uint32_t dx = local - dy * w;
+          // more pairs than the rect holds (a malformed record): skipped
+          if (dy < h && dx < w) tile[k] = s_base[a] + dy * s_tx[a] + dx;
+        }
+        owner[k] = a;
       }
     }
-    for (int64_t jb = lo; jb < hi; jb += EMIT_THREADS) {
-      const int64_t j = jb + tid;
-      const bool valid = j < hi;
-      uint64_t key = 0;
-      if (valid) {
-        int a = 0, b = nw;  // s_off[a] <= j < s_off[b] (s_off[nw] taken as +inf)
-        while (b - a > 1) {
-          const int mid = (a + b) >> 1;
-          if (s_off[mid] <= (uint64_t)j) a = mid; else b = mid;
-        }
-        const uint32_t local = (uint32_t)((uint64_t)j - s_off[a]);
-        const uint32_t geom = s_geom[a];
-        const uint32_t w = geom & 0xffffu, tiles_x = geom >> 16;
-        // row inside the rect: float quotient (local < 2^22 is exact in FP32) corrected by one
-        uint32_t dy = (uint32_t)((float)local * rcp_approx((float)w));
-        if (dy * w > local) --dy;
-        if ((dy + 1u) * w <= local) ++dy;
-        const uint32_t tile = s_base[a] + dy * tiles_x + (local - dy * w);
-        key = ((uint64_t)tile << 32) | (uint64_t)s_depth[a];
-        if (packed) {
-          keys[j] = (key << idx_bits) | (uint64_t)s_rec[a];
-        } else {
-          keys[j] = key;
-          vals[j] = s_rec[a];
-        }
-      }
-      // tile digits: the lowest changes from pair to pair along a rect row (plain atomics
-      // rarely collide); higher ones are shared by runs of pairs (warp-aggregated)
-      if (passes > 4 && valid) atomicAdd(&s_hist[4 * 256 + ((uint32_t)(key >> 32) & 255u)], 1u);
-      for (int p = 5; p < passes; ++p) {
-        const uint32_t d = valid ? (uint32_t)(key >> (8 * p)) & 255u : 0x100u + (threadIdx.x & 31);
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (valid && (peers & lanemask_lt()) == 0u) atomicAdd(&s_hist[p * 256 + d], __popc(peers));
-      }
+    if (!SCATTER) {
+#pragma unroll
+      for (int k = 0; k < PER; ++k)
+        if (tile[k] != 0xffffffffu) atomicAdd(&ranges[2 * (size_t)tile[k]], 1u);
+    } else {
+      uint32_t pos[PER];
+#pragma unroll
+      for (int k = 0; k < PER; ++k)
+        pos[k] = tile[k] != 0xffffffffu ? atomicAdd(&ranges[2 * (size_t)tile[k] + 1], 1u) : 0xffffffffu;
+#pragma unroll
+      for (int k = 0; k < PER; ++k)
+        if (tile[k] != 0xffffffffu && (int64_t)pos[k] < capacity)
+          words[pos[k]] = ((uint64_t)s_depth[owner[k]] << 32) | (uint64_t)s_rec[owner[k]];
     }
   }
-  __syncthreads();
-  for (int e = tid; e < passes * 256; e += EMIT_THREADS)
-    if (s_hist[e]) atomicAdd(hist + e, s_hist[e]);
 }
 
-// Shared memory of one onesweep CTA: two input buffers filled by TMA bulk copies (the next
-// partition lands in one while the current one is ranked in the other, which then serves as
-// the exchange buffer of the local scatter), per-warp digit counters and digit offsets.
-template <bool KV>
-struct SortSmem {
-  uint64_t keys[2][SORT_PART];
-  uint32_t vals[KV ? 2 : 1][KV ? SORT_PART : 4];
-  uint32_t wcnt[SORT_THREADS / 32][256];  // per-warp digit counts -> per-warp offsets
-  uint32_t local_start[256];               // digit start inside the partition
-  uint32_t global_base[256];               // digit base in the output for this partition
-  uint32_t hist_excl[256];                 // exclusive scan of this pass's global histogram
-  uint32_t warp_tmp[8];
-  uint32_t part[2];
-  uint64_t bar[2];
+// Exclusive scan of the per-tile pair counts (tile_ranges[2t], written by the counting pass)
+// over all tiles in global tile order, with decoupled look-back over partitions of TSCAN_PART
+// tiles. Writes tile_ranges[t] = (start, start) for every non-empty tile (the second word is
+// the scatter's cursor and ends as the tile's end) and appends the tile to the list of its
+// segment-size class; empty tiles keep (0, 0).
+__global__ void __launch_bounds__(256)
+    tile_scan_kernel(uint32_t *ranges, int64_t total_tiles, uint64_t *lb,
+                     uint32_t *part_counter, uint32_t *lists, uint32_t *seg_count,
+                     uint32_t *status) {
+  __shared__ uint32_t s_warp[8];
+  __shared__ uint64_t s_prefix;
+  __shared__ uint32_t s_part;
+  __shared__ uint32_t s_cls[2], s_cls_base[2];
+  const int tid = threadIdx.x;
+  if (tid == 0) s_part = atomicAdd(part_counter, 1u);
+  if (tid < 2) s_cls[tid] = 0u;
+  __syncthreads();
+  const int64_t part = s_part;
+  const int64_t base = part * TSCAN_PART;
+  constexpr int ITEMS = TSCAN_PART / 256;
+  uint32_t c[ITEMS];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    const int64_t t = base + tid * ITEMS + k;
+    c[k] = t < total_tiles ? ranges[2 * t] : 0u;
+    sum += c[k];
+  }
+  uint32_t agg;
+  const uint32_t off = block_excl_scan_256(sum, s_warp, &agg);
+  if (tid == 0) {
+    uint64_t prefix = 0;
+    if (part == 0) {
+      st_volatile_u64(lb, LB_INC | agg);
+    } else {
+      st_volatile_u64(lb + part, LB_AGG | agg);
+      prefix = look_back(lb, part, 1, status);
+      st_volatile_u64(lb + part, LB_INC | (prefix + agg));
+    }
+    s_prefix = prefix;
+  }
+  // class ranks inside the CTA (order within a class list is irrelevant)
+  uint32_t cls_rank[ITEMS];
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    const int cls = c[k] <= (uint32_t)SEG_CAP0 ? 0 : 1;
+    cls_rank[k] = c[k] > 0u ? atomicAdd(&s_cls[cls], 1u) : 0u;
+  }
+  __syncthreads();
+  if (tid < 2) s_cls_base[tid] = s_cls[tid] ? atomicAdd(&seg_count[tid], s_cls[tid]) : 0u;
+  __syncthreads();
+  uint64_t o = s_prefix + off;
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    const int64_t t = base + tid * ITEMS + k;
+    if (c[k] > 0u) {
+      ranges[2 * t] = (uint32_t)o;
+      ranges[2 * t + 1] = (uint32_t)o;
+      const int cls = c[k] <= (uint32_t)SEG_CAP0 ? 0 : 1;
+      lists[(size_t)cls * (size_t)total_tiles + s_cls_base[cls] + cls_rank[k]] = (uint32_t)t;
+    }
+    o += c[k];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Per-tile segment sort. A tile's bucket holds its words depth_bits << 32 | record in
+// arbitrary order; sorting the words as 64-bit integers orders them by depth and breaks depth
+// ties by record index, which is the order a stable sort of the keys (tile << 32 | depth) in
+// emission order gives. LSD radix passes over 8-bit digits, skipping digits that are equal in
+// every word of the segment. A first attempt sorts the depth digits only; only a segment that
+// then shows two equal depths is sorted again over all digits.
+//
+// Ranking is stable: warp w owns items [w * 32 * IPT, (w + 1) * 32 * IPT), taken 32 at a time
+// in order; each group of 32 is ranked by warp multi-split (the lanes sharing a digit found
+// through a per-warp shared bitmap that each lane ORs its bit into), and a per-warp digit
+// counter carries the count over the groups.
+template <int NT, int IPT>
+struct SegSmem {
+  static constexpr int CAP = NT * IPT;
+  static constexpr int NB = 2 * CAP;  // sub-buckets of the bucket sort
+  uint64_t buf[CAP];
+  union {
+    struct {
+      uint32_t wcnt[NT / 32][256];   // per-warp digit counts -> per-warp offsets within a digit
+      uint32_t wmask[NT / 32][256];  // per-warp lane masks of one group of 32 (zero between groups)
+    } rx;
+    uint32_t cnt[NB];                // bucket sort: sub-bucket counts -> starts
+  };
+  uint32_t dstart[256];         // digit start (exclusive prefix of the digit counts)
+  uint32_t hist[256];           // chunked path: digit start over the whole segment
+  uint32_t running[256];        // chunked path: digit count of the chunks already placed
+  uint32_t wtot[NT / 32];
+  uint64_t red[2][NT / 32];
 };
 
-// Issue the TMA bulk copies of partition `part` into buffer `b`: the 16-byte-aligned prefix
-// of its keys (and values); the few trailing elements of a ragged last partition are loaded
-// with plain loads after the wait.
-template <bool KV>
-__device__ __forceinline__ void sort_issue(SortSmem<KV> &S, int b, const uint64_t *kin,
-                                           const uint32_t *vin, int64_t part, int64_t n) {
-  const int64_t base = part * SORT_PART;
-  const uint32_t cnt = (uint32_t)min((int64_t)SORT_PART, n - base);
-  const uint32_t kb = (cnt & ~1u) * 8u;
-  const uint32_t vb = KV ? (cnt & ~3u) * 4u : 0u;
-  mbar_arrive_expect_tx(&S.bar[b], kb + vb);
-  if (kb) bulk_g2s(S.keys[b], kin + base, kb, &S.bar[b]);
-  if (KV && vb) bulk_g2s(S.vals[b], vin + base, vb, &S.bar[b]);
-}
-
-// One LSD pass over the 8-bit digit at bit `shift` of the stored words. Persistent CTAs take
-// partitions of SORT_PART keys in claim order. KV: 64-bit keys with 32-bit values; otherwise
-// packed words (key << idx_bits | value) only, and with `unpack` the pass writes the caller's
-// keys (word >> idx_bits) and values (low idx_bits) instead of words.
-template <bool KV>
-__global__ void __launch_bounds__(SORT_THREADS, KV ? 2 : 3)
-    onesweep_kernel(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-                    uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
-                    const int64_t *n_int, int64_t capacity, int shift, int idx_bits, int unpack,
-                    const uint32_t *hist, uint64_t *lb, uint64_t *lb_next,
-                    uint32_t *part_counter, uint32_t *status) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  SortSmem<KV> &S = *reinterpret_cast<SortSmem<KV> *>(smem_raw);
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int64_t n = min(*n_int, capacity);
-  const int64_t nparts = (n + SORT_PART - 1) / SORT_PART;
-
-  // clear the look-back entries the next pass will use (the previous pass is complete)
-  for (int64_t e = (int64_t)blockIdx.x * SORT_THREADS + tid; e < nparts * 256;
-       e += (int64_t)gridDim.x * SORT_THREADS)
-    lb_next[e] = 0ull;
-
-  uint32_t tot;
-  {
-    const uint32_t hx = block_excl_scan_256(hist[tid], S.warp_tmp, &tot);
-    S.hist_excl[tid] = hx;
-  }
-  const uint32_t lt = lanemask_lt();
-  const uint64_t vmask = (idx_bits >= 64) ? ~0ull : ((1ull << idx_bits) - 1ull);
-  // Partitions are dealt round-robin (CTA c takes c, c + G, c + 2G, ...); the launch is
-  // cooperative, so all CTAs are resident and a predecessor's CTA is always making progress.
-  const int64_t G = gridDim.x;
-  int64_t part = blockIdx.x;
-  if (tid == 0) {
-    mbar_init(&S.bar[0], 1);
-    mbar_init(&S.bar[1], 1);
-    fence_mbar_init();
-    if (part < nparts) sort_issue<KV>(S, 0, kin, vin, part, n);
-  }
-  __syncthreads();
-  uint32_t phase = 0u;  // bit b = parity of buffer b's next phase
-  int cur = 0;
-  (void)part_counter;
-
-  while (part < nparts) {
-    const int64_t next = part + G;
-    // prefetch this CTA's next partition into the other buffer
-    if (tid == 0 && next < nparts) {
-      fence_proxy_async_smem();
-      sort_issue<KV>(S, cur ^ 1, kin, vin, next, n);
-    }
-    const bool ok = mbar_wait(&S.bar[cur], (phase >> cur) & 1u, status);
-    phase ^= 1u << cur;
-    if (__syncthreads_or(!ok)) {  // a copy never landed: drain (bounded) and leave
-      if (next < nparts) mbar_wait(&S.bar[cur ^ 1], (phase >> (cur ^ 1)) & 1u, status);
-      return;
-    }
-    const int64_t base = part * SORT_PART;
-    const uint32_t cnt = (uint32_t)min((int64_t)SORT_PART, n - base);
-    // ragged tail of the last partition: plain loads
-    if (tid < 4) {
-      const uint32_t kt = (cnt & ~1u) + tid;
-      if (tid < 1 && kt < cnt) S.keys[cur][kt] = kin[base + kt];
-      const uint32_t vt = (cnt & ~3u) + tid;
-      if (KV && vt < cnt) S.vals[cur][vt] = vin[base + vt];
-    }
-    for (int e = tid; e < (SORT_THREADS / 32) * 256; e += SORT_THREADS) (&S.wcnt[0][0])[e] = 0u;
-    __syncthreads();
-
-    // load (warp-striped, order within a warp = k then lane = input order) and rank: warp
-    // multi-split with match_any, stable
-    uint64_t key[SORT_ITEMS];
-    uint32_t val[SORT_ITEMS];
-    uint32_t rank[SORT_ITEMS];
+template <int NT, int IPT>
+__device__ __forceinline__ void rank_items(SegSmem<NT, IPT> &S, const uint64_t (&x)[IPT],
+                                           uint32_t cnt, int shift, uint32_t (&rank)[IPT]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int e = lane; e < 256; e += 32) S.rx.wcnt[w][e] = 0u;
+  __syncwarp();
+  if ((uint32_t)(w * 32 * IPT) < cnt) {
+    const uint32_t lt = lanemask_lt();
 #pragma unroll
-    for (int k = 0; k < SORT_ITEMS; ++k) {
-      const uint32_t li = (uint32_t)(w * 32 * SORT_ITEMS + k * 32 + lane);
+    for (int k = 0; k < IPT; ++k) {
+      const uint32_t li = (uint32_t)(w * 32 * IPT + k * 32 + lane);
       const bool valid = li < cnt;
-      key[k] = valid ? S.keys[cur][li] : 0ull;
-      val[k] = (KV && valid) ? S.vals[cur][li] : 0u;
-      const uint32_t d = valid ? (uint32_t)(key[k] >> shift) & 255u : 0x100u + lane;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t d = (uint32_t)(x[k] >> shift) & 255u;
+      // lanes holding the same digit: every lane sets its bit in the digit's mask
+      if (valid) atomicOr(&S.rx.wmask[w][d], 1u << lane);
+      __syncwarp();
+      const uint32_t peers = valid ? S.rx.wmask[w][d] : 0u;
       const uint32_t before = __popc(peers & lt);
       uint32_t c = 0;
-      if (valid) c = S.wcnt[w][d];
+      if (valid) c = S.rx.wcnt[w][d];
       __syncwarp();
-      if (valid && before == 0u) S.wcnt[w][d] = c + __popc(peers);
+      if (valid && before == 0u) {
+        S.rx.wcnt[w][d] = c + __popc(peers);
+        S.rx.wmask[w][d] = 0u;
+      }
       __syncwarp();
       rank[k] = c + before;
     }
-    __syncthreads();
-    // per digit: per-warp exclusive offsets and the partition's count
-    const int d = tid;
-    uint32_t run = 0;
-#pragma unroll
-    for (int ww = 0; ww < SORT_THREADS / 32; ++ww) {
-      const uint32_t c = S.wcnt[ww][d];
-      S.wcnt[ww][d] = run;
-      run += c;
+  }
+  __syncthreads();
+}
+
+// Turns S.rx.wcnt[w][d] (counts) into per-warp exclusive offsets within digit d and S.dstart[d]
+// into the exclusive prefix of the digit totals; returns digit tid's total (tid < 256).
+template <int NT, int IPT>
+__device__ __forceinline__ uint32_t digit_offsets(SegSmem<NT, IPT> &S) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  uint32_t dcount = 0, incl = 0;
+  if (tid < 256) {
+#pragma unroll 4
+    for (int ww = 0; ww < NT / 32; ++ww) {
+      const uint32_t c = S.rx.wcnt[ww][tid];
+      S.rx.wcnt[ww][tid] = dcount;
+      dcount += c;
     }
-    const uint32_t dcount = run;
-    uint64_t *my = lb + part * 256 + d;
-    if (part == 0) st_volatile_u64(my, LB_INC | dcount);
-    else st_volatile_u64(my, LB_AGG | dcount);
-    uint32_t ptot;
-    const uint32_t lstart = block_excl_scan_256(dcount, S.warp_tmp, &ptot);
-    S.local_start[d] = lstart;
-    uint64_t prefix = 0;
-    if (part > 0) {
-      prefix = look_back(lb + d, part, 256, status);
-      st_volatile_u64(my, LB_INC | (prefix + dcount));
-    }
-    S.global_base[d] = S.hist_excl[d] + (uint32_t)prefix;
-    __syncthreads();
-    // local scatter into the partition's own buffer, sorted by digit
+    incl = dcount;
 #pragma unroll
-    for (int k = 0; k < SORT_ITEMS; ++k) {
-      const uint32_t li = (uint32_t)(w * 32 * SORT_ITEMS + k * 32 + lane);
-      if (li < cnt) {
-        const uint32_t dd = (uint32_t)(key[k] >> shift) & 255u;
-        const uint32_t pos = S.local_start[dd] + S.wcnt[w][dd] + rank[k];
-        S.keys[cur][pos] = key[k];
-        if (KV) S.vals[cur][pos] = val[k];
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) S.wtot[w] = incl;
+  }
+  __syncthreads();
+  if (tid < 256) {
+    uint32_t before = 0;
+    for (int ww = 0; ww < w; ++ww) before += S.wtot[ww];
+    S.dstart[tid] = before + incl - dcount;
+  }
+  __syncthreads();
+  return dcount;
+}
+
+// Block AND / OR of a 64-bit value; every thread gets the results.
+template <int NT, int IPT>
+__device__ __forceinline__ void block_and_or(SegSmem<NT, IPT> &S, uint64_t &a, uint64_t &o) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    a &= __shfl_xor_sync(0xffffffffu, a, s);
+    o |= __shfl_xor_sync(0xffffffffu, o, s);
+  }
+  if (lane == 0) {
+    S.red[0][w] = a;
+    S.red[1][w] = o;
+  }
+  __syncthreads();
+  a = ~0ull;
+  o = 0ull;
+  for (int ww = 0; ww < NT / 32; ++ww) {
+    a &= S.red[0][ww];
+    o |= S.red[1][ww];
+  }
+  __syncthreads();
+}
+
+// One stable pass over the digit at `shift` of the segment held in registers (x) and shared
+// memory; leaves the result in both.
+template <int NT, int IPT>
+__device__ __forceinline__ void smem_pass(SegSmem<NT, IPT> &S, uint64_t (&x)[IPT], uint32_t cnt,
+                                          int shift) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t rank[IPT];
+  rank_items<NT, IPT>(S, x, cnt, shift, rank);
+  digit_offsets<NT, IPT>(S);
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    const uint32_t li = (uint32_t)(w * 32 * IPT + k * 32 + lane);
+    if (li < cnt) {
+      const uint32_t d = (uint32_t)(x[k] >> shift) & 255u;
+      S.buf[S.dstart[d] + S.rx.wcnt[w][d] + rank[k]] = x[k];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    const uint32_t li = (uint32_t)(w * 32 * IPT + k * 32 + lane);
+    x[k] = li < cnt ? S.buf[li] : 0ull;
+  }
+}
+
+// Sort one segment of cnt <= NT * IPT words in shared memory and write keys / values.
+template <int NT, int IPT>
+__device__ __forceinline__ void sort_segment_smem(SegSmem<NT, IPT> &S, const uint64_t *src,
+                                                  uint32_t cnt, uint64_t tile,
+                                                  uint64_t *kout, uint32_t *vout) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // the lane masks share storage with the bucket sort's counters: clear them first
+  for (int e = threadIdx.x; e < (NT / 32) * 256; e += NT) (&S.rx.wmask[0][0])[e] = 0u;
+  __syncthreads();
+  uint64_t x[IPT];
+  uint64_t a = ~0ull, o = 0ull;
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    const uint32_t li = (uint32_t)(w * 32 * IPT + k * 32 + lane);
+    x[k] = li < cnt ? src[li] : 0ull;
+    if (li < cnt) {
+      S.buf[li] = x[k];
+      a &= x[k];
+      o |= x[k];
+    }
+  }
+  block_and_or<NT, IPT>(S, a, o);
+  const uint64_t varying = a ^ o;
+#pragma unroll
+  for (int p = 4; p < 8; ++p)
+    if ((varying >> (8 * p)) & 255u) smem_pass<NT, IPT>(S, x, cnt, 8 * p);
+  // equal depths (the high halves) in adjacent slots: sort again over every digit
+  bool tie = false;
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    const uint32_t li = (uint32_t)(w * 32 * IPT + k * 32 + lane);
+    if (li + 1 < cnt) tie |= (S.buf[li] >> 32) == (S.buf[li + 1] >> 32);
+  }
+  if (__syncthreads_or(tie)) {
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+      if ((varying >> (8 * p)) & 255u) smem_pass<NT, IPT>(S, x, cnt, 8 * p);
+  }
+  for (uint32_t i = threadIdx.x; i < cnt; i += NT) {
+    const uint64_t v = S.buf[i];
+    kout[i] = (tile << 32) | (v >> 32);
+    vout[i] = (uint32_t)v;
+  }
+  __syncthreads();  // buf reused by the next segment
+}
+
+// Bucket sort of one segment of cnt <= NT * IPT words, the usual path. The depth bits of the
+// segment span [kmin, kmax]; the words are counted into NB = 2 * NT * IPT sub-buckets by the
+// leading bits of depth - kmin (one shared atomic per word, which also gives the word its slot),
+// the counts are scanned, the words placed by sub-bucket, and each word's final place is its
+// sub-bucket's start plus the number of smaller words in its sub-bucket. Words are distinct
+// (the record index is in the low half), so this is a total order equal to that of the 64-bit
+// words. Returns false, having written nothing, when a sub-bucket holds more than BUCKET_KMAX
+// words (depths clustered tighter than the sub-bucket width, or many equal depths); the radix
+// path then sorts the segment.
+constexpr uint32_t BUCKET_KMAX = 32;
+
+template <int NT, int IPT>
+__device__ __forceinline__ bool bucket_sort_segment(SegSmem<NT, IPT> &S, const uint64_t *src,
+                                                    uint32_t cnt, uint64_t tile,
+                                                    uint64_t *kout, uint32_t *vout) {
+  constexpr int NB = SegSmem<NT, IPT>::NB;
+  constexpr int CPT = NB / NT;  // sub-bucket counters per thread
+  constexpr int LOGNB = NB == 4096 ? 12 : 14;
+  static_assert((1 << LOGNB) == NB, "sub-bucket count");
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  uint64_t x[IPT];
+  uint32_t kmin = 0xffffffffu, kmax = 0u;
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    const uint32_t li = (uint32_t)(k * NT + tid);
+    x[k] = li < cnt ? src[li] : 0ull;
+    if (li < cnt) {
+      const uint32_t h = (uint32_t)(x[k] >> 32);
+      kmin = min(kmin, h);
+      kmax = max(kmax, h);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) S.cnt[c * NT + tid] = 0u;
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, s));
+    kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, s));
+  }
+  if (lane == 0) {
+    S.red[0][w] = kmin;
+    S.red[1][w] = kmax;
+  }
+  __syncthreads();
+  kmin = 0xffffffffu;
+  kmax = 0u;
+  for (int ww = 0; ww < NT / 32; ++ww) {
+    kmin = min(kmin, (uint32_t)S.red[0][ww]);
+    kmax = max(kmax, (uint32_t)S.red[1][ww]);
+  }
+  const uint32_t span = kmax - kmin;
+  const int bits = span ? 32 - __clz(span) : 0;
+  const int sh = bits > LOGNB ? bits - LOGNB : 0;  // (depth - kmin) >> sh < NB
+  // per word: sub-bucket << 18 | slot in the sub-bucket (a slot beyond BUCKET_KMAX is never
+  // used: the segment then goes to the radix path)
+  uint32_t bs[IPT];
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    const uint32_t li = (uint32_t)(k * NT + tid);
+    bs[k] = 0u;
+    if (li < cnt) {
+      const uint32_t b = ((uint32_t)(x[k] >> 32) - kmin) >> sh;
+      bs[k] = (b << 18) | min(atomicAdd(&S.cnt[b], 1u), 0x3ffffu);
+    }
+  }
+  __syncthreads();
+  // exclusive scan of the counts (thread tid owns counters [CPT tid, CPT tid + CPT)) and the
+  // largest count
+  uint32_t tot = 0, mx = 0;
+#pragma unroll 8
+  for (int q = 0; q < CPT; ++q) {
+    const uint32_t v = S.cnt[tid * CPT + q];
+    tot += v;
+    mx = max(mx, v);
+  }
+  uint32_t incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, s));
+  __syncthreads();  // everyone has read S.red
+  if (lane == 31) S.wtot[w] = incl;
+  if (lane == 0) S.red[0][w] = mx;
+  __syncthreads();
+  uint32_t before = 0;
+  for (int ww = 0; ww < w; ++ww) before += S.wtot[ww];
+  mx = 0;
+  for (int ww = 0; ww < NT / 32; ++ww) mx = max(mx, (uint32_t)S.red[0][ww]);
+  uint32_t e = before + incl - tot;
+#pragma unroll 8
+  for (int q = 0; q < CPT; ++q) {
+    const uint32_t v = S.cnt[tid * CPT + q];
+    S.cnt[tid * CPT + q] = e;
+    e += v;
+  }
+  __syncthreads();
+  if (mx > BUCKET_KMAX) return false;  // uniform over the CTA
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    const uint32_t li = (uint32_t)(k * NT + tid);
+    if (li < cnt) S.buf[S.cnt[bs[k] >> 18] + (bs[k] & 0x3ffffu)] = x[k];
+  }
+  __syncthreads();
+  // final place: start of the sub-bucket + number of smaller words in it (bs[k] becomes it)
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    const uint32_t li = (uint32_t)(k * NT + tid);
+    if (li < cnt) {
+      const uint32_t b = bs[k] >> 18;
+      const uint32_t b0 = S.cnt[b];
+      const uint32_t b1 = b + 1u < (uint32_t)NB ? S.cnt[b + 1u] : cnt;
+      uint32_t r = 0;
+      for (uint32_t j = b0; j < b1; ++j) r += S.buf[j] < x[k] ? 1u : 0u;
+      bs[k] = b0 + r;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    const uint32_t li = (uint32_t)(k * NT + tid);
+    if (li < cnt) S.buf[bs[k]] = x[k];
+  }
+  __syncthreads();
+  for (uint32_t i = tid; i < cnt; i += NT) {
+    const uint64_t v = S.buf[i];
+    kout[i] = (tile << 32) | (v >> 32);
+    vout[i] = (uint32_t)v;
+  }
+  __syncthreads();  // buf and counters reused by the next segment
+  return true;
+}
+
+// Sort one segment longer than NT * IPT through global memory: per digit, a histogram pass
+// over the segment, then the segment in chunks of NT * IPT words in order, each ranked in
+// shared memory and scattered to its place in the other buffer (words <-> the key output,
+// which serves as scratch). All digits with varying bits are sorted. The last step turns the
+// words into keys and values wherever the data ended (in place if that is the key output).
+template <int NT, int IPT>
+__device__ void sort_segment_chunked(SegSmem<NT, IPT> &S, uint64_t *words, uint32_t cnt,
+                                     uint64_t tile, uint64_t *kout, uint32_t *vout) {
+  constexpr uint32_t CAP = NT * IPT;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int e = tid; e < (NT / 32) * 256; e += NT) (&S.rx.wmask[0][0])[e] = 0u;
+  uint64_t a = ~0ull, o = 0ull;
+  for (uint32_t i = tid; i < cnt; i += NT) {
+    const uint64_t v = words[i];
+    a &= v;
+    o |= v;
+  }
+  block_and_or<NT, IPT>(S, a, o);
+  const uint64_t varying = a ^ o;
+  uint64_t *src = words, *dst = kout;
+  for (int p = 0; p < 8; ++p) {
+    if (((varying >> (8 * p)) & 255u) == 0u) continue;
+    const int shift = 8 * p;
+    for (int e = tid; e < 256; e += NT) {
+      S.hist[e] = 0u;
+      S.running[e] = 0u;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < cnt; i += NT) atomicAdd(&S.hist[(uint32_t)(src[i] >> shift) & 255u], 1u);
+    __syncthreads();
+    {  // exclusive scan of the histogram in place
+      uint32_t c = 0, incl = 0;
+      if (tid < 256) {
+        c = S.hist[tid];
+        incl = c;
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, s);
+          if (lane >= s) incl += y;
+        }
+        if (lane == 31) S.wtot[w] = incl;
       }
+      __syncthreads();
+      if (tid < 256) {
+        uint32_t before = 0;
+        for (int ww = 0; ww < w; ++ww) before += S.wtot[ww];
+        S.hist[tid] = before + incl - c;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    // global scatter: consecutive shared positions of one digit go to consecutive addresses
-    for (uint32_t i = tid; i < cnt; i += SORT_THREADS) {
-      const uint64_t kk = S.keys[cur][i];
-      const uint32_t dd = (uint32_t)(kk >> shift) & 255u;
-      const uint64_t gpos = (uint64_t)S.global_base[dd] + (i - S.local_start[dd]);
-      if (gpos < (uint64_t)n) {
-        if (KV) {
-          kout[gpos] = kk;
-          vout[gpos] = S.vals[cur][i];
-        } else if (unpack) {
-          kout[gpos] = kk >> idx_bits;
-          vout[gpos] = (uint32_t)(kk & vmask);
-        } else {
-          kout[gpos] = kk;
+    for (uint32_t lo = 0; lo < cnt; lo += CAP) {
+      const uint32_t ccnt = min(CAP, cnt - lo);
+      uint64_t x[IPT];
+      uint32_t rank[IPT];
+#pragma unroll
+      for (int k = 0; k < IPT; ++k) {
+        const uint32_t li = (uint32_t)(w * 32 * IPT + k * 32 + lane);
+        x[k] = li < ccnt ? src[lo + li] : 0ull;
+      }
+      rank_items<NT, IPT>(S, x, ccnt, shift, rank);
+      const uint32_t dcount = digit_offsets<NT, IPT>(S);
+#pragma unroll
+      for (int k = 0; k < IPT; ++k) {
+        const uint32_t li = (uint32_t)(w * 32 * IPT + k * 32 + lane);
+        if (li < ccnt) {
+          const uint32_t d = (uint32_t)(x[k] >> shift) & 255u;
+          dst[S.hist[d] + S.running[d] + S.rx.wcnt[w][d] + rank[k]] = x[k];
         }
       }
+      __syncthreads();
+      if (tid < 256) S.running[tid] += dcount;
+      __syncthreads();
     }
-    __syncthreads();  // buffer, counters and offsets are reused by the next partition
-    part = next;
-    cur ^= 1;
+    uint64_t *t = src;
+    src = dst;
+    dst = t;
+  }
+  for (uint32_t i = tid; i < cnt; i += NT) {
+    const uint64_t v = src[i];
+    kout[i] = (tile << 32) | (v >> 32);
+    vout[i] = (uint32_t)v;
+  }
+  __syncthreads();
+}
+
+// One CTA per listed tile of a size class, persistent over the class list.
+// Resident CTAs per SM the register budget is sized for: 4 x 256 threads for the small class,
+// 1 x 512 for the large one.
+template <int NT, int IPT>
+struct SegOcc {
+  static constexpr int value = NT * IPT == SEG_CAP0 ? 4 : 1;
+};
+
+template <int NT, int IPT, bool CHUNKED>
+__global__ void __launch_bounds__(NT, SegOcc<NT, IPT>::value)
+    segsort_kernel(const uint32_t *__restrict__ list, const uint32_t *list_count,
+                   const uint32_t *__restrict__ ranges, uint64_t *words, uint64_t *keys,
+                   uint32_t *vals, int64_t capacity) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SegSmem<NT, IPT> &S = *reinterpret_cast<SegSmem<NT, IPT> *>(smem_raw);
+  const uint32_t count = *list_count;
+  for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
+    const uint32_t t = __ldg(list + i);
+    const uint2 rg = __ldg(reinterpret_cast<const uint2 *>(ranges) + t);
+    // bounds of a bucket that a device-side error left inconsistent: skip it
+    if (rg.y <= rg.x || (int64_t)rg.y > capacity) continue;
+    const uint32_t cnt = rg.y - rg.x;
+    if (cnt <= (uint32_t)(NT * IPT)) {
+      if (!bucket_sort_segment<NT, IPT>(S, words + rg.x, cnt, t, keys + rg.x, vals + rg.x))
+        sort_segment_smem<NT, IPT>(S, words + rg.x, cnt, t, keys + rg.x, vals + rg.x);
+    }
+    else if (CHUNKED)
+      sort_segment_chunked<NT, IPT>(S, words + rg.x, cnt, t, keys + rg.x, vals + rg.x);
   }
 }
 
-// Tile ids come from the sorted keys; they are checked against the tile count so that keys
-// left undefined by a device-side error cannot steer a write out of bounds.
-__global__ void ranges_kernel(const uint64_t *__restrict__ keys, const int64_t *n_int,
-                              int64_t capacity, int64_t total_tiles,
-                              uint32_t *__restrict__ ranges) {
-  const int64_t n = min(*n_int, capacity);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t t = keys[i] >> 32;
-    if (t >= (uint64_t)total_tiles) continue;
-    if (i == 0 || (keys[i - 1] >> 32) != t) ranges[2 * t] = (uint32_t)i;
-    if (i == n - 1 || (keys[i + 1] >> 32) != t) ranges[2 * t + 1] = (uint32_t)(i + 1);
+template <int NT, int IPT, bool CHUNKED>
+cudaError_t launch_segsort(const uint32_t *list, const uint32_t *list_count,
+                           const uint32_t *ranges, uint64_t *words, uint64_t *keys,
+                           uint32_t *vals, int64_t capacity, cudaStream_t st) {
+  static_assert(NT * IPT == SEG_CAP0 || NT * IPT == SEG_CAP1, "class");
+  constexpr size_t smem = sizeof(SegSmem<NT, IPT>);
+  static int occ = 0;
+  if (occ == 0) {
+    cudaError_t e = cudaFuncSetAttribute(segsort_kernel<NT, IPT, CHUNKED>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int a = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, segsort_kernel<NT, IPT, CHUNKED>, NT, smem);
+    occ = a > 0 ? a : 1;
   }
+  segsort_kernel<NT, IPT, CHUNKED><<<(unsigned)(sm_count() * occ), NT, smem, st>>>(
+      list, list_count, ranges, words, keys, vals, capacity);
+  return cudaGetLastError();
 }
-
 
 }  // namespace
 
@@ -458,43 +816,21 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
   cudaError_t e;
   WsHeader *hdr = reinterpret_cast<WsHeader *>(ws + L.header);
   uint64_t *scan_lb = reinterpret_cast<uint64_t *>(ws + L.scan_lb);
-  uint32_t *hist = reinterpret_cast<uint32_t *>(ws + L.hist);
-  uint64_t *sort_lb = reinterpret_cast<uint64_t *>(ws + L.sort_lb);
-  uint64_t *alt_keys = reinterpret_cast<uint64_t *>(ws + L.alt_keys);
-  uint32_t *alt_vals = reinterpret_cast<uint32_t *>(ws + L.alt_vals);
-  const int64_t R = (int64_t)vs.n * n;
-  const int passes = (32 + vs.tile_bits + 7) / 8;
-
-  if ((e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * SORT_MAX_PASSES * 256, st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)vs.total_tiles, st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(sort_lb, 0, sizeof(uint64_t) * 256 * (size_t)L.sort_parts, st)) != cudaSuccess) return e;
-  if (R == 0) return cudaMemsetAsync(n_int, 0, sizeof(int64_t), st);
-  if ((e = cudaMemsetAsync(scan_lb, 0, sizeof(uint64_t) * 2 * (size_t)L.scan_parts, st)) != cudaSuccess) return e;
-
-  // Packed mode when (tile << 32 | depth) << idx_bits | record fits in 64 bits: the passes
-  // move 8-byte words instead of 12-byte pairs and the last pass unpacks into the caller's
-  // keys and values. The ping-pong is arranged so that the last pass never reads the buffer
-  // it writes.
-  int idx_bits = 0;
-  while (idx_bits < 32 && ((int64_t)1 << idx_bits) < R) ++idx_bits;
-  const bool packed = idx_bits + 32 + vs.tile_bits <= 64;
-  uint64_t *k0, *k1;
-  uint32_t *v0 = nullptr, *v1 = nullptr;
-  if (packed) {
-    const bool last_even = ((passes - 1) & 1) == 0;  // last pass reads k0 if even
-    k0 = last_even ? alt_keys : keys;
-    k1 = last_even ? keys : alt_keys;
-  } else {
-    k0 = (passes & 1) ? alt_keys : keys;
-    v0 = (passes & 1) ? alt_vals : vals;
-    k1 = (passes & 1) ? keys : alt_keys;
-    v1 = (passes & 1) ? vals : alt_vals;
-  }
-
+  uint64_t *tile_lb = reinterpret_cast<uint64_t *>(ws + L.tile_lb);
+  uint32_t *lists = reinterpret_cast<uint32_t *>(ws + L.seg_list);
+  uint64_t *words = reinterpret_cast<uint64_t *>(ws + L.words);
   uint32_t *vis_rec = reinterpret_cast<uint32_t *>(ws + L.vis_rec);
   uint64_t *vis_off = reinterpret_cast<uint64_t *>(ws + L.vis_off);
   uint32_t *chunk_first = reinterpret_cast<uint32_t *>(ws + L.chunk_first);
+  const int64_t R = (int64_t)vs.n * n;
+  const int64_t T = vs.total_tiles;
+
+  if ((e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)T, st)) != cudaSuccess) return e;
+  if (R == 0) return cudaMemsetAsync(n_int, 0, sizeof(int64_t), st);
+  if ((e = cudaMemsetAsync(scan_lb, 0, sizeof(uint64_t) * 2 * (size_t)L.scan_parts, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(tile_lb, 0, sizeof(uint64_t) * (size_t)L.tile_parts, st)) != cudaSuccess) return e;
+
   scan_kernel<<<(unsigned)L.scan_parts, EMIT_THREADS, 0, st>>>(
       tiles_touched, R, capacity, n_int, &hdr->n_visible, scan_lb, scan_lb + L.scan_parts,
       &hdr->scan_parts, vis_rec, vis_off, chunk_first, &hdr->status);
@@ -502,66 +838,22 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
   int64_t egrid = (int64_t)sm_count() * 4;
   if (egrid > L.chunks) egrid = L.chunks;
   if (egrid < 1) egrid = 1;
-  emit_kernel<<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
-      records, n, vs, vis_rec, vis_off, chunk_first, n_int, &hdr->n_visible, k0, v0, capacity,
-      hist, passes, idx_bits, packed ? 1 : 0, &hdr->status);
+  pair_kernel<false><<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
+      records, n, vs, vis_rec, vis_off, chunk_first, n_int, &hdr->n_visible, tile_ranges, words,
+      capacity, &hdr->status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-
-  static int occ_kv = 0, occ_packed = 0;
-  const size_t smem_kv = sizeof(SortSmem<true>), smem_packed = sizeof(SortSmem<false>);
-  if (occ_kv == 0) {
-    if ((e = cudaFuncSetAttribute(onesweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_kv)) != cudaSuccess)
-      return e;
-    if ((e = cudaFuncSetAttribute(onesweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_packed)) != cudaSuccess)
-      return e;
-    int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, onesweep_kernel<true>, SORT_THREADS, smem_kv);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, onesweep_kernel<false>, SORT_THREADS, smem_packed);
-    occ_kv = a > 0 ? a : 1;
-    occ_packed = b > 0 ? b : 1;
-  }
-  int64_t grid = (int64_t)sm_count() * (packed ? occ_packed : occ_kv);
-  if (grid > L.sort_parts) grid = L.sort_parts;
-  if (grid < 1) grid = 1;
-  for (int p = 0; p < passes; ++p) {
-    const uint64_t *kin = (p & 1) ? k1 : k0;
-    uint64_t *kout = (p & 1) ? k0 : k1;
-    uint64_t *lb = sort_lb + (size_t)(p & 1) * 256 * (size_t)L.sort_parts;
-    uint64_t *lbn = sort_lb + (size_t)((p + 1) & 1) * 256 * (size_t)L.sort_parts;
-    if (packed) {
-      const bool last = p == passes - 1;
-      const uint64_t *a0 = kin;
-      const uint32_t *a1 = nullptr;
-      uint64_t *a2 = last ? keys : kout;
-      uint32_t *a3 = last ? vals : nullptr;
-      int a6 = idx_bits + 8 * p, a7 = idx_bits, a8 = last ? 1 : 0;
-      const uint32_t *a9 = hist + p * 256;
-      uint32_t *a12 = &hdr->sort_parts[p], *a13 = &hdr->status;
-      void *args[] = {&a0, &a1, &a2, &a3, &n_int, &capacity, &a6, &a7, &a8, &a9, &lb, &lbn,
-                      &a12, &a13};
-      e = cudaLaunchCooperativeKernel((const void *)onesweep_kernel<false>, dim3((unsigned)grid),
-                                      dim3(SORT_THREADS), args, smem_packed, st);
-      if (e != cudaSuccess) return e;
-    } else {
-      const uint32_t *vin = (p & 1) ? v1 : v0;
-      uint32_t *vout = (p & 1) ? v0 : v1;
-      int a6 = 8 * p, a7 = 0, a8 = 0;
-      const uint32_t *a9 = hist + p * 256;
-      uint32_t *a12 = &hdr->sort_parts[p], *a13 = &hdr->status;
-      void *args[] = {&kin, &vin, &kout, &vout, &n_int, &capacity, &a6, &a7, &a8, &a9, &lb, &lbn,
-                      &a12, &a13};
-      e = cudaLaunchCooperativeKernel((const void *)onesweep_kernel<true>, dim3((unsigned)grid),
-                                      dim3(SORT_THREADS), args, smem_kv, st);
-      if (e != cudaSuccess) return e;
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  const int64_t rgrid = (int64_t)sm_count() * 8;
-  ranges_kernel<<<(unsigned)rgrid, 256, 0, st>>>(keys, n_int, capacity, vs.total_tiles,
-                                                  tile_ranges);
-  return cudaGetLastError();
+  tile_scan_kernel<<<(unsigned)L.tile_parts, 256, 0, st>>>(
+      tile_ranges, T, tile_lb, &hdr->tile_parts, lists, hdr->seg_count, &hdr->status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  pair_kernel<true><<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
+      records, n, vs, vis_rec, vis_off, chunk_first, n_int, &hdr->n_visible, tile_ranges, words,
+      capacity, &hdr->status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_segsort<256, 8, false>(lists, &hdr->seg_count[0], tile_ranges, words, keys,
+                                         vals, capacity, st)) != cudaSuccess)
+    return e;
+  return launch_segsort<512, 16, true>(lists + T, &hdr->seg_count[1], tile_ranges, words, keys,
+                                       vals, capacity, st);
 }
 
 }  // namespace fgs

@@ -68,7 +68,9 @@ __device__ __forceinline__ int view_of_tile(const Views &vs, int64_t t) {
 struct WsHeader {
   uint32_t status;            // fgs_status of device-detected errors (first one wins)
   uint32_t scan_parts;        // partition counter of the tiles_touched scan
-  uint32_t sort_parts[8];     // partition counters of the radix-sort passes
+  uint32_t tile_parts;        // partition counter of the per-tile count scan
+  uint32_t seg_count[2];      // tiles in each segment-size class (filled by the tile scan)
+  uint32_t spare[5];
   uint32_t raster_tiles;      // tile queue of the forward rasterizer
   uint32_t backward_tiles;    // tile queue of the backward rasterizer
   // measurement counters, written only by instrumented launches (fgs_set_instrumentation):
@@ -83,47 +85,50 @@ static_assert(sizeof(WsHeader) == 256, "header size");
 constexpr int EMIT_THREADS = 256;
 constexpr int EMIT_ITEMS = 4;
 constexpr int EMIT_PART = EMIT_THREADS * EMIT_ITEMS;  // records per scan partition
-constexpr int EMIT_CHUNK = 2048;                      // (record, tile) pairs per emission CTA
-constexpr int SORT_THREADS = 256;
-constexpr int SORT_ITEMS = 16;
-constexpr int SORT_PART = SORT_THREADS * SORT_ITEMS;  // keys per sort partition
-constexpr int SORT_MAX_PASSES = 8;
+constexpr int EMIT_CHUNK = 1024;                      // (record, tile) pairs per emission CTA
+constexpr int TSCAN_PART = 1024;                     // tiles per partition of the tile scan
+// Segment-size classes of the per-tile sort: segments of at most SEG_CAP0 pairs are sorted
+// in shared memory by CTAs of 256 threads, longer ones by CTAs of 512 threads (in shared memory
+// up to SEG_CAP1 pairs, beyond that in SEG_CAP1-pair chunks through global memory).
+constexpr int SEG_CAP0 = 2048;
+constexpr int SEG_CAP1 = 8192;
 constexpr int G2D_STRIDE = 12;                        // floats per record of screen-space grads
 
 struct WsLayout {
-  size_t header, scan_lb, g2d, vis_rec, vis_off, hist, sort_lb, alt_keys, alt_vals, chunk_first,
-      total;
-  int64_t scan_parts, sort_parts, chunks;
+  size_t header, scan_lb, g2d, vis_rec, vis_off, tile_lb, seg_list, words, chunk_first, total;
+  int64_t scan_parts, tile_parts, chunks, total_tiles;
 };
 
 __host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace layout. Regions that depend on the record count only come first, so the
-// rasterizer and the backward can locate them without knowing the key capacity; with_g2d =
-// false leaves out the backward's accumulator (used by the sort-only variant).
-constexpr WsLayout ws_layout_ex(int64_t n_records, int64_t capacity, bool with_g2d) {
+// rasterizer and the backward can locate them without knowing the key capacity or the tile
+// count; with_g2d = false leaves out the backward's accumulator (used by the sort-only variant).
+constexpr WsLayout ws_layout_ex(int64_t n_records, int64_t capacity, int64_t total_tiles,
+                                bool with_g2d) {
   WsLayout L{};
   const int64_t R = n_records > 0 ? n_records : 1;
+  const int64_t T = total_tiles > 0 ? total_tiles : 1;
   L.scan_parts = (n_records + EMIT_PART - 1) / EMIT_PART;
-  L.sort_parts = (capacity + SORT_PART - 1) / SORT_PART;
+  L.tile_parts = (T + TSCAN_PART - 1) / TSCAN_PART;
   L.chunks = (capacity + EMIT_CHUNK - 1) / EMIT_CHUNK;
+  L.total_tiles = T;
   size_t o = 0;
   L.header = o; o += align256(256);
   L.scan_lb = o; o += align256(sizeof(uint64_t) * 2 * (size_t)(L.scan_parts > 0 ? L.scan_parts : 1));
   L.g2d = o; if (with_g2d) o += align256(sizeof(float) * G2D_STRIDE * (size_t)R);
   L.vis_rec = o; o += align256(sizeof(uint32_t) * (size_t)R);
   L.vis_off = o; o += align256(sizeof(uint64_t) * (size_t)R);
-  L.hist = o; o += align256(sizeof(uint32_t) * SORT_MAX_PASSES * 256);
-  L.sort_lb = o; o += align256(sizeof(uint64_t) * 256 * 2 * (size_t)(L.sort_parts > 0 ? L.sort_parts : 1));
-  L.alt_keys = o; o += align256(sizeof(uint64_t) * (size_t)capacity);
-  L.alt_vals = o; o += align256(sizeof(uint32_t) * ((size_t)capacity + 4));
+  L.tile_lb = o; o += align256(sizeof(uint64_t) * (size_t)L.tile_parts);
+  L.seg_list = o; o += align256(sizeof(uint32_t) * 2 * (size_t)T);
+  L.words = o; o += align256(sizeof(uint64_t) * (size_t)capacity);
   L.chunk_first = o; o += align256(sizeof(uint32_t) * ((size_t)L.chunks + 2));
   L.total = o;
   return L;
 }
 
-inline WsLayout ws_layout(int64_t n_records, int64_t capacity) {
-  return ws_layout_ex(n_records, capacity, true);
+inline WsLayout ws_layout(int64_t n_records, int64_t capacity, int64_t total_tiles) {
+  return ws_layout_ex(n_records, capacity, total_tiles, true);
 }
 
 __device__ __forceinline__ void set_status(uint32_t *status, uint32_t code) {

@@ -4,13 +4,14 @@
 // Some callers have no way to hand this library a workspace: a plugin running inside a host
 // application that owns the whole GPU memory budget and forbids allocation, or a hard real-time
 // loop that must never call cudaMalloc / cudaFree (both can synchronise the device). For them,
-// this entry point keeps all of the sort's scratch (status word, scan look-back, digit
-// histograms, sort look-back, alternate key and value buffers) in one file-scope device array of
-// fixed size, so the only memory the caller provides is the inputs and outputs.
+// this entry point keeps all of the sort's scratch (status word, scan look-backs, compacted
+// record list, tile-class lists, bucketed pair words) in one file-scope device array of fixed
+// size, so the only memory the caller provides is the inputs and outputs.
 //
-// The array is part of the module: every GPU that loads the library holds it (about 13 MB)
-// until the process exits. It supports at most NOALLOC_MAX_RECORDS records (views x Gaussians)
-// and NOALLOC_MAX_CAPACITY key slots; larger requests are rejected before anything is launched.
+// The array is part of the module: every GPU that loads the library holds it (about 12 MB)
+// until the process exits. It supports at most NOALLOC_MAX_RECORDS records (views x Gaussians),
+// NOALLOC_MAX_CAPACITY key slots and NOALLOC_MAX_TILES tiles over all views; larger requests
+// are rejected before anything is launched.
 // All calls share the one array, so calls whose work overlaps on the GPU (concurrent streams,
 // threads) race; calls on one stream, one after another, are safe. Each call clears every part
 // of the array that must start at zero, so the previous call's leftovers do not matter.
@@ -25,9 +26,10 @@ namespace {
 
 constexpr int64_t NOALLOC_MAX_RECORDS = 1 << 19;
 constexpr int64_t NOALLOC_MAX_CAPACITY = 1 << 19;
+constexpr int64_t NOALLOC_MAX_TILES = 1 << 17;
 
 constexpr size_t NOALLOC_BYTES =
-    ws_layout_ex(NOALLOC_MAX_RECORDS, NOALLOC_MAX_CAPACITY, false).total;
+    ws_layout_ex(NOALLOC_MAX_RECORDS, NOALLOC_MAX_CAPACITY, NOALLOC_MAX_TILES, false).total;
 
 // The scratch itself. In host code `g_noalloc_scratch` is only a host-side stand-in for the
 // symbol, never a device address: the device address is looked up per device below.
@@ -69,8 +71,9 @@ extern "C" fgs_status fgs_bin_sort_noalloc(const fgs_record *records,
   if (n > 0 && (!records || !tiles_touched || (reinterpret_cast<uintptr_t>(records) & 15)))
     return FGS_ERR_INVALID_ARG;
   Views vs;
-  if (!build_views(cams, n_views, &vs)) return FGS_ERR_INVALID_ARG;
-  const WsLayout L = ws_layout_ex(R, capacity, false);
+  if (!build_views(cams, n_views, &vs) || vs.total_tiles > NOALLOC_MAX_TILES)
+    return FGS_ERR_INVALID_ARG;
+  const WsLayout L = ws_layout_ex(R, capacity, vs.total_tiles, false);
   if (L.total > NOALLOC_BYTES) return FGS_ERR_INVALID_ARG;
   char *ws = scratch_on_current_device();
   if (ws == nullptr) return FGS_ERR_CUDA;

@@ -27,7 +27,12 @@ namespace fgs {
 namespace {
 
 constexpr int TILE_PIX = TILE * TILE;  // 256 pixels per tile
-constexpr int BATCH = 256;             // Gaussians per staged batch
+// Gaussians per staged batch: 256, or 128 for the 4-pixels-per-thread shape, whose CTAs are
+// small and need a small shared-memory footprint to keep enough of them resident
+template <int PPT>
+struct Batch {
+  static constexpr int N = PPT == 4 ? 128 : 256;
+};
 constexpr uint32_t REC_BYTES = sizeof(fgs_record);
 static_assert(REC_BYTES == 48, "record size");
 
@@ -86,6 +91,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
                       uint32_t *__restrict__ n_processed, uint32_t *tile_counter,
                       uint32_t *status, unsigned long long *counters) {
   constexpr int NT = TILE_PIX / PPT;
+  constexpr int BATCH = Batch<PPT>::N;
   constexpr int PER = BATCH / NT;  // copies each thread issues per batch
   __shared__ __align__(128) fgs_record raw[2][BATCH];
   __shared__ __align__(16) float4 xf[BATCH][3];
@@ -294,6 +300,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
                       float *__restrict__ g2d, uint32_t *tile_counter, uint32_t *status,
                       unsigned long long *counters) {
   constexpr int NT = TILE_PIX / PPT;
+  constexpr int BATCH = Batch<PPT>::N;
   constexpr int PER = BATCH / NT;
   __shared__ __align__(128) fgs_record raw[2][BATCH];
   __shared__ __align__(16) float4 xf[BATCH][3];

@@ -1,5 +1,8 @@
-"""GPU bin/sort (fgs_bin_sort: scan + key emission + onesweep radix sort + tile ranges) against
-the oracle's key builder, bit for bit, on the same seeded synthetic records."""
+"""GPU bin/sort (fgs_bin_sort: scan, per-tile pair count, tile scan, bucket scatter, per-tile
+segment sort) against the oracle's key builder, bit for bit, on the same seeded synthetic
+records. The cases reach every segment-size class of the per-tile sort: buckets sorted in shared
+memory by 256- and 512-thread CTAs, and buckets longer than the largest shared-memory class,
+sorted in chunks through global memory."""
 import numpy as np
 import pytest
 import torch
@@ -82,8 +85,18 @@ def _oracle(rect, depth, n, cams_py):
     (20000, [(1752, 1168)], 4, dict(max_ext=10, big_frac=0.002)),  # ~1M pairs, huge rects
     (4000, [(16, 16)], 5, dict(tie_frac=0.9)),                     # one tile, heavy ties
     (3000, [(64, 64)], 6, dict(p_empty=1.0)),                      # nothing visible
-    # 10 views x 30k records and 80k tiles: 15 + 17 + 32 bits > 64, the key/value sort path
+    # 10 views x 30k records, 80k tiles
     (30000, [(1752, 1168)] * 10, 9, dict(max_ext=3, p_empty=0.5)),
+    # buckets of ~600, ~1000 and ~1200 pairs, across the smallest class limit (1024)
+    (2200, [(48, 16)], 10, dict(max_ext=2, tie_frac=0.0)),
+    # one tile with ~4800 pairs (512 x 16 shared-memory class)
+    (6000, [(16, 16)], 11, dict(tie_frac=0.0)),
+    # one tile with ~16000 pairs: longer than any shared-memory class, chunked sort
+    (20000, [(16, 16)], 12, dict(tie_frac=0.0)),
+    # chunked sort with many equal depths, next to smaller buckets
+    (30000, [(32, 32)], 13, dict(max_ext=1, tie_frac=0.6)),
+    # every pair at one depth: the order is the record order alone
+    (9000, [(16, 16)], 14, dict(tie_frac=1.0)),
 ])
 def test_binsort_bit_exact(cuda_device, n, sizes, seed, kw):
     cams_py = _cams(sizes)
