@@ -360,17 +360,15 @@ __global__ void __launch_bounds__(256)
 // in order; each group of 32 is ranked by warp multi-split (the lanes sharing a digit found
 // through a per-warp shared bitmap that each lane ORs its bit into), and a per-warp digit
 // counter carries the count over the groups.
-template <int NT, int IPT>
+template <int NT, int CAP>
 struct SegSmem {
-  static constexpr int CAP = NT * IPT;
-  static constexpr int NB = 2 * CAP;  // sub-buckets of the bucket sort
   uint64_t buf[CAP];
   union {
     struct {
       uint32_t wcnt[NT / 32][256];   // per-warp digit counts -> per-warp offsets within a digit
       uint32_t wmask[NT / 32][256];  // per-warp lane masks of one group of 32 (zero between groups)
     } rx;
-    uint32_t cnt[NB];                // bucket sort: sub-bucket counts -> starts
+    uint32_t cnt[CAP];               // bucket sort: sub-bucket counts -> starts
   };
   uint32_t dstart[256];         // digit start (exclusive prefix of the digit counts)
   uint32_t hist[256];           // chunked path: digit start over the whole segment
@@ -379,8 +377,8 @@ struct SegSmem {
   uint64_t red[2][NT / 32];
 };
 
-template <int NT, int IPT>
-__device__ __forceinline__ void rank_items(SegSmem<NT, IPT> &S, const uint64_t (&x)[IPT],
+template <int NT, int IPT, int CAP>
+__device__ __forceinline__ void rank_items(SegSmem<NT, CAP> &S, const uint64_t (&x)[IPT],
                                            uint32_t cnt, int shift, uint32_t (&rank)[IPT]) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int e = lane; e < 256; e += 32) S.rx.wcnt[w][e] = 0u;
@@ -413,8 +411,8 @@ __device__ __forceinline__ void rank_items(SegSmem<NT, IPT> &S, const uint64_t (
 
 // Turns S.rx.wcnt[w][d] (counts) into per-warp exclusive offsets within digit d and S.dstart[d]
 // into the exclusive prefix of the digit totals; returns digit tid's total (tid < 256).
-template <int NT, int IPT>
-__device__ __forceinline__ uint32_t digit_offsets(SegSmem<NT, IPT> &S) {
+template <int NT, int IPT, int CAP>
+__device__ __forceinline__ uint32_t digit_offsets(SegSmem<NT, CAP> &S) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   uint32_t dcount = 0, incl = 0;
   if (tid < 256) {
@@ -443,8 +441,8 @@ __device__ __forceinline__ uint32_t digit_offsets(SegSmem<NT, IPT> &S) {
 }
 
 // Block AND / OR of a 64-bit value; every thread gets the results.
-template <int NT, int IPT>
-__device__ __forceinline__ void block_and_or(SegSmem<NT, IPT> &S, uint64_t &a, uint64_t &o) {
+template <int NT, int IPT, int CAP>
+__device__ __forceinline__ void block_and_or(SegSmem<NT, CAP> &S, uint64_t &a, uint64_t &o) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) {
@@ -467,13 +465,13 @@ __device__ __forceinline__ void block_and_or(SegSmem<NT, IPT> &S, uint64_t &a, u
 
 // One stable pass over the digit at `shift` of the segment held in registers (x) and shared
 // memory; leaves the result in both.
-template <int NT, int IPT>
-__device__ __forceinline__ void smem_pass(SegSmem<NT, IPT> &S, uint64_t (&x)[IPT], uint32_t cnt,
+template <int NT, int IPT, int CAP>
+__device__ __forceinline__ void smem_pass(SegSmem<NT, CAP> &S, uint64_t (&x)[IPT], uint32_t cnt,
                                           int shift) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t rank[IPT];
-  rank_items<NT, IPT>(S, x, cnt, shift, rank);
-  digit_offsets<NT, IPT>(S);
+  rank_items<NT, IPT, CAP>(S, x, cnt, shift, rank);
+  digit_offsets<NT, IPT, CAP>(S);
 #pragma unroll
   for (int k = 0; k < IPT; ++k) {
     const uint32_t li = (uint32_t)(w * 32 * IPT + k * 32 + lane);
@@ -491,8 +489,8 @@ __device__ __forceinline__ void smem_pass(SegSmem<NT, IPT> &S, uint64_t (&x)[IPT
 }
 
 // Sort one segment of cnt <= NT * IPT words in shared memory and write keys / values.
-template <int NT, int IPT>
-__device__ __forceinline__ void sort_segment_smem(SegSmem<NT, IPT> &S, const uint64_t *src,
+template <int NT, int IPT, int CAP>
+__device__ __forceinline__ void sort_segment_smem(SegSmem<NT, CAP> &S, const uint64_t *src,
                                                   uint32_t cnt, uint64_t tile,
                                                   uint64_t *kout, uint32_t *vout) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -511,11 +509,11 @@ __device__ __forceinline__ void sort_segment_smem(SegSmem<NT, IPT> &S, const uin
       o |= x[k];
     }
   }
-  block_and_or<NT, IPT>(S, a, o);
+  block_and_or<NT, IPT, CAP>(S, a, o);
   const uint64_t varying = a ^ o;
 #pragma unroll
   for (int p = 4; p < 8; ++p)
-    if ((varying >> (8 * p)) & 255u) smem_pass<NT, IPT>(S, x, cnt, 8 * p);
+    if ((varying >> (8 * p)) & 255u) smem_pass<NT, IPT, CAP>(S, x, cnt, 8 * p);
   // equal depths (the high halves) in adjacent slots: sort again over every digit
   bool tie = false;
 #pragma unroll
@@ -526,7 +524,7 @@ __device__ __forceinline__ void sort_segment_smem(SegSmem<NT, IPT> &S, const uin
   if (__syncthreads_or(tie)) {
 #pragma unroll
     for (int p = 0; p < 8; ++p)
-      if ((varying >> (8 * p)) & 255u) smem_pass<NT, IPT>(S, x, cnt, 8 * p);
+      if ((varying >> (8 * p)) & 255u) smem_pass<NT, IPT, CAP>(S, x, cnt, 8 * p);
   }
   for (uint32_t i = threadIdx.x; i < cnt; i += NT) {
     const uint64_t v = S.buf[i];
@@ -537,25 +535,30 @@ __device__ __forceinline__ void sort_segment_smem(SegSmem<NT, IPT> &S, const uin
 }
 
 // Bucket sort of one segment of cnt <= NT * IPT words, the usual path. The depth bits of the
-// segment span [kmin, kmax]; the words are counted into NB = 2 * NT * IPT sub-buckets by the
-// leading bits of depth - kmin (one shared atomic per word, which also gives the word its slot),
-// the counts are scanned, the words placed by sub-bucket, and each word's final place is its
-// sub-bucket's start plus the number of smaller words in its sub-bucket. Words are distinct
-// (the record index is in the low half), so this is a total order equal to that of the 64-bit
-// words. Returns false, having written nothing, when a sub-bucket holds more than BUCKET_KMAX
-// words (depths clustered tighter than the sub-bucket width, or many equal depths); the radix
-// path then sorts the segment.
+// segment span [kmin, kmax]; the words are counted into NB sub-buckets (NB = the power of two
+// >= cnt, at least 32) by the leading bits of depth - kmin (one shared atomic per word, which
+// also gives the word its slot), the counts are scanned, the words placed by sub-bucket, and each
+// word's final place is its sub-bucket's start plus the number of smaller words in its
+// sub-bucket. Words are distinct (the record index is in the low half), so this is a total order
+// equal to that of the 64-bit words. Returns false, having written nothing, when a sub-bucket
+// holds more than BUCKET_KMAX words (depths clustered tighter than the sub-bucket width, or many
+// equal depths); the radix path then sorts the segment.
 constexpr uint32_t BUCKET_KMAX = 32;
 
-template <int NT, int IPT>
-__device__ __forceinline__ bool bucket_sort_segment(SegSmem<NT, IPT> &S, const uint64_t *src,
+template <int NT, int IPT, int CAP>
+__device__ __forceinline__ bool bucket_sort_segment(SegSmem<NT, CAP> &S, const uint64_t *src,
                                                     uint32_t cnt, uint64_t tile,
                                                     uint64_t *kout, uint32_t *vout) {
-  constexpr int NB = SegSmem<NT, IPT>::NB;
-  constexpr int CPT = NB / NT;  // sub-bucket counters per thread
-  constexpr int LOGNB = NB == 4096 ? 12 : 14;
-  static_assert((1 << LOGNB) == NB, "sub-bucket count");
+  static_assert(NT * IPT <= CAP, "capacity");
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  // NB sub-buckets: CAP for the small class (fixed, so the counter loops unroll), else the
+  // power of two >= cnt, so that a segment of the large class pays for its own length only
+  constexpr bool FIXED = CAP <= SEG_CAP0;
+  constexpr int LOGCAP = CAP == 1024 ? 10 : (CAP == 2048 ? 11 : (CAP == 4096 ? 12 : 13));
+  static_assert((1 << LOGCAP) == CAP, "sub-bucket count");
+  const int lognb = FIXED ? LOGCAP : max(5, 32 - __clz(cnt - 1u));
+  const uint32_t nb = 1u << lognb;
+  const uint32_t cpt = nb > (uint32_t)NT ? nb / NT : 1u;  // counters per thread in the scan
   uint64_t x[IPT];
   uint32_t kmin = 0xffffffffu, kmax = 0u;
 #pragma unroll
@@ -568,8 +571,12 @@ __device__ __forceinline__ bool bucket_sort_segment(SegSmem<NT, IPT> &S, const u
       kmax = max(kmax, h);
     }
   }
+  if (FIXED) {
 #pragma unroll
-  for (int c = 0; c < CPT; ++c) S.cnt[c * NT + tid] = 0u;
+    for (int q = 0; q < CAP / NT; ++q) S.cnt[q * NT + tid] = 0u;
+  } else {
+    for (uint32_t q = tid; q < nb; q += NT) S.cnt[q] = 0u;
+  }
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) {
     kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, s));
@@ -588,7 +595,7 @@ __device__ __forceinline__ bool bucket_sort_segment(SegSmem<NT, IPT> &S, const u
   }
   const uint32_t span = kmax - kmin;
   const int bits = span ? 32 - __clz(span) : 0;
-  const int sh = bits > LOGNB ? bits - LOGNB : 0;  // (depth - kmin) >> sh < NB
+  const int sh = bits > lognb ? bits - lognb : 0;  // (depth - kmin) >> sh < NB
   // per word: sub-bucket << 18 | slot in the sub-bucket (a slot beyond BUCKET_KMAX is never
   // used: the segment then goes to the radix path)
   uint32_t bs[IPT];
@@ -602,14 +609,23 @@ __device__ __forceinline__ bool bucket_sort_segment(SegSmem<NT, IPT> &S, const u
     }
   }
   __syncthreads();
-  // exclusive scan of the counts (thread tid owns counters [CPT tid, CPT tid + CPT)) and the
-  // largest count
+  // exclusive scan of the counts (thread tid owns counters [cpt tid, cpt tid + cpt) below NB)
+  // and the largest count
+  const uint32_t q0 = (uint32_t)tid * cpt;
   uint32_t tot = 0, mx = 0;
-#pragma unroll 8
-  for (int q = 0; q < CPT; ++q) {
-    const uint32_t v = S.cnt[tid * CPT + q];
-    tot += v;
-    mx = max(mx, v);
+  if (FIXED) {
+#pragma unroll
+    for (int q = 0; q < CAP / NT; ++q) {
+      const uint32_t v = S.cnt[q0 + q];
+      tot += v;
+      mx = max(mx, v);
+    }
+  } else if (q0 < nb) {
+    for (uint32_t q = q0; q < q0 + cpt; ++q) {
+      const uint32_t v = S.cnt[q];
+      tot += v;
+      mx = max(mx, v);
+    }
   }
   uint32_t incl = tot;
 #pragma unroll
@@ -627,12 +643,21 @@ __device__ __forceinline__ bool bucket_sort_segment(SegSmem<NT, IPT> &S, const u
   for (int ww = 0; ww < w; ++ww) before += S.wtot[ww];
   mx = 0;
   for (int ww = 0; ww < NT / 32; ++ww) mx = max(mx, (uint32_t)S.red[0][ww]);
-  uint32_t e = before + incl - tot;
-#pragma unroll 8
-  for (int q = 0; q < CPT; ++q) {
-    const uint32_t v = S.cnt[tid * CPT + q];
-    S.cnt[tid * CPT + q] = e;
-    e += v;
+  if (FIXED) {
+    uint32_t e = before + incl - tot;
+#pragma unroll
+    for (int q = 0; q < CAP / NT; ++q) {
+      const uint32_t v = S.cnt[q0 + q];
+      S.cnt[q0 + q] = e;
+      e += v;
+    }
+  } else if (q0 < nb) {
+    uint32_t e = before + incl - tot;
+    for (uint32_t q = q0; q < q0 + cpt; ++q) {
+      const uint32_t v = S.cnt[q];
+      S.cnt[q] = e;
+      e += v;
+    }
   }
   __syncthreads();
   if (mx > BUCKET_KMAX) return false;  // uniform over the CTA
@@ -649,7 +674,7 @@ __device__ __forceinline__ bool bucket_sort_segment(SegSmem<NT, IPT> &S, const u
     if (li < cnt) {
       const uint32_t b = bs[k] >> 18;
       const uint32_t b0 = S.cnt[b];
-      const uint32_t b1 = b + 1u < (uint32_t)NB ? S.cnt[b + 1u] : cnt;
+      const uint32_t b1 = b + 1u < nb ? S.cnt[b + 1u] : cnt;
       uint32_t r = 0;
       for (uint32_t j = b0; j < b1; ++j) r += S.buf[j] < x[k] ? 1u : 0u;
       bs[k] = b0 + r;
@@ -676,10 +701,10 @@ __device__ __forceinline__ bool bucket_sort_segment(SegSmem<NT, IPT> &S, const u
 // shared memory and scattered to its place in the other buffer (words <-> the key output,
 // which serves as scratch). All digits with varying bits are sorted. The last step turns the
 // words into keys and values wherever the data ended (in place if that is the key output).
-template <int NT, int IPT>
-__device__ void sort_segment_chunked(SegSmem<NT, IPT> &S, uint64_t *words, uint32_t cnt,
+template <int NT, int IPT, int CAP>
+__device__ __noinline__ void sort_segment_chunked(SegSmem<NT, CAP> &S, uint64_t *words, uint32_t cnt,
                                      uint64_t tile, uint64_t *kout, uint32_t *vout) {
-  constexpr uint32_t CAP = NT * IPT;
+  constexpr uint32_t CH = NT * IPT;  // words per chunk
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   for (int e = tid; e < (NT / 32) * 256; e += NT) (&S.rx.wmask[0][0])[e] = 0u;
   uint64_t a = ~0ull, o = 0ull;
@@ -688,7 +713,7 @@ __device__ void sort_segment_chunked(SegSmem<NT, IPT> &S, uint64_t *words, uint3
     a &= v;
     o |= v;
   }
-  block_and_or<NT, IPT>(S, a, o);
+  block_and_or<NT, IPT, CAP>(S, a, o);
   const uint64_t varying = a ^ o;
   uint64_t *src = words, *dst = kout;
   for (int p = 0; p < 8; ++p) {
@@ -721,8 +746,8 @@ __device__ void sort_segment_chunked(SegSmem<NT, IPT> &S, uint64_t *words, uint3
       }
       __syncthreads();
     }
-    for (uint32_t lo = 0; lo < cnt; lo += CAP) {
-      const uint32_t ccnt = min(CAP, cnt - lo);
+    for (uint32_t lo = 0; lo < cnt; lo += CH) {
+      const uint32_t ccnt = min(CH, cnt - lo);
       uint64_t x[IPT];
       uint32_t rank[IPT];
 #pragma unroll
@@ -730,8 +755,8 @@ __device__ void sort_segment_chunked(SegSmem<NT, IPT> &S, uint64_t *words, uint3
         const uint32_t li = (uint32_t)(w * 32 * IPT + k * 32 + lane);
         x[k] = li < ccnt ? src[lo + li] : 0ull;
       }
-      rank_items<NT, IPT>(S, x, ccnt, shift, rank);
-      const uint32_t dcount = digit_offsets<NT, IPT>(S);
+      rank_items<NT, IPT, CAP>(S, x, ccnt, shift, rank);
+      const uint32_t dcount = digit_offsets<NT, IPT, CAP>(S);
 #pragma unroll
       for (int k = 0; k < IPT; ++k) {
         const uint32_t li = (uint32_t)(w * 32 * IPT + k * 32 + lane);
@@ -757,20 +782,38 @@ __device__ void sort_segment_chunked(SegSmem<NT, IPT> &S, uint64_t *words, uint3
 }
 
 // One CTA per listed tile of a size class, persistent over the class list.
-// Resident CTAs per SM the register budget is sized for: 4 x 256 threads for the small class,
-// 1 x 512 for the large one.
-template <int NT, int IPT>
-struct SegOcc {
-  static constexpr int value = NT * IPT == SEG_CAP0 ? 4 : 1;
-};
+// The radix path kept out of line for the large class, where inlining it would raise the
+// register needs of the bucket sort that every segment takes first.
+template <int NT, int IPT, int CAP>
+__device__ __noinline__ void sort_segment_smem_outlined(SegSmem<NT, CAP> &S, const uint64_t *src,
+                                                        uint32_t cnt, uint64_t tile,
+                                                        uint64_t *kout, uint32_t *vout) {
+  sort_segment_smem<NT, IPT, CAP>(S, src, cnt, tile, kout, vout);
+}
 
-template <int NT, int IPT, bool CHUNKED>
-__global__ void __launch_bounds__(NT, SegOcc<NT, IPT>::value)
+// Sort one segment of cnt <= NT * IPT words in shared memory: the bucket sort, or the radix
+// passes if the bucket sort declines.
+template <int NT, int IPT, int CAP>
+__device__ __forceinline__ void sort_segment(SegSmem<NT, CAP> &S, uint64_t *words, uint32_t cnt,
+                                             uint64_t tile, uint64_t *kout, uint32_t *vout) {
+  if (bucket_sort_segment<NT, IPT, CAP>(S, words, cnt, tile, kout, vout)) return;
+  if constexpr (CAP <= SEG_CAP0)
+    sort_segment_smem<NT, IPT, CAP>(S, words, cnt, tile, kout, vout);
+  else
+    sort_segment_smem_outlined<NT, IPT, CAP>(S, words, cnt, tile, kout, vout);
+}
+
+// One CTA per listed tile of a size class, persistent over the class list. The number of words
+// per thread is picked per segment (the smallest of IPT_LO, 2 IPT_LO, ... that holds it), so a
+// segment costs in proportion to its own length, not the class's largest.
+template <int NT, int IPT_LO, int CAP, int MIN_BLOCKS, bool CHUNKED>
+__global__ void __launch_bounds__(NT, MIN_BLOCKS)
     segsort_kernel(const uint32_t *__restrict__ list, const uint32_t *list_count,
                    const uint32_t *__restrict__ ranges, uint64_t *words, uint64_t *keys,
                    uint32_t *vals, int64_t capacity) {
+  static_assert(NT * IPT_LO * 2 == CAP, "two word counts per class");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SegSmem<NT, IPT> &S = *reinterpret_cast<SegSmem<NT, IPT> *>(smem_raw);
+  SegSmem<NT, CAP> &S = *reinterpret_cast<SegSmem<NT, CAP> *>(smem_raw);
   const uint32_t count = *list_count;
   for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
     const uint32_t t = __ldg(list + i);
@@ -778,31 +821,31 @@ __global__ void __launch_bounds__(NT, SegOcc<NT, IPT>::value)
     // bounds of a bucket that a device-side error left inconsistent: skip it
     if (rg.y <= rg.x || (int64_t)rg.y > capacity) continue;
     const uint32_t cnt = rg.y - rg.x;
-    if (cnt <= (uint32_t)(NT * IPT)) {
-      if (!bucket_sort_segment<NT, IPT>(S, words + rg.x, cnt, t, keys + rg.x, vals + rg.x))
-        sort_segment_smem<NT, IPT>(S, words + rg.x, cnt, t, keys + rg.x, vals + rg.x);
-    }
+    if (cnt <= (uint32_t)(NT * IPT_LO))
+      sort_segment<NT, IPT_LO, CAP>(S, words + rg.x, cnt, t, keys + rg.x, vals + rg.x);
+    else if (cnt <= (uint32_t)CAP)
+      sort_segment<NT, 2 * IPT_LO, CAP>(S, words + rg.x, cnt, t, keys + rg.x, vals + rg.x);
     else if (CHUNKED)
-      sort_segment_chunked<NT, IPT>(S, words + rg.x, cnt, t, keys + rg.x, vals + rg.x);
+      sort_segment_chunked<NT, 2 * IPT_LO, CAP>(S, words + rg.x, cnt, t, keys + rg.x, vals + rg.x);
   }
 }
 
-template <int NT, int IPT, bool CHUNKED>
+template <int NT, int IPT_LO, int CAP, int MIN_BLOCKS, bool CHUNKED>
 cudaError_t launch_segsort(const uint32_t *list, const uint32_t *list_count,
                            const uint32_t *ranges, uint64_t *words, uint64_t *keys,
                            uint32_t *vals, int64_t capacity, cudaStream_t st) {
-  static_assert(NT * IPT == SEG_CAP0 || NT * IPT == SEG_CAP1, "class");
-  constexpr size_t smem = sizeof(SegSmem<NT, IPT>);
+  constexpr size_t smem = sizeof(SegSmem<NT, CAP>);
   static int occ = 0;
   if (occ == 0) {
-    cudaError_t e = cudaFuncSetAttribute(segsort_kernel<NT, IPT, CHUNKED>,
+    cudaError_t e = cudaFuncSetAttribute(segsort_kernel<NT, IPT_LO, CAP, MIN_BLOCKS, CHUNKED>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int a = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, segsort_kernel<NT, IPT, CHUNKED>, NT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &a, segsort_kernel<NT, IPT_LO, CAP, MIN_BLOCKS, CHUNKED>, NT, smem);
     occ = a > 0 ? a : 1;
   }
-  segsort_kernel<NT, IPT, CHUNKED><<<(unsigned)(sm_count() * occ), NT, smem, st>>>(
+  segsort_kernel<NT, IPT_LO, CAP, MIN_BLOCKS, CHUNKED><<<(unsigned)(sm_count() * occ), NT, smem, st>>>(
       list, list_count, ranges, words, keys, vals, capacity);
   return cudaGetLastError();
 }
@@ -849,11 +892,12 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
       records, n, vs, vis_rec, vis_off, chunk_first, n_int, &hdr->n_visible, tile_ranges, words,
       capacity, &hdr->status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = launch_segsort<256, 8, false>(lists, &hdr->seg_count[0], tile_ranges, words, keys,
-                                         vals, capacity, st)) != cudaSuccess)
+  if ((e = launch_segsort<256, 2, SEG_CAP0, 6, false>(lists, &hdr->seg_count[0], tile_ranges,
+                                                       words, keys, vals, capacity, st)) !=
+      cudaSuccess)
     return e;
-  return launch_segsort<512, 16, true>(lists + T, &hdr->seg_count[1], tile_ranges, words, keys,
-                                       vals, capacity, st);
+  return launch_segsort<512, 8, SEG_CAP1, 1, true>(lists + T, &hdr->seg_count[1], tile_ranges,
+                                                   words, keys, vals, capacity, st);
 }
 
 }  // namespace fgs

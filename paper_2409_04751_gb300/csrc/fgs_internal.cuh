@@ -90,7 +90,7 @@ constexpr int TSCAN_PART = 1024;                     // tiles per partition of t
 // Segment-size classes of the per-tile sort: segments of at most SEG_CAP0 pairs are sorted
 // in shared memory by CTAs of 256 threads, longer ones by CTAs of 512 threads (in shared memory
 // up to SEG_CAP1 pairs, beyond that in SEG_CAP1-pair chunks through global memory).
-constexpr int SEG_CAP0 = 2048;
+constexpr int SEG_CAP0 = 1024;
 constexpr int SEG_CAP1 = 8192;
 constexpr int G2D_STRIDE = 12;                        // floats per record of screen-space grads
 

@@ -83,8 +83,34 @@ __device__ __forceinline__ void load_idx(const uint32_t *__restrict__ vals, uint
   }
 }
 
+
+// The exponent of the blend in base 2, e = A' dx^2 + B' dx dy + C' dy^2 + log2(opacity) with
+// (dx, dy) = pixel centre - mean, A' = -log2(e) conic_xx / 2, B' = -log2(e) conic_xy,
+// C' = -log2(e) conic_yy / 2, written in tile-centred pixel coordinates (u, v) = pixel centre
+// - tile centre: e = K0 + Kx u + Ky v + A' u^2 + B' u v + C' v^2 (five FMAs per pixel; with
+// |u|, |v| <= 7.5 the terms stay small, so rounding stays near that of the direct form). The
+// forward (every work shape) and the backward evaluate it the same way, so they take the same
+// alpha >= 1/255 decisions. xf[0] = (K0, Kx, Ky, A'), xf[1] = (B', C', r, g),
+// xf[2] = (b, mean - tile centre offsets cx, cy, 0) with dx = u + cx, dy = v + cy.
+__device__ __forceinline__ void stage_record(const fgs_record &g, float tile_cx, float tile_cy,
+                                             float4 *xf) {
+  const float A = -0.5f * LOG2E * g.conic[0], B = -LOG2E * g.conic[1];
+  const float C = -0.5f * LOG2E * g.conic[2], lo2o = log2f(g.opacity);
+  const float cx = tile_cx - g.xy[0], cy = tile_cy - g.xy[1];
+  const float K0 = fmaf(cx, fmaf(A, cx, B * cy), fmaf(C * cy, cy, lo2o));
+  const float Kx = fmaf(2.f * A, cx, B * cy), Ky = fmaf(B, cx, 2.f * C * cy);
+  xf[0] = make_float4(K0, Kx, Ky, A);
+  xf[1] = make_float4(B, C, g.rgb[0], g.rgb[1]);
+  xf[2] = make_float4(g.rgb[2], cx, cy, 0.f);
+}
+
+__device__ __forceinline__ float exponent(const float4 &a, const float4 &c, float u, float v,
+                                          float uu, float uv, float vv) {
+  return fmaf(uu, a.w, fmaf(uv, c.x, fmaf(vv, c.y, fmaf(v, a.z, fmaf(u, a.y, a.x)))));
+}
+
 template <int PPT, bool COUNT>
-__global__ void __launch_bounds__(TILE_PIX / PPT)
+__global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
     raster_fwd_kernel(const fgs_record *__restrict__ rec, const uint32_t *__restrict__ vals,
                       const uint32_t *__restrict__ ranges, Views vs, float bg0, float bg1,
                       float bg2, float *__restrict__ images, float *__restrict__ final_T,
@@ -120,6 +146,10 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
     const View &V = vs.v[ti.v];
     const int px = ti.tx * TILE + lx;
     const float fpx = (float)px + 0.5f;
+    // tile centre (between pixel centres 7 and 8) and this pixel's offset from it
+    const float tile_cx = (float)(ti.tx * TILE) + 0.5f * TILE, tile_cy = (float)(ti.ty * TILE) + 0.5f * TILE;
+    const float fu = (float)lx - 7.5f, fv = (float)ly0 - 7.5f;
+    const float uu = fu * fu, uv = fu * fv, vv = fv * fv;
     float fpy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
     uint32_t last[PPT];
     bool live[PPT];
@@ -164,50 +194,76 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
         for (int k = 0; k < PER; ++k) {
           const uint32_t slot = tid + k * NT;
           if (slot < cnt) {
-            const fgs_record &g = raw[s][slot];
-            // exponent in base 2: e = A' dx^2 + B' dx dy + C' dy^2 + log2(opacity)
-            xf[slot][0] = make_float4(g.xy[0], g.xy[1], -0.5f * LOG2E * g.conic[0], -LOG2E * g.conic[1]);
-            xf[slot][1] = make_float4(-0.5f * LOG2E * g.conic[2], log2f(g.opacity), g.rgb[0], g.rgb[1]);
-            xf[slot][2] = make_float4(g.rgb[2], 0.f, 0.f, 0.f);
+            stage_record(raw[s][slot], tile_cx, tile_cy, xf[slot]);
           }
         }
         __syncthreads();
-        if (!__all_sync(0xffffffffu, done)) {
+        if (PPT == 1 && !__all_sync(0xffffffffu, done)) {
+          // one pixel per thread, two list entries per iteration
+          const uint32_t lo1 = lo + 1;
+          if (!done) {
+            bool stop = false;
+            uint32_t j = 0;
+            for (; j < cnt; j += 2) {
+              const bool two = j + 1 < cnt;
+              const float4 a0 = xf[j][0], c0 = xf[j][1];
+              const uint32_t j1 = two ? j + 1 : j;
+              const float4 a1 = xf[j1][0], c1 = xf[j1][1];
+              const float e0 = exponent(a0, c0, fu, fv, uu, uv, vv);
+              const float e1 = exponent(a1, c1, fu, fv, uu, uv, vv);
+              if (COUNT) ++n_eval;
+              if (e0 >= LOG2_ALPHA_MIN) {
+                const float alpha = fminf(ALPHA_MAX, ex2_approx(e0));
+                const float Tn = fmaf(-alpha, T[0], T[0]);
+                if (Tn < T_MIN) {
+                  stop = true;
+                  break;
+                }
+                const float wgt = alpha * T[0];
+                C0[0] = fmaf(c0.z, wgt, C0[0]);
+                C1[0] = fmaf(c0.w, wgt, C1[0]);
+                C2[0] = fmaf(xf[j][2].x, wgt, C2[0]);
+                T[0] = Tn;
+                last[0] = lo1 + j;
+                if (COUNT) ++n_blend;
+              }
+              if (!two) break;
+              if (COUNT) ++n_eval;
+              if (e1 >= LOG2_ALPHA_MIN) {
+                const float alpha = fminf(ALPHA_MAX, ex2_approx(e1));
+                const float Tn = fmaf(-alpha, T[0], T[0]);
+                if (Tn < T_MIN) {
+                  stop = true;
+                  break;
+                }
+                const float wgt = alpha * T[0];
+                C0[0] = fmaf(c1.z, wgt, C0[0]);
+                C1[0] = fmaf(c1.w, wgt, C1[0]);
+                C2[0] = fmaf(xf[j1][2].x, wgt, C2[0]);
+                T[0] = Tn;
+                last[0] = lo1 + j1;
+                if (COUNT) ++n_blend;
+              }
+            }
+            if (stop) live[0] = false;
+            done = !live[0];
+          }
+        } else if (!__all_sync(0xffffffffu, done)) {
           const uint32_t lo1 = lo + 1;
           for (uint32_t j = 0; j < cnt && !done; ++j) {
             const float4 a = xf[j][0];
             const float4 c = xf[j][1];
-            const float dx = fpx - a.x;
-            const float adx = a.z * dx;
-            if (PPT == 1) {
-              const float dy = fpy[0] - a.y;
-              const float e = fmaf(dx, fmaf(a.w, dy, adx), fmaf(c.x * dy, dy, c.y));
-              if (COUNT) ++n_eval;
-              if (e < LOG2_ALPHA_MIN) continue;
-              const float alpha = fminf(ALPHA_MAX, ex2_approx(e));
-              const float Tn = T[0] * (1.f - alpha);
-              if (Tn < T_MIN) {
-                live[0] = false;
-                break;
-              }
-              const float wgt = alpha * T[0];
-              C0[0] = fmaf(c.z, wgt, C0[0]);
-              C1[0] = fmaf(c.w, wgt, C1[0]);
-              C2[0] = fmaf(xf[j][2].x, wgt, C2[0]);
-              T[0] = Tn;
-              last[0] = lo1 + j;
-              if (COUNT) ++n_blend;
-            } else {
+            {
               bool any_live = false;
 #pragma unroll
               for (int k = 0; k < PPT; ++k) {
                 if (live[k]) {
-                  const float dy = fpy[k] - a.y;
-                  const float e = fmaf(dx, fmaf(a.w, dy, adx), fmaf(c.x * dy, dy, c.y));
+                  const float v = fv + (float)k;
+                  const float e = exponent(a, c, fu, v, uu, fu * v, v * v);
                   if (COUNT) ++n_eval;
                   if (e >= LOG2_ALPHA_MIN) {
                     const float alpha = fminf(ALPHA_MAX, ex2_approx(e));
-                    const float Tn = T[k] * (1.f - alpha);
+                    const float Tn = fmaf(-alpha, T[k], T[k]);
                     if (Tn < T_MIN) {
                       live[k] = false;
                     } else {
@@ -332,17 +388,17 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
     const TileInfo ti = tile_info(vs, t, ranges);
     const View &V = vs.v[ti.v];
     const int px = ti.tx * TILE + lx;
-    const float fpx = (float)px + 0.5f;
+    const float tile_cx = (float)(ti.tx * TILE) + 0.5f * TILE, tile_cy = (float)(ti.ty * TILE) + 0.5f * TILE;
+    const float fu = (float)lx - 7.5f, fv = (float)ly0 - 7.5f, uu = fu * fu;
     const int64_t plane = (int64_t)V.width * V.height;
     // per pixel: transmittance, dL/dC, and GS = <dL/dC, colour behind the current entry>
     // (the sum over later blended entries plus T_final bg), kept as one scalar
-    float fpy[PPT], T[PPT], G0[PPT], G1[PPT], G2[PPT], GS[PPT];
+    float T[PPT], G0[PPT], G1[PPT], G2[PPT], GS[PPT];
     uint32_t last[PPT];
     uint32_t my_max = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
       const int py = ti.ty * TILE + ly0 + k;
-      fpy[k] = (float)py + 0.5f;
       T[k] = 1.f; G0[k] = G1[k] = G2[k] = 0.f;
       last[k] = 0;
       if (px < V.width && py < V.height) {
@@ -395,10 +451,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
         for (int k = 0; k < PER; ++k) {
           const uint32_t slot = tid + k * NT;
           if (slot < cnt) {
-            const fgs_record &g = raw[s][slot];
-            xf[slot][0] = make_float4(g.xy[0], g.xy[1], -0.5f * LOG2E * g.conic[0], -LOG2E * g.conic[1]);
-            xf[slot][1] = make_float4(-0.5f * LOG2E * g.conic[2], log2f(g.opacity), g.rgb[0], g.rgb[1]);
-            xf[slot][2] = make_float4(g.rgb[2], 0.f, 0.f, 0.f);
+            stage_record(raw[s][slot], tile_cx, tile_cy, xf[slot]);
           }
         }
         __syncthreads();
@@ -413,18 +466,19 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
           if (any_pos) {
             const float4 a = xf[j][0];
             const float4 c = xf[j][1];
-            const float dx = fpx - a.x;
-            const float adx = a.z * dx;
+            const float4 c2 = xf[j][2];
+            const float dx = fu + c2.y;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
               if (pos < last[k]) {
-                const float dy = fpy[k] - a.y;
-                const float e = fmaf(dx, fmaf(a.w, dy, adx), fmaf(c.x * dy, dy, c.y));
+                const float vk = fv + (float)k;
+                const float e = exponent(a, c, fu, vk, uu, fu * vk, vk * vk);
+                const float dy = vk + c2.z;
                 if (COUNT) ++n_eval;
                 if (e >= LOG2_ALPHA_MIN) {
                   contrib = true;
                   if (COUNT) ++n_contrib;
-                  const float cb = xf[j][2].x;
+                  const float cb = c2.x;
                   const float araw = ex2_approx(e);
                   const float alpha = fminf(ALPHA_MAX, araw);
                   const float om = rcp_approx(1.f - alpha);
