@@ -31,11 +31,12 @@ import numpy as np  # noqa: E402
 METRIC = "fisheye views/s fwd and fwd+bwd at 1752×1168; served p50/p99 latency"
 WORKLOAD = "fisheye-GS 500k Gaussians SH3, 1752x1168 @180deg, random pose, fwd+bwd"
 L2_FLUSH_BYTES = 256 << 20
-# FP32 flops per (pixel, Gaussian) pair in the rasterizer's formulation (FMA = 2):
-FLOPS_FWD_EVAL = 10    # dx, dy, the quadratic form and the log-opacity offset
-FLOPS_FWD_BLEND = 10   # min, 1-alpha, T(1-alpha), alpha T, three colour FMAs
-FLOPS_BWD_EVAL = 10
-FLOPS_BWD_CONTRIB = 58  # transmittance recovery, dL/dalpha, colour suffix, 9 gradients + sum
+# FP32 flops per (pixel, Gaussian) pair in the rasterizer's formulation (FMA = 2, MUFU = 1):
+FLOPS_FWD_EVAL = 10     # the base-2 exponent: five FMAs in tile-centred coordinates
+FLOPS_FWD_BLEND = 11    # exp2, min, T - alpha T, alpha T, three colour FMAs
+FLOPS_BWD_EVAL = 10     # the same exponent
+FLOPS_BWD_CONTRIB = 35  # exp2, min, 1 - alpha, rcp, T recovery, alpha T, <dL/dC, c>, dL/dalpha,
+#                         colour suffix, 3 colour sums, dL/dp and its 6 moments
 
 
 def _env_rank():
