@@ -58,6 +58,11 @@ def _lib_handle():
         lib.orc_jacobian.argtypes = [_D, ctypes.c_double, ctypes.c_double, _D]
         lib.orc_jacobian_grad.argtypes = [_D, ctypes.c_double, ctypes.c_double, _D, _D, _D]
         lib.orc_sh_basis.argtypes = [ctypes.c_int, _D, _D, _D]
+        lib.orc_cam_project.argtypes = [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double, _D]
+        lib.orc_cam_jacobian.argtypes = [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double, _D]
+        lib.orc_cam_jacobian_grad.argtypes = [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double,
+                                              _D, _D, _D]
         lib.orc_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -75,12 +80,16 @@ def num_threads() -> int:
     return int(_lib_handle().orc_num_threads())
 
 
+# camera models (the C oracle's camera[18])
+CAM_EQUIDISTANT, CAM_EQUISOLID, CAM_STEREOGRAPHIC, CAM_ORTHOGRAPHIC, CAM_EQUIRECT = range(5)
+
+
 def cam_array(cam) -> np.ndarray:
-    """double[18] = W (row-major, world -> camera), b, fx, fy, cx, cy, width, height."""
+    """double[19] = W (row-major, world -> camera), b, fx, fy, cx, cy, width, height, model."""
     return _f64(np.concatenate([np.asarray(cam["W"], np.float64).reshape(9),
                                 np.asarray(cam["b"], np.float64).reshape(3),
                                 [cam["fx"], cam["fy"], cam["cx"], cam["cy"],
-                                 cam["width"], cam["height"]]]))
+                                 cam["width"], cam["height"], cam.get("model", 0)]]))
 
 
 def tiles_of(cam):
@@ -180,24 +189,36 @@ def build_keys(view, rect, depth_bits, tile_offset, tiles_x, n_tiles_total):
     return keys[:m], vals[:m], ranges[:int(n_tiles_total)]
 
 
-def project_point(muc, fx, fy, cx=0.0, cy=0.0):
+def project_point(muc, fx, fy, cx=0.0, cy=0.0, model=CAM_EQUIDISTANT):
     lib = _lib_handle()
     m = _f64(muc)
     out = np.zeros(2)
-    lib.orc_project_point(_p(m), fx, fy, cx, cy, _p(out))
+    if model == CAM_EQUIDISTANT:
+        lib.orc_project_point(_p(m), fx, fy, cx, cy, _p(out))
+    else:
+        lib.orc_cam_project(int(model), _p(m), fx, fy, cx, cy, _p(out))
     return out
 
 
-def jacobian(muc, fx, fy):
+def jacobian(muc, fx, fy, model=CAM_EQUIDISTANT):
     lib = _lib_handle()
     m = _f64(muc)
     J = np.zeros(6)
-    lib.orc_jacobian(_p(m), fx, fy, _p(J))
+    lib.orc_cam_jacobian(int(model), _p(m), fx, fy, _p(J))
     return J.reshape(2, 3)
 
 
-def jacobian_grad(muc, fx, fy):
+def jacobian_grad(muc, fx, fy, model=CAM_EQUIDISTANT):
     """(dJ/dx_c, dJ/dy_c, dJ/dz_c), each 2x3."""
+    lib = _lib_handle()
+    m = _f64(muc)
+    a, b, c = np.zeros(6), np.zeros(6), np.zeros(6)
+    lib.orc_cam_jacobian_grad(int(model), _p(m), fx, fy, _p(a), _p(b), _p(c))
+    return a.reshape(2, 3), b.reshape(2, 3), c.reshape(2, 3)
+
+
+def jacobian_grad_paper_form(muc, fx, fy):
+    """The equidistant (dJ/dx_c, dJ/dy_c, dJ/dz_c) in the paper's S1..S8 form (Sec. 4.3)."""
     lib = _lib_handle()
     m = _f64(muc)
     a, b, c = np.zeros(6), np.zeros(6), np.zeros(6)

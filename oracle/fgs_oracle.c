@@ -9,7 +9,8 @@
  * What it computes, step by step, with the passage each step follows:
  *   orc_project     per Gaussian: view transform (Sec. 3.1 "Transformation"), equidistant
  *                   projection of the mean (Sec. 3.2, eq. "equal_distance" and the x_p, y_p
- *                   equations), fisheye Jacobian J_phi (Sec. 4.2), Sigma = R S S^T R^T
+ *                   equations; other models below), fisheye Jacobian J_phi (Sec. 4.2),
+ *                   Sigma = R S S^T R^T
  *                   (Sec. 3.1 "Definition"), Sigma_p = T Sigma T^T with T = J W (Sec. 4.3),
  *                   conic, colour from spherical harmonics, depth, footprint.
  *   orc_render      per pixel: the blending sum of Sec. 3.1 "Rendering" evaluated over every
@@ -20,6 +21,13 @@
  *                   Sec. 4.3), and Sigma -> (s, q), colour -> SH and view direction.
  *   orc_build_keys  tile binning and sort (Sec. 3.1 "Rendering", Sec. 4.1): one
  *                   (tile << 32 | depth bits) key per Gaussian x covered tile, stable order.
+ *
+ * Camera models (camera[18]): 0 the equidistant fisheye of the method; 1 equisolid,
+ * 2 stereographic, 3 orthographic, the other radial models Sec. 3.2 names (r_d = f r(theta)
+ * with r = 2 sin(theta/2), 2 tan(theta/2), sin(theta)); 4 the equirectangular panorama of the
+ * "Extension to Other Camera Models" paragraph (Sec. 6): x_p = cx + fx atan2(x_c, z_c),
+ * y_p = cy + fy atan2(y_c, sqrt(x_c^2 + z_c^2)), which with fx = w / 2 pi, cx = w / 2,
+ * fy = h / pi, cy = h / 2 is the paper's pair of equations.
  *
  * Readings where the paper is silent or garbled (each is a convention, "parity unpinned" as a
  * constant: the paper fixes none of the numbers below):
@@ -32,7 +40,14 @@
  *     all digits to cancellation; for t = l_z / z_c < 1e-2 they are evaluated by their Taylor
  *     series in t (derived from atan's series), which is exact to rounding there.
  *   - camera axes x right, y down, z forward; pixel (i, j) is sampled at (i + 0.5, j + 0.5).
- *   - a Gaussian is visible iff |mu_c| > 0.2, theta < pi - 0.05 and opacity >= 1/255.
+ *   - a Gaussian is visible iff |mu_c| > 0.2, theta < pi - 0.05 and opacity >= 1/255;
+ *     orthographic: theta < pi/2 - 0.05 (beyond it r(theta) decreases and the image folds);
+ *     panorama: |latitude| < pi/2 - 0.05 (the poles, where J is singular). The panorama has no
+ *     wrap-around at longitude +-pi: a Gaussian is drawn on the side of its mean only.
+ *   - every radial model's Jacobian has the form of the equidistant one,
+ *       J = [[fx (g + x^2 h), fx x y h, fx x k], [fy x y h, fy (g + y^2 h), fy y k]],
+ *     g = r(theta) / l_z, h = (1/l) dG/dl, k = dG/dz + z h for g = G(l, z), l = |mu_c|
+ *     (equidistant: k = -1 / l2).
  *   - Sigma_p gets 0.3 added on its diagonal (low-pass dilation of the renderer the method
  *     plugs into).
  *   - colour = max(0, sum_k SH_k Y_k(dir) + 0.5), Y_k the real spherical harmonics with the
@@ -57,6 +72,13 @@
 
 #define ORC_NEAR 0.2
 #define ORC_THETA_MAX (ORC_PI - 0.05)
+#define ORC_THETA_MAX_ORTHO (0.5 * ORC_PI - 0.05)
+#define ORC_LAT_MAX (0.5 * ORC_PI - 0.05)
+#define ORC_CAM_EQUIDISTANT 0
+#define ORC_CAM_EQUISOLID 1
+#define ORC_CAM_STEREOGRAPHIC 2
+#define ORC_CAM_ORTHOGRAPHIC 3
+#define ORC_CAM_EQUIRECT 4
 #define ORC_ALPHA_MIN (1.0 / 255.0)
 #define ORC_ALPHA_MAX 0.99
 #define ORC_T_MIN 1e-4
@@ -87,7 +109,8 @@
 
 int orc_nf(void) { return ORC_NF; }
 
-/* camera: double[18] = W[9] (row-major, world -> camera), b[3], fx, fy, cx, cy, width, height */
+/* camera: double[19] = W[9] (row-major, world -> camera), b[3], fx, fy, cx, cy, width, height,
+ * model */
 
 /* ---------------------------------------------------------------------------------------- */
 /* Equidistant projection (Sec. 3.2) and its Jacobian (Sec. 4.2, f restored on theta terms). */
@@ -165,6 +188,146 @@ void orc_jacobian_grad(const double *muc, double fx, double fy, double *dJx, dou
   dJy[3] = fy * s3; dJy[4] = fy * s4; dJy[5] = fy * S6 / l22;
   dJz[0] = fx * S5 / l22; dJz[1] = 2.0 * fx * x * y / l22; dJz[2] = 2.0 * fx * x * z / l22;
   dJz[3] = 2.0 * fy * x * y / l22; dJz[4] = fy * S6 / l22; dJz[5] = 2.0 * fy * y * z / l22;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* The other radial models: x_p = cx + fx g x, y_p = cy + fy g y with g = r(theta) / l_z, a
+ * function G(l, z) of l = |mu_c| and z = z_c. With cos(theta) = z / l:
+ *   equisolid      r = 2 sin(theta/2):  g = sqrt(2 / (l (l + z)))      (sin(theta/2)^2 = (l - z) / 2l)
+ *   stereographic  r = 2 tan(theta/2):  g = 2 / (l + z)                (tan(theta/2) = l_z / (l + z))
+ *   orthographic   r = sin(theta):      g = 1 / l                      (sin(theta) = l_z / l)
+ * G and its partial derivatives in (l, z) up to second order, from these closed forms. */
+static void orc_radial_G(int model, double l, double z, double *G) {
+  /* G[0..5] = G, G_l, G_z, G_ll, G_lz, G_zz */
+  if (model == ORC_CAM_EQUISOLID) {
+    double P = l * (l + z), Pl = 2 * l + z, Pz = l;  /* P_ll = 2, P_lz = 1, P_zz = 0 */
+    double r2 = sqrt(2.0), Pm12 = 1.0 / sqrt(P), Pm32 = Pm12 / P, Pm52 = Pm32 / P;
+    G[0] = r2 * Pm12;
+    G[1] = -0.5 * r2 * Pm32 * Pl;
+    G[2] = -0.5 * r2 * Pm32 * Pz;
+    G[3] = 0.75 * r2 * Pm52 * Pl * Pl - 0.5 * r2 * Pm32 * 2.0;
+    G[4] = 0.75 * r2 * Pm52 * Pl * Pz - 0.5 * r2 * Pm32 * 1.0;
+    G[5] = 0.75 * r2 * Pm52 * Pz * Pz;
+  } else if (model == ORC_CAM_STEREOGRAPHIC) {
+    double S = l + z;
+    G[0] = 2.0 / S;
+    G[1] = G[2] = -2.0 / (S * S);
+    G[3] = G[4] = G[5] = 4.0 / (S * S * S);
+  } else { /* orthographic */
+    G[0] = 1.0 / l;
+    G[1] = -1.0 / (l * l);
+    G[2] = 0.0;
+    G[3] = 2.0 / (l * l * l);
+    G[4] = G[5] = 0.0;
+  }
+}
+
+/* (g, h, k, h_l, h_z, k_l, k_z) of a radial model at mu_c, where g = G, h = G_l / l,
+ * k = G_z + z h (so dg/dx = x h, dg/dz = k), h_l, k_l = (1/l) d/dl at fixed z, and h_z, k_z the
+ * derivatives in z_c at fixed x_c, y_c. The equidistant model takes g, h, h_l from its series-
+ * stabilised closed forms (h_l = S8 / (l2^2 l_z^5)), k = -1/l2, h_z = 2/l2^2, k_l = 2/l2^2,
+ * k_z = 2 z / l2^2. */
+static void orc_radial_terms(int model, double x, double y, double z, double *t) {
+  double l2 = x * x + y * y + z * z, l = sqrt(l2);
+  if (model == ORC_CAM_EQUIDISTANT) {
+    double th, g, h, s8q;
+    orc_ghs(x, y, z, &th, &g, &h, &s8q);
+    t[0] = g; t[1] = h; t[2] = -1.0 / l2;
+    t[3] = s8q; t[4] = 2.0 / (l2 * l2); t[5] = 2.0 / (l2 * l2); t[6] = 2.0 * z / (l2 * l2);
+    return;
+  }
+  double G[6];
+  orc_radial_G(model, l, z, G);
+  double h = G[1] / l, k = G[2] + z * h;
+  double Hl = G[3] / l - G[1] / (l * l), Hz = G[4] / l;
+  double Kl = G[4] + z * Hl, Kz = G[5] + h + z * Hz;
+  t[0] = G[0]; t[1] = h; t[2] = k;
+  t[3] = Hl / l; t[4] = Hz + z * Hl / l; t[5] = Kl / l; t[6] = Kz + z * Kl / l;
+}
+
+/* Projection of mu_c for any model. */
+void orc_cam_project(int model, const double *muc, double fx, double fy, double cx, double cy,
+                     double *xy) {
+  double x = muc[0], y = muc[1], z = muc[2];
+  if (model == ORC_CAM_EQUIRECT) {
+    xy[0] = cx + fx * atan2(x, z);
+    xy[1] = cy + fy * atan2(y, sqrt(x * x + z * z));
+    return;
+  }
+  double t[7];
+  orc_radial_terms(model, x, y, z, t);
+  xy[0] = cx + fx * t[0] * x;
+  xy[1] = cy + fy * t[0] * y;
+}
+
+/* Jacobian (2x3 row-major) for any model. Panorama (Sec. 6, as printed there):
+ *   [[fx z / rho^2, 0, -fx x / rho^2], [-fy x y / (rho l2), fy rho / l2, -fy y z / (rho l2)]],
+ * rho = sqrt(x^2 + z^2). */
+void orc_cam_jacobian(int model, const double *muc, double fx, double fy, double *J) {
+  double x = muc[0], y = muc[1], z = muc[2];
+  if (model == ORC_CAM_EQUIRECT) {
+    double r2 = x * x + z * z, rho = sqrt(r2), l2 = r2 + y * y, u = 1.0 / (rho * l2);
+    J[0] = fx * z / r2; J[1] = 0.0; J[2] = -fx * x / r2;
+    J[3] = -fy * x * y * u; J[4] = fy * rho / l2; J[5] = -fy * y * z * u;
+    return;
+  }
+  if (model == ORC_CAM_EQUIDISTANT) { orc_jacobian(muc, fx, fy, J); return; }
+  double t[7];
+  orc_radial_terms(model, x, y, z, t);
+  double g = t[0], h = t[1], k = t[2];
+  J[0] = fx * (g + x * x * h); J[1] = fx * x * y * h; J[2] = fx * x * k;
+  J[3] = fy * x * y * h; J[4] = fy * (g + y * y * h); J[5] = fy * y * k;
+}
+
+/* dJ/dx_c, dJ/dy_c, dJ/dz_c for any model; the equidistant one in the paper's S1..S8 form
+ * (orc_jacobian_grad), the other radial models from the terms of orc_radial_terms, the
+ * panorama entry by entry. */
+void orc_cam_jacobian_grad(int model, const double *muc, double fx, double fy, double *dJx,
+                           double *dJy, double *dJz) {
+  double x = muc[0], y = muc[1], z = muc[2];
+  if (model == ORC_CAM_EQUIDISTANT) { orc_jacobian_grad(muc, fx, fy, dJx, dJy, dJz); return; }
+  if (model == ORC_CAM_EQUIRECT) {
+    double r2 = x * x + z * z, r4 = r2 * r2, rho = sqrt(r2), l2 = r2 + y * y;
+    double u = 1.0 / (rho * l2), wq = 1.0 / r2 + 2.0 / l2;  /* du/dx = -x u wq, du/dz = -z u wq, du/dy = -2 y u / l2 */
+    /* row 0: fx z / rho^2, 0, -fx x / rho^2 */
+    dJx[0] = fx * (-2.0 * x * z / r4); dJy[0] = 0.0; dJz[0] = fx * (x * x - z * z) / r4;
+    dJx[1] = 0.0; dJy[1] = 0.0; dJz[1] = 0.0;
+    dJx[2] = fx * (x * x - z * z) / r4; dJy[2] = 0.0; dJz[2] = fx * 2.0 * x * z / r4;
+    /* row 1: -fy x y u, fy rho / l2, -fy y z u */
+    dJx[3] = fy * (-y * u + x * x * y * u * wq);
+    dJy[3] = fy * (-x * u + 2.0 * x * y * y * u / l2);
+    dJz[3] = fy * (x * y * z * u * wq);
+    dJx[4] = fy * x * (u - 2.0 * rho / (l2 * l2));
+    dJy[4] = fy * (-2.0 * y * rho / (l2 * l2));
+    dJz[4] = fy * z * (u - 2.0 * rho / (l2 * l2));
+    dJx[5] = fy * (x * y * z * u * wq);
+    dJy[5] = fy * (-z * u + 2.0 * y * y * z * u / l2);
+    dJz[5] = fy * (-y * u + y * z * z * u * wq);
+    return;
+  }
+  double t[7];
+  orc_radial_terms(model, x, y, z, t);
+  double h = t[1], k = t[2], hl = t[3], hz = t[4], kl = t[5], kz = t[6];
+  /* J00 = fx (g + x^2 h), J01 = fx x y h, J02 = fx x k; row 1 by x <-> y, fx -> fy */
+  dJx[0] = fx * x * (3.0 * h + x * x * hl); dJy[0] = fx * y * (h + x * x * hl); dJz[0] = fx * (k + x * x * hz);
+  dJx[1] = fx * y * (h + x * x * hl); dJy[1] = fx * x * (h + y * y * hl); dJz[1] = fx * x * y * hz;
+  dJx[2] = fx * (k + x * x * kl); dJy[2] = fx * x * y * kl; dJz[2] = fx * x * kz;
+  dJx[3] = fy * y * (h + x * x * hl); dJy[3] = fy * x * (h + y * y * hl); dJz[3] = fy * x * y * hz;
+  dJx[4] = fy * x * (h + y * y * hl); dJy[4] = fy * y * (3.0 * h + y * y * hl); dJz[4] = fy * (k + y * y * hz);
+  dJx[5] = fy * x * y * kl; dJy[5] = fy * (k + y * y * kl); dJz[5] = fy * y * kz;
+}
+
+/* Visibility angle test of a model: radial models bound theta, the panorama its latitude. */
+static int orc_cam_in_field(int model, const double *muc, double *angle) {
+  double x = muc[0], y = muc[1], z = muc[2];
+  if (model == ORC_CAM_EQUIRECT) {
+    double lat = atan2(fabs(y), sqrt(x * x + z * z));
+    *angle = lat;
+    return lat < ORC_LAT_MAX;
+  }
+  double th = atan2(sqrt(x * x + y * y), z);
+  *angle = th;
+  return th < (model == ORC_CAM_ORTHOGRAPHIC ? ORC_THETA_MAX_ORTHO : ORC_THETA_MAX);
 }
 
 /* ---------------------------------------------------------------------------------------- */
@@ -259,7 +422,7 @@ void orc_project(int64_t n, const double *means, const double *scales, const dou
                  double *out) {
   const double *W = cam, *b = cam + 9;
   double fx = cam[12], fy = cam[13], cx = cam[14], cy = cam[15];
-  int width = (int)cam[16], height = (int)cam[17];
+  int width = (int)cam[16], height = (int)cam[17], model = (int)cam[18];
   int tiles_x = (width + ORC_TILE - 1) / ORC_TILE, tiles_y = (height + ORC_TILE - 1) / ORC_TILE;
   int nsh = (degree + 1) * (degree + 1);
   double cc[3];
@@ -274,15 +437,16 @@ void orc_project(int64_t n, const double *means, const double *scales, const dou
     for (int r = 0; r < 3; ++r) muc[r] = W[3 * r] * mu[0] + W[3 * r + 1] * mu[1] + W[3 * r + 2] * mu[2] + b[r];
     for (int r = 0; r < 3; ++r) o[F_MUC + r] = muc[r];
     double dist = sqrt(muc[0] * muc[0] + muc[1] * muc[1] + muc[2] * muc[2]);
-    double theta = atan2(sqrt(muc[0] * muc[0] + muc[1] * muc[1]), muc[2]);
-    o[F_THETA] = theta;
+    double angle;
+    int in_field = orc_cam_in_field(model, muc, &angle);
+    o[F_THETA] = angle;
     o[F_DEP] = dist;
     o[F_OPA] = opac[i];
-    if (!(dist > ORC_NEAR) || !(theta < ORC_THETA_MAX) || !(opac[i] >= ORC_ALPHA_MIN)) continue;
+    if (!(dist > ORC_NEAR) || !in_field || !(opac[i] >= ORC_ALPHA_MIN)) continue;
 
-    orc_project_point(muc, fx, fy, cx, cy, o + F_XY);
+    orc_cam_project(model, muc, fx, fy, cx, cy, o + F_XY);
     double J[6];
-    orc_jacobian(muc, fx, fy, J);
+    orc_cam_jacobian(model, muc, fx, fy, J);
     memcpy(o + F_J, J, sizeof J);
 
     /* Sigma = R S S^T R^T */
@@ -541,6 +705,7 @@ void orc_backward(int64_t n, const double *G, const double *means, const double 
   /* 2) per Gaussian, through the preprocess */
   const double *W = cam;
   double fx = cam[12], fy = cam[13];
+  int model = (int)cam[18];
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     const double *o = G + i * ORC_NF;
@@ -608,7 +773,7 @@ void orc_backward(int64_t n, const double *G, const double *means, const double 
 
     /* J -> mu_c through dJ/d{x,y,z}; mu_p -> mu_c through J^T (Sec. 4.2 and 4.3) */
     double dJx[6], dJy[6], dJz[6], dmuc[3] = {0, 0, 0};
-    orc_jacobian_grad(o + F_MUC, fx, fy, dJx, dJy, dJz);
+    orc_cam_jacobian_grad(model, o + F_MUC, fx, fy, dJx, dJy, dJz);
     for (int e = 0; e < 6; ++e) {
       dmuc[0] += GJ[e] * dJx[e];
       dmuc[1] += GJ[e] * dJy[e];

@@ -73,27 +73,54 @@ def random_rotation(rng):
     return q
 
 
-def fisheye_camera(width, height, fov_deg, rotation=None, centre=(0.0, 0.0, 0.0)):
-    """Equidistant fisheye with horizontal field of view fov_deg: f = width / fov (rad),
-    principal point at the image centre. rotation = world -> camera (identity if None);
-    the camera sits at `centre` in world space, so b = -W centre."""
+# camera models (the C ABI's fgs_camera.model)
+CAM_EQUIDISTANT, CAM_EQUISOLID, CAM_STEREOGRAPHIC, CAM_ORTHOGRAPHIC, CAM_EQUIRECT = range(5)
+RADIAL_R = {CAM_EQUIDISTANT: lambda t: t,
+            CAM_EQUISOLID: lambda t: 2.0 * math.sin(0.5 * t),
+            CAM_STEREOGRAPHIC: lambda t: 2.0 * math.tan(0.5 * t),
+            CAM_ORTHOGRAPHIC: lambda t: math.sin(t)}
+
+
+def _pose(rotation, centre):
     W = np.eye(3) if rotation is None else np.asarray(rotation, np.float64)
     W32 = W.astype(np.float32)
     c = np.asarray(centre, np.float64)
     b = (-(W32.astype(np.float64) @ c)).astype(np.float32)
-    f = float(np.float32(width / math.radians(fov_deg)))
+    return W32, b
+
+
+def fisheye_camera(width, height, fov_deg, rotation=None, centre=(0.0, 0.0, 0.0),
+                   model=CAM_EQUIDISTANT):
+    """Radial fisheye (r_d = f r(theta)) with horizontal field of view fov_deg: the image's
+    half width is f r(fov / 2), so f = (width / 2) / r(fov / 2) (= width / fov in radians for
+    the equidistant model); principal point at the image centre. rotation = world -> camera
+    (identity if None); the camera sits at `centre` in world space, so b = -W centre."""
+    W32, b = _pose(rotation, centre)
+    f = float(np.float32(0.5 * width / RADIAL_R[model](0.5 * math.radians(fov_deg))))
     return dict(W=W32, b=b, fx=f, fy=f, cx=float(width) / 2.0, cy=float(height) / 2.0,
-                width=int(width), height=int(height))
+                width=int(width), height=int(height), model=int(model))
 
 
-def pose_camera(width, height, fov_deg, seed, centre_box=None):
+def panorama_camera(width, height, rotation=None, centre=(0.0, 0.0, 0.0)):
+    """Equirectangular panorama: x_p = w (lon + pi) / 2 pi, y_p = h (lat + pi/2) / pi, i.e.
+    fx = w / 2 pi, cx = w / 2, fy = h / pi, cy = h / 2."""
+    W32, b = _pose(rotation, centre)
+    return dict(W=W32, b=b, fx=float(np.float32(width / (2 * math.pi))),
+                fy=float(np.float32(height / math.pi)), cx=float(width) / 2.0,
+                cy=float(height) / 2.0, width=int(width), height=int(height),
+                model=CAM_EQUIRECT)
+
+
+def pose_camera(width, height, fov_deg, seed, centre_box=None, model=CAM_EQUIDISTANT):
     """Random pose: Haar rotation; centre at the origin, or uniform in centre_box (half
-    extents)."""
+    extents). model = CAM_EQUIRECT gives a panorama (fov_deg unused)."""
     rng = np.random.default_rng(seed)
     R = random_rotation(rng)
     centre = (0.0, 0.0, 0.0) if centre_box is None else rng.uniform(-np.asarray(centre_box),
                                                                     np.asarray(centre_box))
-    return fisheye_camera(width, height, fov_deg, R, centre)
+    if model == CAM_EQUIRECT:
+        return panorama_camera(width, height, R, centre)
+    return fisheye_camera(width, height, fov_deg, R, centre, model)
 
 
 def upstream_grad(n_views_pixels_shape, std, seed):

@@ -1,8 +1,11 @@
 """An independent float64 PyTorch brute-force renderer for tiny scenes, used to pin the C
 oracle (forward and gradients). It shares nothing with the oracle but the conventions:
 
-  * J_phi is not written out: it is torch.autograd's Jacobian of the equidistant projection
-    phi (Sec. 3.2), taken with create_graph=True so the backward also differentiates J;
+  * J_phi is not written out: it is torch.autograd's Jacobian of the projection phi, taken
+    with create_graph=True so the backward also differentiates J. phi is the equidistant
+    model of Sec. 3.2 or, by the camera's `model`, r_d = f r(theta) with r = 2 sin(theta/2),
+    2 tan(theta/2) or sin(theta), or the panorama's longitude / latitude map (Sec. 6), each
+    written from its definition;
   * R comes from rotating the basis vectors by the quaternion (Hamilton product q v q*);
   * the real spherical harmonics come from the associated-Legendre three-term recursion and
     cos / sin of the azimuth;
@@ -89,17 +92,30 @@ def render_and_grad(scene, cam, dLdC=None, bg=(0.0, 0.0, 0.0), grad=True):
     w, h = int(cam["width"]), int(cam["height"])
     centre = -(W.T @ b)
 
+    model = int(cam.get("model", 0))
+    radial = {0: lambda t: t, 1: lambda t: 2 * torch.sin(t / 2), 2: lambda t: 2 * torch.tan(t / 2),
+              3: torch.sin}
+
     def phi(p):
+        if model == 4:
+            return torch.stack([cx + fx * torch.atan2(p[0], p[2]),
+                                cy + fy * torch.atan2(p[1], torch.sqrt(p[0] ** 2 + p[2] ** 2))])
         lz = torch.sqrt(p[0] ** 2 + p[1] ** 2)
         th = torch.atan2(lz, p[2])
-        return torch.stack([cx + fx * th * p[0] / lz, cy + fy * th * p[1] / lz])
+        r = radial[model](th)
+        return torch.stack([cx + fx * r * p[0] / lz, cy + fy * r * p[1] / lz])
+
+    def in_field(p):
+        if model == 4:
+            return float(torch.atan2(p[1].abs(), torch.sqrt(p[0] ** 2 + p[2] ** 2))) < math.pi / 2 - 0.05
+        theta = float(torch.atan2(torch.linalg.norm(p[:2]), p[2]))
+        return theta < (math.pi / 2 - 0.05 if model == 3 else math.pi - 0.05)
 
     gs = []
     for i in range(means.shape[0]):
         muc = W @ means[i] + b
         dist = torch.linalg.norm(muc)
-        theta = torch.atan2(torch.linalg.norm(muc[:2]), muc[2])
-        if not (float(dist) > 0.2 and float(theta) < math.pi - 0.05 and float(opac[i]) >= 1 / 255):
+        if not (float(dist) > 0.2 and in_field(muc) and float(opac[i]) >= 1 / 255):
             continue
         xy = phi(muc)
         J = torch.autograd.functional.jacobian(phi, muc, create_graph=True)
