@@ -49,17 +49,36 @@ typedef enum {
 #define FGS_TILE 16        /* tiles are 16 x 16 pixels (Sec. 3.1 "Rendering") */
 #define FGS_MAX_VIEWS 128  /* views per call */
 
-/* An equidistant fisheye camera (Sec. 3.1 "Transformation", Sec. 3.2):
+/* Camera models. The method is the equidistant fisheye (Sec. 3.2, r_d = f theta). Sec. 3.2
+ * names the other radial fisheye models, r_d = f r(theta) with r = 2 sin(theta/2)
+ * (equisolid), 2 tan(theta/2) (stereographic), sin(theta) (orthographic), and Sec. 6
+ * ("Extension to Other Camera Models") gives the equirectangular panorama:
+ *   x_p = cx + fx atan2(x_c, z_c), y_p = cy + fy atan2(y_c, sqrt(x_c^2 + z_c^2)),
+ * which with fx = w / 2 pi, cx = w / 2, fy = h / pi, cy = h / 2 is the paper's pair. */
+typedef enum {
+  FGS_CAM_EQUIDISTANT = 0,
+  FGS_CAM_EQUISOLID = 1,
+  FGS_CAM_STEREOGRAPHIC = 2,
+  FGS_CAM_ORTHOGRAPHIC = 3,
+  FGS_CAM_EQUIRECTANGULAR = 4
+} fgs_camera_model;
+
+/* A camera (Sec. 3.1 "Transformation", Sec. 3.2):
  *   mu_c = W mu + b (W row-major, world -> camera; camera x right, y down, z forward),
- *   theta = atan2(|(x_c, y_c)|, z_c), x_p = cx + fx theta x_c / l_z, y_p = cy + fy theta y_c / l_z.
+ *   radial models: theta = atan2(|(x_c, y_c)|, z_c), x_p = cx + fx r(theta) x_c / l_z,
+ *   y_p = cy + fy r(theta) y_c / l_z (r(theta) = theta for the equidistant model);
+ *   panorama: as above. Field of view: theta < pi - 0.05 (orthographic: pi/2 - 0.05), or
+ *   |latitude| < pi/2 - 0.05 for the panorama, which does not wrap at longitude +-pi.
  * Pixel (i, j) is sampled at (i + 0.5, j + 0.5).
  * A view holds at most 2^20 tiles and at most 65535 tile columns and rows (the record's tile
- * rect is 16-bit); a call with a larger view returns FGS_ERR_INVALID_ARG. */
+ * rect is 16-bit); a call with a larger view, or a model outside fgs_camera_model, returns
+ * FGS_ERR_INVALID_ARG. */
 typedef struct {
   float W[9];
   float b[3];
   float fx, fy, cx, cy;
   int32_t width, height;
+  int32_t model; /* fgs_camera_model */
 } fgs_camera;
 
 /* The Gaussian set (Sec. 3.1 "Definition"): device pointers, FP32, contiguous.

@@ -41,10 +41,12 @@ bool build_views(const fgs_camera *cams, int n_views, Views *vs) {
     const fgs_camera &c = cams[k];
     if (c.width <= 0 || c.height <= 0) return false;
     if (!(isfinite(c.fx) && isfinite(c.fy) && isfinite(c.cx) && isfinite(c.cy))) return false;
+    if (c.model < FGS_CAM_EQUIDISTANT || c.model > FGS_CAM_EQUIRECTANGULAR) return false;
     View &V = vs->v[k];
     memcpy(V.W, c.W, sizeof V.W);
     memcpy(V.b, c.b, sizeof V.b);
     V.fx = c.fx; V.fy = c.fy; V.cx = c.cx; V.cy = c.cy;
+    V.model = c.model;
     for (int i = 0; i < 3; ++i)
       V.cam_pos[i] = -(c.W[i] * c.b[0] + c.W[3 + i] * c.b[1] + c.W[6 + i] * c.b[2]);
     V.width = c.width;

@@ -43,6 +43,7 @@ struct View {
   float fx, fy, cx, cy;
   float cam_pos[3];  // camera centre -W^T b
   int32_t width, height, tiles_x, tiles_y;
+  int32_t model;     // fgs_camera_model
   int64_t tile_offset, pixel_offset;
 };
 
@@ -282,6 +283,146 @@ __device__ __forceinline__ FishG fisheye_g(float x, float y, float z) {
     r.huu = NEED_HUU ? -(2.f * z / (l2 * l2) + 3.f * r.h) / u2 : 0.f;
   }
   return r;
+}
+
+// ------------------------------------------------------------------------------------------
+// Every camera model: field of view, projection of the mean, Jacobian J (2x3) and, for the
+// backward, dL/dmu_c from dL/dJ.
+//
+// Radial models (x_p = cx + fx g x, y_p = cy + fy g y, g = r(theta) / l_z a function G(l, z) of
+// l = |mu_c| and z) share one Jacobian,
+//   J = [[fx (g + x^2 h), fx x y h, fx x k], [fy x y h, fy (g + y^2 h), fy y k]],
+// h = G_l / l, k = G_z + z h (so dg/dx = x h, dg/dz = k). The backward also needs
+// h_l, k_l = (1/l) d/dl at fixed z (dh/dx = x h_l, dk/dx = x k_l) and h_z, k_z = d/dz at fixed
+// x, y. Equidistant: g, h, h_l from fisheye_g, k = -1/l2, h_z = k_l = 2/l2^2, k_z = 2 z/l2^2.
+// The others from closed forms of G (cos theta = z / l):
+//   equisolid      G = sqrt(2 / (l (l + z)))
+//   stereographic  G = 2 / (l + z)
+//   orthographic   G = 1 / l
+constexpr float COS_THETA_MAX = -0.99875026039f;       // cos(pi - 0.05)
+constexpr float COS_THETA_MAX_ORTHO = 0.04997916927f;  // cos(pi/2 - 0.05)
+constexpr float SIN_LAT_MAX = 0.99875026039f;          // sin(pi/2 - 0.05)
+
+struct RadTerms {
+  float g, h, k, hl, hz, kl, kz;
+};
+
+template <bool BWD>
+__device__ __forceinline__ RadTerms radial_terms(int model, float x, float y, float z, float l2) {
+  RadTerms t;
+  const float il2 = 1.f / l2;
+  if (model == FGS_CAM_EQUIDISTANT) {
+    const FishG fg = fisheye_g<BWD>(x, y, z);
+    t.g = fg.g;
+    t.h = fg.h;
+    t.k = -il2;
+    t.hl = fg.huu;
+    t.hz = 2.f * il2 * il2;
+    t.kl = t.hz;
+    t.kz = z * t.hz;
+    return t;
+  }
+  const float l = sqrtf(l2), il = 1.f / l;
+  // l + z, without the cancellation of z ~ -l behind the camera: (x^2 + y^2) / (l - z) there
+  const float lpz = z >= 0.f ? l + z : (x * x + y * y) / (l - z);
+  float G0, G1, G2, G3, G4, G5;  // G, G_l, G_z, G_ll, G_lz, G_zz
+  if (model == FGS_CAM_EQUISOLID) {
+    const float P = l * lpz, Pl = l + lpz, Pz = l;
+    const float Pm12 = rsqrtf(P), Pm32 = Pm12 / P, Pm52 = Pm32 / P;
+    const float r2 = 1.41421356237f;
+    G0 = r2 * Pm12;
+    G1 = -0.5f * r2 * Pm32 * Pl;
+    G2 = -0.5f * r2 * Pm32 * Pz;
+    G3 = 0.75f * r2 * Pm52 * Pl * Pl - r2 * Pm32;
+    G4 = 0.75f * r2 * Pm52 * Pl * Pz - 0.5f * r2 * Pm32;
+    G5 = 0.75f * r2 * Pm52 * Pz * Pz;
+  } else if (model == FGS_CAM_STEREOGRAPHIC) {
+    const float iS = 1.f / lpz;
+    G0 = 2.f * iS;
+    G1 = G2 = -2.f * iS * iS;
+    G3 = G4 = G5 = 4.f * iS * iS * iS;
+  } else {  // orthographic
+    G0 = il;
+    G1 = -il * il;
+    G2 = 0.f;
+    G3 = 2.f * il * il * il;
+    G4 = G5 = 0.f;
+  }
+  t.g = G0;
+  t.h = G1 * il;
+  t.k = fmaf(z, t.h, G2);
+  if (BWD) {
+    const float Hl = (G3 - G1 * il) * il, Hz = G4 * il;
+    const float Kl = fmaf(z, Hl, G4), Kz = G5 + t.h + z * Hz;
+    t.hl = Hl * il;
+    t.hz = fmaf(z, t.hl, Hz);
+    t.kl = Kl * il;
+    t.kz = fmaf(z, t.kl, Kz);
+  } else {
+    t.hl = t.hz = t.kl = t.kz = 0.f;
+  }
+  return t;
+}
+
+// Inside the model's field of view (the angle tests of the readings, written without atan2
+// for the closed-form models: theta < theta_max <=> z > l cos(theta_max), and for the panorama
+// |latitude| < pi/2 - 0.05 <=> |y| < l sin(pi/2 - 0.05)).
+__device__ __forceinline__ bool in_field(int model, float x, float y, float z, float dist) {
+  if (model == FGS_CAM_EQUIRECTANGULAR) return fabsf(y) < SIN_LAT_MAX * dist;
+  if (model == FGS_CAM_EQUIDISTANT) return atan2f(sqrtf(x * x + y * y), z) < THETA_MAX;
+  if (model == FGS_CAM_ORTHOGRAPHIC) return z > COS_THETA_MAX_ORTHO * dist;
+  return z > COS_THETA_MAX * dist;
+}
+
+// Projection of the mean and J (row-major 2x3) of view V at mu_c.
+__device__ __forceinline__ void project_mean(const View &V, float x, float y, float z, float l2,
+                                             float &px, float &py, float (&J)[6]) {
+  if (V.model == FGS_CAM_EQUIRECTANGULAR) {
+    // Sec. 6: x_p = cx + fx atan2(x, z), y_p = cy + fy atan2(y, rho), rho = sqrt(x^2 + z^2)
+    const float r2 = x * x + z * z, rho = sqrtf(r2), ir2 = 1.f / r2, u = 1.f / (rho * l2);
+    px = fmaf(V.fx, atan2f(x, z), V.cx);
+    py = fmaf(V.fy, atan2f(y, rho), V.cy);
+    J[0] = V.fx * z * ir2; J[1] = 0.f; J[2] = -V.fx * x * ir2;
+    J[3] = -V.fy * x * y * u; J[4] = V.fy * rho / l2; J[5] = -V.fy * y * z * u;
+    return;
+  }
+  const RadTerms t = radial_terms<false>(V.model, x, y, z, l2);
+  px = fmaf(V.fx * t.g, x, V.cx);
+  py = fmaf(V.fy * t.g, y, V.cy);
+  J[0] = V.fx * fmaf(x * x, t.h, t.g); J[1] = V.fx * x * y * t.h; J[2] = V.fx * x * t.k;
+  J[3] = V.fy * x * y * t.h; J[4] = V.fy * fmaf(y * y, t.h, t.g); J[5] = V.fy * y * t.k;
+}
+
+// dL/dmu_c through J (Sec. 4.3 for the equidistant model), from dL/dJ (row-major 2x3).
+// Radial models: with A..F the f-scaled dL/dJ entries, the J-dependent part of L is
+//   (A + E) g + Q h + P k,  Q = A x^2 + (B + D) x y + E y^2,  P = C x + F y.
+__device__ __forceinline__ void jacobian_backward(const View &V, float x, float y, float z,
+                                                  float l2, const float (&GJ)[6],
+                                                  float &d0, float &d1, float &d2) {
+  const float A = V.fx * GJ[0], B = V.fx * GJ[1], Cc = V.fx * GJ[2];
+  const float Dd = V.fy * GJ[3], E = V.fy * GJ[4], F = V.fy * GJ[5];
+  if (V.model == FGS_CAM_EQUIRECTANGULAR) {
+    // J = [[fx z/rho^2, 0, -fx x/rho^2], [-fy x y u, fy rho/l2, -fy y z u]], u = 1/(rho l2):
+    // du/dx = -x u w, du/dz = -z u w (w = 1/rho^2 + 2/l2), du/dy = -2 y u / l2
+    const float r2 = x * x + z * z, rho = sqrtf(r2), ir2 = 1.f / r2, ir4 = ir2 * ir2;
+    const float u = 1.f / (rho * l2), il2 = 1.f / l2, w = ir2 + 2.f * il2;
+    const float q = u - 2.f * rho * il2 * il2;
+    d0 = A * (-2.f * x * z * ir4) + Cc * (x * x - z * z) * ir4 + Dd * y * u * (x * x * w - 1.f) +
+         E * x * q + F * x * y * z * u * w;
+    d1 = Dd * x * u * (2.f * y * y * il2 - 1.f) - E * 2.f * y * rho * il2 * il2 +
+         F * z * u * (2.f * y * y * il2 - 1.f);
+    d2 = A * (x * x - z * z) * ir4 + Cc * 2.f * x * z * ir4 + Dd * x * y * z * u * w + E * z * q +
+         F * y * u * (z * z * w - 1.f);
+    return;
+  }
+  (void)B;
+  const RadTerms t = radial_terms<true>(V.model, x, y, z, l2);
+  const float AE = A + E, BD = B + Dd;
+  const float Q = A * x * x + BD * x * y + E * y * y;
+  const float P = Cc * x + F * y;
+  d0 = AE * x * t.h + (2.f * A * x + BD * y) * t.h + Q * t.hl * x + Cc * t.k + P * x * t.kl;
+  d1 = AE * y * t.h + (BD * x + 2.f * E * y) * t.h + Q * t.hl * y + F * t.k + P * y * t.kl;
+  d2 = AE * t.k + Q * t.hz + P * t.kz;
 }
 
 // ------------------------------------------------------------------------------------------

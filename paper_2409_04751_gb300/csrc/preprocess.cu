@@ -85,17 +85,14 @@ __global__ void __launch_bounds__(256)
     const float z = fmaf(V.W[6], mx, fmaf(V.W[7], my, fmaf(V.W[8], mz, V.b[2])));
     const float l2 = x * x + y * y + z * z;
     const float dist = sqrtf(l2);
-    const FishG fg = fisheye_g<false>(x, y, z);
-    if (!(op_ok && dist > NEAR_DIST && fg.theta < THETA_MAX)) {
+    if (!(op_ok && dist > NEAR_DIST && in_field(V.model, x, y, z, dist))) {
       tt[r] = 0u;
       continue;
     }
-    // mean (Sec. 3.2) and Jacobian (Sec. 4.2)
-    const float px = fmaf(V.fx * fg.g, x, V.cx);
-    const float py = fmaf(V.fy * fg.g, y, V.cy);
-    const float il2 = 1.f / l2;
-    const float J00 = V.fx * fmaf(x * x, fg.h, fg.g), J01 = V.fx * x * y * fg.h, J02 = -V.fx * x * il2;
-    const float J10 = V.fy * x * y * fg.h, J11 = V.fy * fmaf(y * y, fg.h, fg.g), J12 = -V.fy * y * il2;
+    // mean (Sec. 3.2; other models Sec. 3.2 / Sec. 6) and Jacobian (Sec. 4.2)
+    float px, py, J[6];
+    project_mean(V, x, y, z, l2, px, py, J);
+    const float J00 = J[0], J01 = J[1], J02 = J[2], J10 = J[3], J11 = J[4], J12 = J[5];
     // T = J W
     float T0[3], T1[3];
 #pragma unroll
@@ -213,10 +210,11 @@ __global__ void __launch_bounds__(128)
     const float y = fmaf(V.W[3], mx, fmaf(V.W[4], my, fmaf(V.W[5], mz, V.b[1])));
     const float z = fmaf(V.W[6], mx, fmaf(V.W[7], my, fmaf(V.W[8], mz, V.b[2])));
     const float l2 = x * x + y * y + z * z;
-    const float il2 = 1.f / l2;
-    const FishG fg = fisheye_g<true>(x, y, z);
-    const float J00 = V.fx * fmaf(x * x, fg.h, fg.g), J01 = V.fx * x * y * fg.h, J02 = -V.fx * x * il2;
-    const float J10 = V.fy * x * y * fg.h, J11 = V.fy * fmaf(y * y, fg.h, fg.g), J12 = -V.fy * y * il2;
+    float pxm, pym, J[6];
+    project_mean(V, x, y, z, l2, pxm, pym, J);
+    (void)pxm;
+    (void)pym;
+    const float J00 = J[0], J01 = J[1], J02 = J[2], J10 = J[3], J11 = J[4], J12 = J[5];
     float T0[3], T1[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -260,18 +258,10 @@ __global__ void __launch_bounds__(128)
       GJ0[k] = GT0[0] * V.W[3 * k] + GT0[1] * V.W[3 * k + 1] + GT0[2] * V.W[3 * k + 2];
       GJ1[k] = GT1[0] * V.W[3 * k] + GT1[1] * V.W[3 * k + 1] + GT1[2] * V.W[3 * k + 2];
     }
-    // J -> mu_c (Sec. 4.3): with A..F the f-scaled dL/dJ entries,
-    //   L_J = (A + E) g + Q h - P / l2,  Q = A x^2 + (B + D) x y + E y^2,  P = C x + F y,
-    // dg/dx = x h, dg/dy = y h, dg/dz = -1/l2, dh/dx = x huu, dh/dy = y huu, dh/dz = 2/l2^2.
-    const float A = V.fx * GJ0[0], B = V.fx * GJ0[1], Cc = V.fx * GJ0[2];
-    const float Dd = V.fy * GJ1[0], E = V.fy * GJ1[1], F = V.fy * GJ1[2];
-    const float AE = A + E, BD = B + Dd;
-    const float Q = A * x * x + BD * x * y + E * y * y;
-    const float P = Cc * x + F * y;
-    const float il22 = il2 * il2;
-    float dmc0 = AE * x * fg.h + (2.f * A * x + BD * y) * fg.h + Q * fg.huu * x - Cc * il2 + 2.f * P * x * il22;
-    float dmc1 = AE * y * fg.h + (BD * x + 2.f * E * y) * fg.h + Q * fg.huu * y - F * il2 + 2.f * P * y * il22;
-    float dmc2 = -AE * il2 + 2.f * Q * il22 + 2.f * P * z * il22;
+    // J -> mu_c (Sec. 4.3 for the equidistant model; the other models alike)
+    const float GJ[6] = {GJ0[0], GJ0[1], GJ0[2], GJ1[0], GJ1[1], GJ1[2]};
+    float dmc0, dmc1, dmc2;
+    jacobian_backward(V, x, y, z, l2, GJ, dmc0, dmc1, dmc2);
     // mu_p -> mu_c (Sec. 4.2): J^T dL/dmu_p
     dmc0 += J00 * g0.x + J10 * g0.y;
     dmc1 += J01 * g0.x + J11 * g0.y;

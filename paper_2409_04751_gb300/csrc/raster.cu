@@ -145,7 +145,6 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
     const TileInfo ti = tile_info(vs, t, ranges);
     const View &V = vs.v[ti.v];
     const int px = ti.tx * TILE + lx;
-    const float fpx = (float)px + 0.5f;
     // tile centre (between pixel centres 7 and 8) and this pixel's offset from it
     const float tile_cx = (float)(ti.tx * TILE) + 0.5f * TILE, tile_cy = (float)(ti.ty * TILE) + 0.5f * TILE;
     const float fu = (float)lx - 7.5f, fv = (float)ly0 - 7.5f;

@@ -21,6 +21,12 @@ FGS_ERR_INVALID_ARG = 1
 FGS_ERR_CAPACITY = 2
 FGS_ERR_TIMEOUT = 3
 FGS_ERR_CUDA = 4
+# camera models (fgs_camera_model)
+FGS_CAM_EQUIDISTANT = 0
+FGS_CAM_EQUISOLID = 1
+FGS_CAM_STEREOGRAPHIC = 2
+FGS_CAM_ORTHOGRAPHIC = 3
+FGS_CAM_EQUIRECTANGULAR = 4
 
 EXPORTS = ["fgs_workspace_size", "fgs_total_tiles", "fgs_total_pixels", "fgs_preprocess",
            "fgs_bin_sort", "fgs_rasterize", "fgs_backward", "fgs_backward_raster",
@@ -32,7 +38,7 @@ EXPORTS = ["fgs_workspace_size", "fgs_total_tiles", "fgs_total_pixels", "fgs_pre
 class FgsCamera(ctypes.Structure):
     _fields_ = [("W", ctypes.c_float * 9), ("b", ctypes.c_float * 3), ("fx", ctypes.c_float),
                 ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
-                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("model", ctypes.c_int32)]
 
 
 class FgsGaussians(ctypes.Structure):
@@ -116,7 +122,8 @@ def _stream(stream):
 
 
 def cameras(cams):
-    """ctypes array of FgsCamera from camera dicts (W, b, fx, fy, cx, cy, width, height)."""
+    """ctypes array of FgsCamera from camera dicts (W, b, fx, fy, cx, cy, width, height and
+    optionally model, default FGS_CAM_EQUIDISTANT)."""
     arr = (FgsCamera * len(cams))()
     for k, c in enumerate(cams):
         W = [float(v) for v in torch.as_tensor(c["W"]).reshape(9).tolist()]
@@ -126,6 +133,7 @@ def cameras(cams):
         arr[k].fx, arr[k].fy = float(c["fx"]), float(c["fy"])
         arr[k].cx, arr[k].cy = float(c["cx"]), float(c["cy"])
         arr[k].width, arr[k].height = int(c["width"]), int(c["height"])
+        arr[k].model = int(c.get("model", FGS_CAM_EQUIDISTANT))
     return arr
 
 

@@ -62,6 +62,15 @@ def test_invalid_arguments_rejected_before_launch(lib):
     bad = _cam(0, 10)
     assert lib.fgs_workspace_size(10, bad, 1, 10, ctypes.byref(out)) == INV
     assert fgs.fgs_total_tiles(bad) == -1
+    # camera model outside fgs_camera_model; every listed model accepted
+    for m in (-1, fgs.FGS_CAM_EQUIRECTANGULAR + 1):
+        bad = _cam()
+        bad[0].model = m
+        assert lib.fgs_workspace_size(10, bad, 1, 10, ctypes.byref(out)) == INV
+    for m in range(fgs.FGS_CAM_EQUIRECTANGULAR + 1):
+        ok = _cam()
+        ok[0].model = m
+        assert lib.fgs_workspace_size(10, ok, 1, 10, ctypes.byref(out)) == fgs.FGS_OK
     # preprocess: null Gaussians, bad degree, null pointers, misaligned records
     g = fgs.FgsGaussians(16, 16, 16, 16, 16, 10, 4)
     assert lib.fgs_preprocess(ctypes.byref(g), cams, 1, 256, 256, None) == INV
