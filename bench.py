@@ -418,6 +418,9 @@ def run_gpu(args):
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
         serving = run_serving(args, dev)
+    models = None
+    if rank == 0 and world == 1 and not args.no_models:
+        models = run_models(args, dev)
 
     # preprocess; scan, count, tile scan, scatter, two segment-sort classes; raster fwd; raster
     # bwd; preprocess bwd
@@ -439,6 +442,7 @@ def run_gpu(args):
         cpu_baseline=cpu,
         batched=batched,
         serving=serving,
+        camera_models=models,
         e2e=dict(value=world * args.steps / e2e_s, unit="views/s", h2d_bytes_per_step=h2d,
                  d2h_bytes_per_step=d2h),
         gpu_launches=launches_per_step * args.steps,
@@ -534,6 +538,52 @@ def run_batched_compare(args, dev):
                 "stage over all views; plain = one call sequence per view")
 
 
+def run_models(args, dev):
+    """fwd+bwd of the 500k-Gaussian scene through every camera model: the radial fisheye
+    models at 1752x1168 (180 deg; orthographic 170 deg, its field ends at 85 deg) and the
+    equirectangular panorama at 2048x1024, same random pose. Returns a dict for the JSON line."""
+    import torch
+    from paper_2409_04751_gb300 import fgs, scenes
+    from paper_2409_04751_gb300.renderer import FisheyeRenderer, scene_to_device
+
+    scene, _ = scenes.config1()
+    gs = scene_to_device(scene, dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    names = {fgs.FGS_CAM_EQUIDISTANT: "equidistant", fgs.FGS_CAM_EQUISOLID: "equisolid",
+             fgs.FGS_CAM_STEREOGRAPHIC: "stereographic", fgs.FGS_CAM_ORTHOGRAPHIC: "orthographic",
+             fgs.FGS_CAM_EQUIRECTANGULAR: "equirectangular"}
+    out = {}
+    for m, name in names.items():
+        if m == fgs.FGS_CAM_EQUIRECTANGULAR:
+            cam = scenes.pose_camera(2048, 1024, 0.0, 1 * 1000 + 1, model=m)
+        else:
+            cam = scenes.pose_camera(1752, 1168, 170.0 if m == fgs.FGS_CAM_ORTHOGRAPHIC else 180.0,
+                                     1 * 1000 + 1, model=m)
+        r = FisheyeRenderer(dev, capacity=1 << 23)
+        fr = r.forward(gs, [cam], check=True)
+        P = cam["width"] * cam["height"]
+        dL = torch.as_tensor(scenes.upstream_grad((3 * P,), 1e-2, seed=34)).to(dev)
+        r.backward(gs, fr, dL, check=True)
+        ts = []
+        for _ in range(args.model_reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            f2 = r.forward(gs, [cam], check=False)
+            r.backward(gs, f2, dL, check=False)
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        st = fgs.fgs_read_status(r._bufs["ws"])
+        if st != fgs.FGS_OK:
+            raise fgs.FgsError(st, f"camera model {name}")
+        ms = float(np.median(ts))
+        out[name] = dict(width=cam["width"], height=cam["height"], views_per_s=1e3 / ms,
+                         ms_per_view=ms, intersections=int(f2.n_intersections.item()))
+    return dict(workload="500k Gaussians SH3, fwd+bwd, one view per call, every camera model",
+                models=out)
+
+
 def run_serving(args, dev):
     """Continuous-batching server vs plain one-request-at-a-time serving: 4 resident scenes
     (200k, 500k, 1M, 2M Gaussians, SH 3), Poisson arrivals, random pose, square resolution
@@ -577,6 +627,9 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-models", action="store_true",
+                    help="skip the fwd+bwd timing of every camera model")
+    ap.add_argument("--model-reps", type=int, default=5)
     ap.add_argument("--serve-rates", type=int, nargs="*", default=[200, 500, 1000, 2000])
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--serve-slots", type=int, default=3)
