@@ -540,8 +540,9 @@ def run_batched_compare(args, dev):
 
 def run_models(args, dev):
     """fwd+bwd of the 500k-Gaussian scene through every camera model: the radial fisheye
-    models at 1752x1168 (180 deg; orthographic 170 deg, its field ends at 85 deg) and the
-    equirectangular panorama at 2048x1024, same random pose. Returns a dict for the JSON line."""
+    models at 1752x1168 (180 deg; orthographic 170 deg, its field ends at 85 deg), the pinhole
+    camera at 1752x1168 and 120 deg, and the equirectangular panorama at 2048x1024, same random
+    pose. Returns a dict for the JSON line."""
     import torch
     from paper_2409_04751_gb300 import fgs, scenes
     from paper_2409_04751_gb300.renderer import FisheyeRenderer, scene_to_device
@@ -551,14 +552,14 @@ def run_models(args, dev):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     names = {fgs.FGS_CAM_EQUIDISTANT: "equidistant", fgs.FGS_CAM_EQUISOLID: "equisolid",
              fgs.FGS_CAM_STEREOGRAPHIC: "stereographic", fgs.FGS_CAM_ORTHOGRAPHIC: "orthographic",
-             fgs.FGS_CAM_EQUIRECTANGULAR: "equirectangular"}
+             fgs.FGS_CAM_EQUIRECTANGULAR: "equirectangular", fgs.FGS_CAM_PINHOLE: "pinhole"}
+    fovs = {fgs.FGS_CAM_ORTHOGRAPHIC: 170.0, fgs.FGS_CAM_PINHOLE: 120.0}
     out = {}
     for m, name in names.items():
         if m == fgs.FGS_CAM_EQUIRECTANGULAR:
             cam = scenes.pose_camera(2048, 1024, 0.0, 1 * 1000 + 1, model=m)
         else:
-            cam = scenes.pose_camera(1752, 1168, 170.0 if m == fgs.FGS_CAM_ORTHOGRAPHIC else 180.0,
-                                     1 * 1000 + 1, model=m)
+            cam = scenes.pose_camera(1752, 1168, fovs.get(m, 180.0), 1 * 1000 + 1, model=m)
         r = FisheyeRenderer(dev, capacity=1 << 23)
         fr = r.forward(gs, [cam], check=True)
         P = cam["width"] * cam["height"]

@@ -60,14 +60,15 @@ typedef enum {
   FGS_CAM_EQUISOLID = 1,
   FGS_CAM_STEREOGRAPHIC = 2,
   FGS_CAM_ORTHOGRAPHIC = 3,
-  FGS_CAM_EQUIRECTANGULAR = 4
+  FGS_CAM_EQUIRECTANGULAR = 4,
+  FGS_CAM_PINHOLE = 5 /* r = tan(theta): x_p = cx + fx x_c / z_c, the comparison camera */
 } fgs_camera_model;
 
 /* A camera (Sec. 3.1 "Transformation", Sec. 3.2):
  *   mu_c = W mu + b (W row-major, world -> camera; camera x right, y down, z forward),
  *   radial models: theta = atan2(|(x_c, y_c)|, z_c), x_p = cx + fx r(theta) x_c / l_z,
  *   y_p = cy + fy r(theta) y_c / l_z (r(theta) = theta for the equidistant model);
- *   panorama: as above. Field of view: theta < pi - 0.05 (orthographic: pi/2 - 0.05), or
+ *   panorama: as above. Field of view: theta < pi - 0.05 (orthographic, pinhole: pi/2 - 0.05), or
  *   |latitude| < pi/2 - 0.05 for the panorama, which does not wrap at longitude +-pi.
  * Pixel (i, j) is sampled at (i + 0.5, j + 0.5).
  * A view holds at most 2^20 tiles and at most 65535 tile columns and rows (the record's tile

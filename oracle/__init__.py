@@ -81,7 +81,7 @@ def num_threads() -> int:
 
 
 # camera models (the C oracle's camera[18])
-CAM_EQUIDISTANT, CAM_EQUISOLID, CAM_STEREOGRAPHIC, CAM_ORTHOGRAPHIC, CAM_EQUIRECT = range(5)
+CAM_EQUIDISTANT, CAM_EQUISOLID, CAM_STEREOGRAPHIC, CAM_ORTHOGRAPHIC, CAM_EQUIRECT, CAM_PINHOLE = range(6)
 
 
 def cam_array(cam) -> np.ndarray:

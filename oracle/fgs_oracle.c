@@ -24,7 +24,8 @@
  *
  * Camera models (camera[18]): 0 the equidistant fisheye of the method; 1 equisolid,
  * 2 stereographic, 3 orthographic, the other radial models Sec. 3.2 names (r_d = f r(theta)
- * with r = 2 sin(theta/2), 2 tan(theta/2), sin(theta)); 4 the equirectangular panorama of the
+ * with r = 2 sin(theta/2), 2 tan(theta/2), sin(theta)); 5 the pinhole camera the method is
+ * compared with (r = tan(theta): x_p = cx + fx x_c / z_c); 4 the equirectangular panorama of the
  * "Extension to Other Camera Models" paragraph (Sec. 6): x_p = cx + fx atan2(x_c, z_c),
  * y_p = cy + fy atan2(y_c, sqrt(x_c^2 + z_c^2)), which with fx = w / 2 pi, cx = w / 2,
  * fy = h / pi, cy = h / 2 is the paper's pair of equations.
@@ -41,7 +42,8 @@
  *     series in t (derived from atan's series), which is exact to rounding there.
  *   - camera axes x right, y down, z forward; pixel (i, j) is sampled at (i + 0.5, j + 0.5).
  *   - a Gaussian is visible iff |mu_c| > 0.2, theta < pi - 0.05 and opacity >= 1/255;
- *     orthographic: theta < pi/2 - 0.05 (beyond it r(theta) decreases and the image folds);
+ *     orthographic and pinhole: theta < pi/2 - 0.05 (beyond it r(theta) decreases, or does
+ *     not exist);
  *     panorama: |latitude| < pi/2 - 0.05 (the poles, where J is singular). The panorama has no
  *     wrap-around at longitude +-pi: a Gaussian is drawn on the side of its mean only.
  *   - every radial model's Jacobian has the form of the equidistant one,
@@ -79,6 +81,7 @@
 #define ORC_CAM_STEREOGRAPHIC 2
 #define ORC_CAM_ORTHOGRAPHIC 3
 #define ORC_CAM_EQUIRECT 4
+#define ORC_CAM_PINHOLE 5
 #define ORC_ALPHA_MIN (1.0 / 255.0)
 #define ORC_ALPHA_MAX 0.99
 #define ORC_T_MIN 1e-4
@@ -196,6 +199,7 @@ void orc_jacobian_grad(const double *muc, double fx, double fy, double *dJx, dou
  *   equisolid      r = 2 sin(theta/2):  g = sqrt(2 / (l (l + z)))      (sin(theta/2)^2 = (l - z) / 2l)
  *   stereographic  r = 2 tan(theta/2):  g = 2 / (l + z)                (tan(theta/2) = l_z / (l + z))
  *   orthographic   r = sin(theta):      g = 1 / l                      (sin(theta) = l_z / l)
+ *   pinhole        r = tan(theta):      g = 1 / z
  * G and its partial derivatives in (l, z) up to second order, from these closed forms. */
 static void orc_radial_G(int model, double l, double z, double *G) {
   /* G[0..5] = G, G_l, G_z, G_ll, G_lz, G_zz */
@@ -213,6 +217,12 @@ static void orc_radial_G(int model, double l, double z, double *G) {
     G[0] = 2.0 / S;
     G[1] = G[2] = -2.0 / (S * S);
     G[3] = G[4] = G[5] = 4.0 / (S * S * S);
+  } else if (model == ORC_CAM_PINHOLE) { /* x_p = cx + fx x / z: g = 1 / z */
+    G[0] = 1.0 / z;
+    G[1] = 0.0;
+    G[2] = -1.0 / (z * z);
+    G[3] = G[4] = 0.0;
+    G[5] = 2.0 / (z * z * z);
   } else { /* orthographic */
     G[0] = 1.0 / l;
     G[1] = -1.0 / (l * l);
@@ -327,7 +337,8 @@ static int orc_cam_in_field(int model, const double *muc, double *angle) {
   }
   double th = atan2(sqrt(x * x + y * y), z);
   *angle = th;
-  return th < (model == ORC_CAM_ORTHOGRAPHIC ? ORC_THETA_MAX_ORTHO : ORC_THETA_MAX);
+  return th < ((model == ORC_CAM_ORTHOGRAPHIC || model == ORC_CAM_PINHOLE) ? ORC_THETA_MAX_ORTHO
+                                                                          : ORC_THETA_MAX);
 }
 
 /* ---------------------------------------------------------------------------------------- */

@@ -41,7 +41,7 @@ bool build_views(const fgs_camera *cams, int n_views, Views *vs) {
     const fgs_camera &c = cams[k];
     if (c.width <= 0 || c.height <= 0) return false;
     if (!(isfinite(c.fx) && isfinite(c.fy) && isfinite(c.cx) && isfinite(c.cy))) return false;
-    if (c.model < FGS_CAM_EQUIDISTANT || c.model > FGS_CAM_EQUIRECTANGULAR) return false;
+    if (c.model < FGS_CAM_EQUIDISTANT || c.model > FGS_CAM_PINHOLE) return false;
     View &V = vs->v[k];
     memcpy(V.W, c.W, sizeof V.W);
     memcpy(V.b, c.b, sizeof V.b);

@@ -299,6 +299,7 @@ __device__ __forceinline__ FishG fisheye_g(float x, float y, float z) {
 //   equisolid      G = sqrt(2 / (l (l + z)))
 //   stereographic  G = 2 / (l + z)
 //   orthographic   G = 1 / l
+//   pinhole        G = 1 / z
 constexpr float COS_THETA_MAX = -0.99875026039f;       // cos(pi - 0.05)
 constexpr float COS_THETA_MAX_ORTHO = 0.04997916927f;  // cos(pi/2 - 0.05)
 constexpr float SIN_LAT_MAX = 0.99875026039f;          // sin(pi/2 - 0.05)
@@ -341,6 +342,13 @@ __device__ __forceinline__ RadTerms radial_terms(int model, float x, float y, fl
     G0 = 2.f * iS;
     G1 = G2 = -2.f * iS * iS;
     G3 = G4 = G5 = 4.f * iS * iS * iS;
+  } else if (model == FGS_CAM_PINHOLE) {  // g = 1 / z
+    const float iz = 1.f / z;
+    G0 = iz;
+    G1 = 0.f;
+    G2 = -iz * iz;
+    G3 = G4 = 0.f;
+    G5 = 2.f * iz * iz * iz;
   } else {  // orthographic
     G0 = il;
     G1 = -il * il;
@@ -370,7 +378,7 @@ __device__ __forceinline__ RadTerms radial_terms(int model, float x, float y, fl
 __device__ __forceinline__ bool in_field(int model, float x, float y, float z, float dist) {
   if (model == FGS_CAM_EQUIRECTANGULAR) return fabsf(y) < SIN_LAT_MAX * dist;
   if (model == FGS_CAM_EQUIDISTANT) return atan2f(sqrtf(x * x + y * y), z) < THETA_MAX;
-  if (model == FGS_CAM_ORTHOGRAPHIC) return z > COS_THETA_MAX_ORTHO * dist;
+  if (model == FGS_CAM_ORTHOGRAPHIC || model == FGS_CAM_PINHOLE) return z > COS_THETA_MAX_ORTHO * dist;
   return z > COS_THETA_MAX * dist;
 }
 

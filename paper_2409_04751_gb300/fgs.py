@@ -27,6 +27,7 @@ FGS_CAM_EQUISOLID = 1
 FGS_CAM_STEREOGRAPHIC = 2
 FGS_CAM_ORTHOGRAPHIC = 3
 FGS_CAM_EQUIRECTANGULAR = 4
+FGS_CAM_PINHOLE = 5
 
 EXPORTS = ["fgs_workspace_size", "fgs_total_tiles", "fgs_total_pixels", "fgs_preprocess",
            "fgs_bin_sort", "fgs_rasterize", "fgs_backward", "fgs_backward_raster",

@@ -74,11 +74,12 @@ def random_rotation(rng):
 
 
 # camera models (the C ABI's fgs_camera.model)
-CAM_EQUIDISTANT, CAM_EQUISOLID, CAM_STEREOGRAPHIC, CAM_ORTHOGRAPHIC, CAM_EQUIRECT = range(5)
+CAM_EQUIDISTANT, CAM_EQUISOLID, CAM_STEREOGRAPHIC, CAM_ORTHOGRAPHIC, CAM_EQUIRECT, CAM_PINHOLE = range(6)
 RADIAL_R = {CAM_EQUIDISTANT: lambda t: t,
             CAM_EQUISOLID: lambda t: 2.0 * math.sin(0.5 * t),
             CAM_STEREOGRAPHIC: lambda t: 2.0 * math.tan(0.5 * t),
-            CAM_ORTHOGRAPHIC: lambda t: math.sin(t)}
+            CAM_ORTHOGRAPHIC: lambda t: math.sin(t),
+            CAM_PINHOLE: lambda t: math.tan(t)}
 
 
 def _pose(rotation, centre):

@@ -63,11 +63,11 @@ def test_invalid_arguments_rejected_before_launch(lib):
     assert lib.fgs_workspace_size(10, bad, 1, 10, ctypes.byref(out)) == INV
     assert fgs.fgs_total_tiles(bad) == -1
     # camera model outside fgs_camera_model; every listed model accepted
-    for m in (-1, fgs.FGS_CAM_EQUIRECTANGULAR + 1):
+    for m in (-1, fgs.FGS_CAM_PINHOLE + 1):
         bad = _cam()
         bad[0].model = m
         assert lib.fgs_workspace_size(10, bad, 1, 10, ctypes.byref(out)) == INV
-    for m in range(fgs.FGS_CAM_EQUIRECTANGULAR + 1):
+    for m in range(fgs.FGS_CAM_PINHOLE + 1):
         ok = _cam()
         ok[0].model = m
         assert lib.fgs_workspace_size(10, ok, 1, 10, ctypes.byref(out)) == fgs.FGS_OK

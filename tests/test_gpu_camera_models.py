@@ -16,13 +16,13 @@ from tests.test_gpu_render import _grad_case, _render
 pytestmark = pytest.mark.gpu
 
 MODELS = [fgs.FGS_CAM_EQUISOLID, fgs.FGS_CAM_STEREOGRAPHIC, fgs.FGS_CAM_ORTHOGRAPHIC,
-          fgs.FGS_CAM_EQUIRECTANGULAR]
+          fgs.FGS_CAM_EQUIRECTANGULAR, fgs.FGS_CAM_PINHOLE]
 
 
 def _cam(model, w, h, seed, fov=None):
     if model == fgs.FGS_CAM_EQUIRECTANGULAR:
         return scenes.pose_camera(2 * h, h, 0.0, seed=seed, model=model)
-    fov = fov or (170.0 if model == fgs.FGS_CAM_ORTHOGRAPHIC else 190.0)
+    fov = fov or {fgs.FGS_CAM_ORTHOGRAPHIC: 170.0, fgs.FGS_CAM_PINHOLE: 120.0}.get(model, 190.0)
     return scenes.pose_camera(w, h, fov, seed=seed, model=model)
 
 
@@ -78,7 +78,7 @@ def test_gradients_match_oracle(cuda_device, model):
     parity.check_grads(g, ref, f"model {model}")
 
 
-@pytest.mark.parametrize("model", MODELS[:3])
+@pytest.mark.parametrize("model", MODELS[:3] + MODELS[4:])
 def test_gradients_near_axis(cuda_device, model):
     """Gaussians within t = l_z / z < 0.3 of the optical axis and on it."""
     rng = np.random.default_rng(80 + model)
@@ -88,7 +88,8 @@ def test_gradients_near_axis(cuda_device, model):
     a = rng.uniform(0, 2 * math.pi, n)
     scene = scenes.shell_scene(n, seed=81 + model, sh_degree=1)
     scene["means"] = np.stack([t * z * np.cos(a), t * z * np.sin(a), z], 1).astype(np.float32)
-    cam = scenes.fisheye_camera(128, 128, 170.0, model=model)
+    cam = scenes.fisheye_camera(128, 128, 120.0 if model == fgs.FGS_CAM_PINHOLE else 170.0,
+                                model=model)
     g, ref = _grad_case(scene, [cam], seed=82 + model)
     parity.check_grads(g, ref, f"near-axis model {model}")
 

@@ -1,6 +1,7 @@
 """Pins of the oracle's other camera models: the radial fisheye models Sec. 3.2 names
-(equisolid, stereographic, orthographic; r_d = f r(theta)) and the equirectangular panorama of
-Sec. 6 ("Extension to Other Camera Models").
+(equisolid, stereographic, orthographic; r_d = f r(theta)), the pinhole camera the method is
+compared with (r = tan(theta)), and the equirectangular panorama of Sec. 6 ("Extension to
+Other Camera Models").
 
 What pins them, other than the oracle itself:
   * projections at special angles, against values of r(theta) known in closed form
@@ -23,7 +24,7 @@ torch = pytest.importorskip("torch")
 from tests import torch_brute  # noqa: E402
 
 RADIAL = [oracle.CAM_EQUIDISTANT, oracle.CAM_EQUISOLID, oracle.CAM_STEREOGRAPHIC,
-          oracle.CAM_ORTHOGRAPHIC]
+          oracle.CAM_ORTHOGRAPHIC, oracle.CAM_PINHOLE]
 ALL = RADIAL + [oracle.CAM_EQUIRECT]
 
 # r(theta) at 60 and 90 degrees, from the special values of sin and tan
@@ -32,6 +33,7 @@ R_SPECIAL = {
     oracle.CAM_EQUISOLID: {60: 1.0, 90: math.sqrt(2.0)},            # 2 sin 30, 2 sin 45
     oracle.CAM_STEREOGRAPHIC: {60: 2.0 / math.sqrt(3.0), 90: 2.0},  # 2 tan 30, 2 tan 45
     oracle.CAM_ORTHOGRAPHIC: {60: math.sqrt(3.0) / 2.0, 90: 1.0},   # sin 60, sin 90
+    oracle.CAM_PINHOLE: {30: 1.0 / math.sqrt(3.0), 60: math.sqrt(3.0)},  # tan 30, tan 60
 }
 
 
@@ -77,7 +79,7 @@ def test_radial_models_are_pinhole_on_the_axis(model):
 
 def _points(model, rng, n=40):
     out = []
-    lim = math.radians(85.0) if model == oracle.CAM_ORTHOGRAPHIC else math.radians(170.0)
+    lim = math.radians(85.0) if model in (oracle.CAM_ORTHOGRAPHIC, oracle.CAM_PINHOLE) else math.radians(170.0)
     while len(out) < n:
         p = rng.normal(size=3) * rng.uniform(0.3, 5.0)
         l = np.linalg.norm(p)
@@ -159,7 +161,7 @@ def _tiny_scene(seed, n=7, degree=2):
 
 
 @pytest.mark.parametrize("model", [oracle.CAM_EQUISOLID, oracle.CAM_STEREOGRAPHIC,
-                                   oracle.CAM_ORTHOGRAPHIC, oracle.CAM_EQUIRECT])
+                                   oracle.CAM_ORTHOGRAPHIC, oracle.CAM_EQUIRECT, oracle.CAM_PINHOLE])
 def test_tiny_scene_matches_torch_autograd(model):
     scene = _tiny_scene(40 + model)
     if model == oracle.CAM_EQUIRECT:
@@ -167,8 +169,8 @@ def test_tiny_scene_matches_torch_autograd(model):
         cam["fx"], cam["fy"] = 4 * cam["fx"], 4 * cam["fy"]   # zoomed so the scene fills it
         h_, w_ = 20, 40
     else:
-        cam = scenes.fisheye_camera(24, 20, 170.0 if model == oracle.CAM_ORTHOGRAPHIC else 190.0,
-                                    model=model)
+        fov = {oracle.CAM_ORTHOGRAPHIC: 170.0, oracle.CAM_PINHOLE: 120.0}.get(model, 190.0)
+        cam = scenes.fisheye_camera(24, 20, fov, model=model)
         h_, w_ = 20, 24
     rng = np.random.default_rng(200 + model)
     g = rng.normal(0, 1, (3, h_, w_))

@@ -4,8 +4,8 @@ oracle (forward and gradients). It shares nothing with the oracle but the conven
   * J_phi is not written out: it is torch.autograd's Jacobian of the projection phi, taken
     with create_graph=True so the backward also differentiates J. phi is the equidistant
     model of Sec. 3.2 or, by the camera's `model`, r_d = f r(theta) with r = 2 sin(theta/2),
-    2 tan(theta/2) or sin(theta), or the panorama's longitude / latitude map (Sec. 6), each
-    written from its definition;
+    2 tan(theta/2), sin(theta) or tan(theta) (pinhole), or the panorama's longitude / latitude
+    map (Sec. 6), each written from its definition;
   * R comes from rotating the basis vectors by the quaternion (Hamilton product q v q*);
   * the real spherical harmonics come from the associated-Legendre three-term recursion and
     cos / sin of the azimuth;
@@ -94,7 +94,7 @@ def render_and_grad(scene, cam, dLdC=None, bg=(0.0, 0.0, 0.0), grad=True):
 
     model = int(cam.get("model", 0))
     radial = {0: lambda t: t, 1: lambda t: 2 * torch.sin(t / 2), 2: lambda t: 2 * torch.tan(t / 2),
-              3: torch.sin}
+              3: torch.sin, 5: torch.tan}
 
     def phi(p):
         if model == 4:
@@ -109,7 +109,7 @@ def render_and_grad(scene, cam, dLdC=None, bg=(0.0, 0.0, 0.0), grad=True):
         if model == 4:
             return float(torch.atan2(p[1].abs(), torch.sqrt(p[0] ** 2 + p[2] ** 2))) < math.pi / 2 - 0.05
         theta = float(torch.atan2(torch.linalg.norm(p[:2]), p[2]))
-        return theta < (math.pi / 2 - 0.05 if model == 3 else math.pi - 0.05)
+        return theta < (math.pi / 2 - 0.05 if model in (3, 5) else math.pi - 0.05)
 
     gs = []
     for i in range(means.shape[0]):
