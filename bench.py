@@ -419,8 +419,10 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_serving:
         serving = run_serving(args, dev)
     models = None
+    exact = None
     if rank == 0 and world == 1 and not args.no_models:
         models = run_models(args, dev)
+        exact = run_exact_binning(args, dev)
 
     # preprocess; scan, count, tile scan, scatter, two segment-sort classes; raster fwd; raster
     # bwd; preprocess bwd
@@ -443,6 +445,7 @@ def run_gpu(args):
         batched=batched,
         serving=serving,
         camera_models=models,
+        exact_binning=exact,
         e2e=dict(value=world * args.steps / e2e_s, unit="views/s", h2d_bytes_per_step=h2d,
                  d2h_bytes_per_step=d2h),
         gpu_launches=launches_per_step * args.steps,
@@ -585,6 +588,53 @@ def run_models(args, dev):
                 models=out)
 
 
+def run_exact_binning(args, dev):
+    """The bench workload (500k Gaussians, 1752x1168 at 180 deg) with the rect binning of the
+    method and with the exact ellipse binning (fgs_bin_sort_ex, FGS_BIN_ELLIPSE): intersections
+    (Table 3's axis), fwd and fwd+bwd views/s, same images. Returns a dict for the JSON line."""
+    import torch
+    from paper_2409_04751_gb300 import fgs, scenes
+    from paper_2409_04751_gb300.renderer import FisheyeRenderer, scene_to_device
+
+    scene, cams = scenes.config1()
+    gs = scene_to_device(scene, dev)
+    cam = cams[0]
+    P = cam["width"] * cam["height"]
+    dL = torch.as_tensor(scenes.upstream_grad((3 * P,), 1e-2, seed=35)).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = {}
+    imgs = {}
+    for binning in ("rect", "ellipse"):
+        r = FisheyeRenderer(dev, capacity=1 << 23, binning=binning)
+        fr = r.forward(gs, [cam], check=True)
+        r.backward(gs, fr, dL, check=True)
+        imgs[binning] = fr.images.clone()
+        tf, tb = [], []
+        for _ in range(args.model_reps):
+            flush.zero_()
+            a, m, b = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record()
+            f2 = r.forward(gs, [cam], check=False)
+            m.record()
+            r.backward(gs, f2, dL, check=False)
+            b.record()
+            b.synchronize()
+            tf.append(a.elapsed_time(m))
+            tb.append(a.elapsed_time(b))
+        st = fgs.fgs_read_status(r._bufs["ws"])
+        if st != fgs.FGS_OK:
+            raise fgs.FgsError(st, f"binning {binning}")
+        out[binning] = dict(intersections=int(f2.n_intersections.item()),
+                            key_bytes=int(f2.n_intersections.item()) * 12,
+                            fwd_views_per_s=1e3 / float(np.median(tf)),
+                            fwd_bwd_views_per_s=1e3 / float(np.median(tb)))
+    return dict(workload=WORKLOAD, **out,
+                images_equal=bool(torch.equal(imgs["rect"], imgs["ellipse"])),
+                note="ellipse = fgs_bin_sort_ex with FGS_BIN_ELLIPSE: only the tiles the alpha "
+                     ">= 1/255 ellipse reaches; the rect binning is the method's and the "
+                     "headline value")
+
+
 def run_serving(args, dev):
     """Continuous-batching server vs plain one-request-at-a-time serving: 4 resident scenes
     (200k, 500k, 1M, 2M Gaussians, SH 3), Poisson arrivals, random pose, square resolution
@@ -629,7 +679,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-models", action="store_true",
-                    help="skip the fwd+bwd timing of every camera model")
+                    help="skip the fwd+bwd timing of every camera model and of the exact binning")
     ap.add_argument("--model-reps", type=int, default=5)
     ap.add_argument("--serve-rates", type=int, nargs="*", default=[200, 500, 1000, 2000])
     ap.add_argument("--serve-seconds", type=float, default=1.0)

@@ -151,6 +151,23 @@ fgs_status fgs_bin_sort(const fgs_record *records, const uint32_t *tiles_touched
                         int64_t capacity, uint32_t *tile_ranges, int64_t *n_intersections,
                         void *workspace, size_t workspace_bytes, fgs_stream stream);
 
+/* fgs_bin_sort with options. flags = 0 is fgs_bin_sort. flags = FGS_BIN_ELLIPSE emits only the
+ * pairs whose tile the Gaussian's alpha >= 1/255 ellipse d^T conic d <= 2 ln(255 opacity)
+ * reaches: the minimum of the quadratic over the rectangle of the tile's pixel centres is
+ * compared with the level (times 1 + 1e-3, plus 1e-2, a conservative margin). This is the
+ * precise Gaussian-tile intersection of the renderers the method adapts to (Sec. 6 and
+ * Table 3, FlashGS). A dropped pair has alpha < 1/255 at every pixel of its tile, so the images,
+ * transmittances and gradients equal those of the rect binning; only the lists are shorter.
+ * *n_intersections is then the number of pairs kept (the rect count if it exceeds capacity,
+ * with FGS_ERR_CAPACITY); capacity must still hold the rect count. Other flag bits:
+ * FGS_ERR_INVALID_ARG. */
+#define FGS_BIN_ELLIPSE 1u
+fgs_status fgs_bin_sort_ex(const fgs_record *records, const uint32_t *tiles_touched, int64_t n,
+                           const fgs_camera *cams, int n_views, uint64_t *keys, uint32_t *vals,
+                           int64_t capacity, uint32_t *tile_ranges, int64_t *n_intersections,
+                           void *workspace, size_t workspace_bytes, uint32_t flags,
+                           fgs_stream stream);
+
 /* Stage 5, rasterize (Sec. 3.1 "Rendering", Sec. 4.1 renderCUDA): per pixel, front to back
  * over its tile's sorted list: skip alpha < 1/255, stop before a Gaussian whose blend would
  * take T below 1e-4, C += rgb alpha T, T *= 1 - alpha; finally C += T bg.

@@ -50,8 +50,11 @@ def _lib_handle():
         lib.orc_backward.argtypes = [ctypes.c_int64, _D, _D, _D, _D, _D, _D, ctypes.c_int, _D,
                                      ctypes.c_int64, _I32, _D, _D, ctypes.c_int, _D, _D, _D, _D,
                                      _D, _D]
+        lib.orc_rect_min_q.argtypes = [_D, _D, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double]
+        lib.orc_rect_min_q.restype = ctypes.c_double
         lib.orc_build_keys.argtypes = [ctypes.c_int64, _I32, _I32, _U32, _I64, _I32,
-                                       ctypes.c_int64, ctypes.c_int64, _U64, _U32, _U32]
+                                       ctypes.c_int64, ctypes.c_int64, _U64, _U32, _U32, _D]
         lib.orc_build_keys.restype = ctypes.c_int64
         lib.orc_project_point.argtypes = [_D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, _D]
@@ -166,9 +169,10 @@ def backward(G, scene, cam, pixels, dLdC, bg=(0.0, 0.0, 0.0), use_bbox=True):
                 g2d=g2d[:n])
 
 
-def build_keys(view, rect, depth_bits, tile_offset, tiles_x, n_tiles_total):
+def build_keys(view, rect, depth_bits, tile_offset, tiles_x, n_tiles_total, ellipse=None):
     """Sorted (keys u64, vals u32) and tile_ranges [n_tiles, 2] u32 from per-record
-    (view, rect x0 y0 x1 y1 inclusive, FP32 depth bits)."""
+    (view, rect x0 y0 x1 y1 inclusive, FP32 depth bits). ellipse: None (rect binning) or
+    [nrec, 6] = (mean x, y, conic A, B, C, q*) for the exact binning."""
     lib = _lib_handle()
     view = np.ascontiguousarray(view, np.int32)
     rect = np.ascontiguousarray(rect, np.int32).reshape(-1, 4)
@@ -182,11 +186,18 @@ def build_keys(view, rect, depth_bits, tile_offset, tiles_x, n_tiles_total):
     keys = np.zeros(max(m, 1), np.uint64)
     vals = np.zeros(max(m, 1), np.uint32)
     ranges = np.zeros((max(int(n_tiles_total), 1), 2), np.uint32)
+    ell = None if ellipse is None else _f64(np.asarray(ellipse).reshape(-1, 6))
     r = lib.orc_build_keys(nrec, _p(view, _I32), _p(rect, _I32), _p(db, _U32), _p(to, _I64),
                            _p(tx, _I32), int(n_tiles_total), m, _p(keys, _U64), _p(vals, _U32),
-                           _p(ranges, _U32))
-    assert r == m
+                           _p(ranges, _U32), None if ell is None else _p(ell))
+    assert 0 <= r <= m
+    m = r
     return keys[:m], vals[:m], ranges[:int(n_tiles_total)]
+
+
+def rect_min_q(mu, conic, xl, xh, yl, yh):
+    """min over [xl, xh] x [yl, yh] of (p - mu)^T [[A, B], [B, C]] (p - mu)."""
+    return float(_lib_handle().orc_rect_min_q(_p(_f64(mu)), _p(_f64(conic)), xl, xh, yl, yh))
 
 
 def project_point(muc, fx, fy, cx=0.0, cy=0.0, model=CAM_EQUIDISTANT):

@@ -20,7 +20,9 @@
  *                   S1..S8 (Sec. 4.3 backward), the accumulation of both on mu (end of
  *                   Sec. 4.3), and Sigma -> (s, q), colour -> SH and view direction.
  *   orc_build_keys  tile binning and sort (Sec. 3.1 "Rendering", Sec. 4.1): one
- *                   (tile << 32 | depth bits) key per Gaussian x covered tile, stable order.
+ *                   (tile << 32 | depth bits) key per Gaussian x covered tile, stable order;
+ *                   optionally only the tiles the alpha >= 1/255 ellipse reaches (the precise
+ *                   Gaussian-tile intersection of the renderers of Sec. 6 / Table 3).
  *
  * Camera models (camera[18]): 0 the equidistant fisheye of the method; 1 equisolid,
  * 2 stereographic, 3 orthographic, the other radial models Sec. 3.2 names (r_d = f r(theta)
@@ -840,15 +842,55 @@ static int orc_kv_cmp(const void *pa, const void *pb) {
   return (a->val > b->val) - (a->val < b->val);
 }
 
+/* Minimum over the rectangle [xl, xh] x [yl, yh] of q(d) = A dx^2 + 2 B dx dy + C dy^2,
+ * d = p - mu, for a positive definite conic (A, B, C): 0 when mu lies in the rectangle, else
+ * the smallest of the four edge minima (on an edge, the 1D minimiser of the free coordinate,
+ * -B d_fixed / C or -B d_fixed / A, clamped to the edge). */
+double orc_rect_min_q(const double *mu, const double *conic, double xl, double xh, double yl,
+                      double yh) {
+  double A = conic[0], B = conic[1], C = conic[2];
+  if (mu[0] >= xl && mu[0] <= xh && mu[1] >= yl && mu[1] <= yh) return 0.0;
+  double best = HUGE_VAL;
+  for (int e = 0; e < 2; ++e) {
+    double dx = (e ? xh : xl) - mu[0];
+    double dy = -B * dx / C;
+    if (dy < yl - mu[1]) dy = yl - mu[1];
+    if (dy > yh - mu[1]) dy = yh - mu[1];
+    double q = A * dx * dx + 2 * B * dx * dy + C * dy * dy;
+    if (q < best) best = q;
+    double ey = (e ? yh : yl) - mu[1];
+    double ex = -B * ey / A;
+    if (ex < xl - mu[0]) ex = xl - mu[0];
+    if (ex > xh - mu[0]) ex = xh - mu[0];
+    q = A * ex * ex + 2 * B * ex * ey + C * ey * ey;
+    if (q < best) best = q;
+  }
+  return best;
+}
+
+/* Whether the exact binning keeps tile (tx, ty) of a record: the rectangle of the tile's pixel
+ * centres against the level q* = 2 ln(255 opacity), with the margin q* (1 + 1e-3) + 1e-2. */
+static int orc_keep_tile(const double *ell, int tx, int ty) {
+  double xl = tx * ORC_TILE + 0.5, yl = ty * ORC_TILE + 0.5;
+  double qs = ell[5] > 0 ? ell[5] : 0.0;
+  return orc_rect_min_q(ell, ell + 2, xl, xl + ORC_TILE - 1, yl, yl + ORC_TILE - 1) <=
+         qs * 1.001 + 1e-2;
+}
+
+/* ell: NULL (rect binning) or [nrec, 6] = mean x, y, conic A, B, C, q* (exact binning: only
+ * the pairs orc_keep_tile accepts). */
 int64_t orc_build_keys(int64_t nrec, const int32_t *view, const int32_t *rect /* [nrec,4] */,
                        const uint32_t *depth_bits, const int64_t *tile_offset,
                        const int32_t *tiles_x, int64_t n_tiles_total, int64_t capacity,
-                       uint64_t *keys, uint32_t *vals, uint32_t *tile_ranges /* [n_tiles,2] */) {
+                       uint64_t *keys, uint32_t *vals, uint32_t *tile_ranges /* [n_tiles,2] */,
+                       const double *ell) {
   int64_t m = 0;
   for (int64_t r = 0; r < nrec; ++r) {
     const int32_t *rc = rect + 4 * r;
     if (rc[0] < 0 || rc[2] < rc[0] || rc[3] < rc[1]) continue;
-    m += (int64_t)(rc[2] - rc[0] + 1) * (rc[3] - rc[1] + 1);
+    for (int ty = rc[1]; ty <= rc[3]; ++ty)
+      for (int tx = rc[0]; tx <= rc[2]; ++tx)
+        if (!ell || orc_keep_tile(ell + 6 * r, tx, ty)) ++m;
   }
   if (m > capacity) return -1;
   orc_kv *kv = (orc_kv *)malloc(sizeof(orc_kv) * (m ? m : 1));
@@ -858,6 +900,7 @@ int64_t orc_build_keys(int64_t nrec, const int32_t *view, const int32_t *rect /*
     if (rc[0] < 0 || rc[2] < rc[0] || rc[3] < rc[1]) continue;
     for (int ty = rc[1]; ty <= rc[3]; ++ty)
       for (int tx = rc[0]; tx <= rc[2]; ++tx) {
+        if (ell && !orc_keep_tile(ell + 6 * r, tx, ty)) continue;
         uint64_t tile = (uint64_t)(tile_offset[view[r]] + (int64_t)ty * tiles_x[view[r]] + tx);
         kv[e].key = (tile << 32) | depth_bits[r];
         kv[e].val = (uint32_t)r;

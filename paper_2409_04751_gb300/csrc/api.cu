@@ -128,13 +128,15 @@ fgs_status fgs_preprocess(const fgs_gaussians *g, const fgs_camera *cams, int n_
                                            reinterpret_cast<cudaStream_t>(stream)));
 }
 
-fgs_status fgs_bin_sort(const fgs_record *records, const uint32_t *tiles_touched, int64_t n,
-                        const fgs_camera *cams, int n_views, uint64_t *keys, uint32_t *vals,
-                        int64_t capacity, uint32_t *tile_ranges, int64_t *n_intersections,
-                        void *workspace, size_t workspace_bytes, fgs_stream stream) {
+fgs_status fgs_bin_sort_ex(const fgs_record *records, const uint32_t *tiles_touched, int64_t n,
+                           const fgs_camera *cams, int n_views, uint64_t *keys, uint32_t *vals,
+                           int64_t capacity, uint32_t *tile_ranges, int64_t *n_intersections,
+                           void *workspace, size_t workspace_bytes, uint32_t flags,
+                           fgs_stream stream) {
   Views vs;
   if (n < 0 || capacity <= 0 || capacity > 0xffffffffLL || !build_views(cams, n_views, &vs))
     return FGS_ERR_INVALID_ARG;
+  if ((flags & ~(uint32_t)FGS_BIN_ELLIPSE) != 0) return FGS_ERR_INVALID_ARG;
   if ((int64_t)n_views * n > 0xffffffffLL) return FGS_ERR_INVALID_ARG;
   if (!keys || !vals || !tile_ranges || !n_intersections || !workspace) return FGS_ERR_INVALID_ARG;
   if (n > 0 && (!records || !tiles_touched || !aligned(records, 16))) return FGS_ERR_INVALID_ARG;
@@ -143,8 +145,16 @@ fgs_status fgs_bin_sort(const fgs_record *records, const uint32_t *tiles_touched
   if (workspace_bytes < L.total) return FGS_ERR_INVALID_ARG;
   return cuda_status(launch_bin_sort(records, tiles_touched, n, vs, keys, vals, capacity,
                                      tile_ranges, n_intersections,
-                                     reinterpret_cast<char *>(workspace), L,
+                                     reinterpret_cast<char *>(workspace), L, flags,
                                      reinterpret_cast<cudaStream_t>(stream)));
+}
+
+fgs_status fgs_bin_sort(const fgs_record *records, const uint32_t *tiles_touched, int64_t n,
+                        const fgs_camera *cams, int n_views, uint64_t *keys, uint32_t *vals,
+                        int64_t capacity, uint32_t *tile_ranges, int64_t *n_intersections,
+                        void *workspace, size_t workspace_bytes, fgs_stream stream) {
+  return fgs_bin_sort_ex(records, tiles_touched, n, cams, n_views, keys, vals, capacity,
+                         tile_ranges, n_intersections, workspace, workspace_bytes, 0u, stream);
 }
 
 fgs_status fgs_rasterize(const fgs_record *records, const uint32_t *vals,

@@ -99,7 +99,8 @@ __device__ __forceinline__ uint64_t look_back(const uint64_t *lb, int64_t part, 
 
 __global__ void __launch_bounds__(EMIT_THREADS)
     scan_kernel(const uint32_t *__restrict__ tt, int64_t R, int64_t capacity, int64_t *n_int,
-                unsigned long long *n_vis, uint64_t *lb_pairs, uint64_t *lb_vis,
+                unsigned long long *n_cand, unsigned long long *n_vis, uint64_t *lb_pairs,
+                uint64_t *lb_vis,
                 uint32_t *part_counter, uint32_t *__restrict__ vis_rec,
                 uint64_t *__restrict__ vis_off, uint32_t *__restrict__ chunk_first,
                 uint32_t *status) {
@@ -138,8 +139,12 @@ __global__ void __launch_bounds__(EMIT_THREADS)
     }
     s_prefix[tid == 0 ? 0 : 1] = prefix;
     if (base + EMIT_PART >= R) {
-      if (tid == 0) *n_int = (int64_t)(prefix + agg);
-      else *n_vis = prefix + agg;
+      if (tid == 0) {
+        *n_int = (int64_t)(prefix + agg);
+        *n_cand = prefix + agg;
+      } else {
+        *n_vis = prefix + agg;
+      }
     }
   }
   __syncthreads();
@@ -170,11 +175,11 @@ __global__ void __launch_bounds__(EMIT_THREADS)
 // depth_bits << 32 | record there. Both passes visit the same pairs in the same way, so every
 // bucket is filled exactly. Pairs whose tile falls outside their view's grid (a malformed
 // caller record) are skipped by both.
-template <bool SCATTER>
+template <bool SCATTER, bool ELLIPSE>
 __global__ void __launch_bounds__(EMIT_THREADS)
     pair_kernel(const fgs_record *__restrict__ rec, int64_t n_per_view, Views vs,
                 const uint32_t *__restrict__ vis_rec, const uint64_t *__restrict__ vis_off,
-                const uint32_t *__restrict__ chunk_first, const int64_t *n_int,
+                const uint32_t *__restrict__ chunk_first, const unsigned long long *n_cand,
                 const unsigned long long *n_vis, uint32_t *ranges, uint64_t *__restrict__ words,
                 int64_t capacity, uint32_t *status) {
   constexpr int PER = EMIT_CHUNK / EMIT_THREADS;  // pairs per thread and chunk
@@ -186,8 +191,12 @@ __global__ void __launch_bounds__(EMIT_THREADS)
   __shared__ uint32_t s_rec[EMIT_CHUNK + 1];
   __shared__ uint16_t s_own[EMIT_CHUNK];       // record (window slot) owning each pair
   __shared__ uint32_t s_wmax[EMIT_THREADS / 32];
+  // exact mode: mean, conic, q* and the rect corner of each record of the window
+  __shared__ float2 s_mu[ELLIPSE ? EMIT_CHUNK + 1 : 1];
+  __shared__ float4 s_con[ELLIPSE ? EMIT_CHUNK + 1 : 1];
+  __shared__ uint32_t s_rc[ELLIPSE ? EMIT_CHUNK + 1 : 1];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int64_t total = *n_int;
+  const int64_t total = (int64_t)*n_cand;
   if (!SCATTER && blockIdx.x == 0 && tid == 0 && total > capacity) set_status(status, ST_CAPACITY);
   const int64_t n = min(total, capacity);
   const int64_t nchunks = (n + EMIT_CHUNK - 1) / EMIT_CHUNK;
@@ -218,6 +227,13 @@ __global__ void __launch_bounds__(EMIT_THREADS)
       s_geom[i] = ok ? (x1 - x0 + 1u) | ((y1 - y0 + 1u) << 16) : 0u;
       s_tx[i] = tiles_x;
       s_depth[i] = w2.y;
+      if (ELLIPSE) {
+        const float4 w0 = __ldg(reinterpret_cast<const float4 *>(rec + r));
+        const float4 w1 = __ldg(reinterpret_cast<const float4 *>(rec + r) + 1);
+        s_mu[i] = make_float2(w0.x, w0.y);
+        s_con[i] = make_float4(w0.z, w0.w, w1.x, fmaxf(2.f * logf(255.f * w1.y), 0.f));
+        s_rc[i] = x0 | (y0 << 16);
+      }
       if (i > 0 && off < (uint64_t)hi) s_own[off - (uint64_t)lo] = (uint16_t)i;
     }
     __syncthreads();
@@ -261,7 +277,17 @@ __global__ void __launch_bounds__(EMIT_THREADS)
           if ((dy + 1u) * w <= local) ++dy;
           const uint32_t dx = local - dy * w;
           // more pairs than the rect holds (a malformed record): skipped
-          if (dy < h && dx < w) tile[k] = s_base[a] + dy * s_tx[a] + dx;
+          bool keep = dy < h && dx < w;
+          if (ELLIPSE && keep) {
+            const float2 mu = s_mu[a];
+            const float4 cq = s_con[a];
+            const uint32_t rc = s_rc[a];
+            const float xl = (float)(((rc & 0xffffu) + dx) * TILE) + 0.5f;
+            const float yl = (float)(((rc >> 16) + dy) * TILE) + 0.5f;
+            keep = ellipse_reaches_tile(mu.x, mu.y, cq.x, cq.y, cq.z, cq.w, xl, xl + (TILE - 1),
+                                        yl, yl + (TILE - 1));
+          }
+          if (keep) tile[k] = s_base[a] + dy * s_tx[a] + dx;
         }
         owner[k] = a;
       }
@@ -291,6 +317,7 @@ __global__ void __launch_bounds__(EMIT_THREADS)
 __global__ void __launch_bounds__(256)
     tile_scan_kernel(uint32_t *ranges, int64_t total_tiles, uint64_t *lb,
                      uint32_t *part_counter, uint32_t *lists, uint32_t *seg_count,
+                     const unsigned long long *n_cand, int64_t capacity, int64_t *n_int,
                      uint32_t *status) {
   __shared__ uint32_t s_warp[8];
   __shared__ uint64_t s_prefix;
@@ -323,6 +350,10 @@ __global__ void __launch_bounds__(256)
       st_volatile_u64(lb + part, LB_INC | (prefix + agg));
     }
     s_prefix = prefix;
+    // the pairs kept (fewer than the candidates in the exact mode); with more candidates than
+    // capacity the candidate count stays, so the caller can grow the buffers
+    if (base + TSCAN_PART >= total_tiles && (int64_t)*n_cand <= capacity)
+      *n_int = (int64_t)(prefix + agg);
   }
   // class ranks inside the CTA (order within a class list is irrelevant)
   uint32_t cls_rank[ITEMS];
@@ -855,7 +886,7 @@ cudaError_t launch_segsort(const uint32_t *list, const uint32_t *list_count,
 cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_touched,
                             int64_t n, const Views &vs, uint64_t *keys, uint32_t *vals,
                             int64_t capacity, uint32_t *tile_ranges, int64_t *n_int,
-                            char *ws, const WsLayout &L, cudaStream_t st) {
+                            char *ws, const WsLayout &L, uint32_t flags, cudaStream_t st) {
   cudaError_t e;
   WsHeader *hdr = reinterpret_cast<WsHeader *>(ws + L.header);
   uint64_t *scan_lb = reinterpret_cast<uint64_t *>(ws + L.scan_lb);
@@ -875,22 +906,34 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
   if ((e = cudaMemsetAsync(tile_lb, 0, sizeof(uint64_t) * (size_t)L.tile_parts, st)) != cudaSuccess) return e;
 
   scan_kernel<<<(unsigned)L.scan_parts, EMIT_THREADS, 0, st>>>(
-      tiles_touched, R, capacity, n_int, &hdr->n_visible, scan_lb, scan_lb + L.scan_parts,
-      &hdr->scan_parts, vis_rec, vis_off, chunk_first, &hdr->status);
+      tiles_touched, R, capacity, n_int, &hdr->n_candidates, &hdr->n_visible, scan_lb,
+      scan_lb + L.scan_parts, &hdr->scan_parts, vis_rec, vis_off, chunk_first, &hdr->status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int64_t egrid = (int64_t)sm_count() * 4;
   if (egrid > L.chunks) egrid = L.chunks;
   if (egrid < 1) egrid = 1;
-  pair_kernel<false><<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
-      records, n, vs, vis_rec, vis_off, chunk_first, n_int, &hdr->n_visible, tile_ranges, words,
-      capacity, &hdr->status);
+  const bool ellipse = (flags & FGS_BIN_ELLIPSE) != 0;
+  if (ellipse)
+    pair_kernel<false, true><<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
+        records, n, vs, vis_rec, vis_off, chunk_first, &hdr->n_candidates, &hdr->n_visible,
+        tile_ranges, words, capacity, &hdr->status);
+  else
+    pair_kernel<false, false><<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
+        records, n, vs, vis_rec, vis_off, chunk_first, &hdr->n_candidates, &hdr->n_visible,
+        tile_ranges, words, capacity, &hdr->status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   tile_scan_kernel<<<(unsigned)L.tile_parts, 256, 0, st>>>(
-      tile_ranges, T, tile_lb, &hdr->tile_parts, lists, hdr->seg_count, &hdr->status);
+      tile_ranges, T, tile_lb, &hdr->tile_parts, lists, hdr->seg_count, &hdr->n_candidates,
+      capacity, n_int, &hdr->status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  pair_kernel<true><<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
-      records, n, vs, vis_rec, vis_off, chunk_first, n_int, &hdr->n_visible, tile_ranges, words,
-      capacity, &hdr->status);
+  if (ellipse)
+    pair_kernel<true, true><<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
+        records, n, vs, vis_rec, vis_off, chunk_first, &hdr->n_candidates, &hdr->n_visible,
+        tile_ranges, words, capacity, &hdr->status);
+  else
+    pair_kernel<true, false><<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
+        records, n, vs, vis_rec, vis_off, chunk_first, &hdr->n_candidates, &hdr->n_visible,
+        tile_ranges, words, capacity, &hdr->status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_segsort<256, 2, SEG_CAP0, 6, false>(lists, &hdr->seg_count[0], tile_ranges,
                                                        words, keys, vals, capacity, st)) !=

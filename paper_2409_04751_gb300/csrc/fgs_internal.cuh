@@ -79,7 +79,8 @@ struct WsHeader {
   // [2] backward evaluations, [3] backward contributions
   unsigned long long counters[4];
   unsigned long long n_visible;  // records with a non-empty rect (written by the scan)
-  uint32_t pad[42];
+  unsigned long long n_candidates;  // (record, tile) pairs of the rects (written by the scan)
+  uint32_t pad[40];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
 
@@ -283,6 +284,35 @@ __device__ __forceinline__ FishG fisheye_g(float x, float y, float z) {
     r.huu = NEED_HUU ? -(2.f * z / (l2 * l2) + 3.f * r.h) / u2 : 0.f;
   }
   return r;
+}
+
+// ------------------------------------------------------------------------------------------
+// Ellipse-tile test of the binning's exact mode. A Gaussian can reach alpha >= 1/255 at a pixel
+// of a tile only if the minimum over the tile's rectangle of pixel centres [xl, xh] x [yl, yh]
+// of q(d) = A dx^2 + 2 B dx dy + C dy^2 (conic (A, B, C), d = pixel - mean) is at most
+// q* = 2 ln(255 opacity). The minimum of this convex quadratic over the rectangle is 0 with the
+// mean inside it, else it lies on an edge, where it is the 1D minimum in the free coordinate
+// clamped to the edge. The pair is kept when the minimum is at most q* (1 + 1e-3) + 1e-2, a
+// margin far above the rounding of the rasterizer's exponent, so no contributing pair is lost.
+__device__ __forceinline__ bool ellipse_reaches_tile(float mx, float my, float A, float B,
+                                                     float C, float qs, float xl, float xh,
+                                                     float yl, float yh) {
+  if (mx >= xl && mx <= xh && my >= yl && my <= yh) return true;
+  const float thr = fmaf(qs, 1.001f, 1e-2f);
+  const float iA = 1.f / A, iC = 1.f / C;
+  float qmin = 3.0e38f;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    // vertical edge x = xl or xh: dy* = -B dx / C, clamped
+    const float dx = (e ? xh : xl) - mx;
+    const float dy = fminf(fmaxf(-B * dx * iC, yl - my), yh - my);
+    qmin = fminf(qmin, fmaf(dx, fmaf(A, dx, 2.f * B * dy), C * dy * dy));
+    // horizontal edge y = yl or yh: dx* = -B dy / A, clamped
+    const float ey = (e ? yh : yl) - my;
+    const float ex = fminf(fmaxf(-B * ey * iA, xl - mx), xh - mx);
+    qmin = fminf(qmin, fmaf(ex, fmaf(A, ex, 2.f * B * ey), C * ey * ey));
+  }
+  return qmin <= thr;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -536,7 +566,7 @@ cudaError_t launch_preprocess_fwd(const GaussPtrs &g, const Views &vs, fgs_recor
 cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_touched,
                             int64_t n, const Views &vs, uint64_t *keys, uint32_t *vals,
                             int64_t capacity, uint32_t *tile_ranges, int64_t *n_int,
-                            char *ws, const WsLayout &L, cudaStream_t st);
+                            char *ws, const WsLayout &L, uint32_t flags, cudaStream_t st);
 cudaError_t launch_raster_fwd(const fgs_record *records, const uint32_t *vals,
                               const uint32_t *tile_ranges, const Views &vs, float bg0, float bg1,
                               float bg2, float *images, float *final_T, uint32_t *n_processed,

@@ -79,7 +79,7 @@ extern "C" fgs_status fgs_bin_sort_noalloc(const fgs_record *records,
   if (ws == nullptr) return FGS_ERR_CUDA;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (launch_bin_sort(records, tiles_touched, n, vs, keys, vals, capacity, tile_ranges,
-                      n_intersections, ws, L, st) != cudaSuccess)
+                      n_intersections, ws, L, 0u, st) != cudaSuccess)
     return FGS_ERR_CUDA;
   // hand the device status word to the caller's buffer (a device-to-device copy, no host sync)
   if (cudaMemcpyAsync(status, ws + L.header, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) !=

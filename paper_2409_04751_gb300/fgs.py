@@ -28,10 +28,12 @@ FGS_CAM_STEREOGRAPHIC = 2
 FGS_CAM_ORTHOGRAPHIC = 3
 FGS_CAM_EQUIRECTANGULAR = 4
 FGS_CAM_PINHOLE = 5
+# fgs_bin_sort_ex flags
+FGS_BIN_ELLIPSE = 1
 
 EXPORTS = ["fgs_workspace_size", "fgs_total_tiles", "fgs_total_pixels", "fgs_preprocess",
            "fgs_bin_sort", "fgs_rasterize", "fgs_backward", "fgs_backward_raster",
-           "fgs_backward_preprocess", "fgs_bin_sort_noalloc", "fgs_read_status",
+           "fgs_backward_preprocess", "fgs_bin_sort_noalloc", "fgs_bin_sort_ex", "fgs_read_status",
            "fgs_set_instrumentation", "fgs_read_counters", "fgs_set_raster_shape",
            "fgs_status_string"]
 
@@ -84,6 +86,8 @@ def lib():
         L.fgs_backward_preprocess.argtypes = [g_p, cam_p, i32, vp, vp, vp, vp, vp, vp, vp, vp,
                                               ctypes.c_size_t, vp]
         L.fgs_bin_sort_noalloc.argtypes = [vp, vp, i64, cam_p, i32, vp, vp, i64, vp, vp, vp, vp]
+        L.fgs_bin_sort_ex.argtypes = [vp, vp, i64, cam_p, i32, vp, vp, i64, vp, vp, vp,
+                                      ctypes.c_size_t, ctypes.c_uint32, vp]
         L.fgs_read_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int)]
         L.fgs_set_instrumentation.argtypes = [ctypes.c_int]
         L.fgs_set_instrumentation.restype = None
@@ -173,6 +177,16 @@ def fgs_bin_sort(records, tiles_touched, n, cams, keys, vals, capacity, tile_ran
                               _ptr(keys), _ptr(vals), int(capacity), _ptr(tile_ranges),
                               _ptr(n_intersections), _ptr(workspace), int(workspace_bytes),
                               _stream(stream)), "fgs_bin_sort")
+
+
+def fgs_bin_sort_ex(records, tiles_touched, n, cams, keys, vals, capacity, tile_ranges,
+                    n_intersections, workspace, workspace_bytes, flags, stream=None):
+    """fgs_bin_sort with flags (FGS_BIN_ELLIPSE: keep only the pairs whose tile the alpha >=
+    1/255 ellipse reaches)."""
+    _check(lib().fgs_bin_sort_ex(_ptr(records), _ptr(tiles_touched), int(n), cams, len(cams),
+                                 _ptr(keys), _ptr(vals), int(capacity), _ptr(tile_ranges),
+                                 _ptr(n_intersections), _ptr(workspace), int(workspace_bytes),
+                                 int(flags), _stream(stream)), "fgs_bin_sort_ex")
 
 
 def _bg_arg(bg):

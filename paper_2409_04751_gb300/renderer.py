@@ -56,12 +56,17 @@ class FisheyeRenderer:
     """Renders fisheye views of one Gaussian set through libfgs.
 
     capacity: key-buffer size (intersections); grows automatically on overflow when the
-    forward is run with check=True (one host sync per call)."""
+    forward is run with check=True (one host sync per call).
+    binning: "rect" (the tile rect of each footprint, as the method bins) or "ellipse" (only
+    the tiles the alpha >= 1/255 ellipse reaches; same images, shorter tile lists)."""
 
-    def __init__(self, device="cuda", capacity=1 << 20, growth=1.25):
+    def __init__(self, device="cuda", capacity=1 << 20, growth=1.25, binning="rect"):
         self.device = torch.device(device)
         self.capacity = int(capacity)
         self.growth = float(growth)
+        if binning not in ("rect", "ellipse"):
+            raise ValueError("binning is 'rect' or 'ellipse'")
+        self.flags = fgs.FGS_BIN_ELLIPSE if binning == "ellipse" else 0
         self._bufs = {}
 
     def _buf(self, name, numel, dtype):
@@ -90,8 +95,8 @@ class FisheyeRenderer:
             ranges = self._buf("ranges", 2 * tiles, torch.int32)
             nint = self._buf("nint", 1, torch.int64)
             ws = self._buf("ws", ws_bytes, torch.uint8)
-            fgs.fgs_bin_sort(records, tt, n, cams, keys, vals, cap, ranges, nint, ws, ws_bytes,
-                             stream)
+            fgs.fgs_bin_sort_ex(records, tt, n, cams, keys, vals, cap, ranges, nint, ws,
+                                ws_bytes, self.flags, stream)
             if not check:
                 break
             st = fgs.fgs_read_status(ws, stream)
