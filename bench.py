@@ -589,27 +589,33 @@ def run_models(args, dev):
 
 
 def run_exact_binning(args, dev):
-    """The bench workload (500k Gaussians, 1752x1168 at 180 deg) with the rect binning of the
-    method and with the exact ellipse binning (fgs_bin_sort_ex, FGS_BIN_ELLIPSE): intersections
-    (Table 3's axis), fwd and fwd+bwd views/s, same images. Returns a dict for the JSON line."""
+    """The bench workload (500k Gaussians, 1752x1168 at 180 deg) binned and sorted three ways:
+    the rect binning of the method with the per-tile sort (the headline path), the exact ellipse
+    binning (fgs_bin_sort_ex, FGS_BIN_ELLIPSE) and the rect binning with the device-wide onesweep
+    radix sort (FGS_BIN_ONESWEEP). Intersections (Table 3's axis), the bin/sort stage alone, fwd
+    and fwd+bwd views/s; the images of all three are compared. Returns a dict for the JSON line."""
     import torch
     from paper_2409_04751_gb300 import fgs, scenes
-    from paper_2409_04751_gb300.renderer import FisheyeRenderer, scene_to_device
+    from paper_2409_04751_gb300.renderer import FisheyeRenderer, gaussians_of, scene_to_device
 
     scene, cams = scenes.config1()
     gs = scene_to_device(scene, dev)
     cam = cams[0]
+    n = scene["means"].shape[0]
     P = cam["width"] * cam["height"]
     dL = torch.as_tensor(scenes.upstream_grad((3 * P,), 1e-2, seed=35)).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     out = {}
     imgs = {}
-    for binning in ("rect", "ellipse"):
-        r = FisheyeRenderer(dev, capacity=1 << 23, binning=binning)
+    for name, binning, sort in (("rect_tile_sort", "rect", "tile"),
+                                ("ellipse_tile_sort", "ellipse", "tile"),
+                                ("rect_onesweep_sort", "rect", "onesweep")):
+        r = FisheyeRenderer(dev, capacity=1 << 23, binning=binning, sort=sort)
         fr = r.forward(gs, [cam], check=True)
         r.backward(gs, fr, dL, check=True)
-        imgs[binning] = fr.images.clone()
-        tf, tb = [], []
+        imgs[name] = fr.images.clone()
+        ws = r._bufs["ws"]
+        tf, tb, ts = [], [], []
         for _ in range(args.model_reps):
             flush.zero_()
             a, m, b = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -621,18 +627,30 @@ def run_exact_binning(args, dev):
             b.synchronize()
             tf.append(a.elapsed_time(m))
             tb.append(a.elapsed_time(b))
-        st = fgs.fgs_read_status(r._bufs["ws"])
+            # the bin/sort stage alone, on the records of this frame
+            flush.zero_()
+            c, d = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c.record()
+            fgs.fgs_bin_sort_ex(f2.records, f2.tiles_touched, n, f2.cams, f2.keys, f2.vals,
+                                r.capacity, f2.tile_ranges, f2.n_intersections, ws, ws.numel(),
+                                r.flags)
+            d.record()
+            d.synchronize()
+            ts.append(c.elapsed_time(d))
+        st = fgs.fgs_read_status(ws)
         if st != fgs.FGS_OK:
-            raise fgs.FgsError(st, f"binning {binning}")
-        out[binning] = dict(intersections=int(f2.n_intersections.item()),
-                            key_bytes=int(f2.n_intersections.item()) * 12,
-                            fwd_views_per_s=1e3 / float(np.median(tf)),
-                            fwd_bwd_views_per_s=1e3 / float(np.median(tb)))
+            raise fgs.FgsError(st, name)
+        out[name] = dict(intersections=int(f2.n_intersections.item()),
+                         key_bytes=int(f2.n_intersections.item()) * 12,
+                         bin_sort_ms=float(np.median(ts)),
+                         fwd_views_per_s=1e3 / float(np.median(tf)),
+                         fwd_bwd_views_per_s=1e3 / float(np.median(tb)))
+    ref = imgs["rect_tile_sort"]
     return dict(workload=WORKLOAD, **out,
-                images_equal=bool(torch.equal(imgs["rect"], imgs["ellipse"])),
-                note="ellipse = fgs_bin_sort_ex with FGS_BIN_ELLIPSE: only the tiles the alpha "
-                     ">= 1/255 ellipse reaches; the rect binning is the method's and the "
-                     "headline value")
+                images_equal=all(bool(torch.equal(ref, v)) for v in imgs.values()),
+                note="rect_tile_sort is the headline path; ellipse keeps only the tiles the "
+                     "alpha >= 1/255 ellipse reaches; onesweep is the device-wide radix sort "
+                     "of the renderer the method plugs into (same keys)")
 
 
 def run_serving(args, dev):

@@ -121,6 +121,11 @@ typedef struct {
 fgs_status fgs_workspace_size(int64_t n, const fgs_camera *cams, int n_views, int64_t capacity,
                               size_t *bytes);
 
+/* Workspace for fgs_bin_sort_ex with the given flags (fgs_workspace_size = flags 0; only
+ * FGS_BIN_ONESWEEP needs more). */
+fgs_status fgs_workspace_size_ex(int64_t n, const fgs_camera *cams, int n_views, int64_t capacity,
+                                 uint32_t flags, size_t *bytes);
+
 /* Number of 16x16 tiles over all views (global tile ids are view-major, row-major inside a
  * view) and number of pixels over all views. Host-only helpers. */
 int64_t fgs_total_tiles(const fgs_camera *cams, int n_views);
@@ -159,9 +164,14 @@ fgs_status fgs_bin_sort(const fgs_record *records, const uint32_t *tiles_touched
  * Table 3, FlashGS). A dropped pair has alpha < 1/255 at every pixel of its tile, so the images,
  * transmittances and gradients equal those of the rect binning; only the lists are shorter.
  * *n_intersections is then the number of pairs kept (the rect count if it exceeds capacity,
- * with FGS_ERR_CAPACITY); capacity must still hold the rect count. Other flag bits:
+ * with FGS_ERR_CAPACITY); capacity must still hold the rect count. Unknown flag bits:
  * FGS_ERR_INVALID_ARG. */
 #define FGS_BIN_ELLIPSE 1u
+/* flags = FGS_BIN_ONESWEEP sorts the rect pairs with a device-wide onesweep LSD radix sort over
+ * the key bits (the renderer's own sort design) instead of the default per-tile sort; same
+ * output bit for bit. It needs the larger workspace of fgs_workspace_size_ex(..., flags, ...)
+ * and cannot be combined with FGS_BIN_ELLIPSE. */
+#define FGS_BIN_ONESWEEP 2u
 fgs_status fgs_bin_sort_ex(const fgs_record *records, const uint32_t *tiles_touched, int64_t n,
                            const fgs_camera *cams, int n_views, uint64_t *keys, uint32_t *vals,
                            int64_t capacity, uint32_t *tile_ranges, int64_t *n_intersections,

@@ -96,14 +96,21 @@ using namespace fgs;
 
 extern "C" {
 
-fgs_status fgs_workspace_size(int64_t n, const fgs_camera *cams, int n_views, int64_t capacity,
-                              size_t *bytes) {
+fgs_status fgs_workspace_size_ex(int64_t n, const fgs_camera *cams, int n_views,
+                                 int64_t capacity, uint32_t flags, size_t *bytes) {
   Views vs;
   if (bytes == nullptr || n < 0 || capacity <= 0 || capacity > 0xffffffffLL ||
       !build_views(cams, n_views, &vs))
     return FGS_ERR_INVALID_ARG;
-  *bytes = ws_layout((int64_t)n_views * n, capacity, vs.total_tiles).total;
+  if ((flags & ~(uint32_t)(FGS_BIN_ELLIPSE | FGS_BIN_ONESWEEP)) != 0) return FGS_ERR_INVALID_ARG;
+  *bytes = ws_layout((int64_t)n_views * n, capacity, vs.total_tiles,
+                     (flags & FGS_BIN_ONESWEEP) != 0).total;
   return FGS_OK;
+}
+
+fgs_status fgs_workspace_size(int64_t n, const fgs_camera *cams, int n_views, int64_t capacity,
+                              size_t *bytes) {
+  return fgs_workspace_size_ex(n, cams, n_views, capacity, 0u, bytes);
 }
 
 int64_t fgs_total_tiles(const fgs_camera *cams, int n_views) {
@@ -136,13 +143,21 @@ fgs_status fgs_bin_sort_ex(const fgs_record *records, const uint32_t *tiles_touc
   Views vs;
   if (n < 0 || capacity <= 0 || capacity > 0xffffffffLL || !build_views(cams, n_views, &vs))
     return FGS_ERR_INVALID_ARG;
-  if ((flags & ~(uint32_t)FGS_BIN_ELLIPSE) != 0) return FGS_ERR_INVALID_ARG;
+  if ((flags & ~(uint32_t)(FGS_BIN_ELLIPSE | FGS_BIN_ONESWEEP)) != 0) return FGS_ERR_INVALID_ARG;
+  // the onesweep sort bins by the rect only
+  if ((flags & FGS_BIN_ELLIPSE) && (flags & FGS_BIN_ONESWEEP)) return FGS_ERR_INVALID_ARG;
+  const bool onesweep = (flags & FGS_BIN_ONESWEEP) != 0;
   if ((int64_t)n_views * n > 0xffffffffLL) return FGS_ERR_INVALID_ARG;
   if (!keys || !vals || !tile_ranges || !n_intersections || !workspace) return FGS_ERR_INVALID_ARG;
   if (n > 0 && (!records || !tiles_touched || !aligned(records, 16))) return FGS_ERR_INVALID_ARG;
   if (!aligned(workspace, 256)) return FGS_ERR_INVALID_ARG;
-  const WsLayout L = ws_layout((int64_t)n_views * n, capacity, vs.total_tiles);
+  const WsLayout L = ws_layout((int64_t)n_views * n, capacity, vs.total_tiles, onesweep);
   if (workspace_bytes < L.total) return FGS_ERR_INVALID_ARG;
+  if (onesweep)
+    return cuda_status(launch_bin_sort_onesweep(records, tiles_touched, n, vs, keys, vals,
+                                                capacity, tile_ranges, n_intersections,
+                                                reinterpret_cast<char *>(workspace), L,
+                                                reinterpret_cast<cudaStream_t>(stream)));
   return cuda_status(launch_bin_sort(records, tiles_touched, n, vs, keys, vals, capacity,
                                      tile_ranges, n_intersections,
                                      reinterpret_cast<char *>(workspace), L, flags,

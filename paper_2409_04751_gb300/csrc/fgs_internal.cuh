@@ -89,6 +89,11 @@ constexpr int EMIT_ITEMS = 4;
 constexpr int EMIT_PART = EMIT_THREADS * EMIT_ITEMS;  // records per scan partition
 constexpr int EMIT_CHUNK = 1024;                      // (record, tile) pairs per emission CTA
 constexpr int TSCAN_PART = 1024;                     // tiles per partition of the tile scan
+// device-wide onesweep radix sort (onesweep.cu)
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_PART = SORT_THREADS * SORT_ITEMS;  // keys per sort partition
+constexpr int SORT_MAX_PASSES = 8;
 // Segment-size classes of the per-tile sort: segments of at most SEG_CAP0 pairs are sorted
 // in shared memory by CTAs of 256 threads, longer ones by CTAs of 512 threads (in shared memory
 // up to SEG_CAP1 pairs, beyond that in SEG_CAP1-pair chunks through global memory).
@@ -97,17 +102,20 @@ constexpr int SEG_CAP1 = 8192;
 constexpr int G2D_STRIDE = 12;                        // floats per record of screen-space grads
 
 struct WsLayout {
-  size_t header, scan_lb, g2d, vis_rec, vis_off, tile_lb, seg_list, words, chunk_first, total;
-  int64_t scan_parts, tile_parts, chunks, total_tiles;
+  size_t header, scan_lb, g2d, vis_rec, vis_off, tile_lb, seg_list, words, chunk_first;
+  size_t sort_hist, sort_lb, alt_vals;  // the onesweep sort's regions (0 bytes unless requested)
+  size_t total;
+  int64_t scan_parts, tile_parts, chunks, total_tiles, sort_parts;
 };
 
 __host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace layout. Regions that depend on the record count only come first, so the
 // rasterizer and the backward can locate them without knowing the key capacity or the tile
-// count; with_g2d = false leaves out the backward's accumulator (used by the sort-only variant).
+// count; with_g2d = false leaves out the backward's accumulator (used by the sort-only variant);
+// with_onesweep adds the regions of the device-wide radix sort (onesweep.cu).
 constexpr WsLayout ws_layout_ex(int64_t n_records, int64_t capacity, int64_t total_tiles,
-                                bool with_g2d) {
+                                bool with_g2d, bool with_onesweep = false) {
   WsLayout L{};
   const int64_t R = n_records > 0 ? n_records : 1;
   const int64_t T = total_tiles > 0 ? total_tiles : 1;
@@ -125,12 +133,21 @@ constexpr WsLayout ws_layout_ex(int64_t n_records, int64_t capacity, int64_t tot
   L.seg_list = o; o += align256(sizeof(uint32_t) * 2 * (size_t)T);
   L.words = o; o += align256(sizeof(uint64_t) * (size_t)capacity);
   L.chunk_first = o; o += align256(sizeof(uint32_t) * ((size_t)L.chunks + 2));
+  L.sort_parts = (capacity + SORT_PART - 1) / SORT_PART;
+  L.sort_hist = o;
+  if (with_onesweep) o += align256(sizeof(uint32_t) * SORT_MAX_PASSES * 256);
+  L.sort_lb = o;
+  if (with_onesweep)
+    o += align256(sizeof(uint64_t) * 256 * 2 * (size_t)(L.sort_parts > 0 ? L.sort_parts : 1));
+  L.alt_vals = o;
+  if (with_onesweep) o += align256(sizeof(uint32_t) * ((size_t)capacity + 4));
   L.total = o;
   return L;
 }
 
-inline WsLayout ws_layout(int64_t n_records, int64_t capacity, int64_t total_tiles) {
-  return ws_layout_ex(n_records, capacity, total_tiles, true);
+inline WsLayout ws_layout(int64_t n_records, int64_t capacity, int64_t total_tiles,
+                          bool with_onesweep = false) {
+  return ws_layout_ex(n_records, capacity, total_tiles, true, with_onesweep);
 }
 
 __device__ __forceinline__ void set_status(uint32_t *status, uint32_t code) {
@@ -567,6 +584,11 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
                             int64_t n, const Views &vs, uint64_t *keys, uint32_t *vals,
                             int64_t capacity, uint32_t *tile_ranges, int64_t *n_int,
                             char *ws, const WsLayout &L, uint32_t flags, cudaStream_t st);
+cudaError_t launch_bin_sort_onesweep(const fgs_record *records, const uint32_t *tiles_touched,
+                                     int64_t n, const Views &vs, uint64_t *keys,
+                                     uint32_t *vals, int64_t capacity, uint32_t *tile_ranges,
+                                     int64_t *n_int, char *ws, const WsLayout &L,
+                                     cudaStream_t st);
 cudaError_t launch_raster_fwd(const fgs_record *records, const uint32_t *vals,
                               const uint32_t *tile_ranges, const Views &vs, float bg0, float bg1,
                               float bg2, float *images, float *final_T, uint32_t *n_processed,

@@ -30,8 +30,9 @@ FGS_CAM_EQUIRECTANGULAR = 4
 FGS_CAM_PINHOLE = 5
 # fgs_bin_sort_ex flags
 FGS_BIN_ELLIPSE = 1
+FGS_BIN_ONESWEEP = 2
 
-EXPORTS = ["fgs_workspace_size", "fgs_total_tiles", "fgs_total_pixels", "fgs_preprocess",
+EXPORTS = ["fgs_workspace_size", "fgs_workspace_size_ex", "fgs_total_tiles", "fgs_total_pixels", "fgs_preprocess",
            "fgs_bin_sort", "fgs_rasterize", "fgs_backward", "fgs_backward_raster",
            "fgs_backward_preprocess", "fgs_bin_sort_noalloc", "fgs_bin_sort_ex", "fgs_read_status",
            "fgs_set_instrumentation", "fgs_read_counters", "fgs_set_raster_shape",
@@ -70,6 +71,8 @@ def lib():
         vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
         cam_p, g_p = ctypes.POINTER(FgsCamera), ctypes.POINTER(FgsGaussians)
         L.fgs_workspace_size.argtypes = [i64, cam_p, i32, i64, ctypes.POINTER(ctypes.c_size_t)]
+        L.fgs_workspace_size_ex.argtypes = [i64, cam_p, i32, i64, ctypes.c_uint32,
+                                            ctypes.POINTER(ctypes.c_size_t)]
         L.fgs_total_tiles.argtypes = [cam_p, i32]
         L.fgs_total_tiles.restype = i64
         L.fgs_total_pixels.argtypes = [cam_p, i32]
@@ -151,10 +154,14 @@ def gaussians(means, scales, quats, opacities, sh, sh_degree):
                         int(sh_degree))
 
 
-def fgs_workspace_size(n, cams, capacity) -> int:
+def fgs_workspace_size(n, cams, capacity, flags=0) -> int:
     out = ctypes.c_size_t(0)
-    _check(lib().fgs_workspace_size(int(n), cams, len(cams), int(capacity), ctypes.byref(out)),
-           "fgs_workspace_size")
+    if flags:
+        _check(lib().fgs_workspace_size_ex(int(n), cams, len(cams), int(capacity), int(flags),
+                                           ctypes.byref(out)), "fgs_workspace_size_ex")
+    else:
+        _check(lib().fgs_workspace_size(int(n), cams, len(cams), int(capacity),
+                                        ctypes.byref(out)), "fgs_workspace_size")
     return int(out.value)
 
 

@@ -58,15 +58,21 @@ class FisheyeRenderer:
     capacity: key-buffer size (intersections); grows automatically on overflow when the
     forward is run with check=True (one host sync per call).
     binning: "rect" (the tile rect of each footprint, as the method bins) or "ellipse" (only
-    the tiles the alpha >= 1/255 ellipse reaches; same images, shorter tile lists)."""
+    the tiles the alpha >= 1/255 ellipse reaches; same images, shorter tile lists).
+    sort: "tile" (the per-tile sort, default) or "onesweep" (the device-wide radix sort; rect
+    binning only); same keys."""
 
-    def __init__(self, device="cuda", capacity=1 << 20, growth=1.25, binning="rect"):
+    def __init__(self, device="cuda", capacity=1 << 20, growth=1.25, binning="rect",
+                 sort="tile"):
         self.device = torch.device(device)
         self.capacity = int(capacity)
         self.growth = float(growth)
-        if binning not in ("rect", "ellipse"):
-            raise ValueError("binning is 'rect' or 'ellipse'")
-        self.flags = fgs.FGS_BIN_ELLIPSE if binning == "ellipse" else 0
+        if binning not in ("rect", "ellipse") or sort not in ("tile", "onesweep"):
+            raise ValueError("binning is 'rect' or 'ellipse', sort 'tile' or 'onesweep'")
+        if binning == "ellipse" and sort == "onesweep":
+            raise ValueError("the onesweep sort bins by the rect")
+        self.flags = ((fgs.FGS_BIN_ELLIPSE if binning == "ellipse" else 0) |
+                      (fgs.FGS_BIN_ONESWEEP if sort == "onesweep" else 0))
         self._bufs = {}
 
     def _buf(self, name, numel, dtype):
@@ -89,7 +95,7 @@ class FisheyeRenderer:
         fgs.fgs_preprocess(g, cams, records, tt, stream)
         while True:
             cap = self.capacity
-            ws_bytes = fgs.fgs_workspace_size(n, cams, cap)
+            ws_bytes = fgs.fgs_workspace_size(n, cams, cap, self.flags)
             keys = self._buf("keys", cap, torch.int64)
             vals = self._buf("vals", cap + 4, torch.int32)
             ranges = self._buf("ranges", 2 * tiles, torch.int32)

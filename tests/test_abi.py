@@ -90,3 +90,14 @@ def test_invalid_arguments_rejected_before_launch(lib):
                             256, 256, 256, 256, None, 256, 256, 0, 256, 256, 256, 256, 256, 256,
                             1 << 20, None) == INV
     assert fgs.status_string(fgs.FGS_ERR_CAPACITY).startswith("more intersections")
+    # bin_sort_ex flags: unknown bits and ellipse + onesweep rejected; onesweep needs the larger
+    # workspace
+    a = fgs.fgs_workspace_size(1000, cams, 1 << 16)
+    b = fgs.fgs_workspace_size(1000, cams, 1 << 16, fgs.FGS_BIN_ONESWEEP)
+    assert b > a and fgs.fgs_workspace_size(1000, cams, 1 << 16, fgs.FGS_BIN_ELLIPSE) == a
+    assert lib.fgs_workspace_size_ex(10, cams, 1, 10, 4, ctypes.byref(out)) == INV
+    for fl in (4, fgs.FGS_BIN_ELLIPSE | fgs.FGS_BIN_ONESWEEP):
+        assert lib.fgs_bin_sort_ex(256, 256, 10, cams, 1, 256, 256, 100, 256, 256, 256, 1 << 30,
+                                   fl, None) == INV
+    assert lib.fgs_bin_sort_ex(256, 256, 10, cams, 1, 256, 256, 100, 256, 256, 256, 1 << 12,
+                               fgs.FGS_BIN_ONESWEEP, None) == INV  # workspace too small

@@ -1,5 +1,6 @@
 """GPU bin/sort (fgs_bin_sort: scan, per-tile pair count, tile scan, bucket scatter, per-tile
-segment sort) against the oracle's key builder, bit for bit, on the same seeded synthetic
+segment sort; and fgs_bin_sort_ex with FGS_BIN_ONESWEEP: key emission and device-wide onesweep
+radix sort) against the oracle's key builder, bit for bit, on the same seeded synthetic
 records. The cases reach every segment-size class of the per-tile sort: buckets sorted in shared
 memory by 256- and 512-thread CTAs, and buckets longer than the largest shared-memory class,
 sorted in chunks through global memory."""
@@ -48,7 +49,10 @@ def _records(rng, n, cams_py, p_empty=0.2, max_ext=3, tie_frac=0.3, big_frac=0.0
     return rec, rect, depth, tt.astype(np.uint32)
 
 
-def _run(rec, tt, n, cams_py, capacity):
+SORTS = [0, fgs.FGS_BIN_ONESWEEP]  # the per-tile sort and the device-wide onesweep sort
+
+
+def _run(rec, tt, n, cams_py, capacity, flags=0):
     dev = torch.device("cuda:0")
     cams = fgs.cameras(cams_py)
     R = rec.shape[0]
@@ -59,9 +63,9 @@ def _run(rec, tt, n, cams_py, capacity):
     tiles = fgs.fgs_total_tiles(cams)
     ranges = torch.full((2 * tiles,), -7, dtype=torch.int32, device=dev)
     nint = torch.zeros(1, dtype=torch.int64, device=dev)
-    wsb = fgs.fgs_workspace_size(n, cams, capacity)
+    wsb = fgs.fgs_workspace_size(n, cams, capacity, flags)
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
-    fgs.fgs_bin_sort(records, ttd, n, cams, keys, vals, capacity, ranges, nint, ws, wsb)
+    fgs.fgs_bin_sort_ex(records, ttd, n, cams, keys, vals, capacity, ranges, nint, ws, wsb, flags)
     st = fgs.fgs_read_status(ws)
     return dict(keys=keys.cpu().numpy().view(np.uint64), vals=vals.cpu().numpy().view(np.uint32),
                 ranges=ranges.cpu().numpy().view(np.uint32).reshape(-1, 2), n=int(nint.item()),
@@ -98,13 +102,14 @@ def _oracle(rect, depth, n, cams_py):
     # every pair at one depth: the order is the record order alone
     (9000, [(16, 16)], 14, dict(tie_frac=1.0)),
 ])
-def test_binsort_bit_exact(cuda_device, n, sizes, seed, kw):
+@pytest.mark.parametrize("flags", SORTS)
+def test_binsort_bit_exact(cuda_device, n, sizes, seed, kw, flags):
     cams_py = _cams(sizes)
     rng = np.random.default_rng(seed)
     rec, rect, depth, tt = _records(rng, n, cams_py, **kw)
     m = int(tt.astype(np.int64).sum())
     cap = max(m, 1) + 37
-    out = _run(rec, tt, n, cams_py, cap)
+    out = _run(rec, tt, n, cams_py, cap, flags)
     assert out["status"] == 0 and out["n"] == m
     k, v, rg = _oracle(rect, depth, n, cams_py)
     assert np.array_equal(out["keys"][:m], k)
@@ -112,21 +117,23 @@ def test_binsort_bit_exact(cuda_device, n, sizes, seed, kw):
     assert np.array_equal(out["ranges"], rg)
 
 
-def test_binsort_capacity_overflow_reports_status(cuda_device):
+@pytest.mark.parametrize("flags", SORTS)
+def test_binsort_capacity_overflow_reports_status(cuda_device, flags):
     cams_py = _cams([(256, 256)])
     rng = np.random.default_rng(7)
     rec, rect, depth, tt = _records(rng, 4000, cams_py, max_ext=5)
     m = int(tt.astype(np.int64).sum())
-    out = _run(rec, tt, 4000, cams_py, m // 2)
+    out = _run(rec, tt, 4000, cams_py, m // 2, flags)
     assert out["status"] == fgs.FGS_ERR_CAPACITY
     assert out["n"] == m  # the true count, so the caller can grow the buffers
     # a repeat with enough room succeeds (the status word is reset by the call)
-    out = _run(rec, tt, 4000, cams_py, m)
+    out = _run(rec, tt, 4000, cams_py, m, flags)
     assert out["status"] == 0
 
 
 @pytest.mark.slow
-def test_binsort_full_size_bit_exact(cuda_device):
+@pytest.mark.parametrize("flags", SORTS)
+def test_binsort_full_size_bit_exact(cuda_device, flags):
     """~14M pairs over the 1752x1168 tile grid (the intersection count of the 500k-Gaussian,
     180-degree workload), bit-exact against the oracle."""
     cams_py = _cams([(1752, 1168)])
@@ -135,7 +142,7 @@ def test_binsort_full_size_bit_exact(cuda_device):
                                     big_frac=0.0005, tie_frac=0.05)
     m = int(tt.astype(np.int64).sum())
     assert m > 8_000_000
-    out = _run(rec, tt, 500_000, cams_py, m + 4096)
+    out = _run(rec, tt, 500_000, cams_py, m + 4096, flags)
     assert out["status"] == 0 and out["n"] == m
     k, v, rg = _oracle(rect, depth, 500_000, cams_py)
     assert np.array_equal(out["keys"][:m], k)
