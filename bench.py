@@ -423,6 +423,9 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_models:
         models = run_models(args, dev)
         exact = run_exact_binning(args, dev)
+    training = None
+    if rank == 0 and world == 1 and not args.no_training:
+        training = run_training(args, dev)
 
     # preprocess; scan, count, tile scan, scatter, two segment-sort classes; raster fwd; raster
     # bwd; preprocess bwd
@@ -446,6 +449,7 @@ def run_gpu(args):
         serving=serving,
         camera_models=models,
         exact_binning=exact,
+        training=training,
         e2e=dict(value=world * args.steps / e2e_s, unit="views/s", h2d_bytes_per_step=h2d,
                  d2h_bytes_per_step=d2h),
         gpu_launches=launches_per_step * args.steps,
@@ -653,6 +657,47 @@ def run_exact_binning(args, dev):
                      "of the renderer the method plugs into (same keys)")
 
 
+def run_training(args, dev):
+    """Training steps (Sec. 5.1; §8(f) rank 4): 500k Gaussians (the bench scene, perturbed),
+    8 views of 1752x1168 at 180 deg whose targets are renders of the unperturbed scene; each step
+    is one CUDA-graph replay of fwd over all views -> L1 loss -> bwd -> Adam. Returns a dict for
+    the JSON line."""
+    import torch
+    from paper_2409_04751_gb300 import scenes
+    from paper_2409_04751_gb300.renderer import FisheyeRenderer, scene_to_device
+    from paper_2409_04751_gb300.train import Trainer, raw_from_scene
+
+    scene, _ = scenes.config1()
+    cams = [scenes.pose_camera(1752, 1168, 180.0, seed=7000 + k) for k in range(args.train_views)]
+    r = FisheyeRenderer(dev, capacity=1 << 24)
+    targets = r.forward(scene_to_device(scene, dev), cams).images.clone()
+    del r
+    rng = np.random.default_rng(77)
+    raw = raw_from_scene(scene)
+    raw["means"] = raw["means"] + rng.normal(0, 0.005, raw["means"].shape)
+    raw["log_scales"] = raw["log_scales"] + 0.2
+    raw["sh"] = raw["sh"] + rng.normal(0, 0.05, raw["sh"].shape)
+    tr = Trainer(raw, cams, targets, device=dev)
+    tr.step()
+    first = tr.check()
+    for _ in range(3):
+        tr.step()
+    tr.check()
+    # graph replays run on the current stream: time them there
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.train_steps):
+        tr.step()
+    b.record()
+    b.synchronize()
+    last = tr.check()
+    ms = a.elapsed_time(b) / args.train_steps
+    return dict(workload=f"500k Gaussians SH3, {len(cams)} views 1752x1168 @180deg, L1 + Adam, "
+                         "one CUDA-graph replay per step", views=len(cams), ms_per_step=ms,
+                steps_per_s=1e3 / ms, views_per_s=len(cams) * 1e3 / ms,
+                loss_first=first, loss_last=last, steps=int(tr.step_count.item()))
+
+
 def run_serving(args, dev):
     """Continuous-batching server vs plain one-request-at-a-time serving: 4 resident scenes
     (200k, 500k, 1M, 2M Gaussians, SH 3), Poisson arrivals, random pose, square resolution
@@ -699,6 +744,9 @@ def main():
     ap.add_argument("--no-models", action="store_true",
                     help="skip the fwd+bwd timing of every camera model and of the exact binning")
     ap.add_argument("--model-reps", type=int, default=5)
+    ap.add_argument("--no-training", action="store_true", help="skip the training-step timing")
+    ap.add_argument("--train-views", type=int, default=8)
+    ap.add_argument("--train-steps", type=int, default=20)
     ap.add_argument("--serve-rates", type=int, nargs="*", default=[200, 500, 1000, 2000])
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--serve-slots", type=int, default=3)

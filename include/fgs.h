@@ -206,6 +206,38 @@ fgs_status fgs_backward(const fgs_gaussians *g, const fgs_camera *cams, int n_vi
                         float *d_quats, float *d_opacities, float *d_sh, void *workspace,
                         size_t workspace_bytes, fgs_stream stream);
 
+/* Training (Sec. 5.1 "Optimization": the loss, optimiser and hyperparameters of the renderer
+ * the method plugs into - Adam on the per-Gaussian parameters).
+ *
+ * fgs_loss_l1: L = scale * sum_i |images_i - targets_i| into *loss (DEVICE float, reset by the
+ * call) and dL_dimages_i = scale * sign(images_i - targets_i) (0 where equal); n floats.
+ *
+ * fgs_adam_step: one Adam step (Kingma & Ba, Algorithm 1; bias-corrected moments) over up to
+ * FGS_ADAM_MAX_GROUPS parameter tensors in one launch. Per group: raw parameters (updated in
+ * place), the gradient of the ACTIVATED parameters (as fgs_backward writes it), the two moment
+ * buffers (zero before step 1), and the activation act = raw (FGS_ACT_NONE), exp(raw)
+ * (FGS_ACT_EXP, for scales) or 1 / (1 + exp(-raw)) (FGS_ACT_SIGMOID, for opacities); the
+ * gradient is chained through it at the current raw value, and act(new raw) is written to `act`
+ * (NULL or == raw: not written). step: DEVICE int64 holding the number of steps taken (0
+ * before the first); the call advances it on the device and uses the new value t in the bias
+ * correction, so the call can be captured in a CUDA graph and replayed. All other pointers of
+ * a group are DEVICE, FP32, `count` elements each; the group array itself is HOST memory. */
+#define FGS_ADAM_MAX_GROUPS 8
+typedef enum { FGS_ACT_NONE = 0, FGS_ACT_EXP = 1, FGS_ACT_SIGMOID = 2 } fgs_activation;
+typedef struct {
+  float *raw;
+  float *act;
+  const float *grad;
+  float *m, *v;
+  int64_t count;
+  int32_t activation; /* fgs_activation */
+  float lr;
+} fgs_adam_group;
+fgs_status fgs_loss_l1(const float *images, const float *targets, float *dL_dimages, int64_t n,
+                       float scale, float *loss, fgs_stream stream);
+fgs_status fgs_adam_step(const fgs_adam_group *groups, int n_groups, double beta1,
+                         double beta2, float eps, int64_t *step, fgs_stream stream);
+
 /* fgs_bin_sort for callers that cannot allocate device memory (the paper has no counterpart:
  * this is a deployment variant). Plugins running inside a host application that owns the GPU
  * memory budget, and real-time loops that must never call cudaMalloc / cudaFree (which can

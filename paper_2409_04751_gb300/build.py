@@ -12,7 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libfgs.so")
-SOURCES = ["api.cu", "preprocess.cu", "binsort.cu", "onesweep.cu", "raster.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "preprocess.cu", "binsort.cu", "onesweep.cu", "raster.cu", "noalloc.cu",
+           "train.cu"]
 HEADERS = ["fgs_internal.cuh", "scan.cuh", os.path.join("..", "..", "include", "fgs.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

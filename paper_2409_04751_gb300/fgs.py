@@ -34,7 +34,8 @@ FGS_BIN_ONESWEEP = 2
 
 EXPORTS = ["fgs_workspace_size", "fgs_workspace_size_ex", "fgs_total_tiles", "fgs_total_pixels", "fgs_preprocess",
            "fgs_bin_sort", "fgs_rasterize", "fgs_backward", "fgs_backward_raster",
-           "fgs_backward_preprocess", "fgs_bin_sort_noalloc", "fgs_bin_sort_ex", "fgs_read_status",
+           "fgs_backward_preprocess", "fgs_bin_sort_noalloc", "fgs_bin_sort_ex", "fgs_loss_l1",
+           "fgs_adam_step", "fgs_read_status",
            "fgs_set_instrumentation", "fgs_read_counters", "fgs_set_raster_shape",
            "fgs_status_string"]
 
@@ -49,6 +50,16 @@ class FgsGaussians(ctypes.Structure):
     _fields_ = [("means", ctypes.c_void_p), ("scales", ctypes.c_void_p),
                 ("quats", ctypes.c_void_p), ("opacities", ctypes.c_void_p),
                 ("sh", ctypes.c_void_p), ("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32)]
+
+
+ADAM_MAX_GROUPS = 8
+FGS_ACT_NONE, FGS_ACT_EXP, FGS_ACT_SIGMOID = 0, 1, 2
+
+
+class FgsAdamGroup(ctypes.Structure):
+    _fields_ = [("raw", ctypes.c_void_p), ("act", ctypes.c_void_p), ("grad", ctypes.c_void_p),
+                ("m", ctypes.c_void_p), ("v", ctypes.c_void_p), ("count", ctypes.c_int64),
+                ("activation", ctypes.c_int32), ("lr", ctypes.c_float)]
 
 
 class FgsError(RuntimeError):
@@ -73,6 +84,9 @@ def lib():
         L.fgs_workspace_size.argtypes = [i64, cam_p, i32, i64, ctypes.POINTER(ctypes.c_size_t)]
         L.fgs_workspace_size_ex.argtypes = [i64, cam_p, i32, i64, ctypes.c_uint32,
                                             ctypes.POINTER(ctypes.c_size_t)]
+        L.fgs_loss_l1.argtypes = [vp, vp, vp, i64, ctypes.c_float, vp, vp]
+        L.fgs_adam_step.argtypes = [ctypes.POINTER(FgsAdamGroup), i32, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_float, vp, vp]
         L.fgs_total_tiles.argtypes = [cam_p, i32]
         L.fgs_total_tiles.restype = i64
         L.fgs_total_pixels.argtypes = [cam_p, i32]
@@ -194,6 +208,33 @@ def fgs_bin_sort_ex(records, tiles_touched, n, cams, keys, vals, capacity, tile_
                                  _ptr(keys), _ptr(vals), int(capacity), _ptr(tile_ranges),
                                  _ptr(n_intersections), _ptr(workspace), int(workspace_bytes),
                                  int(flags), _stream(stream)), "fgs_bin_sort_ex")
+
+
+def fgs_loss_l1(images, targets, dL_dimages, n, scale, loss, stream=None):
+    _check(lib().fgs_loss_l1(_ptr(images), _ptr(targets), _ptr(dL_dimages), int(n), float(scale),
+                             _ptr(loss), _stream(stream)), "fgs_loss_l1")
+
+
+def adam_groups(groups):
+    """ctypes array of FgsAdamGroup from dicts (raw, act, grad, m, v tensors; activation; lr)."""
+    arr = (FgsAdamGroup * len(groups))()
+    for k, g in enumerate(groups):
+        arr[k].raw = _ptr(g["raw"])
+        arr[k].act = _ptr(g["act"]) if g.get("act") is not None else None
+        arr[k].grad = _ptr(g["grad"])
+        arr[k].m = _ptr(g["m"])
+        arr[k].v = _ptr(g["v"])
+        arr[k].count = int(g["raw"].numel())
+        arr[k].activation = int(g.get("activation", FGS_ACT_NONE))
+        arr[k].lr = float(g["lr"])
+    return arr
+
+
+def fgs_adam_step(groups, beta1, beta2, eps, step, stream=None):
+    """groups: ctypes array from adam_groups(); step: device int64 tensor [1], the number of
+    steps taken (advanced by the call)."""
+    _check(lib().fgs_adam_step(groups, len(groups), float(beta1), float(beta2), float(eps),
+                               _ptr(step), _stream(stream)), "fgs_adam_step")
 
 
 def _bg_arg(bg):
