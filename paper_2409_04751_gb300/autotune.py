@@ -14,6 +14,7 @@ import torch
 from . import fgs
 
 SHAPES = (1, 2, 4)
+BWD_SHAPES = (1, 2, 4, 8)  # the backward also has a one-warp-per-tile shape
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tuning.json")
 
 
@@ -71,10 +72,10 @@ def tune_raster(renderer, gs, frame, dL_dimages, reps=3, use_cache=True):
     best_f = min(SHAPES, key=lambda s: ms[f"fwd{s}"])
     fgs.fgs_set_raster_shape(best_f, 2)
     fwd()  # the backward reads the forward's per-pixel state
-    for s in SHAPES:
+    for s in BWD_SHAPES:
         fgs.fgs_set_raster_shape(best_f, s)
         ms[f"bwd{s}"] = _time(bwd, reps)
-    best_b = min(SHAPES, key=lambda s: ms[f"bwd{s}"])
+    best_b = min(BWD_SHAPES, key=lambda s: ms[f"bwd{s}"])
     fgs.fgs_set_raster_shape(best_f, best_b)
     # leave the frame's buffers as a plain forward + backward would
     fwd()

@@ -272,7 +272,8 @@ void fgs_set_instrumentation(int on) { g_instrument = on ? 1 : 0; }
 
 fgs_status fgs_set_raster_shape(int fwd_pixels_per_thread, int bwd_pixels_per_thread) {
   auto ok = [](int v) { return v == 1 || v == 2 || v == 4; };
-  if (!ok(fwd_pixels_per_thread) || !ok(bwd_pixels_per_thread)) return FGS_ERR_INVALID_ARG;
+  if (!ok(fwd_pixels_per_thread) || !(ok(bwd_pixels_per_thread) || bwd_pixels_per_thread == 8))
+    return FGS_ERR_INVALID_ARG;
   g_raster_shape[0] = fwd_pixels_per_thread;
   g_raster_shape[1] = bwd_pixels_per_thread;
   return FGS_OK;

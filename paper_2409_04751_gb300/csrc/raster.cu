@@ -31,7 +31,7 @@ constexpr int TILE_PIX = TILE * TILE;  // 256 pixels per tile
 // small and need a small shared-memory footprint to keep enough of them resident
 template <int PPT>
 struct Batch {
-  static constexpr int N = PPT == 4 ? 128 : 256;
+  static constexpr int N = PPT == 8 ? 64 : (PPT == 4 ? 128 : 256);
 };
 constexpr uint32_t REC_BYTES = sizeof(fgs_record);
 static_assert(REC_BYTES == 48, "record size");
@@ -610,6 +610,7 @@ cudaError_t launch_raster_bwd(const fgs_record *records, const uint32_t *vals,
     return e;
   switch (raster_shape(1)) {
     case 1: return bwd_launch<1>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, hdr, st);
+    case 8: return bwd_launch<8>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, hdr, st);
     case 4: return bwd_launch<4>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, hdr, st);
     default: return bwd_launch<2>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, hdr, st);
   }
