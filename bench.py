@@ -426,6 +426,9 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_models:
         models = run_models(args, dev)
         exact = run_exact_binning(args, dev)
+    large = None
+    if rank == 0 and world == 1 and not args.no_large:
+        large = run_large_scene(args, dev)
     training = None
     if rank == 0 and world == 1 and not args.no_training:
         training = run_training(args, dev)
@@ -452,6 +455,7 @@ def run_gpu(args):
         serving=serving,
         camera_models=models,
         exact_binning=exact,
+        large_scene=large,
         training=training,
         e2e=dict(value=world * args.steps / e2e_s, unit="views/s", h2d_bytes_per_step=h2d,
                  d2h_bytes_per_step=d2h),
@@ -593,6 +597,47 @@ def run_models(args, dev):
                          ms_per_view=ms, intersections=int(f2.n_intersections.item()))
     return dict(workload="500k Gaussians SH3, fwd+bwd, one view per call, every camera model",
                 models=out)
+
+
+def run_large_scene(args, dev):
+    """Large-scene forward throughput: 3M Gaussians in a 20 x 20 x 5 box (log-scales
+    N(-4, 0.7), SH degree 3), 2048 x 2048 at 190 degrees, `--large-poses` random poses inside
+    the box, each a single-view forward (preprocess -> bin/sort -> rasterize) timed with CUDA
+    events, L2 flushed before each. Returns a dict for the JSON line."""
+    import torch
+    from paper_2409_04751_gb300 import fgs, scenes
+    from paper_2409_04751_gb300.renderer import FisheyeRenderer, scene_to_device
+
+    scene, cams = scenes.config2(n_poses=args.large_poses)
+    gs = scene_to_device(scene, dev)
+    del scene
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    r = FisheyeRenderer(dev, capacity=32_000_000)
+    inter = []
+    for cam in cams:  # sizing pass (grows the key buffers if a pose needs it), untimed
+        fr = r.forward(gs, [cam], check=True)
+        inter.append(int(fr.n_intersections.item()))
+    ts = []
+    for cam in cams:
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        r.forward(gs, [cam], check=False)
+        b.record()
+        ts.append((a, b))
+    torch.cuda.synchronize()
+    st = fgs.fgs_read_status(r._bufs["ws"])
+    if st != fgs.FGS_OK:
+        raise fgs.FgsError(st, "large scene")
+    ms = np.array([a.elapsed_time(b) for a, b in ts])
+    P = 2048 * 2048
+    return dict(workload="3M Gaussians SH3 in a 20x20x5 box, 2048x2048 @190deg, "
+                         f"{len(cams)} poses inside the box, single-view forward per pose",
+                views_per_s=len(cams) / (ms.sum() / 1e3),
+                mpix_per_s=len(cams) * P / (ms.sum() / 1e3) / 1e6,
+                ms_p50=float(np.percentile(ms, 50)), ms_p99=float(np.percentile(ms, 99)),
+                ms_max=float(ms.max()), intersections_mean=float(np.mean(inter)),
+                intersections_max=int(max(inter)), l2="flushed before each pose")
 
 
 def run_exact_binning(args, dev):
@@ -747,6 +792,9 @@ def main():
     ap.add_argument("--no-models", action="store_true",
                     help="skip the fwd+bwd timing of every camera model and of the exact binning")
     ap.add_argument("--model-reps", type=int, default=5)
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 3M-Gaussian 2048x2048 @190deg forward timing")
+    ap.add_argument("--large-poses", type=int, default=100)
     ap.add_argument("--no-training", action="store_true", help="skip the training-step timing")
     ap.add_argument("--train-views", type=int, default=8)
     ap.add_argument("--train-steps", type=int, default=20)

@@ -79,3 +79,27 @@ def records_np(frame_records, R):
     rect = f[:, 10:12].copy().view(np.uint16).reshape(R, 4)
     return dict(xy=f[:, 0:2], conic=f[:, 2:5], opacity=f[:, 5], rgb=f[:, 6:9], depth=f[:, 9],
                 depth_bits=f[:, 9].copy().view(np.uint32), rect=rect.astype(np.int32))
+
+
+def rows_near_pixels(G, pixels, width, height):
+    """Ascending indices of the visible oracle rows whose FP64 bounding box (the oracle's own
+    prefilter: |p - xy| <= ext per axis, pixel centres at +0.5) contains at least one of the
+    given pixels, widened by one pixel per side. Rendering those rows alone gives the same
+    pixels: every other row is skipped by the oracle's box test anyway, and keeping the rows
+    in ascending order keeps the index tie-break. Lets the oracle render sampled pixels of a
+    multi-million-Gaussian scene without scanning every row per pixel."""
+    F = oracle.F
+    pix = np.asarray(pixels, np.int64).reshape(-1, 2)
+    occ = np.zeros((height + 1, width + 1), np.int64)
+    occ[pix[:, 1] + 1, pix[:, 0] + 1] = 1
+    sat = occ.cumsum(0).cumsum(1)  # sat[j, i] = samples with row < j and column < i
+    rows = np.nonzero(G[:, F["vis"]] > 0)[0]
+    H = G[rows]
+    x, y = H[:, F["xy"]], H[:, F["xy"] + 1]
+    ex, ey = H[:, F["ext"]], H[:, F["ext"] + 1]
+    i0 = np.clip(np.floor(x - ex - 0.5) - 1, 0, width).astype(np.int64)
+    i1 = np.clip(np.ceil(x + ex - 0.5) + 2, 0, width).astype(np.int64)
+    j0 = np.clip(np.floor(y - ey - 0.5) - 1, 0, height).astype(np.int64)
+    j1 = np.clip(np.ceil(y + ey - 0.5) + 2, 0, height).astype(np.int64)
+    cnt = sat[j1, i1] - sat[j0, i1] - sat[j1, i0] + sat[j0, i0]
+    return rows[cnt > 0]

@@ -89,3 +89,68 @@ def test_config1_sampled_gradient(cfg1):
     ref = oracle.backward(G, scene, cam, pix, dL[:, idx].T.astype(np.float64))
     g = r.backward(gs, fr, torch.as_tensor(dL.reshape(-1)).cuda())
     parity.check_grads(g, ref, "config1 sampled")
+
+
+# ------------------------------------------------------------------------------------------
+# Large scene: 3M Gaussians in a 20 x 20 x 5 box, SH degree 3, 2048 x 2048 at 190 degrees
+# (theta up to 95 degrees), poses inside the box; single-view forward, as its throughput
+# benchmark launches it.
+
+@pytest.fixture(scope="module")
+def cfg2():
+    scene, cams = scenes.config2(n_poses=3)
+    dev = torch.device("cuda:0")
+    gs = scene_to_device(scene, dev)
+    r = FisheyeRenderer(dev, capacity=32_000_000)
+    return scene, cams, gs, r
+
+
+@pytest.mark.parametrize("pose", [0, 2])
+def test_config2_sampled_pixels_and_keys(cfg2, pose):
+    scene, cams, gs, r = cfg2
+    cam = cams[pose]
+    n = scene["means"].shape[0]
+    fr = r.forward(gs, [cam])
+    w, h = cam["width"], cam["height"]
+    rng = np.random.default_rng(77 + pose)
+    pix = np.stack([rng.integers(0, w, 2500), rng.integers(0, h, 2500)], 1).astype(np.int32)
+    G = oracle.project(scene, cam)
+    rows = parity.rows_near_pixels(G, pix, w, h)
+    ref = oracle.render(G[rows], pix, impact_min=parity.IMPACT_MIN)
+    img = fr.view_images([cam])[0].cpu().numpy()
+    got = img[:, pix[:, 1], pix[:, 0]].T
+    d = np.abs(got - ref["color"])
+    fl = parity.flagged(ref["margins"])
+    assert (ref["n_contrib"] > 0).mean() > 0.5  # the sample sees the scene
+    assert fl.mean() < 0.08, (fl.mean(), d[~fl].max(), d.mean(0))
+    assert d[~fl].max() <= parity.IMG_MAX
+    assert np.all(d.mean(0) <= parity.IMG_MEAN)
+    Tg = fr.final_T.view(h, w).cpu().numpy()[pix[:, 1], pix[:, 0]]
+    assert np.abs(Tg - ref["T_final"])[~fl].max() <= parity.IMG_MAX
+
+    # keys: sorted, stable, each record's pair count = its rect area, ranges consistent
+    m = int(fr.n_intersections.item())
+    keys = parity.u64(fr.keys)[:m]
+    vals = parity.u32(fr.vals)[:m]
+    assert m > 1_000_000
+    assert np.all(keys[1:] >= keys[:-1])
+    same = keys[1:] == keys[:-1]
+    assert np.all(vals[1:][same] > vals[:-1][same])
+    rec = parity.records_np(fr.records, n)
+    tt = fr.tiles_touched.cpu().numpy().astype(np.int64)
+    assert np.array_equal(np.bincount(vals, minlength=n), tt)
+    rc = rec["rect"]
+    area = np.where(tt > 0, (rc[:, 2] - rc[:, 0] + 1) * (rc[:, 3] - rc[:, 1] + 1), 0)
+    assert np.array_equal(area, tt)
+    assert np.array_equal((keys & np.uint64(0xFFFFFFFF)).astype(np.uint32), rec["depth_bits"][vals])
+    tile = (keys >> np.uint64(32)).astype(np.int64)
+    ranges = parity.u32(fr.tile_ranges).reshape(-1, 2).astype(np.int64)
+    assert ranges.shape[0] == 128 * 128
+    assert np.array_equal(ranges[:, 1] - ranges[:, 0], np.bincount(tile, minlength=128 * 128))
+    # visibility and rects against the oracle's FP64 decisions away from rounding boundaries
+    F = oracle.F
+    vis = G[:, F["vis"]] > 0
+    near = G[:, F["rmargin"]] < 1e-4
+    ok = vis & (tt > 0) & ~near
+    assert np.array_equal(rc[ok], G[ok][:, F["rect"]:F["rect"] + 4].astype(np.int32))
+    assert np.array_equal(vis[~near], (tt > 0)[~near])
