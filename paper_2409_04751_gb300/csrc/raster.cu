@@ -87,26 +87,82 @@ __device__ __forceinline__ void load_idx(const uint32_t *__restrict__ vals, uint
 // The exponent of the blend in base 2, e = A' dx^2 + B' dx dy + C' dy^2 + log2(opacity) with
 // (dx, dy) = pixel centre - mean, A' = -log2(e) conic_xx / 2, B' = -log2(e) conic_xy,
 // C' = -log2(e) conic_yy / 2, written in tile-centred pixel coordinates (u, v) = pixel centre
-// - tile centre: e = K0 + Kx u + Ky v + A' u^2 + B' u v + C' v^2 (five FMAs per pixel; with
-// |u|, |v| <= 7.5 the terms stay small, so rounding stays near that of the direct form). The
-// forward (every work shape) and the backward evaluate it the same way, so they take the same
-// alpha >= 1/255 decisions. xf[0] = (K0, Kx, Ky, A'), xf[1] = (B', C', r, g),
-// xf[2] = (b, mean - tile centre offsets cx, cy, 0) with dx = u + cx, dy = v + cy.
-__device__ __forceinline__ void stage_record(const fgs_record &g, float tile_cx, float tile_cy,
-                                             float4 *xf) {
-  const float A = -0.5f * LOG2E * g.conic[0], B = -LOG2E * g.conic[1];
-  const float C = -0.5f * LOG2E * g.conic[2], lo2o = log2f(g.opacity);
+// - tile centre (|u|, |v| <= 7.5, so the terms stay small and rounding stays near that of the
+// direct form) and factored per pixel row:
+//   e = base + v slope + C' v^2,  base = K0 + Kx u + A' u^2,  slope = Ky + B' u.
+// Every pixel evaluates exactly this sequence of FMAs whatever the work shape, in the forward
+// and in the backward, so both passes take the same alpha >= 1/255 decisions.
+//
+// Records are staged in pairs (list entries 2p and 2p + 1) so that one paired FP32 FMA
+// (fma.rn.f32x2, rounding each half like fmaf) advances a pixel's exponent for both Gaussians:
+//   cf[p][0] = (K0_a, K0_b, Kx_a, Kx_b)   cf[p][1] = (Ky_a, Ky_b, A_a, A_b)
+//   cf[p][2] = (B_a, B_b, C_a, C_b)       cf[p][3] = (r_a, g_a, b_a, cx_a)
+//   cf[p][4] = (r_b, g_b, b_b, cx_b)      cf[p][5] = (cy_a, cy_b, 0, 0)   (backward only)
+// with (cx, cy) = tile centre - mean, so dx = u + cx, dy = v + cy. A missing second entry (odd
+// count) is staged with K0 = -inf: its exponent is -inf and it never passes the alpha test.
+struct Coef {
+  float K0, Kx, Ky, A, B, C, r, g, b, cx, cy;
+};
+
+__device__ __forceinline__ Coef coef_of(const fgs_record &g, float tile_cx, float tile_cy) {
+  Coef k;
+  k.A = -0.5f * LOG2E * g.conic[0];
+  k.B = -LOG2E * g.conic[1];
+  k.C = -0.5f * LOG2E * g.conic[2];
+  const float lo2o = log2f(g.opacity);
   const float cx = tile_cx - g.xy[0], cy = tile_cy - g.xy[1];
-  const float K0 = fmaf(cx, fmaf(A, cx, B * cy), fmaf(C * cy, cy, lo2o));
-  const float Kx = fmaf(2.f * A, cx, B * cy), Ky = fmaf(B, cx, 2.f * C * cy);
-  xf[0] = make_float4(K0, Kx, Ky, A);
-  xf[1] = make_float4(B, C, g.rgb[0], g.rgb[1]);
-  xf[2] = make_float4(g.rgb[2], cx, cy, 0.f);
+  k.K0 = fmaf(cx, fmaf(k.A, cx, k.B * cy), fmaf(k.C * cy, cy, lo2o));
+  k.Kx = fmaf(2.f * k.A, cx, k.B * cy);
+  k.Ky = fmaf(k.B, cx, 2.f * k.C * cy);
+  k.r = g.rgb[0]; k.g = g.rgb[1]; k.b = g.rgb[2];
+  k.cx = cx; k.cy = cy;
+  return k;
 }
 
-__device__ __forceinline__ float exponent(const float4 &a, const float4 &c, float u, float v,
-                                          float uu, float uv, float vv) {
-  return fmaf(uu, a.w, fmaf(uv, c.x, fmaf(vv, c.y, fmaf(v, a.z, fmaf(u, a.y, a.x)))));
+// Stage list entry `slot` of a batch of `cnt` into its half of pair slot / 2: each thread
+// stages its own records. The slot just past an odd count is staged as the missing entry.
+template <int NF>
+__device__ __forceinline__ void stage_entry(const fgs_record *raw, uint32_t slot, uint32_t cnt,
+                                            float tile_cx, float tile_cy, float4 (*cf)[NF]) {
+  Coef k;
+  if (slot < cnt) {
+    k = coef_of(raw[slot], tile_cx, tile_cy);
+  } else if (slot == cnt && (cnt & 1u)) {
+    k.K0 = -INFINITY;
+    k.Kx = k.Ky = k.A = k.B = k.C = k.r = k.g = k.b = k.cx = k.cy = 0.f;
+  } else {
+    return;
+  }
+  float *q = reinterpret_cast<float *>(cf[slot >> 1]);
+  const uint32_t h = slot & 1u;
+  q[0 + h] = k.K0; q[2 + h] = k.Kx;
+  q[4 + h] = k.Ky; q[6 + h] = k.A;
+  q[8 + h] = k.B;  q[10 + h] = k.C;
+  cf[slot >> 1][3 + h] = make_float4(k.r, k.g, k.b, k.cx);
+  if (NF > 5) q[20 + h] = k.cy;
+}
+
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 lo2(const float4 &q) { return make_float2(q.x, q.y); }
+__device__ __forceinline__ float2 hi2(const float4 &q) { return make_float2(q.z, q.w); }
+__device__ __forceinline__ float2 dup2(float x) { return make_float2(x, x); }
+
+// Per-pair terms shared by a thread's pixels (its column u): base and slope of both entries.
+struct PairTerms {
+  float2 base, slope, C;
+};
+
+__device__ __forceinline__ PairTerms pair_terms(const float4 &q0, const float4 &q1,
+                                                const float4 &q2, float2 u2, float2 uu2) {
+  PairTerms t;
+  t.base = ffma2(uu2, hi2(q1), ffma2(u2, hi2(q0), lo2(q0)));
+  t.slope = ffma2(u2, lo2(q2), lo2(q1));
+  t.C = hi2(q2);
+  return t;
+}
+
+__device__ __forceinline__ float2 pair_exponent(const PairTerms &t, float v) {
+  return ffma2(dup2(v * v), t.C, ffma2(dup2(v), t.slope, t.base));
 }
 
 template <int PPT, bool COUNT>
@@ -120,7 +176,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
   constexpr int BATCH = Batch<PPT>::N;
   constexpr int PER = BATCH / NT;  // copies each thread issues per batch
   __shared__ __align__(128) fgs_record raw[2][BATCH];
-  __shared__ __align__(16) float4 xf[BATCH][3];
+  __shared__ __align__(16) float4 cf[BATCH / 2][5];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int64_t s_tile;
   const int tid = threadIdx.x;
@@ -133,6 +189,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
   uint32_t phase0 = 0, phase1 = 0;
   uint32_t n_eval = 0, n_blend = 0;
   const int lx = tid & (TILE - 1), ly0 = (tid / TILE) * PPT;
+  const float fu = (float)lx - 7.5f, fv = (float)ly0 - 7.5f;
+  const float2 u2 = dup2(fu), uu2 = dup2(fu * fu);
   // after a device-side error in the binning the lists are undefined: render background only
   const bool lists_ok = *(volatile const uint32_t *)status == 0u;
 
@@ -145,17 +203,14 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
     const TileInfo ti = tile_info(vs, t, ranges);
     const View &V = vs.v[ti.v];
     const int px = ti.tx * TILE + lx;
-    // tile centre (between pixel centres 7 and 8) and this pixel's offset from it
+    // tile centre (between pixel centres 7 and 8)
     const float tile_cx = (float)(ti.tx * TILE) + 0.5f * TILE, tile_cy = (float)(ti.ty * TILE) + 0.5f * TILE;
-    const float fu = (float)lx - 7.5f, fv = (float)ly0 - 7.5f;
-    const float uu = fu * fu, uv = fu * fv, vv = fv * fv;
-    float fpy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
+    float T[PPT], C0[PPT], C1[PPT], C2[PPT];
     uint32_t last[PPT];
     bool live[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
       const int py = ti.ty * TILE + ly0 + k;
-      fpy[k] = (float)py + 0.5f;
       T[k] = 1.f; C0[k] = C1[k] = C2[k] = 0.f;
       last[k] = 0;
       live[k] = px < V.width && py < V.height;
@@ -189,102 +244,107 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
           if (b + 1 < nb) mbar_wait(&bar[s ^ 1], s ? phase0 : phase1, status);
           return;
         }
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-          const uint32_t slot = tid + k * NT;
-          if (slot < cnt) {
-            stage_record(raw[s][slot], tile_cx, tile_cy, xf[slot]);
-          }
-        }
+#pragma unroll 1
+        for (int k = 0; k < PER; ++k) stage_entry<5>(raw[s], tid + k * NT, cnt, tile_cx, tile_cy, cf);
         __syncthreads();
+        const uint32_t npairs = (cnt + 1) / 2;
         if (PPT == 1 && !__all_sync(0xffffffffu, done)) {
-          // one pixel per thread, two list entries per iteration
-          const uint32_t lo1 = lo + 1;
+          // one pixel per thread: a tight loop over the pairs, left at the stop
           if (!done) {
+            const float2 v2 = dup2(fv), vv2 = dup2(fv * fv);
             bool stop = false;
-            uint32_t j = 0;
-            for (; j < cnt; j += 2) {
-              const bool two = j + 1 < cnt;
-              const float4 a0 = xf[j][0], c0 = xf[j][1];
-              const uint32_t j1 = two ? j + 1 : j;
-              const float4 a1 = xf[j1][0], c1 = xf[j1][1];
-              const float e0 = exponent(a0, c0, fu, fv, uu, uv, vv);
-              const float e1 = exponent(a1, c1, fu, fv, uu, uv, vv);
-              if (COUNT) ++n_eval;
-              if (e0 >= LOG2_ALPHA_MIN) {
-                const float alpha = fminf(ALPHA_MAX, ex2_approx(e0));
+            for (uint32_t p = 0; p < npairs; ++p) {
+              const PairTerms pt = pair_terms(cf[p][0], cf[p][1], cf[p][2], u2, uu2);
+              const float2 e = ffma2(vv2, pt.C, ffma2(v2, pt.slope, pt.base));
+              if (COUNT) n_eval += 2 * p + 1 < cnt ? 2 : 1;
+              if (e.x >= LOG2_ALPHA_MIN) {
+                const float alpha = fminf(ALPHA_MAX, ex2_approx(e.x));
                 const float Tn = fmaf(-alpha, T[0], T[0]);
                 if (Tn < T_MIN) {
                   stop = true;
+                  if (COUNT && 2 * p + 1 < cnt) --n_eval;
                   break;
                 }
+                const float4 c = cf[p][3];
                 const float wgt = alpha * T[0];
-                C0[0] = fmaf(c0.z, wgt, C0[0]);
-                C1[0] = fmaf(c0.w, wgt, C1[0]);
-                C2[0] = fmaf(xf[j][2].x, wgt, C2[0]);
+                C0[0] = fmaf(c.x, wgt, C0[0]);
+                C1[0] = fmaf(c.y, wgt, C1[0]);
+                C2[0] = fmaf(c.z, wgt, C2[0]);
                 T[0] = Tn;
-                last[0] = lo1 + j;
+                last[0] = lo + 2 * p + 1;
                 if (COUNT) ++n_blend;
               }
-              if (!two) break;
-              if (COUNT) ++n_eval;
-              if (e1 >= LOG2_ALPHA_MIN) {
-                const float alpha = fminf(ALPHA_MAX, ex2_approx(e1));
+              if (e.y >= LOG2_ALPHA_MIN) {  // never true for a missing second entry
+                const float alpha = fminf(ALPHA_MAX, ex2_approx(e.y));
                 const float Tn = fmaf(-alpha, T[0], T[0]);
                 if (Tn < T_MIN) {
                   stop = true;
                   break;
                 }
+                const float4 c = cf[p][4];
                 const float wgt = alpha * T[0];
-                C0[0] = fmaf(c1.z, wgt, C0[0]);
-                C1[0] = fmaf(c1.w, wgt, C1[0]);
-                C2[0] = fmaf(xf[j1][2].x, wgt, C2[0]);
+                C0[0] = fmaf(c.x, wgt, C0[0]);
+                C1[0] = fmaf(c.y, wgt, C1[0]);
+                C2[0] = fmaf(c.z, wgt, C2[0]);
                 T[0] = Tn;
-                last[0] = lo1 + j1;
+                last[0] = lo + 2 * p + 2;
                 if (COUNT) ++n_blend;
               }
             }
             if (stop) live[0] = false;
             done = !live[0];
           }
-        } else if (!__all_sync(0xffffffffu, done)) {
-          const uint32_t lo1 = lo + 1;
-          for (uint32_t j = 0; j < cnt && !done; ++j) {
-            const float4 a = xf[j][0];
-            const float4 c = xf[j][1];
-            {
-              bool any_live = false;
+        } else if (PPT > 1 && !__all_sync(0xffffffffu, done)) {
+          for (uint32_t p = 0; p < npairs && !done; ++p) {
+            const PairTerms pt = pair_terms(cf[p][0], cf[p][1], cf[p][2], u2, uu2);
+            const bool has_b = 2 * p + 1 < cnt;
+            const uint32_t ia = lo + 2 * p + 1;  // 1-based list position of entry a
+            bool any_live = false;
 #pragma unroll
-              for (int k = 0; k < PPT; ++k) {
+            for (int k = 0; k < PPT; ++k) {
+              if (live[k]) {
+                const float2 e = pair_exponent(pt, fv + (float)k);
+                if (COUNT) ++n_eval;
+                if (e.x >= LOG2_ALPHA_MIN) {
+                  const float alpha = fminf(ALPHA_MAX, ex2_approx(e.x));
+                  const float Tn = fmaf(-alpha, T[k], T[k]);
+                  if (Tn < T_MIN) {
+                    live[k] = false;
+                  } else {
+                    const float4 c = cf[p][3];
+                    const float wgt = alpha * T[k];
+                    C0[k] = fmaf(c.x, wgt, C0[k]);
+                    C1[k] = fmaf(c.y, wgt, C1[k]);
+                    C2[k] = fmaf(c.z, wgt, C2[k]);
+                    T[k] = Tn;
+                    last[k] = ia;
+                    if (COUNT) ++n_blend;
+                  }
+                }
                 if (live[k]) {
-                  const float v = fv + (float)k;
-                  const float e = exponent(a, c, fu, v, uu, fu * v, v * v);
-                  if (COUNT) ++n_eval;
-                  if (e >= LOG2_ALPHA_MIN) {
-                    const float alpha = fminf(ALPHA_MAX, ex2_approx(e));
+                  if (COUNT && has_b) ++n_eval;
+                  if (e.y >= LOG2_ALPHA_MIN) {  // never true for a missing second entry
+                    const float alpha = fminf(ALPHA_MAX, ex2_approx(e.y));
                     const float Tn = fmaf(-alpha, T[k], T[k]);
                     if (Tn < T_MIN) {
                       live[k] = false;
                     } else {
+                      const float4 c = cf[p][4];
                       const float wgt = alpha * T[k];
-                      C0[k] = fmaf(c.z, wgt, C0[k]);
-                      C1[k] = fmaf(c.w, wgt, C1[k]);
-                      C2[k] = fmaf(xf[j][2].x, wgt, C2[k]);
+                      C0[k] = fmaf(c.x, wgt, C0[k]);
+                      C1[k] = fmaf(c.y, wgt, C1[k]);
+                      C2[k] = fmaf(c.z, wgt, C2[k]);
                       T[k] = Tn;
-                      last[k] = lo1 + j;
+                      last[k] = ia + 1;
                       if (COUNT) ++n_blend;
                     }
                   }
                 }
-                any_live = any_live || live[k];
               }
-              if (!any_live) break;
+              any_live = any_live || live[k];
             }
+            done = !any_live;
           }
-          bool any_live = false;
-#pragma unroll
-          for (int k = 0; k < PPT; ++k) any_live = any_live || live[k];
-          done = !any_live;
         }
         if (__syncthreads_count(!done) == 0) {
           if (b + 1 < nb) {  // drain the batch in flight before leaving the tile
@@ -316,34 +376,79 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
   }
 }
 
-// Warp sum of eight values by transpose reduction: at each exchange a lane keeps half of its
-// values and sends the other half to its partner, so 4 + 2 + 1 + 1 + 1 shuffles reduce all
-// eight. On return lane l holds the total of value 4*b4 + 2*b3 + b2 (b_i = bit i of l).
-__device__ __forceinline__ float warp_transpose_sum8(const float (&a)[8], int lane) {
-  float b[4], c[2];
-  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+// Warp sums of two entries' nine values by transpose reduction. At each exchange a lane keeps
+// half of its values and sends the other half to its partner, so the sixteen values
+// a[0..7], b[0..7] take 8 + 4 + 2 + 1 + 1 shuffles; on return lanes 2i and 2i + 1 hold the
+// total of value i of (a[0..7], b[0..7]). The ninth values a8, b8 take 1 + 4 shuffles; on
+// return lanes 0..15 hold the total of a8 and lanes 16..31 that of b8.
+__device__ __forceinline__ float warp_transpose_sum16(const float (&a)[9], const float (&b)[9],
+                                                      int lane, float &tot8) {
+  float c[8], d[4], e[2];
+  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float keep = h4 ? b[k] : a[k];
+    const float send = h4 ? a[k] : b[k];
+    c[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  {
+    const float keep = h4 ? b[8] : a[8];
+    const float send = h4 ? a[8] : b[8];
+    float t = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    t += __shfl_xor_sync(0xffffffffu, t, 8);
+    t += __shfl_xor_sync(0xffffffffu, t, 4);
+    t += __shfl_xor_sync(0xffffffffu, t, 2);
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    tot8 = t;
+  }
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const float keep = h4 ? a[k + 4] : a[k];
-    const float send = h4 ? a[k] : a[k + 4];
-    b[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    const float keep = h3 ? c[k + 4] : c[k];
+    const float send = h3 ? c[k] : c[k + 4];
+    d[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
   }
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    const float keep = h3 ? b[k + 2] : b[k];
-    const float send = h3 ? b[k] : b[k + 2];
-    c[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    const float keep = h2 ? d[k + 2] : d[k];
+    const float send = h2 ? d[k] : d[k + 2];
+    e[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
   }
-  float d = (h2 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, h2 ? c[0] : c[1], 4);
-  d += __shfl_xor_sync(0xffffffffu, d, 2);
-  d += __shfl_xor_sync(0xffffffffu, d, 1);
-  return d;
+  float f = (h1 ? e[1] : e[0]) + __shfl_xor_sync(0xffffffffu, h1 ? e[0] : e[1], 2);
+  f += __shfl_xor_sync(0xffffffffu, f, 1);
+  return f;
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+// One contributing (pixel, Gaussian) pair of the backward, back to front: recovers the
+// transmittance in front of the Gaussian, updates the colour-behind sum GS and adds the
+// pixel's terms to the nine per-record sums v.
+__device__ __forceinline__ void bwd_contrib(float e, float r, float g, float b, float dx, float dy,
+                                            float G0, float G1, float G2, float &T, float &GS,
+                                            float (&v)[9]) {
+  const float araw = ex2_approx(e);
+  const float alpha = fminf(ALPHA_MAX, araw);
+  const float om = rcp_approx(1.f - alpha);
+  T *= om;  // transmittance before this Gaussian
+  const float wgt = alpha * T;
+  const float gc = G0 * r + G1 * g + G2 * b;  // <dL/dC, colour>
+  // dL/dalpha = <dL/dC, colour T - behind / (1 - alpha)>
+  const float dLda = fmaf(T, gc, -om * GS);
+  GS = fmaf(gc, wgt, GS);
+  v[6] = fmaf(G0, wgt, v[6]);
+  v[7] = fmaf(G1, wgt, v[7]);
+  v[8] = fmaf(G2, wgt, v[8]);
+  if (araw < ALPHA_MAX) {
+    // alpha = opacity exp(p), p = -0.5 d^T conic d: accumulate the moments of dL/dp over the
+    // pixel offsets; the conic and opacity are applied once per record in the preprocess
+    // backward
+    const float dLdp = dLda * alpha;
+    const float tx = dLdp * dx, ty = dLdp * dy;
+    v[0] += tx;
+    v[1] += ty;
+    v[2] = fmaf(tx, dx, v[2]);
+    v[3] = fmaf(tx, dy, v[3]);
+    v[4] = fmaf(ty, dy, v[4]);
+    v[5] = fmaf(dLda, araw, v[5]);
+  }
 }
 
 template <int PPT, bool COUNT>
@@ -358,7 +463,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
   constexpr int BATCH = Batch<PPT>::N;
   constexpr int PER = BATCH / NT;
   __shared__ __align__(128) fgs_record raw[2][BATCH];
-  __shared__ __align__(16) float4 xf[BATCH][3];
+  __shared__ __align__(16) float4 cf[BATCH / 2][6];
   __shared__ uint32_t xidx[BATCH];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int64_t s_tile;
@@ -373,6 +478,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
   uint32_t phase0 = 0, phase1 = 0;
   uint32_t n_eval = 0, n_contrib = 0;
   const int lx = tid & (TILE - 1), ly0 = (tid / TILE) * PPT;
+  const float fu = (float)lx - 7.5f, fv = (float)ly0 - 7.5f;
+  const float2 u2 = dup2(fu), uu2 = dup2(fu * fu);
   // after a device-side error in the binning the lists are undefined: no gradient flows
   const bool lists_ok = *(volatile const uint32_t *)status == 0u;
 
@@ -388,7 +495,6 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
     const View &V = vs.v[ti.v];
     const int px = ti.tx * TILE + lx;
     const float tile_cx = (float)(ti.tx * TILE) + 0.5f * TILE, tile_cy = (float)(ti.ty * TILE) + 0.5f * TILE;
-    const float fu = (float)lx - 7.5f, fv = (float)ly0 - 7.5f, uu = fu * fu;
     const int64_t plane = (int64_t)V.width * V.height;
     // per pixel: transmittance, dL/dC, and GS = <dL/dC, colour behind the current entry>
     // (the sum over later blended entries plus T_final bg), kept as one scalar
@@ -446,77 +552,61 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
           if (b >= 1) mbar_wait(&bar[s ^ 1], s ? phase0 : phase1, status);
           return;
         }
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-          const uint32_t slot = tid + k * NT;
-          if (slot < cnt) {
-            stage_record(raw[s][slot], tile_cx, tile_cy, xf[slot]);
-          }
-        }
+#pragma unroll 1
+        for (int k = 0; k < PER; ++k) stage_entry<6>(raw[s], tid + k * NT, cnt, tile_cx, tile_cy, cf);
         __syncthreads();
-        for (int j = (int)cnt - 1; j >= 0; --j) {
-          const uint32_t pos = lo + (uint32_t)j;
-          const bool any_pos = pos < my_max;
+        const uint32_t npairs = (cnt + 1) / 2;
+        for (int p = (int)npairs - 1; p >= 0; --p) {
+          const uint32_t pos_a = lo + 2u * (uint32_t)p, pos_b = pos_a + 1u;
+          const bool any_pos = pos_a < my_max;
           if (!__any_sync(0xffffffffu, any_pos)) continue;
-          float v[9];
+          float va[9], vb[9];
 #pragma unroll
-          for (int q = 0; q < 9; ++q) v[q] = 0.f;
-          bool contrib = false;
+          for (int q = 0; q < 9; ++q) va[q] = vb[q] = 0.f;
+          bool ca = false, cb = false;
           if (any_pos) {
-            const float4 a = xf[j][0];
-            const float4 c = xf[j][1];
-            const float4 c2 = xf[j][2];
-            const float dx = fu + c2.y;
+            const PairTerms pt = pair_terms(cf[p][0], cf[p][1], cf[p][2], u2, uu2);
+            const float4 qa = cf[p][3], qb = cf[p][4], qy = cf[p][5];
+            const float dxa = fu + qa.w, dxb = fu + qb.w;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-              if (pos < last[k]) {
+              if (pos_a < last[k]) {
                 const float vk = fv + (float)k;
-                const float e = exponent(a, c, fu, vk, uu, fu * vk, vk * vk);
-                const float dy = vk + c2.z;
-                if (COUNT) ++n_eval;
-                if (e >= LOG2_ALPHA_MIN) {
-                  contrib = true;
-                  if (COUNT) ++n_contrib;
-                  const float cb = c2.x;
-                  const float araw = ex2_approx(e);
-                  const float alpha = fminf(ALPHA_MAX, araw);
-                  const float om = rcp_approx(1.f - alpha);
-                  T[k] *= om;  // transmittance before this Gaussian
-                  const float wgt = alpha * T[k];
-                  const float gc = G0[k] * c.z + G1[k] * c.w + G2[k] * cb;  // <dL/dC, colour>
-                  // dL/dalpha = <dL/dC, colour T - behind / (1 - alpha)>
-                  const float dLda = fmaf(T[k], gc, -om * GS[k]);
-                  GS[k] = fmaf(gc, wgt, GS[k]);
-                  v[6] = fmaf(G0[k], wgt, v[6]);
-                  v[7] = fmaf(G1[k], wgt, v[7]);
-                  v[8] = fmaf(G2[k], wgt, v[8]);
-                  if (araw < ALPHA_MAX) {
-                    // alpha = opacity exp(p), p = -0.5 d^T conic d: accumulate the moments of
-                    // dL/dp over the pixel offsets; the conic and opacity are applied once per
-                    // record in the preprocess backward
-                    const float dLdp = dLda * alpha;
-                    const float tx = dLdp * dx, ty = dLdp * dy;
-                    v[0] += tx;
-                    v[1] += ty;
-                    v[2] = fmaf(tx, dx, v[2]);
-                    v[3] = fmaf(tx, dy, v[3]);
-                    v[4] = fmaf(ty, dy, v[4]);
-                    v[5] = fmaf(dLda, araw, v[5]);
+                const float2 e = pair_exponent(pt, vk);
+                if (pos_b < last[k]) {  // the later entry first (back to front)
+                  if (COUNT) ++n_eval;
+                  if (e.y >= LOG2_ALPHA_MIN) {
+                    cb = true;
+                    if (COUNT) ++n_contrib;
+                    bwd_contrib(e.y, qb.x, qb.y, qb.z, dxb, vk + qy.y, G0[k], G1[k], G2[k],
+                                T[k], GS[k], vb);
                   }
+                }
+                if (COUNT) ++n_eval;
+                if (e.x >= LOG2_ALPHA_MIN) {
+                  ca = true;
+                  if (COUNT) ++n_contrib;
+                  bwd_contrib(e.x, qa.x, qa.y, qa.z, dxa, vk + qy.x, G0[k], G1[k], G2[k],
+                              T[k], GS[k], va);
                 }
               }
             }
           }
-          if (__any_sync(0xffffffffu, contrib)) {
-            const float a8[8] = {v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7]};
-            const float tot = warp_transpose_sum8(a8, lane);
-            const float tot8 = warp_sum(v[8]);
-            float *dst = g2d + (size_t)xidx[j] * G2D_STRIDE;
-            if ((lane & 3) == 0) atomicAdd(dst + (lane >> 2), tot);
-            if (lane == 0) atomicAdd(dst + 8, tot8);
+          const bool any_a = __any_sync(0xffffffffu, ca), any_b = __any_sync(0xffffffffu, cb);
+          if (any_a || any_b) {
+            float tot8;
+            const float tot = warp_transpose_sum16(va, vb, lane, tot8);
+            const int q = lane >> 1;  // value index of this lane's total: 0..7 a, 8..15 b
+            const bool is_b = q >= 8;
+            if ((lane & 1) == 0 && (is_b ? any_b : any_a)) {
+              float *dst = g2d + (size_t)xidx[2 * p + (is_b ? 1 : 0)] * G2D_STRIDE;
+              atomicAdd(dst + (q & 7), tot);
+            }
+            if (lane == 0 && any_a) atomicAdd(g2d + (size_t)xidx[2 * p] * G2D_STRIDE + 8, tot8);
+            if (lane == 16 && any_b) atomicAdd(g2d + (size_t)xidx[2 * p + 1] * G2D_STRIDE + 8, tot8);
           }
         }
-        __syncthreads();  // xf / xidx reused by the next batch
+        __syncthreads();  // cf / xidx reused by the next batch
         if (b >= 1) {
 #pragma unroll
           for (int k = 0; k < PER; ++k) xidx[tid + k * NT] = mine[k];
