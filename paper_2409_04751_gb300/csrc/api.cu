@@ -203,8 +203,9 @@ fgs_status fgs_backward_raster(const fgs_record *records, const uint32_t *vals,
     return FGS_ERR_INVALID_ARG;
   if (R > 0 && (!records || !aligned(records, 16))) return FGS_ERR_INVALID_ARG;
   if (!aligned(workspace, 256)) return FGS_ERR_INVALID_ARG;
-  // the header and the screen-space gradient region precede every capacity-dependent region
-  const WsLayout L = ws_layout(R, 1, 1);
+  // the header, the screen-space gradient region and the tile order precede every
+  // capacity-dependent region
+  const WsLayout L = ws_layout(R, 1, vs.total_tiles);
   if (workspace_bytes < L.vis_rec) return FGS_ERR_INVALID_ARG;
   const float b0 = bg ? bg[0] : 0.f, b1 = bg ? bg[1] : 0.f, b2 = bg ? bg[2] : 0.f;
   return cuda_status(launch_raster_bwd(records, vals, tile_ranges, vs, b0, b1, b2, final_T,

@@ -89,6 +89,7 @@ constexpr int EMIT_ITEMS = 4;
 constexpr int EMIT_PART = EMIT_THREADS * EMIT_ITEMS;  // records per scan partition
 constexpr int EMIT_CHUNK = 1024;                      // (record, tile) pairs per emission CTA
 constexpr int TSCAN_PART = 1024;                     // tiles per partition of the tile scan
+constexpr int WORK_BUCKETS = 32;                     // log2 classes of a tile's backward work
 // device-wide onesweep radix sort (onesweep.cu)
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 16;
@@ -102,7 +103,7 @@ constexpr int SEG_CAP1 = 8192;
 constexpr int G2D_STRIDE = 12;                        // floats per record of screen-space grads
 
 struct WsLayout {
-  size_t header, scan_lb, g2d, vis_rec, vis_off, tile_lb, seg_list, words, chunk_first;
+  size_t header, scan_lb, g2d, tile_order, vis_rec, vis_off, tile_lb, seg_list, words, chunk_first;
   size_t sort_hist, sort_lb, alt_vals;  // the onesweep sort's regions (0 bytes unless requested)
   size_t total;
   int64_t scan_parts, tile_parts, chunks, total_tiles, sort_parts;
@@ -127,6 +128,8 @@ constexpr WsLayout ws_layout_ex(int64_t n_records, int64_t capacity, int64_t tot
   L.header = o; o += align256(256);
   L.scan_lb = o; o += align256(sizeof(uint64_t) * 2 * (size_t)(L.scan_parts > 0 ? L.scan_parts : 1));
   L.g2d = o; if (with_g2d) o += align256(sizeof(float) * G2D_STRIDE * (size_t)R);
+  // the backward's tile order: per-tile work bucket, tile ids by decreasing work, histogram
+  L.tile_order = o; if (with_g2d) o += align256(sizeof(uint32_t) * (2 * (size_t)T + 2 * WORK_BUCKETS));
   L.vis_rec = o; o += align256(sizeof(uint32_t) * (size_t)R);
   L.vis_off = o; o += align256(sizeof(uint64_t) * (size_t)R);
   L.tile_lb = o; o += align256(sizeof(uint64_t) * (size_t)L.tile_parts);

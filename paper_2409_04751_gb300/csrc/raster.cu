@@ -457,8 +457,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
                       const uint32_t *__restrict__ ranges, Views vs, float bg0, float bg1,
                       float bg2, const float *__restrict__ final_T,
                       const uint32_t *__restrict__ n_processed, const float *__restrict__ dLdimg,
-                      float *__restrict__ g2d, uint32_t *tile_counter, uint32_t *status,
-                      unsigned long long *counters) {
+                      float *__restrict__ g2d, const uint32_t *__restrict__ order,
+                      uint32_t *tile_counter, uint32_t *status, unsigned long long *counters) {
   constexpr int NT = TILE_PIX / PPT;
   constexpr int BATCH = Batch<PPT>::N;
   constexpr int PER = BATCH / NT;
@@ -484,8 +484,9 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
   const bool lists_ok = *(volatile const uint32_t *)status == 0u;
 
   for (;;) {
-    if (tid == 0) {
-      s_tile = (int64_t)atomicAdd(tile_counter, 1u);
+    if (tid == 0) {  // tiles in decreasing order of work
+      const uint32_t q = atomicAdd(tile_counter, 1u);
+      s_tile = q < vs.total_tiles ? (int64_t)order[q] : vs.total_tiles;
       s_max = 0u;
     }
     __syncthreads();
@@ -621,6 +622,73 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
   }
 }
 
+// Longest-first order of the backward's tiles: a tile's work is the largest number of list
+// entries any of its pixels processed in the forward; tiles are ordered by the log2 class of
+// that work, most first, so that the persistent CTAs start the long tiles early and the short
+// ones fill in at the end. Any order gives the same gradients up to the order of their sums.
+__global__ void __launch_bounds__(256)
+    tile_work_kernel(const uint32_t *__restrict__ ranges, const uint32_t *__restrict__ n_processed,
+                     Views vs, const uint32_t *status, uint32_t *__restrict__ bucket,
+                     uint32_t *__restrict__ hist) {
+  __shared__ uint32_t s_hist[WORK_BUCKETS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < WORK_BUCKETS) s_hist[threadIdx.x] = 0u;
+  __syncthreads();
+  const int64_t t = (int64_t)blockIdx.x * 8 + warp;
+  if (t < vs.total_tiles) {
+    const TileInfo ti = tile_info(vs, t, ranges);
+    const View &V = vs.v[ti.v];
+    const bool lists_ok = *(volatile const uint32_t *)status == 0u;
+    uint32_t m = 0;
+    const int px = ti.tx * TILE + (lane & (TILE - 1));
+#pragma unroll
+    for (int r = 0; r < TILE / 2; ++r) {
+      const int py = ti.ty * TILE + 2 * r + (lane >> 4);
+      if (px < V.width && py < V.height)
+        m = max(m, __ldg(n_processed + V.pixel_offset + (int64_t)py * V.width + px));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    m = lists_ok ? min(m, ti.count) : 0u;
+    const uint32_t b = min(32u - (uint32_t)__clz(m), (uint32_t)WORK_BUCKETS - 1u);
+    if (lane == 0) {
+      bucket[t] = b;
+      atomicAdd(&s_hist[b], 1u);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < WORK_BUCKETS && s_hist[threadIdx.x]) atomicAdd(&hist[threadIdx.x], s_hist[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(1024)
+    tile_order_kernel(const uint32_t *__restrict__ bucket, const uint32_t *__restrict__ hist,
+                      uint32_t *__restrict__ cursor, int64_t total_tiles,
+                      uint32_t *__restrict__ order) {
+  __shared__ uint32_t s_off[WORK_BUCKETS];
+  if (threadIdx.x < 32) {  // start of each class: the tiles of all heavier classes come first
+    const uint32_t h = hist[threadIdx.x];
+    uint32_t x = h;  // suffix sum over the classes b' >= b
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_down_sync(0xffffffffu, x, o);
+      if (threadIdx.x + o < 32) x += y;
+    }
+    s_off[threadIdx.x] = x - h;
+  }
+  __syncthreads();
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = t < total_tiles;
+  const uint32_t b = in ? bucket[t] : 0xffffffffu;
+  // one atomic per (warp, class): lanes of the same class share the leader's claim
+  const uint32_t peers = __match_any_sync(0xffffffffu, b);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (in && lane == leader) base = atomicAdd(&cursor[b], (uint32_t)__popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (in) order[s_off[b] + base + __popc(peers & lanemask_lt())] = (uint32_t)t;
+}
+
 template <typename K>
 int occupancy_of(K kernel, int threads) {
   int occ = 0;
@@ -652,8 +720,8 @@ cudaError_t fwd_launch(const fgs_record *records, const uint32_t *vals, const ui
 template <int PPT>
 cudaError_t bwd_launch(const fgs_record *records, const uint32_t *vals, const uint32_t *ranges,
                        const Views &vs, float bg0, float bg1, float bg2, const float *final_T,
-                       const uint32_t *n_processed, const float *dL, float *g2d, WsHeader *hdr,
-                       cudaStream_t st) {
+                       const uint32_t *n_processed, const float *dL, float *g2d,
+                       const uint32_t *order, WsHeader *hdr, cudaStream_t st) {
   constexpr int NT = TILE_PIX / PPT;
   static int occ = 0;
   if (occ == 0) occ = occupancy_of(raster_bwd_kernel<PPT, false>, NT);
@@ -662,11 +730,11 @@ cudaError_t bwd_launch(const fgs_record *records, const uint32_t *vals, const ui
   if (grid < 1) grid = 1;
   if (instrumented())
     raster_bwd_kernel<PPT, true><<<(unsigned)grid, NT, 0, st>>>(
-        records, vals, ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL, g2d,
+        records, vals, ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL, g2d, order,
         &hdr->backward_tiles, &hdr->status, hdr->counters);
   else
     raster_bwd_kernel<PPT, false><<<(unsigned)grid, NT, 0, st>>>(
-        records, vals, ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL, g2d,
+        records, vals, ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL, g2d, order,
         &hdr->backward_tiles, &hdr->status, hdr->counters);
   return cudaGetLastError();
 }
@@ -694,15 +762,26 @@ cudaError_t launch_raster_bwd(const fgs_record *records, const uint32_t *vals,
                               const WsLayout &L, cudaStream_t st) {
   WsHeader *hdr = reinterpret_cast<WsHeader *>(ws + L.header);
   float *g2d = reinterpret_cast<float *>(ws + L.g2d);
+  uint32_t *order = reinterpret_cast<uint32_t *>(ws + L.tile_order);
+  uint32_t *bucket = order + vs.total_tiles;
+  uint32_t *hist = bucket + vs.total_tiles;  // WORK_BUCKETS counts, then WORK_BUCKETS cursors
   cudaError_t e = cudaMemsetAsync(&hdr->backward_tiles, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(g2d, 0, sizeof(float) * G2D_STRIDE * (size_t)n_records, st)) != cudaSuccess)
     return e;
+  if ((e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 2 * WORK_BUCKETS, st)) != cudaSuccess) return e;
+  if (vs.total_tiles > 0) {
+    tile_work_kernel<<<(unsigned)((vs.total_tiles + 7) / 8), 256, 0, st>>>(
+        tile_ranges, n_processed, vs, &hdr->status, bucket, hist);
+    tile_order_kernel<<<(unsigned)((vs.total_tiles + 1023) / 1024), 1024, 0, st>>>(
+        bucket, hist, hist + WORK_BUCKETS, vs.total_tiles, order);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   switch (raster_shape(1)) {
-    case 1: return bwd_launch<1>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, hdr, st);
-    case 8: return bwd_launch<8>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, hdr, st);
-    case 4: return bwd_launch<4>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, hdr, st);
-    default: return bwd_launch<2>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, hdr, st);
+    case 1: return bwd_launch<1>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, st);
+    case 8: return bwd_launch<8>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, st);
+    case 4: return bwd_launch<4>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, st);
+    default: return bwd_launch<2>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, st);
   }
 }
 
