@@ -2,8 +2,9 @@
 //
 // Forward (Sec. 4.1 preprocessCUDA with the fisheye projection of Sec. 4.2 / 4.3): one thread
 // per Gaussian, looping over the views of the call, so each Gaussian's parameters (236 B at SH
-// degree 3) are read from HBM once however many views there are. Quaternions and SH rows are
-// read with 16-byte vector loads when their rows are 16-byte aligned.
+// degree 3) are read from HBM once however many views there are (a later view finds its SH
+// row in L1). Quaternions and SH rows are read with 16-byte vector loads when their rows are
+// 16-byte aligned.
 //
 // Backward (Sec. 4.2 / 4.3 backward): one thread per Gaussian; the per-view screen-space
 // gradients (written by the rasterizer backward) are pulled back through the conic,
@@ -14,23 +15,6 @@
 namespace fgs {
 
 namespace {
-
-template <int D, bool VEC>
-__device__ __forceinline__ void load_sh(const float *__restrict__ sh, int64_t i, float *c) {
-  constexpr int K3 = (D + 1) * (D + 1) * 3;
-  const float *p = sh + (size_t)i * K3;
-  if (VEC && (K3 % 4) == 0) {
-    const float4 *p4 = reinterpret_cast<const float4 *>(p);
-#pragma unroll
-    for (int k = 0; k < K3 / 4; ++k) {
-      float4 v = __ldg(p4 + k);
-      c[4 * k] = v.x; c[4 * k + 1] = v.y; c[4 * k + 2] = v.z; c[4 * k + 3] = v.w;
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < K3; ++k) c[k] = __ldg(p + k);
-  }
-}
 
 template <bool VEC>
 __device__ __forceinline__ float4 load_quat(const float *__restrict__ q, int64_t i) {
@@ -74,8 +58,6 @@ __global__ void __launch_bounds__(256)
                __ldg(g.scales + 3 * i + 2), S);
     qs = fmaxf(2.f * logf(255.f * op), 0.f);
   }
-  float shc[K * 3];
-  bool sh_loaded = false;
 
   for (int v = 0; v < vs.n; ++v) {
     const View &V = vs.v[v];
@@ -125,24 +107,32 @@ __global__ void __launch_bounds__(256)
     const int y0 = ly < 0.f ? 0 : (int)floorf(ly);
     const int x1 = (int)floorf(fminf(hx, (float)(V.tiles_x - 1)));
     const int y1 = (int)floorf(fminf(hy, (float)(V.tiles_y - 1)));
-    // colour from SH along (mu - camera centre)
-    if (!sh_loaded) {
-      load_sh<D, VEC>(g.sh, i, shc);
-      sh_loaded = true;
-    }
+    // colour from SH along (mu - camera centre); the coefficients are streamed in as they
+    // are used (a later view of the call finds them in L1) rather than held in registers
     float dx = mx - V.cam_pos[0], dy = my - V.cam_pos[1], dz = mz - V.cam_pos[2];
     const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
     dx *= dn; dy *= dn; dz *= dn;
     float Y[K];
     sh_basis<D>(dx, dy, dz, Y);
-    float rgb[3];
+    float rgb[3] = {0.5f, 0.5f, 0.5f};
+    const float *shp = g.sh + (size_t)i * K * 3;
+    if (VEC && ((K * 3) % 4) == 0) {
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      float s = 0.5f;
+      for (int q = 0; q < K * 3 / 4; ++q) {
+        const float4 w = __ldg(reinterpret_cast<const float4 *>(shp) + q);
+        const float wv[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-      for (int k = 0; k < K; ++k) s = fmaf(shc[3 * k + ch], Y[k], s);
-      rgb[ch] = fmaxf(s, 0.f);
+        for (int t = 0; t < 4; ++t) {
+          const int j = 4 * q + t;
+          rgb[j % 3] = fmaf(wv[t], Y[j / 3], rgb[j % 3]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < K * 3; ++j) rgb[j % 3] = fmaf(__ldg(shp + j), Y[j / 3], rgb[j % 3]);
     }
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(rgb[ch], 0.f);
     float4 *o = reinterpret_cast<float4 *>(rec + r);
     o[0] = make_float4(px, py, c * idet, -b * idet);
     o[1] = make_float4(a * idet, op, rgb[0], rgb[1]);
@@ -153,33 +143,42 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+constexpr int PRE_BWD_THREADS = 128;
+
+// The SH gradient rows of a block's Gaussians are accumulated in shared memory (one private
+// row per thread, padded to an odd stride so that the threads' rows fall in distinct banks)
+// and written out together at the end as one contiguous, coalesced block; the SH
+// coefficients are read as they are needed. Neither is held in registers, which keeps enough
+// warps resident to hide the memory latency.
 template <int D, bool VEC>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(PRE_BWD_THREADS, 4)
     preprocess_bwd_kernel(GaussPtrs g, Views vs, const fgs_record *__restrict__ rec,
                           const uint32_t *__restrict__ tt, const float *__restrict__ g2d,
                           float *__restrict__ d_means, float *__restrict__ d_scales,
                           float *__restrict__ d_quats, float *__restrict__ d_opac,
                           float *__restrict__ d_sh) {
   constexpr int K = (D + 1) * (D + 1);
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.n) return;
-  const float mx = __ldg(g.means + 3 * i), my = __ldg(g.means + 3 * i + 1),
-              mz = __ldg(g.means + 3 * i + 2);
+  constexpr int K3 = K * 3, KS = K3 + 1;
+  __shared__ float s_dsh[PRE_BWD_THREADS * KS];
+  float *my_dsh = s_dsh + threadIdx.x * KS;
+  const int64_t i0 = (int64_t)blockIdx.x * PRE_BWD_THREADS;
+  const int64_t i = i0 + threadIdx.x;
+  const bool in = i < g.n;
   float dmu[3] = {0.f, 0.f, 0.f};
   float dS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma (symmetric, xx xy xz yy yz zz)
-  float dsh[K * 3];
-#pragma unroll
-  for (int k = 0; k < K * 3; ++k) dsh[k] = 0.f;
   float dop = 0.f;
   bool any = false;
   float S[6], R[9], qnv[4], qnorm = 1.f;
-  float shc[K * 3];
+  const float mx = in ? __ldg(g.means + 3 * i) : 0.f, my = in ? __ldg(g.means + 3 * i + 1) : 0.f,
+              mz = in ? __ldg(g.means + 3 * i + 2) : 0.f;
+  const float *shp = g.sh + (size_t)(in ? i : 0) * K3;
 
-  for (int v = 0; v < vs.n; ++v) {
+  for (int v = 0; in && v < vs.n; ++v) {
     const int64_t r = (int64_t)v * g.n + i;
     if (tt[r] == 0u) continue;
     const View &V = vs.v[v];
-    if (!any) {
+    const bool first = !any;
+    if (first) {
       any = true;
       float4 q = load_quat<VEC>(g.quats, i);
       qnorm = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
@@ -188,7 +187,6 @@ __global__ void __launch_bounds__(128)
       quat_to_rot(qnv[0], qnv[1], qnv[2], qnv[3], R);
       covariance(R, __ldg(g.scales + 3 * i), __ldg(g.scales + 3 * i + 1),
                  __ldg(g.scales + 3 * i + 2), S);
-      load_sh<D, VEC>(g.sh, i, shc);
     }
     // the rasterizer backward leaves, per record, the moments of dL/dp over the pixel offsets
     // d = pixel - xy (p = -0.5 d^T conic d): m = sum dL/dp (dx, dy, dx^2, dx dy, dy^2), then
@@ -285,8 +283,9 @@ __global__ void __launch_bounds__(128)
       float s = 0.f;
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
-        dsh[3 * k + ch] = fmaf(Y[k], grgb[ch], dsh[3 * k + ch]);
-        s = fmaf(shc[3 * k + ch], grgb[ch], s);
+        const int j = 3 * k + ch;
+        my_dsh[j] = fmaf(Y[k], grgb[ch], first ? 0.f : my_dsh[j]);
+        s = fmaf(__ldg(shp + j), grgb[ch], s);
       }
       dd0 = fmaf(s, dY[k][0], dd0);
       dd1 = fmaf(s, dY[k][1], dd1);
@@ -331,20 +330,22 @@ __global__ void __launch_bounds__(128)
     dq[0] = (gw - w * dot) * iq; dq[1] = (gx - x * dot) * iq;
     dq[2] = (gy - y * dot) * iq; dq[3] = (gz - z * dot) * iq;
   }
-  d_means[3 * i] = dmu[0]; d_means[3 * i + 1] = dmu[1]; d_means[3 * i + 2] = dmu[2];
-  d_scales[3 * i] = dsc[0]; d_scales[3 * i + 1] = dsc[1]; d_scales[3 * i + 2] = dsc[2];
-  d_quats[4 * i] = dq[0]; d_quats[4 * i + 1] = dq[1]; d_quats[4 * i + 2] = dq[2]; d_quats[4 * i + 3] = dq[3];
-  d_opac[i] = dop;
-  float *o = d_sh + (size_t)i * K * 3;
-  if (VEC && ((K * 3) % 4) == 0) {
-    float4 *o4 = reinterpret_cast<float4 *>(o);
+  if (in) {
+    d_means[3 * i] = dmu[0]; d_means[3 * i + 1] = dmu[1]; d_means[3 * i + 2] = dmu[2];
+    d_scales[3 * i] = dsc[0]; d_scales[3 * i + 1] = dsc[1]; d_scales[3 * i + 2] = dsc[2];
+    d_quats[4 * i] = dq[0]; d_quats[4 * i + 1] = dq[1]; d_quats[4 * i + 2] = dq[2]; d_quats[4 * i + 3] = dq[3];
+    d_opac[i] = dop;
+    if (!any) {
 #pragma unroll
-    for (int k = 0; k < K * 3 / 4; ++k)
-      o4[k] = make_float4(dsh[4 * k], dsh[4 * k + 1], dsh[4 * k + 2], dsh[4 * k + 3]);
-  } else {
-#pragma unroll
-    for (int k = 0; k < K * 3; ++k) o[k] = dsh[k];
+      for (int j = 0; j < K3; ++j) my_dsh[j] = 0.f;
+    }
   }
+  __syncthreads();
+  // the block's rows are contiguous in d_sh: consecutive threads store consecutive floats
+  const int64_t rows = g.n - i0 < PRE_BWD_THREADS ? g.n - i0 : PRE_BWD_THREADS;
+  float *dst = d_sh + (size_t)i0 * K3;
+  for (int j = threadIdx.x; j < rows * K3; j += PRE_BWD_THREADS)
+    dst[j] = s_dsh[(j / K3) * KS + j % K3];
 }
 
 template <int D>
@@ -361,7 +362,7 @@ template <int D>
 cudaError_t bwd_dispatch(const GaussPtrs &g, const Views &vs, const fgs_record *rec,
                          const uint32_t *tt, const float *g2d, float *dm, float *ds, float *dq,
                          float *dop, float *dsh, bool vec, cudaStream_t st) {
-  const int threads = 128;
+  const int threads = PRE_BWD_THREADS;
   const unsigned blocks = (unsigned)((g.n + threads - 1) / threads);
   if (vec)
     preprocess_bwd_kernel<D, true><<<blocks, threads, 0, st>>>(g, vs, rec, tt, g2d, dm, ds, dq, dop, dsh);
