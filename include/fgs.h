@@ -145,7 +145,10 @@ fgs_status fgs_preprocess(const fgs_gaussians *g, const fgs_camera *cams, int n_
  * one pair (key = t << 32 | bits(depth_r), value = r), t the global tile id; the pairs are
  * sorted by key, equal keys in increasing r (a stable sort of the emission in record order).
  * Inputs: records, tiles_touched [n_views * n] (as written by fgs_preprocess, or any records
- * whose rect and depth fields are set and tiles_touched = rect area).
+ * whose rect and depth fields are set and tiles_touched = rect area). With a smaller
+ * tiles_touched a record's pairs are the first tiles_touched tiles of its rect in row-major
+ * order; with a larger one the default sort keeps the rect's tiles only (FGS_BIN_ONESWEEP
+ * continues along the rows below it). Either way every write stays inside its buffer.
  * Outputs: keys [capacity] u64, vals [capacity] u32 (first *n_intersections entries valid),
  * tile_ranges [fgs_total_tiles * 2] u32 = [start, end) of each global tile,
  * n_intersections (device int64, the true count even when it exceeds capacity).

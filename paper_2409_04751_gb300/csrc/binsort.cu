@@ -11,8 +11,10 @@
 //     1024 records claimed in order through an atomic counter). For every record with pairs it
 //     writes its pair offset and its rank among such records (a compacted list), and for every
 //     1024-pair chunk the rank of the record holding the chunk's first pair.
-//  2. pair_kernel<false>: one CTA per 1024-pair chunk (the work per CTA is fixed however many
-//     tiles one Gaussian covers) counts the pairs of every tile.
+//  2. rect binning: rect_diff_kernel and grid_scan_kernel count the pairs of every tile from a
+//     2D difference grid of the records' rects (at most eight atomics per record). Exact
+//     (ellipse) binning: pair_kernel<false>, one CTA per 1024-pair chunk (the work per CTA is
+//     fixed however many tiles one Gaussian covers), counts them pair by pair.
 //  3. tile_scan_kernel: exclusive scan of the tile counts (decoupled look-back) gives every
 //     tile's start; tiles are listed by segment size.
 //  4. pair_kernel<true>: the same walk over the pairs claims a slot in the pair's tile bucket and
@@ -169,6 +171,89 @@ __global__ void __launch_bounds__(EMIT_THREADS)
         if (tile[k] != 0xffffffffu && (int64_t)pos[k] < capacity)
           words[pos[k]] = ((uint64_t)s_depth[owner[k]] << 32) | (uint64_t)s_rec[owner[k]];
     }
+  }
+}
+
+// Rect binning's tile counts without a pass over the pairs. A record's pairs are the first
+// k = min(tiles_touched, w h) tiles of its w x h rect in row-major order (exactly what the pair
+// walk emits): fr = k / w full rows and a partial row of k - fr w tiles. Each such block adds
+// +1, -1, -1, +1 at the corners (x_lo, y_lo), (x_hi + 1, y_lo), (x_lo, y_hi + 1),
+// (x_hi + 1, y_hi + 1) of a 2D difference grid held in tile_ranges[2t] (corners past the
+// grid's edge are dropped: they only reach tiles beyond it); inclusive prefix sums along the
+// rows and then the columns of every view turn it into the per-tile pair counts. Eight
+// atomics per record at most, instead of one per pair. With more candidates than capacity the
+// counts stay zero and the capacity status is set (the outputs are then undefined, but every
+// later stage stays inside its buffers).
+__global__ void __launch_bounds__(256)
+    rect_diff_kernel(const fgs_record *__restrict__ rec, const uint32_t *__restrict__ tt,
+                     int64_t n_per_view, Views vs, const uint32_t *__restrict__ vis_rec,
+                     const unsigned long long *n_vis, const unsigned long long *n_cand,
+                     int64_t capacity, uint32_t *ranges, uint32_t *status) {
+  if ((int64_t)*n_cand > capacity) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_status(status, ST_CAPACITY);
+    return;
+  }
+  const int64_t nv = (int64_t)*n_vis;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nv;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t r = vis_rec[q];
+    const uint4 w2 = __ldg(reinterpret_cast<const uint4 *>(rec + r) + 2);
+    const uint32_t x0 = w2.z & 0xffffu, y0 = w2.z >> 16, x1 = w2.w & 0xffffu, y1 = w2.w >> 16;
+    const View &V = vs.v[(int)(r / (uint32_t)n_per_view)];
+    const uint32_t tiles_x = (uint32_t)V.tiles_x, tiles_y = (uint32_t)V.tiles_y;
+    if (!(x0 <= x1 && y0 <= y1 && x1 < tiles_x && y1 < tiles_y)) continue;  // as the pair walk
+    const uint32_t w = x1 - x0 + 1u, h = y1 - y0 + 1u;
+    const uint32_t k = (uint32_t)min((uint64_t)__ldg(tt + r), (uint64_t)w * h);
+    const uint32_t fr = k / w, rem = k - fr * w;
+    uint32_t *grid = ranges + 2 * V.tile_offset;
+    auto add = [&](uint32_t x, uint32_t y, uint32_t d) {
+      if (x < tiles_x && y < tiles_y) atomicAdd(grid + 2 * ((size_t)y * tiles_x + x), d);
+    };
+    if (fr > 0u) {
+      add(x0, y0, 1u); add(x1 + 1u, y0, 0xffffffffu);
+      add(x0, y0 + fr, 0xffffffffu); add(x1 + 1u, y0 + fr, 1u);
+    }
+    if (rem > 0u) {
+      const uint32_t y = y0 + fr;
+      add(x0, y, 1u); add(x0 + rem, y, 0xffffffffu);
+      add(x0, y + 1u, 0xffffffffu); add(x0 + rem, y + 1u, 1u);
+    }
+  }
+}
+
+// In-place inclusive prefix sums of the difference grid, one warp per line: ROWS = true sums
+// along every view's tile rows, false along its columns (run after the rows). Sums are
+// modulo 2^32, so the negative differences need no sign.
+template <bool ROWS>
+__global__ void __launch_bounds__(256)
+    grid_scan_kernel(Views vs, int64_t n_lines, uint32_t *ranges,
+                     const unsigned long long *n_cand, int64_t capacity) {
+  if ((int64_t)*n_cand > capacity) return;
+  const int lane = threadIdx.x & 31;
+  int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (g >= n_lines) return;
+  int v = 0;
+  for (; v < vs.n - 1; ++v) {
+    const int64_t lines = ROWS ? vs.v[v].tiles_y : vs.v[v].tiles_x;
+    if (g < lines) break;
+    g -= lines;
+  }
+  const View &V = vs.v[v];
+  const int64_t len = ROWS ? V.tiles_x : V.tiles_y;
+  const int64_t step = ROWS ? 2 : 2 * (int64_t)V.tiles_x;  // words between consecutive entries
+  uint32_t *p = ranges + 2 * (V.tile_offset + (ROWS ? g * V.tiles_x : g));
+  uint32_t carry = 0u;
+  for (int64_t c = 0; c < len; c += 32) {
+    const int64_t j = c + lane;
+    uint32_t x = j < len ? p[j * step] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    x += carry;
+    if (j < len) p[j * step] = x;
+    carry = __shfl_sync(0xffffffffu, x, 31);
   }
 }
 
@@ -776,14 +861,28 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
   if (egrid > L.chunks) egrid = L.chunks;
   if (egrid < 1) egrid = 1;
   const bool ellipse = (flags & FGS_BIN_ELLIPSE) != 0;
-  if (ellipse)
+  if (ellipse) {
     pair_kernel<false, true><<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
         records, n, vs, vis_rec, vis_off, chunk_first, &hdr->n_candidates, &hdr->n_visible,
         tile_ranges, words, capacity, &hdr->status);
-  else
-    pair_kernel<false, false><<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
-        records, n, vs, vis_rec, vis_off, chunk_first, &hdr->n_candidates, &hdr->n_visible,
-        tile_ranges, words, capacity, &hdr->status);
+  } else {
+    int64_t rows = 0, cols = 0;
+    for (int v = 0; v < vs.n; ++v) {
+      rows += vs.v[v].tiles_y;
+      cols += vs.v[v].tiles_x;
+    }
+    int64_t dgrid = (int64_t)sm_count() * 4;
+    const int64_t need = (R + 255) / 256;
+    if (dgrid > need) dgrid = need;
+    if (dgrid < 1) dgrid = 1;
+    rect_diff_kernel<<<(unsigned)dgrid, 256, 0, st>>>(records, tiles_touched, n, vs, vis_rec,
+                                                       &hdr->n_visible, &hdr->n_candidates,
+                                                       capacity, tile_ranges, &hdr->status);
+    grid_scan_kernel<true><<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(
+        vs, rows, tile_ranges, &hdr->n_candidates, capacity);
+    grid_scan_kernel<false><<<(unsigned)((cols * 32 + 255) / 256), 256, 0, st>>>(
+        vs, cols, tile_ranges, &hdr->n_candidates, capacity);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   tile_scan_kernel<<<(unsigned)L.tile_parts, 256, 0, st>>>(
       tile_ranges, T, tile_lb, &hdr->tile_parts, lists, hdr->seg_count, &hdr->n_candidates,

@@ -148,3 +148,62 @@ def test_binsort_full_size_bit_exact(cuda_device, flags):
     assert np.array_equal(out["keys"][:m], k)
     assert np.array_equal(out["vals"][:m], v)
     assert np.array_equal(out["ranges"], rg)
+
+
+@pytest.mark.parametrize("flags", SORTS)
+def test_binsort_tiles_touched_differs_from_rect(cuda_device, flags):
+    """Records made by a caller whose tiles_touched is not their rect's area: a record's pairs
+    are the first min(tiles_touched, w h) tiles of its rect in row-major order (a shorter count
+    takes whole rows and part of the next; a longer one stops at the rect). The per-tile counts
+    and the scattered pairs must agree exactly, so the keys, values and ranges are those of
+    that definition, written out here by brute force. (Longer counts only for the per-tile
+    sort: the device-wide sort's emission assumes tiles_touched = w h, as fgs_preprocess
+    writes it, and stays inside its buffers otherwise.)"""
+    cams_py = _cams([(160, 96), (64, 64)])
+    rng = np.random.default_rng(21)
+    n = 1500
+    rec, rect, depth, tt = _records(rng, n, cams_py, max_ext=4, tie_frac=0.2)
+    area = tt.astype(np.int64)
+    vis = area > 0
+    pick = rng.random(tt.size)
+    short = vis & (pick < 0.4)
+    tt = tt.astype(np.int64)
+    tt[short] = rng.integers(1, area[short] + 1)
+    if flags == 0:  # the device-wide sort emits tiles_touched pairs whatever the rect
+        longer = vis & (pick > 0.8)
+        tt[longer] = area[longer] + rng.integers(1, 4, int(longer.sum()))
+    tt = tt.astype(np.uint32)
+    cand = int(tt.astype(np.int64).sum())
+    out = _run(rec, tt, n, cams_py, cand + 11, flags)
+    assert out["status"] == 0
+    txs = [(c["width"] + 15) // 16 for c in cams_py]
+    tys = [(c["height"] + 15) // 16 for c in cams_py]
+    offs = np.cumsum([0] + [a * b for a, b in zip(txs, tys)])
+    bits = depth.view(np.uint32)
+    key, val = [], []
+    for r in range(tt.size):
+        if tt[r] == 0 or rect[r, 0] < 0:
+            continue
+        v = r // n
+        x0, y0, x1, y1 = (int(t) for t in rect[r])
+        w, h = x1 - x0 + 1, y1 - y0 + 1
+        for local in range(int(min(tt[r], w * h))):
+            dy, dx = divmod(local, w)
+            tile = int(offs[v]) + (y0 + dy) * txs[v] + x0 + dx
+            key.append((tile << 32) | int(bits[r]))
+            val.append(r)
+    key = np.array(key, np.uint64)
+    val = np.array(val, np.uint32)
+    order = np.lexsort((val, key))
+    key, val = key[order], val[order]
+    m = key.size
+    assert out["n"] == m
+    assert np.array_equal(out["keys"][:m], key)
+    assert np.array_equal(out["vals"][:m], val)
+    tile = (key >> np.uint64(32)).astype(np.int64)
+    cnt = np.bincount(tile, minlength=out["tiles"])
+    rg = out["ranges"].astype(np.int64)
+    assert np.array_equal(rg[:, 1] - rg[:, 0], cnt)
+    starts = np.concatenate([[0], np.cumsum(cnt)[:-1]])
+    nz = cnt > 0
+    assert np.array_equal(rg[nz, 0], starts[nz])

@@ -31,9 +31,12 @@ def test_served_results_equal_alone(cuda_device):
 
 
 def test_capacity_overflow_is_retried(cuda_device):
-    """A batch sized too small is detected on completion and re-run."""
+    """A batch sized too small is detected on completion and re-run. At 384 x 384 one view of
+    this scene holds about 110k pairs, more than the 65536-slot floor of a first batch sized
+    from the far too small estimate, so the first batch overflows however the arrivals are
+    grouped."""
     scs = [scene_to_device(scenes.shell_scene(30_000, seed=77, sh_degree=0))]
-    reqs = poisson_requests(2000.0, 0.01, 1, seed=6, sizes=[256])
+    reqs = poisson_requests(2000.0, 0.01, 1, seed=6, sizes=[384])
     srv = Server(scs, n_slots=2, max_batch_views=4, keep_images=True)
     srv.ipp = [0.01]  # far too small: the first batches overflow
     stats = srv.run(reqs)
