@@ -44,6 +44,28 @@ def _env_rank():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def rank_camera(rank):
+    """Weak scaling over views: rank 0 renders the benchmark view (config 1's pose); rank r > 0
+    renders its own random pose of the same scene, so every rank does one view's work."""
+    from paper_2409_04751_gb300 import scenes
+    return scenes.pose_camera(1752, 1168, 180.0, seed=1000 + 1 + rank)
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest value of x over the ranks (the slowest rank's time); x itself on one rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, steps, seconds):
+    """Whole-job views/s: every rank renders `steps` views in `seconds` (the slowest rank's)."""
+    return world * steps / seconds
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -222,9 +244,8 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    scene, cams = scenes.config1()
-    if rank > 0:  # weak scaling: each rank renders its own pose of the same scene
-        cams = [scenes.pose_camera(1752, 1168, 180.0, seed=1000 + 1 + rank)]
+    scene, _ = scenes.config1()
+    cams = [rank_camera(rank)]  # weak scaling: each rank renders its own pose of the same scene
     gs = scene_to_device(scene, dev)
     n = scene["means"].shape[0]
     P = 1752 * 1168
@@ -361,15 +382,8 @@ def run_gpu(args):
     barrier()
     e2e_s = e0.elapsed_time(e1) / 1e3
 
-    def gmax(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    total_s, fwd_s, e2e_s = gmax(total_s), gmax(fwd_s), gmax(e2e_s)
-    value = world * args.steps / total_s
+    total_s, fwd_s, e2e_s = (max_over_ranks(x, dist, dev) for x in (total_s, fwd_s, e2e_s))
+    value = job_rate(world, args.steps, total_s)
 
     # roofline of the dominant kernel
     peaks = _peaks()
@@ -444,7 +458,7 @@ def run_gpu(args):
                     sh_degree=3, l2="flushed between steps (256 MiB write, untimed)",
                     parallelism=f"views x{world} (replicas)",
                     raster_pixels_per_thread=dict(fwd=shape["fwd"], bwd=shape["bwd"])),
-        fwd_views_per_s=world * args.steps / fwd_s,
+        fwd_views_per_s=job_rate(world, args.steps, fwd_s),
         mpix_per_s_fwd_bwd=value * P / 1e6,
         stage_ms=dict(zip(names, [round(float(x), 4) for x in stage_ms])),
         tuning_ms={k: round(v, 4) for k, v in shape.get("ms", {}).items()},
@@ -457,7 +471,7 @@ def run_gpu(args):
         exact_binning=exact,
         large_scene=large,
         training=training,
-        e2e=dict(value=world * args.steps / e2e_s, unit="views/s", h2d_bytes_per_step=h2d,
+        e2e=dict(value=job_rate(world, args.steps, e2e_s), unit="views/s", h2d_bytes_per_step=h2d,
                  d2h_bytes_per_step=d2h),
         gpu_launches=launches_per_step * args.steps,
         clocks=clocks, wall_s=round(t_wall, 3))
