@@ -7,7 +7,9 @@ its outputs leave set i % 2 while step i + 1 computes: the host link and the GPU
 so a stream of steps runs at about the slower of the two instead of their sum. Each step is the
 plain call sequence fgs_preprocess -> fgs_bin_sort -> fgs_rasterize -> fgs_backward on its own
 inputs, with the scratch buffers (records, keys, workspace) shared on the compute stream; events
-order the three streams, so every step's results equal those of the plain path.
+order the three streams, so every step's results equal those of the plain path. With
+use_graph=True (the default) that call sequence is captured once per input set in a CUDA graph
+when the pipeline is sized, and each step replays the graph of its set.
 """
 import torch
 
@@ -19,7 +21,7 @@ _KEYS = ("means", "scales", "quats", "opacities", "sh")
 
 class HostPipeline:
     def __init__(self, n, sh_degree, cams_py, device="cuda", capacity=1 << 22, bg=None,
-                 backward=True):
+                 backward=True, use_graph=True):
         self.device = torch.device(device)
         dev = self.device
         self.n, self.sh_degree = int(n), int(sh_degree)
@@ -44,6 +46,8 @@ class HostPipeline:
         self.ev_run = [E(), E()]   # compute on set k done
         self.ev_out = [E(), E()]   # outputs of set k left
         self.step = 0
+        self.use_graph = bool(use_graph)
+        self.graphs = None
 
     def size(self, host_inputs):
         """Size the key buffers with one checked forward on these inputs (synchronises)."""
@@ -55,6 +59,39 @@ class HostPipeline:
         r.capacity = int(int(r._bufs["nint"].item()) * 1.1) + 4096
         r.forward(gs, self.cams_py, bg=self.bg, check=True)
         torch.cuda.synchronize(self.device)
+        if self.use_graph:
+            # one warm pass of the full call sequence, then one capture per input set
+            self.s_run.wait_stream(torch.cuda.current_stream(self.device))
+            with torch.cuda.stream(self.s_run):
+                self._compute(0)
+            self.s_run.synchronize()
+            self.graphs = []
+            for k in range(2):
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=self.s_run):
+                    self._compute(k)
+                self.graphs.append(g)
+            torch.cuda.synchronize(self.device)
+
+    def _compute(self, k):
+        """The step's calls on input/output set k, on the current stream."""
+        inp, dL, img, grad = self.inp[k], self.dL[k], self.img[k], self.grad[k]
+        r = self.renderer
+        gs = dict(inp, sh_degree=self.sh_degree)
+        g = gaussians_of(gs)
+        ws = r._bufs["ws"]
+        cap = r.capacity
+        wsb = fgs.fgs_workspace_size(self.n, self.cams, cap)
+        rec, tt = r._bufs["records"], r._bufs["tt"]
+        keys, vals, rg, nint = r._bufs["keys"], r._bufs["vals"], r._bufs["ranges"], r._bufs["nint"]
+        fT, npr = r._bufs["final_T"], r._bufs["nproc"]
+        fgs.fgs_preprocess(g, self.cams, rec, tt)
+        fgs.fgs_bin_sort(rec, tt, self.n, self.cams, keys, vals, cap, rg, nint, ws, wsb)
+        fgs.fgs_rasterize(rec, vals, rg, self.cams, self.bg, img, fT, npr, ws, wsb)
+        if self.backward:
+            fgs.fgs_backward(g, self.cams, rec, tt, vals, rg, self.bg, fT, npr, dL,
+                             grad["means"], grad["scales"], grad["quats"],
+                             grad["opacities"], grad["sh"], ws, wsb)
 
     def submit(self, host_inputs, host_dL, host_img, host_grads):
         """Queue one step: host_inputs (dict of pinned tensors) and host_dL in, host_img and
@@ -72,23 +109,11 @@ class HostPipeline:
         # compute once the inputs landed and the outputs of set k have left
         self.s_run.wait_event(self.ev_in[k])
         self.s_run.wait_event(self.ev_out[k])
-        r = self.renderer
         with torch.cuda.stream(self.s_run):
-            gs = dict(inp, sh_degree=self.sh_degree)
-            g = gaussians_of(gs)
-            ws = r._bufs["ws"]
-            cap = r.capacity
-            wsb = fgs.fgs_workspace_size(self.n, self.cams, cap)
-            rec, tt = r._bufs["records"], r._bufs["tt"]
-            keys, vals, rg, nint = r._bufs["keys"], r._bufs["vals"], r._bufs["ranges"], r._bufs["nint"]
-            fT, npr = r._bufs["final_T"], r._bufs["nproc"]
-            fgs.fgs_preprocess(g, self.cams, rec, tt)
-            fgs.fgs_bin_sort(rec, tt, self.n, self.cams, keys, vals, cap, rg, nint, ws, wsb)
-            fgs.fgs_rasterize(rec, vals, rg, self.cams, self.bg, img, fT, npr, ws, wsb)
-            if self.backward:
-                fgs.fgs_backward(g, self.cams, rec, tt, vals, rg, self.bg, fT, npr, dL,
-                                 grad["means"], grad["scales"], grad["quats"],
-                                 grad["opacities"], grad["sh"], ws, wsb)
+            if self.graphs is not None:
+                self.graphs[k].replay()
+            else:
+                self._compute(k)
             self.ev_run[k].record(self.s_run)
         # copy out after the compute
         self.s_out.wait_event(self.ev_run[k])

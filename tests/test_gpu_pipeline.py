@@ -1,6 +1,7 @@
-"""HostPipeline (host-streamed fwd+bwd steps whose copies overlap the compute): every step's
-image equals the plain call sequence's bit for bit and its gradients to summation order, for a
-stream of steps with different inputs."""
+"""HostPipeline (host-streamed fwd+bwd steps whose copies overlap the compute, the compute
+replayed from CUDA graphs or called step by step): every step's image equals the plain call
+sequence's bit for bit and its gradients to summation order, for a stream of steps with
+different inputs."""
 import numpy as np
 import pytest
 import torch
@@ -15,7 +16,8 @@ pytestmark = pytest.mark.gpu
 KEYS = ("means", "scales", "quats", "opacities", "sh")
 
 
-def test_pipeline_steps_equal_plain_calls(cuda_device):
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_pipeline_steps_equal_plain_calls(cuda_device, use_graph):
     scene = scenes.shell_scene(20_000, seed=5, sh_degree=2)
     cams = [scenes.pose_camera(200, 150, 180.0, seed=51), scenes.pose_camera(96, 128, 190.0, seed=52)]
     P = sum(c["width"] * c["height"] for c in cams)
@@ -26,7 +28,7 @@ def test_pipeline_steps_equal_plain_calls(cuda_device):
         sc = dict(scene)
         sc["means"] = (scene["means"] + rng.normal(0, 0.01, scene["means"].shape)).astype(np.float32)
         steps.append((sc, scenes.upstream_grad((3 * P,), 1.0, 60 + s)))
-    pipe = HostPipeline(n, 2, cams, capacity=1 << 20)
+    pipe = HostPipeline(n, 2, cams, capacity=1 << 20, use_graph=use_graph)
     pin = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32)).pin_memory()
     host_in = [{k: pin(sc[k]) for k in KEYS} for sc, _ in steps]
     host_dL = [pin(d) for _, d in steps]
