@@ -63,6 +63,18 @@ def max_over_ranks(x, dist=None, device="cpu"):
     return float(t.item())
 
 
+def render_bytes(fgs, n, cams_c, n_views, m, flags=0):
+    """Device bytes one fwd+bwd of n Gaussians over these views holds besides the scene, with
+    the key buffers sized to exactly m intersections: records and tiles_touched, keys and
+    values, tile ranges, workspace (the backward's accumulators included), images, final T and
+    processed counts. The memory axis of the method's comparison table."""
+    R = n * n_views
+    T = fgs.fgs_total_tiles(cams_c)
+    P = fgs.fgs_total_pixels(cams_c)
+    ws = fgs.fgs_workspace_size(n, cams_c, max(int(m), 1), flags)
+    return R * (48 + 4) + int(m) * 12 + T * 8 + ws + P * (12 + 4 + 4)
+
+
 def job_rate(world, steps, seconds):
     """Whole-job views/s: every rank renders `steps` views in `seconds` (the slowest rank's)."""
     return world * steps / seconds
@@ -408,6 +420,7 @@ def run_gpu(args):
     barrier()
     e2e_s = e0.elapsed_time(e1) / 1e3
 
+    peak_main = torch.cuda.max_memory_allocated(dev)  # before the other workloads' legs
     total_s, fwd_s, e2e_s, gtot_s, gfwd_s = (max_over_ranks(x, dist, dev) for x in
                                              (total_s, fwd_s, e2e_s, graph_s[True], graph_s[False]))
     value = job_rate(world, args.steps, gtot_s)
@@ -494,6 +507,14 @@ def run_gpu(args):
         stage_ms=dict(zip(names, [round(float(x), 4) for x in stage_ms])),
         tuning_ms={k: round(v, 4) for k, v in shape.get("ms", {}).items()},
         intersections=m, visible=vis, pair_counters=counters,
+        memory=dict(scene_mb=sum(gs[k].numel() * 4 for k in ("means", "scales", "quats",
+                                                                "opacities", "sh")) / 1e6,
+                    render_mb=render_bytes(fgs, n, cam_c, 1, m) / 1e6,
+                    peak_allocated_mb=peak_main / 1e6,
+                    note="render_mb: buffers of one fwd+bwd sized to the exact intersection "
+                         "count; peak_allocated_mb: what torch held at most for this workload "
+                         "(scene, sized per-call buffers, 256 MiB L2 flush buffer, the two graphs' "
+                         "and the host pipeline's own copies), before the other workloads ran"),
         roofline=roof, kernels=kern,
         cpu_baseline=cpu,
         batched=batched,
@@ -737,8 +758,10 @@ def run_exact_binning(args, dev):
         st = fgs.fgs_read_status(ws)
         if st != fgs.FGS_OK:
             raise fgs.FgsError(st, name)
-        out[name] = dict(intersections=int(f2.n_intersections.item()),
-                         key_bytes=int(f2.n_intersections.item()) * 12,
+        m = int(f2.n_intersections.item())
+        out[name] = dict(intersections=m,
+                         key_bytes=m * 12,
+                         render_mb=render_bytes(fgs, n, f2.cams, 1, m, r.flags) / 1e6,
                          bin_sort_ms=float(np.median(ts)),
                          fwd_views_per_s=1e3 / float(np.median(tf)),
                          fwd_bwd_views_per_s=1e3 / float(np.median(tb)))
