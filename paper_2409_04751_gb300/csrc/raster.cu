@@ -119,27 +119,104 @@ __device__ __forceinline__ Coef coef_of(const fgs_record &g, float tile_cx, floa
   return k;
 }
 
-// Stage list entry `slot` of a batch of `cnt` into its half of pair slot / 2: each thread
-// stages its own records. The slot just past an odd count is staged as the missing entry.
-template <int NF>
-__device__ __forceinline__ void stage_entry(const fgs_record *raw, uint32_t slot, uint32_t cnt,
-                                            float tile_cx, float tile_cy, float4 (*cf)[NF]) {
-  Coef k;
-  if (slot < cnt) {
-    k = coef_of(raw[slot], tile_cx, tile_cy);
-  } else if (slot == cnt && (cnt & 1u)) {
-    k.K0 = -INFINITY;
-    k.Kx = k.Ky = k.A = k.B = k.C = k.r = k.g = k.b = k.cx = k.cy = 0.f;
-  } else {
-    return;
+// The exact binning's ellipse-tile test (ellipse_reaches_tile) with hardware reciprocals for
+// 1/A and 1/C: their relative error (below 2^-22) moves the clamped edge minimum by far less
+// than the test's margin (q* (1 + 1e-3) + 1e-2), so the test stays conservative, and it avoids
+// the full-precision division's registers inside the rasterizers.
+__device__ __forceinline__ bool reaches_tile(float mx, float my, float A, float B, float C,
+                                             float qs, float xl, float xh, float yl, float yh) {
+  if (mx >= xl && mx <= xh && my >= yl && my <= yh) return true;
+  const float thr = fmaf(qs, 1.001f, 1e-2f);
+  const float iA = rcp_approx(A), iC = rcp_approx(C);
+  float qmin = 3.0e38f;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const float dx = (e ? xh : xl) - mx;
+    const float dy = fminf(fmaxf(-B * dx * iC, yl - my), yh - my);
+    qmin = fminf(qmin, fmaf(dx, fmaf(A, dx, 2.f * B * dy), C * dy * dy));
+    const float ey = (e ? yh : yl) - my;
+    const float ex = fminf(fmaxf(-B * ey * iA, xl - mx), xh - mx);
+    qmin = fminf(qmin, fmaf(ex, fmaf(A, ex, 2.f * B * ey), C * ey * ey));
   }
-  float *q = reinterpret_cast<float *>(cf[slot >> 1]);
-  const uint32_t h = slot & 1u;
+  return qmin <= thr;
+}
+
+// Writes the coefficients of one list entry to its half of pair c / 2, with its list position
+// (forward: in the colour float4's spare component; backward: in the pair's last float4).
+template <int NF>
+__device__ __forceinline__ void write_entry(float4 (*cf)[NF], uint32_t c, const Coef &k,
+                                            uint32_t pos) {
+  float *q = reinterpret_cast<float *>(cf[c >> 1]);
+  const uint32_t h = c & 1u;
   q[0 + h] = k.K0; q[2 + h] = k.Kx;
   q[4 + h] = k.Ky; q[6 + h] = k.A;
   q[8 + h] = k.B;  q[10 + h] = k.C;
-  cf[slot >> 1][3 + h] = make_float4(k.r, k.g, k.b, k.cx);
-  if (NF > 5) q[20 + h] = k.cy;
+  cf[c >> 1][3 + h] = make_float4(k.r, k.g, k.b, NF > 5 ? k.cx : __uint_as_float(pos));
+  if (NF > 5) {
+    q[20 + h] = k.cy;
+    q[22 + h] = __uint_as_float(pos);
+  }
+}
+
+// Stages a batch of cnt list entries (list positions lo, lo + 1, ...) for the tile whose centre
+// is (tile_cx, tile_cy), keeping only the entries whose alpha >= 1/255 ellipse reaches the
+// tile's rectangle of pixel centres: the conservative test of the exact binning (the minimum
+// of the conic's quadratic over the rectangle against q* = 2 ln(255 opacity), with its margin),
+// so a dropped entry contributes to no pixel of the tile and the image is the one of the full
+// list. The kept entries are written in list order to positions 0, 1, ... with their list
+// positions; the keys, the sort and the tile lists stay those of the rect binning. ridx_in /
+// ridx_out (backward) carry the record indices along. A missing second entry of the last pair
+// (odd count) gets K0 = -inf and position 2^32 - 1: its exponent never passes the alpha test.
+// Each thread takes slots tid, tid + NT, ... (the slots it issued the copies of). Returns the
+// number kept; the caller synchronises before reading cf. Kept out of line: inlined, the test's
+// registers would count against the blending loop's occupancy.
+template <int NT, int PER, int NF>
+__device__ __noinline__ uint32_t stage_batch(const fgs_record *raw, uint32_t lo, uint32_t cnt,
+                                                float tile_cx, float tile_cy, float4 (*cf)[NF],
+                                                const uint32_t *ridx_in, uint32_t *ridx_out,
+                                                uint32_t *s_cnt) {
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const float xl = tile_cx - 7.5f, xh = tile_cx + 7.5f, yl = tile_cy - 7.5f, yh = tile_cy + 7.5f;
+  uint32_t base = 0;
+#pragma unroll 1
+  for (int k = 0; k < PER; ++k) {
+    const uint32_t slot = tid + k * NT;
+    bool keep = false;
+    if (slot < cnt) {
+      const fgs_record &g = raw[slot];
+      const float qs = fmaxf(2.f * logf(255.f * g.opacity), 0.f);
+      keep = reaches_tile(g.xy[0], g.xy[1], g.conic[0], g.conic[1], g.conic[2], qs, xl, xh, yl,
+                          yh);
+    }
+    const uint32_t m = __ballot_sync(0xffffffffu, keep);
+    uint32_t before = 0, total = __popc(m);
+    if (NW > 1) {
+      if (lane == 0) s_cnt[w] = total;
+      __syncthreads();
+      total = 0;
+#pragma unroll
+      for (int ww = 0; ww < NW; ++ww) {
+        const uint32_t c = s_cnt[ww];
+        before += ww < w ? c : 0u;
+        total += c;
+      }
+    }
+    if (keep) {
+      const uint32_t c = base + before + __popc(m & lanemask_lt());
+      write_entry<NF>(cf, c, coef_of(raw[slot], tile_cx, tile_cy), lo + slot);
+      if (ridx_out) ridx_out[c] = ridx_in[slot];
+    }
+    base += total;
+    if (NW > 1) __syncthreads();  // s_cnt is rewritten by the next group
+  }
+  if ((base & 1u) && tid == 0) {
+    Coef d;
+    d.K0 = -INFINITY;
+    d.Kx = d.Ky = d.A = d.B = d.C = d.r = d.g = d.b = d.cx = d.cy = 0.f;
+    write_entry<NF>(cf, base, d, 0xffffffffu);
+  }
+  return base;
 }
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -179,6 +256,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
   __shared__ __align__(16) float4 cf[BATCH / 2][5];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int64_t s_tile;
+  __shared__ uint32_t s_cnt[NT / 32];
   const int tid = threadIdx.x;
   if (tid == 0) {
     mbar_init(&bar[0], NT);
@@ -244,10 +322,10 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
           if (b + 1 < nb) mbar_wait(&bar[s ^ 1], s ? phase0 : phase1, status);
           return;
         }
-#pragma unroll 1
-        for (int k = 0; k < PER; ++k) stage_entry<5>(raw[s], tid + k * NT, cnt, tile_cx, tile_cy, cf);
+        const uint32_t kept = stage_batch<NT, PER, 5>(raw[s], lo, cnt, tile_cx, tile_cy, cf,
+                                                      nullptr, nullptr, s_cnt);
         __syncthreads();
-        const uint32_t npairs = (cnt + 1) / 2;
+        const uint32_t npairs = (kept + 1) / 2;
         if (PPT == 1 && !__all_sync(0xffffffffu, done)) {
           // one pixel per thread: a tight loop over the pairs, left at the stop
           if (!done) {
@@ -256,13 +334,13 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
             for (uint32_t p = 0; p < npairs; ++p) {
               const PairTerms pt = pair_terms(cf[p][0], cf[p][1], cf[p][2], u2, uu2);
               const float2 e = ffma2(vv2, pt.C, ffma2(v2, pt.slope, pt.base));
-              if (COUNT) n_eval += 2 * p + 1 < cnt ? 2 : 1;
+              if (COUNT) n_eval += 2 * p + 1 < kept ? 2 : 1;
               if (e.x >= LOG2_ALPHA_MIN) {
                 const float alpha = fminf(ALPHA_MAX, ex2_approx(e.x));
                 const float Tn = fmaf(-alpha, T[0], T[0]);
                 if (Tn < T_MIN) {
                   stop = true;
-                  if (COUNT && 2 * p + 1 < cnt) --n_eval;
+                  if (COUNT && 2 * p + 1 < kept) --n_eval;
                   break;
                 }
                 const float4 c = cf[p][3];
@@ -271,7 +349,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
                 C1[0] = fmaf(c.y, wgt, C1[0]);
                 C2[0] = fmaf(c.z, wgt, C2[0]);
                 T[0] = Tn;
-                last[0] = lo + 2 * p + 1;
+                last[0] = __float_as_uint(c.w) + 1;
                 if (COUNT) ++n_blend;
               }
               if (e.y >= LOG2_ALPHA_MIN) {  // never true for a missing second entry
@@ -287,7 +365,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
                 C1[0] = fmaf(c.y, wgt, C1[0]);
                 C2[0] = fmaf(c.z, wgt, C2[0]);
                 T[0] = Tn;
-                last[0] = lo + 2 * p + 2;
+                last[0] = __float_as_uint(c.w) + 1;
                 if (COUNT) ++n_blend;
               }
             }
@@ -297,8 +375,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
         } else if (PPT > 1 && !__all_sync(0xffffffffu, done)) {
           for (uint32_t p = 0; p < npairs && !done; ++p) {
             const PairTerms pt = pair_terms(cf[p][0], cf[p][1], cf[p][2], u2, uu2);
-            const bool has_b = 2 * p + 1 < cnt;
-            const uint32_t ia = lo + 2 * p + 1;  // 1-based list position of entry a
+            const bool has_b = 2 * p + 1 < kept;
             bool any_live = false;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
@@ -317,7 +394,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
                     C1[k] = fmaf(c.y, wgt, C1[k]);
                     C2[k] = fmaf(c.z, wgt, C2[k]);
                     T[k] = Tn;
-                    last[k] = ia;
+                    last[k] = __float_as_uint(c.w) + 1;
                     if (COUNT) ++n_blend;
                   }
                 }
@@ -335,7 +412,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
                       C1[k] = fmaf(c.y, wgt, C1[k]);
                       C2[k] = fmaf(c.z, wgt, C2[k]);
                       T[k] = Tn;
-                      last[k] = ia + 1;
+                      last[k] = __float_as_uint(c.w) + 1;
                       if (COUNT) ++n_blend;
                     }
                   }
@@ -464,10 +541,12 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
   constexpr int PER = BATCH / NT;
   __shared__ __align__(128) fgs_record raw[2][BATCH];
   __shared__ __align__(16) float4 cf[BATCH / 2][6];
-  __shared__ uint32_t xidx[BATCH];
+  __shared__ uint32_t xidx[BATCH];  // record of each slot of the batch
+  __shared__ uint32_t cidx[BATCH];  // record of each kept entry
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int64_t s_tile;
   __shared__ uint32_t s_max;
+  __shared__ uint32_t s_cnt[NT / 32];
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid == 0) {
     mbar_init(&bar[0], NT);
@@ -553,12 +632,13 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
           if (b >= 1) mbar_wait(&bar[s ^ 1], s ? phase0 : phase1, status);
           return;
         }
-#pragma unroll 1
-        for (int k = 0; k < PER; ++k) stage_entry<6>(raw[s], tid + k * NT, cnt, tile_cx, tile_cy, cf);
+        const uint32_t kept = stage_batch<NT, PER, 6>(raw[s], lo, cnt, tile_cx, tile_cy, cf, xidx,
+                                                      cidx, s_cnt);
         __syncthreads();
-        const uint32_t npairs = (cnt + 1) / 2;
+        const uint32_t npairs = (kept + 1) / 2;
         for (int p = (int)npairs - 1; p >= 0; --p) {
-          const uint32_t pos_a = lo + 2u * (uint32_t)p, pos_b = pos_a + 1u;
+          const float4 qy = cf[p][5];
+          const uint32_t pos_a = __float_as_uint(qy.z), pos_b = __float_as_uint(qy.w);
           const bool any_pos = pos_a < my_max;
           if (!__any_sync(0xffffffffu, any_pos)) continue;
           float va[9], vb[9];
@@ -567,7 +647,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
           bool ca = false, cb = false;
           if (any_pos) {
             const PairTerms pt = pair_terms(cf[p][0], cf[p][1], cf[p][2], u2, uu2);
-            const float4 qa = cf[p][3], qb = cf[p][4], qy = cf[p][5];
+            const float4 qa = cf[p][3], qb = cf[p][4];
             const float dxa = fu + qa.w, dxb = fu + qb.w;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
@@ -600,14 +680,14 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
             const int q = lane >> 1;  // value index of this lane's total: 0..7 a, 8..15 b
             const bool is_b = q >= 8;
             if ((lane & 1) == 0 && (is_b ? any_b : any_a)) {
-              float *dst = g2d + (size_t)xidx[2 * p + (is_b ? 1 : 0)] * G2D_STRIDE;
+              float *dst = g2d + (size_t)cidx[2 * p + (is_b ? 1 : 0)] * G2D_STRIDE;
               atomicAdd(dst + (q & 7), tot);
             }
-            if (lane == 0 && any_a) atomicAdd(g2d + (size_t)xidx[2 * p] * G2D_STRIDE + 8, tot8);
-            if (lane == 16 && any_b) atomicAdd(g2d + (size_t)xidx[2 * p + 1] * G2D_STRIDE + 8, tot8);
+            if (lane == 0 && any_a) atomicAdd(g2d + (size_t)cidx[2 * p] * G2D_STRIDE + 8, tot8);
+            if (lane == 16 && any_b) atomicAdd(g2d + (size_t)cidx[2 * p + 1] * G2D_STRIDE + 8, tot8);
           }
         }
-        __syncthreads();  // cf / xidx reused by the next batch
+        __syncthreads();  // cf, xidx and cidx reused by the next batch
         if (b >= 1) {
 #pragma unroll
           for (int k = 0; k < PER; ++k) xidx[tid + k * NT] = mine[k];
