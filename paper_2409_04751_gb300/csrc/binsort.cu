@@ -857,7 +857,9 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
       tiles_touched, R, capacity, n_int, &hdr->n_candidates, &hdr->n_visible, scan_lb,
       scan_lb + L.scan_parts, &hdr->scan_parts, vis_rec, vis_off, chunk_first, &hdr->status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  int64_t egrid = (int64_t)sm_count() * 4;
+  // two waves of the 8 CTAs an SM holds: the pair walks wait on record loads and returning
+  // atomics, so more chunks in flight hide more of that latency
+  int64_t egrid = (int64_t)sm_count() * 16;
   if (egrid > L.chunks) egrid = L.chunks;
   if (egrid < 1) egrid = 1;
   const bool ellipse = (flags & FGS_BIN_ELLIPSE) != 0;
