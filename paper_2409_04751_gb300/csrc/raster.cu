@@ -2,24 +2,28 @@
 // backward, sm_103a.
 //
 // One CTA per 16x16 tile with 256/PPT threads; each thread owns PPT vertically adjacent pixels
-// (PPT = 1, 2 or 4, the "work shape"; the image does not depend on it). CTAs are persistent and
-// take tiles from an atomic queue. Each tile's Gaussians are staged through shared memory in
-// batches of 256 records: every thread issues TMA bulk copies (cp.async.bulk, 48 bytes each) of
-// its share, completing on an mbarrier, and the next batch is in flight while the current one is
-// blended (two stages). The sorted indices of the batch after next are prefetched into registers.
-// A warp whose pixels have all stopped skips the batch (warp ballot); the CTA leaves the tile
-// when all its pixels have stopped.
+// (PPT = 1, 2, 4 or 8 in the backward, the "work shape"; the image does not depend on it). CTAs
+// are persistent and take tiles from an atomic queue. Each tile's Gaussians are staged through
+// shared memory in batches: every thread issues TMA bulk copies (cp.async.bulk, 48 bytes each)
+// of its share, completing on an mbarrier, and the next batch is in flight while the current
+// one is blended (two stages); the sorted indices of the batch after next are prefetched into
+// registers. Staging drops the list entries whose alpha >= 1/255 ellipse cannot reach the tile
+// (the exact binning's conservative test: the tile lists keep the rect binning of the method,
+// the blend skips what the rect over-covers) and writes the rest in pairs, so that one paired
+// FP32 FMA (fma.rn.f32x2) advances a pixel's exponent for two Gaussians; every kept entry
+// carries its list position. A warp whose pixels have all stopped skips the batch (warp
+// ballot); the CTA leaves the tile when all its pixels have stopped.
 //
 // The backward replays each pixel's blend back to front from its final transmittance and the
 // number of list entries it processed (both written by the forward), recovering the
 // transmittance before each Gaussian by division; nothing per (pixel, Gaussian) is stored. Per
 // contributing pair it accumulates nine sums that depend on the pixel only: the moments
 // sum dL/dp (dx, dy, dx^2, dx dy, dy^2) of the exponent p = -0.5 d^T conic d, sum dL/dalpha
-// alpha_raw, and dL/drgb. Each thread first sums its own pixels; the warp then reduces the nine
-// sums with a transpose reduction (each exchange halves the values a lane carries: 14 shuffles
-// instead of 45) and eight lanes add their totals to the record's accumulator. The preprocess
-// backward turns the moments into dL/dxy, dL/dconic and dL/dopacity with the record's conic and
-// opacity.
+// alpha_raw, and dL/drgb. Each thread first sums its own pixels; the warp then reduces two
+// entries' eighteen sums with a transpose reduction (each exchange halves the values a lane
+// carries) and lanes add the totals to the records' accumulators. The preprocess backward turns
+// the moments into dL/dxy, dL/dconic and dL/dopacity with the record's conic and opacity. The
+// backward takes its tiles longest first (tile_work_kernel, tile_order_kernel).
 #include "fgs_internal.cuh"
 
 namespace fgs {
