@@ -339,8 +339,11 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
               const PairTerms pt = pair_terms(cf[p][0], cf[p][1], cf[p][2], u2, uu2);
               const float2 e = ffma2(vv2, pt.C, ffma2(v2, pt.slope, pt.base));
               if (COUNT) n_eval += 2 * p + 1 < kept ? 2 : 1;
-              if (e.x >= LOG2_ALPHA_MIN) {
-                const float alpha = fminf(ALPHA_MAX, ex2_approx(e.x));
+              // branch-free blends: an entry below 1/255 gets alpha = 0, which leaves T, the
+              // colour and the processed count exactly as they were
+              const bool ca = e.x >= LOG2_ALPHA_MIN, cb = e.y >= LOG2_ALPHA_MIN;
+              {
+                const float alpha = ca ? fminf(ALPHA_MAX, ex2_approx(e.x)) : 0.f;
                 const float Tn = fmaf(-alpha, T[0], T[0]);
                 if (Tn < T_MIN) {
                   stop = true;
@@ -353,11 +356,11 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
                 C1[0] = fmaf(c.y, wgt, C1[0]);
                 C2[0] = fmaf(c.z, wgt, C2[0]);
                 T[0] = Tn;
-                last[0] = __float_as_uint(c.w) + 1;
-                if (COUNT) ++n_blend;
+                last[0] = ca ? __float_as_uint(c.w) + 1 : last[0];
+                if (COUNT && ca) ++n_blend;
               }
-              if (e.y >= LOG2_ALPHA_MIN) {  // never true for a missing second entry
-                const float alpha = fminf(ALPHA_MAX, ex2_approx(e.y));
+              {
+                const float alpha = cb ? fminf(ALPHA_MAX, ex2_approx(e.y)) : 0.f;
                 const float Tn = fmaf(-alpha, T[0], T[0]);
                 if (Tn < T_MIN) {
                   stop = true;
@@ -369,8 +372,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
                 C1[0] = fmaf(c.y, wgt, C1[0]);
                 C2[0] = fmaf(c.z, wgt, C2[0]);
                 T[0] = Tn;
-                last[0] = __float_as_uint(c.w) + 1;
-                if (COUNT) ++n_blend;
+                last[0] = cb ? __float_as_uint(c.w) + 1 : last[0];
+                if (COUNT && cb) ++n_blend;
               }
             }
             if (stop) live[0] = false;
