@@ -502,15 +502,20 @@ __device__ __forceinline__ float warp_transpose_sum16(const float (&a)[9], const
   return f;
 }
 
-// One contributing (pixel, Gaussian) pair of the backward, back to front: recovers the
-// transmittance in front of the Gaussian, updates the colour-behind sum GS and adds the
-// pixel's terms to the nine per-record sums v.
-__device__ __forceinline__ void bwd_contrib(float e, float r, float g, float b, float dx, float dy,
-                                            float G0, float G1, float G2, float &T, float &GS,
-                                            float (&v)[9]) {
-  const float araw = ex2_approx(e);
+// One (pixel, Gaussian) pair of the backward, back to front, its contribution decided by c:
+// recovers the transmittance in front of the Gaussian, updates the colour-behind sum GS and
+// adds the pixel's terms to the nine per-record sums v. A pixel that does not take part (not
+// yet reached back to front, or alpha below 1/255) gets alpha = 0 and 1/(1 - alpha) = 1 by
+// selection, so its transmittance, GS and sums stay exactly as they were. The backward calls
+// it for every pixel and entry without branching: the cull at staging leaves most evaluations
+// contributing, and straight-line code lets the compiler interleave the independent
+// transmittance chains of a thread's pixels, which hides the latency of each chain.
+__device__ __forceinline__ void bwd_contrib(bool c, float e, float r, float g, float b, float dx,
+                                            float dy, float G0, float G1, float G2, float &T,
+                                            float &GS, float (&v)[9]) {
+  const float araw = c ? ex2_approx(e) : 0.f;
   const float alpha = fminf(ALPHA_MAX, araw);
-  const float om = rcp_approx(1.f - alpha);
+  const float om = c ? rcp_approx(1.f - alpha) : 1.f;
   T *= om;  // transmittance before this Gaussian
   const float wgt = alpha * T;
   const float gc = G0 * r + G1 * g + G2 * b;  // <dL/dC, colour>
@@ -520,19 +525,18 @@ __device__ __forceinline__ void bwd_contrib(float e, float r, float g, float b, 
   v[6] = fmaf(G0, wgt, v[6]);
   v[7] = fmaf(G1, wgt, v[7]);
   v[8] = fmaf(G2, wgt, v[8]);
-  if (araw < ALPHA_MAX) {
-    // alpha = opacity exp(p), p = -0.5 d^T conic d: accumulate the moments of dL/dp over the
-    // pixel offsets; the conic and opacity are applied once per record in the preprocess
-    // backward
-    const float dLdp = dLda * alpha;
-    const float tx = dLdp * dx, ty = dLdp * dy;
-    v[0] += tx;
-    v[1] += ty;
-    v[2] = fmaf(tx, dx, v[2]);
-    v[3] = fmaf(tx, dy, v[3]);
-    v[4] = fmaf(ty, dy, v[4]);
-    v[5] = fmaf(dLda, araw, v[5]);
-  }
+  // alpha = opacity exp(p), p = -0.5 d^T conic d: the moments of dL/dp over the pixel offsets
+  // and the opacity term, where alpha is below its cap; the conic and opacity are applied once
+  // per record in the preprocess backward
+  const bool free_ = araw < ALPHA_MAX;
+  const float dLdp = dLda * (free_ ? alpha : 0.f);
+  const float tx = dLdp * dx, ty = dLdp * dy;
+  v[0] += tx;
+  v[1] += ty;
+  v[2] = fmaf(tx, dx, v[2]);
+  v[3] = fmaf(tx, dy, v[3]);
+  v[4] = fmaf(ty, dy, v[4]);
+  v[5] = fmaf(dLda, free_ ? araw : 0.f, v[5]);
 }
 
 template <int PPT, bool COUNT>
@@ -652,32 +656,26 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
 #pragma unroll
           for (int q = 0; q < 9; ++q) va[q] = vb[q] = 0.f;
           bool ca = false, cb = false;
-          if (any_pos) {
+          {
             const PairTerms pt = pair_terms(cf[p][0], cf[p][1], cf[p][2], u2, uu2);
             const float4 qa = cf[p][3], qb = cf[p][4];
             const float dxa = fu + qa.w, dxb = fu + qb.w;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-              if (pos_a < last[k]) {
-                const float vk = fv + (float)k;
-                const float2 e = pair_exponent(pt, vk);
-                if (pos_b < last[k]) {  // the later entry first (back to front)
-                  if (COUNT) ++n_eval;
-                  if (e.y >= LOG2_ALPHA_MIN) {
-                    cb = true;
-                    if (COUNT) ++n_contrib;
-                    bwd_contrib(e.y, qb.x, qb.y, qb.z, dxb, vk + qy.y, G0[k], G1[k], G2[k],
-                                T[k], GS[k], vb);
-                  }
-                }
-                if (COUNT) ++n_eval;
-                if (e.x >= LOG2_ALPHA_MIN) {
-                  ca = true;
-                  if (COUNT) ++n_contrib;
-                  bwd_contrib(e.x, qa.x, qa.y, qa.z, dxa, vk + qy.x, G0[k], G1[k], G2[k],
-                              T[k], GS[k], va);
-                }
+              const bool in_a = pos_a < last[k], in_b = pos_b < last[k];
+              const float vk = fv + (float)k;
+              const float2 e = pair_exponent(pt, vk);
+              const bool cbk = in_b && e.y >= LOG2_ALPHA_MIN, cak = in_a && e.x >= LOG2_ALPHA_MIN;
+              if (COUNT) {
+                n_eval += (in_a ? 1u : 0u) + (in_b ? 1u : 0u);
+                n_contrib += (cak ? 1u : 0u) + (cbk ? 1u : 0u);
               }
+              cb = cb || cbk;
+              ca = ca || cak;
+              bwd_contrib(cbk, e.y, qb.x, qb.y, qb.z, dxb, vk + qy.y, G0[k], G1[k], G2[k], T[k],
+                            GS[k], vb);
+              bwd_contrib(cak, e.x, qa.x, qa.y, qa.z, dxa, vk + qy.x, G0[k], G1[k], G2[k], T[k],
+                            GS[k], va);
             }
           }
           const bool any_a = __any_sync(0xffffffffu, ca), any_b = __any_sync(0xffffffffu, cb);
