@@ -246,6 +246,29 @@ __device__ __forceinline__ float2 pair_exponent(const PairTerms &t, float v) {
   return ffma2(dup2(v * v), t.C, ffma2(dup2(v), t.slope, t.base));
 }
 
+// One list entry blended into one pixel without branches: the entry takes part if the pixel is
+// live and its exponent reaches 1/255; the pixel stops (and is left unchanged) if the blend
+// would take its transmittance below 1e-4. alpha is selected to 0 otherwise, which leaves T,
+// the colour and the processed count exactly as they were. q = (r, g, b, list position bits).
+template <bool COUNT>
+__device__ __forceinline__ void fwd_blend(bool &live, float e, const float4 &q, float &T,
+                                          float &C0, float &C1, float &C2, uint32_t &last,
+                                          uint32_t &n_blend) {
+  const bool c = live && e >= LOG2_ALPHA_MIN;
+  const float alpha = c ? fminf(ALPHA_MAX, ex2_approx(e)) : 0.f;
+  const bool stop = c && fmaf(-alpha, T, T) < T_MIN;
+  live = live && !stop;
+  const float a = stop ? 0.f : alpha;
+  const float wgt = a * T;
+  C0 = fmaf(q.x, wgt, C0);
+  C1 = fmaf(q.y, wgt, C1);
+  C2 = fmaf(q.z, wgt, C2);
+  T = fmaf(-a, T, T);
+  const bool blended = c && !stop;
+  last = blended ? __float_as_uint(q.w) + 1 : last;
+  if (COUNT && blended) ++n_blend;
+}
+
 template <int PPT, bool COUNT>
 __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
     raster_fwd_kernel(const fgs_record *__restrict__ rec, const uint32_t *__restrict__ vals,
@@ -380,51 +403,21 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
             done = !live[0];
           }
         } else if (PPT > 1 && !__all_sync(0xffffffffu, done)) {
+          // several pixels per thread, blended without branches (alpha selected to 0 where a
+          // pixel does not take part or has stopped), so that the compiler interleaves the
+          // pixels' transmittance chains
           for (uint32_t p = 0; p < npairs && !done; ++p) {
             const PairTerms pt = pair_terms(cf[p][0], cf[p][1], cf[p][2], u2, uu2);
+            const float4 qa = cf[p][3], qb = cf[p][4];
             const bool has_b = 2 * p + 1 < kept;
             bool any_live = false;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-              if (live[k]) {
-                const float2 e = pair_exponent(pt, fv + (float)k);
-                if (COUNT) ++n_eval;
-                if (e.x >= LOG2_ALPHA_MIN) {
-                  const float alpha = fminf(ALPHA_MAX, ex2_approx(e.x));
-                  const float Tn = fmaf(-alpha, T[k], T[k]);
-                  if (Tn < T_MIN) {
-                    live[k] = false;
-                  } else {
-                    const float4 c = cf[p][3];
-                    const float wgt = alpha * T[k];
-                    C0[k] = fmaf(c.x, wgt, C0[k]);
-                    C1[k] = fmaf(c.y, wgt, C1[k]);
-                    C2[k] = fmaf(c.z, wgt, C2[k]);
-                    T[k] = Tn;
-                    last[k] = __float_as_uint(c.w) + 1;
-                    if (COUNT) ++n_blend;
-                  }
-                }
-                if (live[k]) {
-                  if (COUNT && has_b) ++n_eval;
-                  if (e.y >= LOG2_ALPHA_MIN) {  // never true for a missing second entry
-                    const float alpha = fminf(ALPHA_MAX, ex2_approx(e.y));
-                    const float Tn = fmaf(-alpha, T[k], T[k]);
-                    if (Tn < T_MIN) {
-                      live[k] = false;
-                    } else {
-                      const float4 c = cf[p][4];
-                      const float wgt = alpha * T[k];
-                      C0[k] = fmaf(c.x, wgt, C0[k]);
-                      C1[k] = fmaf(c.y, wgt, C1[k]);
-                      C2[k] = fmaf(c.z, wgt, C2[k]);
-                      T[k] = Tn;
-                      last[k] = __float_as_uint(c.w) + 1;
-                      if (COUNT) ++n_blend;
-                    }
-                  }
-                }
-              }
+              const float2 e = pair_exponent(pt, fv + (float)k);
+              if (COUNT && live[k]) ++n_eval;
+              fwd_blend<COUNT>(live[k], e.x, qa, T[k], C0[k], C1[k], C2[k], last[k], n_blend);
+              if (COUNT && live[k] && has_b) ++n_eval;
+              fwd_blend<COUNT>(live[k], e.y, qb, T[k], C0[k], C1[k], C2[k], last[k], n_blend);
               any_live = any_live || live[k];
             }
             done = !any_live;
