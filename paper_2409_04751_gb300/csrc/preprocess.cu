@@ -49,13 +49,15 @@ __global__ void __launch_bounds__(256)
   // view-independent: Sigma and the footprint level q* = 2 ln(255 opacity)
   float S[6] = {0, 0, 0, 0, 0, 0};
   float qs = 0.f;
+  // issued with the mean and opacity, not after the opacity test: one memory round trip
+  const float4 q = load_quat<VEC>(g.quats, i);
+  const float sx = __ldg(g.scales + 3 * i), sy = __ldg(g.scales + 3 * i + 1),
+              sz = __ldg(g.scales + 3 * i + 2);
   if (op_ok) {
-    float4 q = load_quat<VEC>(g.quats, i);
     float qn = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
     float R[9];
     quat_to_rot(q.x * qn, q.y * qn, q.z * qn, q.w * qn, R);
-    covariance(R, __ldg(g.scales + 3 * i), __ldg(g.scales + 3 * i + 1),
-               __ldg(g.scales + 3 * i + 2), S);
+    covariance(R, sx, sy, sz, S);
     qs = fmaxf(2.f * logf(255.f * op), 0.f);
   }
 
@@ -172,6 +174,10 @@ __global__ void __launch_bounds__(PRE_BWD_THREADS, 4)
   const float mx = in ? __ldg(g.means + 3 * i) : 0.f, my = in ? __ldg(g.means + 3 * i + 1) : 0.f,
               mz = in ? __ldg(g.means + 3 * i + 2) : 0.f;
   const float *shp = g.sh + (size_t)(in ? i : 0) * K3;
+  // issued with the mean, not after the visibility test: one memory round trip fewer
+  const float4 q0 = in ? load_quat<VEC>(g.quats, i) : make_float4(1.f, 0.f, 0.f, 0.f);
+  const float sc0 = in ? __ldg(g.scales + 3 * i) : 1.f, sc1 = in ? __ldg(g.scales + 3 * i + 1) : 1.f,
+              sc2 = in ? __ldg(g.scales + 3 * i + 2) : 1.f;
 
   for (int v = 0; in && v < vs.n; ++v) {
     const int64_t r = (int64_t)v * g.n + i;
@@ -180,13 +186,12 @@ __global__ void __launch_bounds__(PRE_BWD_THREADS, 4)
     const bool first = !any;
     if (first) {
       any = true;
-      float4 q = load_quat<VEC>(g.quats, i);
+      const float4 q = q0;
       qnorm = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
       const float iq = 1.f / qnorm;
       qnv[0] = q.x * iq; qnv[1] = q.y * iq; qnv[2] = q.z * iq; qnv[3] = q.w * iq;
       quat_to_rot(qnv[0], qnv[1], qnv[2], qnv[3], R);
-      covariance(R, __ldg(g.scales + 3 * i), __ldg(g.scales + 3 * i + 1),
-                 __ldg(g.scales + 3 * i + 2), S);
+      covariance(R, sc0, sc1, sc2, S);
     }
     // the rasterizer backward leaves, per record, the moments of dL/dp over the pixel offsets
     // d = pixel - xy (p = -0.5 d^T conic d): m = sum dL/dp (dx, dy, dx^2, dx dy, dy^2), then
