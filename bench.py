@@ -144,9 +144,20 @@ class ClockSampler:
                     samples=len(rows))
 
 
+def code_hash(text):
+    """sha256 prefix of C/C++/CUDA source with its comments and whitespace removed: the same for
+    two versions of a file that differ only in comments or layout, so a comment edit does not
+    retire a profile taken on the same code."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    text = re.sub(r"\s+", " ", text).strip()
+    return hashlib.sha256(text.encode()).hexdigest()[:16]
+
+
 def _traffic(kernel_name):
     """DRAM bytes per launch of `kernel_name` from the committed ncu summary, if it was taken
-    on the current source (sha256 of the kernel's .cu file); else None."""
+    on the current code of the kernel's .cu file (code_hash); else None."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(p):
         return None
@@ -157,8 +168,7 @@ def _traffic(kernel_name):
         src = os.path.join(ROOT, "paper_2409_04751_gb300", "csrc", f.get("source", ""))
         if not os.path.exists(src):
             return None
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if sha != f.get("sha"):
+        if code_hash(open(src).read()) != f.get("code"):
             return None
         return float(f["dram_bytes_per_launch"])
     return None

@@ -31,8 +31,8 @@ namespace fgs {
 namespace {
 
 constexpr int TILE_PIX = TILE * TILE;  // 256 pixels per tile
-// Gaussians per staged batch: 256, or 128 for the 4-pixels-per-thread shape, whose CTAs are
-// small and need a small shared-memory footprint to keep enough of them resident
+// Gaussians per staged batch: 256, or 128 and 64 for the 4- and 8-pixels-per-thread shapes,
+// whose CTAs are small and need a small shared-memory footprint to keep enough of them resident
 template <int PPT>
 struct Batch {
   static constexpr int N = PPT == 8 ? 64 : (PPT == 4 ? 128 : 256);
