@@ -8,7 +8,7 @@
 // each tile's bucket is sorted on its own:
 //
 //  1. scan_kernel: single-pass scan of tiles_touched with decoupled look-back (partitions of
-//     1024 records claimed in order through an atomic counter). For every record with pairs it
+//     4096 records claimed in order through an atomic counter). For every record with pairs it
 //     writes its pair offset and its rank among such records (a compacted list), and for every
 //     1024-pair chunk the rank of the record holding the chunk's first pair.
 //  2. rect binning: rect_diff_kernel and grid_scan_kernel count the pairs of every tile from a

@@ -85,7 +85,7 @@ struct WsHeader {
 static_assert(sizeof(WsHeader) == 256, "header size");
 
 constexpr int EMIT_THREADS = 256;
-constexpr int EMIT_ITEMS = 4;
+constexpr int EMIT_ITEMS = 16;
 constexpr int EMIT_PART = EMIT_THREADS * EMIT_ITEMS;  // records per scan partition
 constexpr int EMIT_CHUNK = 1024;                      // (record, tile) pairs per emission CTA
 constexpr int TSCAN_PART = 1024;                     // tiles per partition of the tile scan
