@@ -84,7 +84,7 @@ def _oracle(rect, depth, n, cams_py):
 @pytest.mark.parametrize("n,sizes,seed,kw", [
     (1, [(64, 48)], 0, {}),
     (700, [(100, 90)], 1, {}),                                     # one scan partition
-    (5000, [(256, 256)], 2, dict(max_ext=6)),                      # several partitions
+    (9000, [(256, 256)], 2, dict(max_ext=6)),                      # several partitions
     (3000, [(256, 256), (96, 40), (1752, 1168)], 3, dict(max_ext=4)),  # multi-view, ragged
     (20000, [(1752, 1168)], 4, dict(max_ext=10, big_frac=0.002)),  # ~1M pairs, huge rects
     (4000, [(16, 16)], 5, dict(tie_frac=0.9)),                     # one tile, heavy ties
