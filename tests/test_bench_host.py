@@ -1,0 +1,35 @@
+"""Host-side helpers of the benchmark: the code hash that keys committed ncu figures to the
+kernel source they were taken on (blind to comments and layout, not to code), the job rate and
+the single-process max over ranks, and the render working-set formula."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_code_hash_ignores_comments_and_layout_only():
+    a = "int f(int x) {\n  return x + 1;  // one more\n}\n"
+    b = "/* header\n   comment */\nint f(int x)\n{\n    return x + 1;\n}\n"
+    c = "int f(int x) {\n  return x + 2;\n}\n"
+    assert bench.code_hash(a) == bench.code_hash(b)
+    assert bench.code_hash(a) != bench.code_hash(c)
+
+
+def test_rates_and_single_process_max():
+    assert bench.job_rate(4, 10, 2.0) == pytest.approx(20.0)
+    assert bench.max_over_ranks(1.5) == 1.5
+
+
+def test_render_bytes_counts_every_buffer():
+    from paper_2409_04751_gb300 import fgs, scenes
+    cam = scenes.fisheye_camera(64, 32, 180.0)
+    cams = fgs.cameras([cam])
+    n, m = 1000, 5000
+    got = bench.render_bytes(fgs, n, cams, 1, m)
+    tiles, pix = 4 * 2, 64 * 32
+    ws = fgs.fgs_workspace_size(n, cams, m, 0)
+    assert got == n * 52 + m * 12 + tiles * 8 + ws + pix * 20
