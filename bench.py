@@ -75,6 +75,17 @@ def render_bytes(fgs, n, cams_c, n_views, m, flags=0):
     return R * (48 + 4) + int(m) * 12 + T * 8 + ws + P * (12 + 4 + 4)
 
 
+# pixels per thread of the rasterizers when the tuner is off (the library's defaults)
+DEFAULT_SHAPE = (1, 8)
+
+
+def fp32_units(props):
+    """(SM count, FP32 lanes per SM) of a device: the count from its properties, the lanes
+    from its compute capability (128 on every architecture from 8.6 on, 64 on 8.0 and 6.0)."""
+    lanes = 64 if (props.major, props.minor) in ((6, 0), (8, 0)) else 128
+    return int(props.multi_processor_count), lanes
+
+
 def job_rate(world, steps, seconds):
     """Whole-job views/s: every rank renders `steps` views in `seconds` (the slowest rank's)."""
     return world * steps / seconds
@@ -179,8 +190,8 @@ def _traffic(kernel_name):
 
 def _oracle_sample_rate(scene, cam, target_s, rng_seed=0):
     """Time the FP64 oracle's fwd+bwd on a pixel sample sized for about target_s seconds and
-    extrapolate to views/s for the full view. Returns (views_per_s, seconds, sample_desc,
-    threads)."""
+    extrapolate to views/s for the full view. The sample holds at least 256 pixels per thread,
+    so every OpenMP thread has work. Returns (views_per_s, seconds, sample_desc, threads)."""
     import oracle
     w, h = cam["width"], cam["height"]
     P = w * h
@@ -188,7 +199,7 @@ def _oracle_sample_rate(scene, cam, target_s, rng_seed=0):
     t0 = time.perf_counter()
     G = oracle.project(scene, cam)
     t_proj = time.perf_counter() - t0
-    n_pix = 256
+    n_pix = min(P, 256 * oracle.num_threads())
     spent = 0.0
     per_pix = None
     while True:
@@ -205,12 +216,90 @@ def _oracle_sample_rate(scene, cam, target_s, rng_seed=0):
             break
         n_pix = int(min(P, max(n_pix * 2, (target_s - spent) / max(per_pix, 1e-9))))
     est = t_proj + per_pix * P
-    desc = (f"oracle fwd+bwd on {n_pix} random pixels of the 1752x1168 view "
+    desc = (f"oracle fwd+bwd on {n_pix} random pixels of the {w}x{h} view "
             f"(+ projection of all Gaussians), extrapolated to the full view")
     return 1.0 / est, spent + t_proj, desc, oracle.num_threads()
 
 
+def _oracle_full_view(scene, cam):
+    """The FP64 oracle on every pixel of one view: (forward seconds, fwd+bwd seconds, threads).
+    Forward = projection + blend of every pixel; backward = the analytic gradient of every
+    parameter for dL/dimage ~ N(0, 1e-2)."""
+    import oracle
+    t0 = time.perf_counter()
+    G = oracle.project(scene, cam)
+    pix = oracle.all_pixels(cam)
+    oracle.render(G, pix)
+    t1 = time.perf_counter()
+    g = np.random.default_rng(1).normal(0, 1e-2, (pix.shape[0], 3))
+    oracle.backward(G, scene, cam, pix, g)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t0, oracle.num_threads()
+
+
+def cpu_job(kind, target_s):
+    """One CPU leg, run in a fresh process whose OpenMP thread count the caller set:
+    'config0' times the 10k-Gaussian 256x256 view in full, 'config1' a bounded sample of the
+    benchmark view. Returns a dict."""
+    from paper_2409_04751_gb300 import scenes
+    if kind == "config0":
+        scene, cams = scenes.config0()
+        fwd, both, thr = _oracle_full_view(scene, cams[0])
+        return dict(threads=thr, fwd_s=fwd, fwd_bwd_s=both, fwd_views_per_s=1.0 / fwd,
+                    fwd_bwd_views_per_s=1.0 / both)
+    scene, cams = scenes.config1()
+    v, secs, desc, thr = _oracle_sample_rate(scene, cams[0], target_s)
+    return dict(threads=thr, fwd_bwd_views_per_s=v, seconds=secs, sample=desc)
+
+
+def run_cpu_job(kind, threads, target_s):
+    """cpu_job in a subprocess (a fresh process: no CUDA state, its own OpenMP runtime) with
+    OMP_NUM_THREADS = threads (0 = the runtime's default, every host core)."""
+    env = dict(os.environ)
+    if threads:
+        env["OMP_NUM_THREADS"] = str(threads)
+    else:
+        env.pop("OMP_NUM_THREADS", None)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-job", kind,
+                        "--cpu-seconds", str(target_s)], env=env, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"cpu job {kind} failed: {r.stderr[-2000:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_legs(target_s):
+    """The oracle on the host cores, single-threaded and on every core: config 0 (10k Gaussians,
+    256x256) in full, forward and fwd+bwd; the benchmark view (config 1) as a bounded sample of
+    pixels, extrapolated. Returns the cpu_baseline object of the JSON line."""
+    legs = {}
+    for threads, tag in ((0, "all_cores"), (1, "one_core")):
+        legs[tag] = dict(config0=run_cpu_job("config0", threads, target_s),
+                         config1=run_cpu_job("config1", threads, target_s))
+    allc = legs["all_cores"]
+    return dict(value=allc["config1"]["fwd_bwd_views_per_s"], unit="views/s",
+                cores=allc["config1"]["threads"], kind="oracle",
+                sample=allc["config1"]["sample"], seconds=round(allc["config1"]["seconds"], 2),
+                host_cpus=os.cpu_count(),
+                config0_full={tag: dict(threads=l["config0"]["threads"],
+                                        fwd_s=round(l["config0"]["fwd_s"], 3),
+                                        fwd_bwd_s=round(l["config0"]["fwd_bwd_s"], 3),
+                                        fwd_views_per_s=l["config0"]["fwd_views_per_s"],
+                                        fwd_bwd_views_per_s=l["config0"]["fwd_bwd_views_per_s"])
+                              for tag, l in legs.items()},
+                config1_sample={tag: dict(threads=l["config1"]["threads"],
+                                          fwd_bwd_views_per_s=l["config1"]["fwd_bwd_views_per_s"],
+                                          seconds=round(l["config1"]["seconds"], 2))
+                                for tag, l in legs.items()},
+                note="value: the benchmark view (500k Gaussians, 1752x1168) on every core, "
+                     "from a timed pixel sample; config0_full: the 10k-Gaussian 256x256 view "
+                     "rendered and differentiated at every pixel")
+
+
 def run_reference(args):
+    """The FP64 oracle on the host cores for the benchmark workload. A step is a bounded sample
+    of one view: the projection of all Gaussians and fwd+bwd of 256 random pixels per OpenMP
+    thread (so every core has work). ms_per_step is that step's measured time; value is views/s
+    extrapolated from it (projection + per-pixel time x the view's pixels)."""
     rank, world, _ = _env_rank()
     if rank != 0:
         return 0
@@ -218,13 +307,14 @@ def run_reference(args):
     scene, cams = scenes.config1()
     cam = cams[0]
     import oracle
-    G = oracle.project(scene, cam)
     w, h = cam["width"], cam["height"]
+    P = w * h
     rng = np.random.default_rng(5)
-    n_pix = 512
-    times = []
+    threads = oracle.num_threads()
+    n_pix = min(P, 256 * threads)
+    step_s, view_s = [], []
     for step in range(args.warmup + args.steps):
-        idx = rng.choice(w * h, n_pix, replace=False)
+        idx = rng.choice(P, n_pix, replace=False)
         pix = np.stack([idx % w, idx // w], 1).astype(np.int32)
         g = rng.normal(0, 1e-2, (n_pix, 3))
         t0 = time.perf_counter()
@@ -234,19 +324,22 @@ def run_reference(args):
         oracle.backward(Gs, scene, cam, pix, g)
         t2 = time.perf_counter()
         if step >= args.warmup:
-            times.append((t1 - t0) + (t2 - t1) * (w * h) / n_pix)
-    per_view = sum(times) / len(times)
+            step_s.append(t2 - t0)
+            view_s.append((t1 - t0) + (t2 - t1) * P / n_pix)
+    per_view = sum(view_s) / len(view_s)
     value = 1.0 / per_view
+    sample = (f"per step: projection of all 500k Gaussians + fwd+bwd of {n_pix} random pixels "
+              f"({threads} OpenMP threads x 256) of the 1752x1168 view; views/s extrapolated to "
+              "the full view")
     line = dict(metric=METRIC, value=value, unit="views/s", n_gpus=args.gpus, steps=args.steps,
-                warmup=args.warmup, ms_per_step=per_view * 1e3, higher_is_better=True,
-                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-                impl="reference",
+                warmup=args.warmup, ms_per_step=1e3 * sum(step_s) / len(step_s),
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic", impl="reference",
                 config=dict(workload=WORKLOAD, n_gaussians=500000, width=1752, height=1168,
                             fov_deg=180.0, sh_degree=3),
-                cpu_baseline=dict(value=value, unit="views/s", cores=oracle.num_threads(),
-                                  kind="oracle",
-                                  sample=f"per step: projection of all Gaussians + fwd+bwd of "
-                                         f"{n_pix} random pixels, extrapolated to 1752x1168"),
+                view_fraction_per_step=n_pix / P, ms_per_view_extrapolated=per_view * 1e3,
+                cpu_baseline=dict(value=value, unit="views/s", cores=threads, kind="oracle",
+                                  sample=sample),
                 e2e=dict(value=value, unit="views/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0),
                 gpu_launches=0)
     print(json.dumps(line))
@@ -287,7 +380,8 @@ def run_gpu(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def stages(ev, with_bwd=True):
+    def stages(ev, with_bwd=True, opts=None):
+        opts = opts or r.opts
         ev[0].record(stream)
         fgs.fgs_preprocess(g, cam_c, fr.records, fr.tiles_touched)
         ev[1].record(stream)
@@ -295,11 +389,11 @@ def run_gpu(args):
                          fr.tile_ranges, fr.n_intersections, ws, wsb)
         ev[2].record(stream)
         fgs.fgs_rasterize(fr.records, fr.vals, fr.tile_ranges, cam_c, None, fr.images,
-                          fr.final_T, fr.n_processed, ws, wsb)
+                          fr.final_T, fr.n_processed, ws, wsb, opts=opts)
         ev[3].record(stream)
         if with_bwd:
             fgs.fgs_backward_raster(fr.records, fr.vals, fr.tile_ranges, n, cam_c, None,
-                                    fr.final_T, fr.n_processed, dL, ws, wsb)
+                                    fr.final_T, fr.n_processed, dL, ws, wsb, opts=opts)
             ev[4].record(stream)
             fgs.fgs_backward_preprocess(g, cam_c, fr.records, fr.tiles_touched, grads["means"],
                                         grads["scales"], grads["quats"], grads["opacities"],
@@ -312,23 +406,23 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # work shape of the rasterizers, chosen by the autotuner on this workload (untimed)
-    shape = {"fwd": 2, "bwd": 2}
+    # work shape of the rasterizers, chosen by the autotuner on this workload (untimed) and
+    # passed with every call of this renderer (fgs_options)
+    shape = {"fwd": DEFAULT_SHAPE[0], "bwd": DEFAULT_SHAPE[1]}
     if args.raster_shape:
         f, b = (int(x) for x in args.raster_shape.split(","))
         shape = {"fwd": f, "bwd": b}
-        fgs.fgs_set_raster_shape(f, b)
+        r.set_shape(f, b)
     elif not args.no_tune:
         from paper_2409_04751_gb300.autotune import tune_raster
         shape = tune_raster(r, gs, fr, dL, use_cache=False)
     else:
-        fgs.fgs_set_raster_shape(2, 2)
+        r.set_shape(*DEFAULT_SHAPE)
 
     # instrumented pass (untimed): algorithmic work of the rasterizer
-    fgs.fgs_set_instrumentation(True)
-    stages([torch.cuda.Event(enable_timing=True) for _ in range(6)])
+    stages([torch.cuda.Event(enable_timing=True) for _ in range(6)],
+           opts=fgs.options(fwd=shape["fwd"], bwd=shape["bwd"], instrument=True))
     counters = fgs.fgs_read_counters(ws)
-    fgs.fgs_set_instrumentation(False)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -377,7 +471,7 @@ def run_gpu(args):
     from paper_2409_04751_gb300.batched import GraphBatch
     graph_s = {}
     for with_bwd in (True, False):
-        gb = GraphBatch(gs, cams, backward=with_bwd, device=dev)
+        gb = GraphBatch(gs, cams, backward=with_bwd, device=dev, shape=r.shape)
         gb.dL_dimages.copy_(dL)
         for _ in range(args.warmup):
             flush.zero_()
@@ -413,7 +507,7 @@ def run_gpu(args):
     host_g = {k: torch.empty_like(host_in[k]).pin_memory() for k in host_in}
     h2d = sum(t.numel() * 4 for t in host_in.values()) + host_dL.numel() * 4
     d2h = host_img.numel() * 4 + sum(t.numel() * 4 for t in host_g.values())
-    pipe = HostPipeline(n, scene["sh_degree"], cams, dev, capacity=cap)
+    pipe = HostPipeline(n, scene["sh_degree"], cams, dev, capacity=cap, shape=r.shape)
     pipe.size(host_in)
     for _ in range(args.warmup):
         h = pipe.submit(host_in, host_dL, host_img, host_g)
@@ -439,7 +533,8 @@ def run_gpu(args):
     peaks = _peaks()
     names = ["preprocess_fwd", "bin_sort", "raster_fwd", "raster_bwd", "preprocess_bwd"]
     dom = int(np.argmax(stage_ms))
-    fp32_peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12  # TFLOP/s
+    sms, lanes = fp32_units(torch.cuda.get_device_properties(dev))
+    fp32_peak = sms * lanes * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12  # TFLOP/s
     kern = {}
     fwd_flops = counters[0] * FLOPS_FWD_EVAL + counters[1] * FLOPS_FWD_BLEND
     bwd_flops = counters[2] * FLOPS_BWD_EVAL + counters[3] * FLOPS_BWD_CONTRIB
@@ -469,15 +564,14 @@ def run_gpu(args):
                                 "bin_sort": "segsort_kernel",
                                 "preprocess_fwd": "preprocess_fwd_kernel",
                                 "preprocess_bwd": "preprocess_bwd_kernel"}[names[dom]])
-    roof["peak_source"] = ("FP32: 152 SMs x 128 lanes x 2 x max SM clock "
-                           f"({peaks['sm_max_mhz']:.0f} MHz, {peaks['source']})"
+    roof["peak_source"] = (f"FP32: {sms} SMs (device properties) x {lanes} FP32 lanes per SM "
+                           f"(compute capability {torch.cuda.get_device_capability(dev)}) x 2 x "
+                           f"max SM clock ({peaks['sm_max_mhz']:.0f} MHz, {peaks['source']})"
                            if roof["bound"] == "alu" else f"HBM copy, {peaks['source']}")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, secs, desc, thr = _oracle_sample_rate(scene, cams[0], args.cpu_seconds)
-        cpu = dict(value=v, unit="views/s", cores=thr, kind="oracle", sample=desc,
-                   seconds=round(secs, 2))
+        cpu = cpu_baseline_legs(args.cpu_seconds)
 
     batched = None
     if rank == 0 and world == 1 and not args.no_batched:
@@ -863,7 +957,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="fgs", choices=["fgs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--cpu-job", default="", help=argparse.SUPPRESS)
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
@@ -883,8 +978,12 @@ def main():
     ap.add_argument("--batch-views", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--raster-shape", default="",
-                    help="pixels per thread 'fwd,bwd' (1, 2 or 4); skips the autotuner")
+                    help="pixels per thread 'fwd,bwd' (fwd 1, 2 or 4; bwd 1, 2, 4 or 8); skips "
+                         "the autotuner")
     args = ap.parse_args()
+    if args.cpu_job:
+        print(json.dumps(cpu_job(args.cpu_job, args.cpu_seconds)))
+        return 0
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -20,11 +20,14 @@
  *  - Errors found on the device (more intersections than `capacity`; a bounded wait that ran
  *    out) are written to a status word in the workspace; fgs_bin_sort resets it and
  *    fgs_read_status reads it. Outputs are then undefined but every access stays in bounds:
- *    while the word is set, fgs_rasterize draws the background only and fgs_backward's
- *    screen-space pass adds nothing.
+ *    after a wait of the binning ran out its later kernels do nothing, and while the word is
+ *    set fgs_rasterize draws the background only and fgs_backward's screen-space pass adds
+ *    nothing.
  *  - Gradients are overwritten, not accumulated.
- *  - Calls on distinct workspaces are independent; calls sharing a workspace must not
- *    overlap in time (they share its counters).
+ *  - The library keeps no settings of its own: the work shape, the measurement counters and
+ *    the wait bound are chosen per call (fgs_options). Calls on distinct workspaces are
+ *    independent; calls sharing a workspace must not overlap in time (they share its
+ *    counters).
  */
 #ifndef FGS_H
 #define FGS_H
@@ -69,7 +72,10 @@ typedef enum {
  *   radial models: theta = atan2(|(x_c, y_c)|, z_c), x_p = cx + fx r(theta) x_c / l_z,
  *   y_p = cy + fy r(theta) y_c / l_z (r(theta) = theta for the equidistant model);
  *   panorama: as above. Field of view: theta < pi - 0.05 (orthographic, pinhole: pi/2 - 0.05), or
- *   |latitude| < pi/2 - 0.05 for the panorama, which does not wrap at longitude +-pi.
+ *   |latitude| < pi/2 - 0.05 for the panorama, which does not wrap at longitude +-pi. The
+ *   pinhole also culls a Gaussian whose projected mean lies outside the guard band
+ *   |x_p - cx| <= 1.3 width / 2, |y_p - cy| <= 1.3 height / 2 (the 1.3 tan(FOV/2) limit of the
+ *   pinhole renderer the method is compared with, applied as a cull).
  * Pixel (i, j) is sampled at (i + 0.5, j + 0.5).
  * A view holds at most 2^20 tiles and at most 65535 tile columns and rows (the record's tile
  * rect is 16-bit); a call with a larger view, or a model outside fgs_camera_model, returns
@@ -116,6 +122,37 @@ typedef struct {
   uint16_t rect[4];
 } fgs_record;
 
+/* Per-call options of fgs_bin_sort_ex, fgs_rasterize_ex, fgs_backward_ex and
+ * fgs_backward_raster_ex (HOST pointer, read during the call; NULL = every field 0 = the
+ * defaults). None of them changes a result beyond the order of floating-point sums.
+ *   fwd_pixels_per_thread  work shape of the forward rasterizer: 1, 2 or 4 pixels per thread
+ *                          (a 16x16 tile runs on 256 / that many threads); 0 = 1.
+ *   bwd_pixels_per_thread  the same for the backward rasterizer: 1, 2, 4 or 8 (8 = one warp
+ *                          per tile); 0 = 8.
+ *                          Images, final transmittances and processed counts do not depend on
+ *                          either, bit for bit; gradients only through the order of their
+ *                          floating-point sums. A tuner may pick whichever is fastest.
+ *   flags                  FGS_OPT_INSTRUMENT: fgs_rasterize_ex and fgs_backward_ex /
+ *                          fgs_backward_raster_ex launch variants of their kernels that also
+ *                          count work into the workspace (fgs_read_counters); slower, they
+ *                          exist to size the algorithmic work of a timed, uninstrumented run.
+ *                          FGS_OPT_NO_WAIT: the decoupled look-back waits of fgs_bin_sort_ex
+ *                          (record scan, tile scan, onesweep passes) give up before their first
+ *                          poll, so every partition that has a predecessor reports
+ *                          FGS_ERR_TIMEOUT; this exercises the timeout path of a real call.
+ *   wait_limit             polls after which one look-back wait gives up with FGS_ERR_TIMEOUT;
+ *                          0 = 2^20 (about a second of polling). The waits of the rasterizers'
+ *                          bulk copies keep their own bound of 2^20 polls.
+ * Unknown flag bits or a shape outside the lists: FGS_ERR_INVALID_ARG before any launch. */
+#define FGS_OPT_INSTRUMENT 1u
+#define FGS_OPT_NO_WAIT 2u
+typedef struct {
+  int32_t fwd_pixels_per_thread;
+  int32_t bwd_pixels_per_thread;
+  uint32_t flags;
+  uint32_t wait_limit;
+} fgs_options;
+
 /* Bytes of workspace needed by fgs_bin_sort, fgs_rasterize and fgs_backward for this set of
  * views, n Gaussians and a key capacity (0 < capacity < 2^32). */
 fgs_status fgs_workspace_size(int64_t n, const fgs_camera *cams, int n_views, int64_t capacity,
@@ -147,8 +184,9 @@ fgs_status fgs_preprocess(const fgs_gaussians *g, const fgs_camera *cams, int n_
  * Inputs: records, tiles_touched [n_views * n] (as written by fgs_preprocess, or any records
  * whose rect and depth fields are set and tiles_touched = rect area). With a smaller
  * tiles_touched a record's pairs are the first tiles_touched tiles of its rect in row-major
- * order; with a larger one the default sort keeps the rect's tiles only (FGS_BIN_ONESWEEP
- * continues along the rows below it). Either way every write stays inside its buffer.
+ * order; a larger one keeps the rect's tiles only (the surplus pairs are dropped, by both sorts,
+ * and not counted in *n_intersections), and so does a rect outside its view's tile grid (no
+ * pairs). Every write stays inside its buffer.
  * Outputs: keys [capacity] u64, vals [capacity] u32 (first *n_intersections entries valid),
  * tile_ranges [fgs_total_tiles * 2] u32 = [start, end) of each global tile,
  * n_intersections (device int64, the true count even when it exceeds capacity).
@@ -179,7 +217,7 @@ fgs_status fgs_bin_sort_ex(const fgs_record *records, const uint32_t *tiles_touc
                            const fgs_camera *cams, int n_views, uint64_t *keys, uint32_t *vals,
                            int64_t capacity, uint32_t *tile_ranges, int64_t *n_intersections,
                            void *workspace, size_t workspace_bytes, uint32_t flags,
-                           fgs_stream stream);
+                           const fgs_options *opt, fgs_stream stream);
 
 /* Stage 5, rasterize (Sec. 3.1 "Rendering", Sec. 4.1 renderCUDA): per pixel, front to back
  * over its tile's sorted list: skip alpha < 1/255, stop before a Gaussian whose blend would
@@ -193,6 +231,11 @@ fgs_status fgs_rasterize(const fgs_record *records, const uint32_t *vals,
                          const float *bg, float *images, float *final_T,
                          uint32_t *n_processed, void *workspace, size_t workspace_bytes,
                          fgs_stream stream);
+fgs_status fgs_rasterize_ex(const fgs_record *records, const uint32_t *vals,
+                            const uint32_t *tile_ranges, const fgs_camera *cams, int n_views,
+                            const float *bg, float *images, float *final_T,
+                            uint32_t *n_processed, void *workspace, size_t workspace_bytes,
+                            const fgs_options *opt, fgs_stream stream);
 
 /* Stages 5-1 backward (Sec. 4.2 / 4.3 backward and the blend derivative): gradients of
  * L = <dL_dimages, images> with respect to the fgs_gaussians inputs, summed over views.
@@ -208,6 +251,13 @@ fgs_status fgs_backward(const fgs_gaussians *g, const fgs_camera *cams, int n_vi
                         const float *dL_dimages, float *d_means, float *d_scales,
                         float *d_quats, float *d_opacities, float *d_sh, void *workspace,
                         size_t workspace_bytes, fgs_stream stream);
+fgs_status fgs_backward_ex(const fgs_gaussians *g, const fgs_camera *cams, int n_views,
+                           const fgs_record *records, const uint32_t *tiles_touched,
+                           const uint32_t *vals, const uint32_t *tile_ranges, const float *bg,
+                           const float *final_T, const uint32_t *n_processed,
+                           const float *dL_dimages, float *d_means, float *d_scales,
+                           float *d_quats, float *d_opacities, float *d_sh, void *workspace,
+                           size_t workspace_bytes, const fgs_options *opt, fgs_stream stream);
 
 /* Training (Sec. 5.1 "Optimization": the loss, optimiser and hyperparameters of the renderer
  * the method plugs into - Adam on the per-Gaussian parameters).
@@ -253,7 +303,9 @@ fgs_status fgs_adam_step(const fgs_adam_group *groups, int n_groups, double beta
  *  - status: DEVICE pointer to one uint32 the call fills, in stream order, with the device
  *    status word (FGS_OK, FGS_ERR_CAPACITY or FGS_ERR_TIMEOUT) once the sort has run.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- *    make that first call before any stream capture on that device.
+ *    make that first call before any stream capture on that device. The address is kept with
+ *    the id of the context it belongs to; a call that finds another context current (a
+ *    non-primary one, or the new primary context after cudaDeviceReset) looks it up again.
  *  - All calls share the one array and leave their contents in it (each call clears what must
  *    start at zero): calls whose work overlaps on the GPU race; calls ordered on one stream
  *    are safe. */
@@ -267,12 +319,19 @@ fgs_status fgs_bin_sort_noalloc(const fgs_record *records, const uint32_t *tiles
  * (the moments of dL/d exponent over the pixel offsets, dL/d opacity and dL/d rgb terms) into
  * the workspace; fgs_backward_preprocess
  * pulls them back to the Gaussian inputs (overwriting the d_* outputs). Called in this order
- * on one workspace they equal fgs_backward. n = Gaussians per view. */
+ * on one workspace they equal fgs_backward. n = Gaussians per view. The _ex variants take
+ * fgs_options; the others use the defaults. */
 fgs_status fgs_backward_raster(const fgs_record *records, const uint32_t *vals,
                                const uint32_t *tile_ranges, int64_t n, const fgs_camera *cams,
                                int n_views, const float *bg, const float *final_T,
                                const uint32_t *n_processed, const float *dL_dimages,
                                void *workspace, size_t workspace_bytes, fgs_stream stream);
+fgs_status fgs_backward_raster_ex(const fgs_record *records, const uint32_t *vals,
+                                  const uint32_t *tile_ranges, int64_t n, const fgs_camera *cams,
+                                  int n_views, const float *bg, const float *final_T,
+                                  const uint32_t *n_processed, const float *dL_dimages,
+                                  void *workspace, size_t workspace_bytes,
+                                  const fgs_options *opt, fgs_stream stream);
 fgs_status fgs_backward_preprocess(const fgs_gaussians *g, const fgs_camera *cams, int n_views,
                                    const fgs_record *records, const uint32_t *tiles_touched,
                                    float *d_means, float *d_scales, float *d_quats,
@@ -283,22 +342,12 @@ fgs_status fgs_backward_preprocess(const fgs_gaussians *g, const fgs_camera *cam
  * (an fgs_status value). */
 fgs_status fgs_read_status(const void *workspace, fgs_stream stream, int *status);
 
-/* Measurement hooks (not part of the rendering path). While instrumentation is on (process
- * wide), fgs_rasterize and fgs_backward launch variants of their kernels that also count
- * work into the workspace: counters[0] = forward (pixel, Gaussian) evaluations, [1] = forward
+/* Measurement hook (not part of the rendering path): after calls made with FGS_OPT_INSTRUMENT,
+ * the workspace holds counters[0] = forward (pixel, Gaussian) evaluations, [1] = forward
  * blends, [2] = backward evaluations, [3] = backward contributions. The counters are reset by
- * fgs_bin_sort. Instrumented launches are slower; they exist to size the algorithmic work of
- * a timed (uninstrumented) run. fgs_read_counters synchronises `stream` and copies the four
- * counters to host memory. */
-void fgs_set_instrumentation(int on);
+ * fgs_bin_sort. fgs_read_counters synchronises `stream` and copies the four counters to host
+ * memory. */
 fgs_status fgs_read_counters(const void *workspace, fgs_stream stream, uint64_t *counters);
-
-/* Work shape of the rasterizers (process wide): pixels per thread of the forward and the
- * backward kernels, each 1, 2 or 4 (a 16x16 tile runs on 256 / that many threads). Images,
- * final transmittances and processed counts do not depend on it, bit for bit; gradients only
- * through the order of their floating-point sums. It trades parallelism against per-thread
- * reuse, so a tuner may pick whichever is fastest. Default 2 and 2. */
-fgs_status fgs_set_raster_shape(int fwd_pixels_per_thread, int bwd_pixels_per_thread);
 
 /* Static description of a status code. */
 const char *fgs_status_string(int status);

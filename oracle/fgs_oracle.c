@@ -45,7 +45,10 @@
  *   - camera axes x right, y down, z forward; pixel (i, j) is sampled at (i + 0.5, j + 0.5).
  *   - a Gaussian is visible iff |mu_c| > 0.2, theta < pi - 0.05 and opacity >= 1/255;
  *     orthographic and pinhole: theta < pi/2 - 0.05 (beyond it r(theta) decreases, or does
- *     not exist);
+ *     not exist); the pinhole also culls a Gaussian whose projected mean lies outside the
+ *     guard band |x_p - c_x| <= 1.3 W/2, |y_p - c_y| <= 1.3 H/2 (the 1.3 tan(FOV/2) limit of
+ *     the pinhole renderer the method is compared with, applied as a cull: outside it the
+ *     affine footprint of a Gaussian grazing the image is ill-conditioned);
  *     panorama: |latitude| < pi/2 - 0.05 (the poles, where J is singular). The panorama has no
  *     wrap-around at longitude +-pi: a Gaussian is drawn on the side of its mean only.
  *   - every radial model's Jacobian has the form of the equidistant one,
@@ -77,6 +80,7 @@
 #define ORC_NEAR 0.2
 #define ORC_THETA_MAX (ORC_PI - 0.05)
 #define ORC_THETA_MAX_ORTHO (0.5 * ORC_PI - 0.05)
+#define ORC_PINHOLE_GUARD 1.3
 #define ORC_LAT_MAX (0.5 * ORC_PI - 0.05)
 #define ORC_CAM_EQUIDISTANT 0
 #define ORC_CAM_EQUISOLID 1
@@ -458,6 +462,14 @@ void orc_project(int64_t n, const double *means, const double *scales, const dou
     if (!(dist > ORC_NEAR) || !in_field || !(opac[i] >= ORC_ALPHA_MIN)) continue;
 
     orc_cam_project(model, muc, fx, fy, cx, cy, o + F_XY);
+    /* the pinhole's guard band (distance to it kept as a decision margin, in tiles) */
+    double guard_margin = 1e9;
+    if (model == ORC_CAM_PINHOLE) {
+      double gx = ORC_PINHOLE_GUARD * 0.5 * width - fabs(o[F_XY] - cx);
+      double gy = ORC_PINHOLE_GUARD * 0.5 * height - fabs(o[F_XY + 1] - cy);
+      if (!(gx >= 0 && gy >= 0)) continue;
+      guard_margin = (gx < gy ? gx : gy) / ORC_TILE;
+    }
     double J[6];
     orc_cam_jacobian(model, muc, fx, fy, J);
     memcpy(o + F_J, J, sizeof J);
@@ -517,7 +529,7 @@ void orc_project(int64_t n, const double *means, const double *scales, const dou
     double x1 = floor(hx), y1 = floor(hy);
     if (x1 > tiles_x - 1) x1 = tiles_x - 1;
     if (y1 > tiles_y - 1) y1 = tiles_y - 1;
-    double rm = 1e9;
+    double rm = guard_margin;
     if (lx >= 0) { double m = orc_tile_margin(lx); rm = m < rm ? m : rm; }
     if (ly >= 0) { double m = orc_tile_margin(ly); rm = m < rm ? m : rm; }
     if (hx < tiles_x) { double m = orc_tile_margin(hx); rm = m < rm ? m : rm; }

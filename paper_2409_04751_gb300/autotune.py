@@ -37,7 +37,9 @@ def _time(fn, reps):
 
 def tune_raster(renderer, gs, frame, dL_dimages, reps=3, use_cache=True):
     """Pick the fastest (forward, backward) pixels-per-thread for this frame's workload, set it
-    with fgs_set_raster_shape and return {"fwd": ppt, "bwd": ppt, "ms": {...}}."""
+    as `renderer`'s work shape (renderer.set_shape; every later call of that renderer passes it
+    in its fgs_options) and return {"fwd": ppt, "bwd": ppt, "ms": {...}}. Other renderers are
+    not affected."""
     n = int(gs["means"].shape[0])
     sig = _signature(frame, n)
     cache = {}
@@ -48,37 +50,35 @@ def tune_raster(renderer, gs, frame, dL_dimages, reps=3, use_cache=True):
             cache = {}
     if use_cache and sig in cache:
         c = cache[sig]
-        fgs.fgs_set_raster_shape(c["fwd"], c["bwd"])
+        renderer.set_shape(c["fwd"], c["bwd"])
         return c
     ws = renderer._bufs["ws"]
-    g = None
     from .renderer import gaussians_of
     g = gaussians_of(gs)
     grads = {k: torch.empty_like(gs[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
     ms = {}
 
-    def fwd():
+    def fwd(f):
         fgs.fgs_rasterize(frame.records, frame.vals, frame.tile_ranges, frame.cams, frame.bg,
-                          frame.images, frame.final_T, frame.n_processed, ws, ws.numel())
+                          frame.images, frame.final_T, frame.n_processed, ws, ws.numel(),
+                          opts=fgs.options(fwd=f))
 
-    def bwd():
+    def bwd(b):
         fgs.fgs_backward_raster(frame.records, frame.vals, frame.tile_ranges, n, frame.cams,
                                 frame.bg, frame.final_T, frame.n_processed, dL_dimages, ws,
-                                ws.numel())
+                                ws.numel(), opts=fgs.options(bwd=b))
 
     for s in SHAPES:
-        fgs.fgs_set_raster_shape(s, 2)
-        ms[f"fwd{s}"] = _time(fwd, reps)
+        ms[f"fwd{s}"] = _time(lambda: fwd(s), reps)
     best_f = min(SHAPES, key=lambda s: ms[f"fwd{s}"])
-    fgs.fgs_set_raster_shape(best_f, 2)
-    fwd()  # the backward reads the forward's per-pixel state
+    fwd(best_f)  # the backward reads the forward's per-pixel state
     for s in BWD_SHAPES:
-        fgs.fgs_set_raster_shape(best_f, s)
-        ms[f"bwd{s}"] = _time(bwd, reps)
+        ms[f"bwd{s}"] = _time(lambda: bwd(s), reps)
     best_b = min(BWD_SHAPES, key=lambda s: ms[f"bwd{s}"])
-    fgs.fgs_set_raster_shape(best_f, best_b)
+    renderer.set_shape(best_f, best_b)
     # leave the frame's buffers as a plain forward + backward would
-    fwd()
+    fwd(best_f)
+    bwd(best_b)
     fgs.fgs_backward_preprocess(g, frame.cams, frame.records, frame.tiles_touched,
                                 grads["means"], grads["scales"], grads["quats"],
                                 grads["opacities"], grads["sh"], ws, ws.numel())

@@ -21,7 +21,7 @@ class GraphBatch:
     """
 
     def __init__(self, gs, cams_py, bg=None, backward=True, capacity_margin=1.15,
-                 device="cuda", stream=None):
+                 device="cuda", stream=None, shape=(0, 0)):
         if len(cams_py) > fgs.MAX_VIEWS:
             raise ValueError(f"at most {fgs.MAX_VIEWS} views per batch")
         self.gs = gs
@@ -29,7 +29,8 @@ class GraphBatch:
         self.bg = None if bg is None else tuple(float(v) for v in bg)
         self.backward_enabled = backward
         self.device = torch.device(device)
-        self.renderer = FisheyeRenderer(self.device, capacity=1 << 20)
+        self.renderer = FisheyeRenderer(self.device, capacity=1 << 20, fwd_ppt=shape[0],
+                                        bwd_ppt=shape[1])
         # size the key buffers with one checked eager forward, then fix them for the capture
         fr = self.renderer.forward(gs, self.cams_py, bg=self.bg, check=True)
         need = int(fr.n_intersections.item())
@@ -64,13 +65,15 @@ class GraphBatch:
         fgs.fgs_preprocess(self.g, cam, fr.records, fr.tiles_touched)
         fgs.fgs_bin_sort(fr.records, fr.tiles_touched, n, cam, fr.keys, fr.vals, cap,
                          fr.tile_ranges, fr.n_intersections, ws, wb)
+        opts = self.renderer.opts
         fgs.fgs_rasterize(fr.records, fr.vals, fr.tile_ranges, cam, self.bg, fr.images,
-                          fr.final_T, fr.n_processed, ws, wb)
+                          fr.final_T, fr.n_processed, ws, wb, opts=opts)
         if self.backward_enabled:
             g = self.grads
             fgs.fgs_backward(self.g, cam, fr.records, fr.tiles_touched, fr.vals, fr.tile_ranges,
                              self.bg, fr.final_T, fr.n_processed, self.dL_dimages, g["means"],
-                             g["scales"], g["quats"], g["opacities"], g["sh"], ws, wb)
+                             g["scales"], g["quats"], g["opacities"], g["sh"], ws, wb,
+                             opts=opts)
 
     def replay(self):
         """Launch the captured graph on the current stream's device (asynchronous)."""

@@ -20,14 +20,6 @@ int sm_count() {
   return cached[dev];
 }
 
-static int g_instrument = 0;
-bool instrumented() { return g_instrument != 0; }
-
-// Pixels per thread of the forward [0] and backward [1] rasterizers (1, 2 or 4). Any value
-// gives the same image and gradients; it only changes the work shape.
-static int g_raster_shape[2] = {2, 2};
-int raster_shape(int which) { return g_raster_shape[which & 1]; }
-
 // Largest tile grid accepted per view: a view's tile count must fit 20 bits so that a
 // record's tile count and a 1024-record partition's sum stay well inside 32 bits.
 constexpr int64_t MAX_TILES_PER_VIEW = 1 << 20;
@@ -89,6 +81,22 @@ bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p
 
 fgs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FGS_OK : FGS_ERR_CUDA; }
 
+// fgs_options -> CallOpts (NULL or zero fields: the defaults); false if a field is invalid.
+bool resolve_opts(const fgs_options *o, CallOpts *c) {
+  *c = CallOpts();
+  if (o == nullptr) return true;
+  if ((o->flags & ~(uint32_t)(FGS_OPT_INSTRUMENT | FGS_OPT_NO_WAIT)) != 0) return false;
+  const int f = o->fwd_pixels_per_thread, b = o->bwd_pixels_per_thread;
+  if (!(f == 0 || f == 1 || f == 2 || f == 4)) return false;
+  if (!(b == 0 || b == 1 || b == 2 || b == 4 || b == 8)) return false;
+  if (f) c->fwd_ppt = f;
+  if (b) c->bwd_ppt = b;
+  c->instrument = (o->flags & FGS_OPT_INSTRUMENT) != 0;
+  if (o->wait_limit) c->wait_limit = o->wait_limit;
+  if (o->flags & FGS_OPT_NO_WAIT) c->wait_limit = 0;
+  return true;
+}
+
 }  // namespace
 }  // namespace fgs
 
@@ -99,7 +107,8 @@ extern "C" {
 fgs_status fgs_workspace_size_ex(int64_t n, const fgs_camera *cams, int n_views,
                                  int64_t capacity, uint32_t flags, size_t *bytes) {
   Views vs;
-  if (bytes == nullptr || n < 0 || capacity <= 0 || capacity > 0xffffffffLL ||
+  // n is bounded before it is multiplied by the view count (at most FGS_MAX_VIEWS)
+  if (bytes == nullptr || n < 0 || n > 0xffffffffLL || capacity <= 0 || capacity > 0xffffffffLL ||
       !build_views(cams, n_views, &vs))
     return FGS_ERR_INVALID_ARG;
   if ((flags & ~(uint32_t)(FGS_BIN_ELLIPSE | FGS_BIN_ONESWEEP)) != 0) return FGS_ERR_INVALID_ARG;
@@ -139,9 +148,11 @@ fgs_status fgs_bin_sort_ex(const fgs_record *records, const uint32_t *tiles_touc
                            const fgs_camera *cams, int n_views, uint64_t *keys, uint32_t *vals,
                            int64_t capacity, uint32_t *tile_ranges, int64_t *n_intersections,
                            void *workspace, size_t workspace_bytes, uint32_t flags,
-                           fgs_stream stream) {
+                           const fgs_options *opt, fgs_stream stream) {
   Views vs;
-  if (n < 0 || capacity <= 0 || capacity > 0xffffffffLL || !build_views(cams, n_views, &vs))
+  CallOpts co;
+  if (n < 0 || n > 0xffffffffLL || capacity <= 0 || capacity > 0xffffffffLL ||
+      !build_views(cams, n_views, &vs) || !resolve_opts(opt, &co))
     return FGS_ERR_INVALID_ARG;
   if ((flags & ~(uint32_t)(FGS_BIN_ELLIPSE | FGS_BIN_ONESWEEP)) != 0) return FGS_ERR_INVALID_ARG;
   // the onesweep sort bins by the rect only
@@ -156,11 +167,11 @@ fgs_status fgs_bin_sort_ex(const fgs_record *records, const uint32_t *tiles_touc
   if (onesweep)
     return cuda_status(launch_bin_sort_onesweep(records, tiles_touched, n, vs, keys, vals,
                                                 capacity, tile_ranges, n_intersections,
-                                                reinterpret_cast<char *>(workspace), L,
+                                                reinterpret_cast<char *>(workspace), L, co,
                                                 reinterpret_cast<cudaStream_t>(stream)));
   return cuda_status(launch_bin_sort(records, tiles_touched, n, vs, keys, vals, capacity,
                                      tile_ranges, n_intersections,
-                                     reinterpret_cast<char *>(workspace), L, flags,
+                                     reinterpret_cast<char *>(workspace), L, flags, co,
                                      reinterpret_cast<cudaStream_t>(stream)));
 }
 
@@ -169,15 +180,18 @@ fgs_status fgs_bin_sort(const fgs_record *records, const uint32_t *tiles_touched
                         int64_t capacity, uint32_t *tile_ranges, int64_t *n_intersections,
                         void *workspace, size_t workspace_bytes, fgs_stream stream) {
   return fgs_bin_sort_ex(records, tiles_touched, n, cams, n_views, keys, vals, capacity,
-                         tile_ranges, n_intersections, workspace, workspace_bytes, 0u, stream);
+                         tile_ranges, n_intersections, workspace, workspace_bytes, 0u, nullptr,
+                         stream);
 }
 
-fgs_status fgs_rasterize(const fgs_record *records, const uint32_t *vals,
-                         const uint32_t *tile_ranges, const fgs_camera *cams, int n_views,
-                         const float *bg, float *images, float *final_T, uint32_t *n_processed,
-                         void *workspace, size_t workspace_bytes, fgs_stream stream) {
+fgs_status fgs_rasterize_ex(const fgs_record *records, const uint32_t *vals,
+                            const uint32_t *tile_ranges, const fgs_camera *cams, int n_views,
+                            const float *bg, float *images, float *final_T,
+                            uint32_t *n_processed, void *workspace, size_t workspace_bytes,
+                            const fgs_options *opt, fgs_stream stream) {
   Views vs;
-  if (!build_views(cams, n_views, &vs)) return FGS_ERR_INVALID_ARG;
+  CallOpts co;
+  if (!build_views(cams, n_views, &vs) || !resolve_opts(opt, &co)) return FGS_ERR_INVALID_ARG;
   if (!records || !vals || !tile_ranges || !images || !final_T || !n_processed || !workspace)
     return FGS_ERR_INVALID_ARG;
   if (!aligned(records, 16) || !aligned(workspace, 256) || workspace_bytes < sizeof(WsHeader))
@@ -187,16 +201,27 @@ fgs_status fgs_rasterize(const fgs_record *records, const uint32_t *vals,
   memset(&L, 0, sizeof L);
   return cuda_status(launch_raster_fwd(records, vals, tile_ranges, vs, b0, b1, b2, images,
                                        final_T, n_processed, reinterpret_cast<char *>(workspace),
-                                       L, reinterpret_cast<cudaStream_t>(stream)));
+                                       L, co, reinterpret_cast<cudaStream_t>(stream)));
 }
 
-fgs_status fgs_backward_raster(const fgs_record *records, const uint32_t *vals,
-                               const uint32_t *tile_ranges, int64_t n, const fgs_camera *cams,
-                               int n_views, const float *bg, const float *final_T,
-                               const uint32_t *n_processed, const float *dL_dimages,
-                               void *workspace, size_t workspace_bytes, fgs_stream stream) {
+fgs_status fgs_rasterize(const fgs_record *records, const uint32_t *vals,
+                         const uint32_t *tile_ranges, const fgs_camera *cams, int n_views,
+                         const float *bg, float *images, float *final_T, uint32_t *n_processed,
+                         void *workspace, size_t workspace_bytes, fgs_stream stream) {
+  return fgs_rasterize_ex(records, vals, tile_ranges, cams, n_views, bg, images, final_T,
+                          n_processed, workspace, workspace_bytes, nullptr, stream);
+}
+
+fgs_status fgs_backward_raster_ex(const fgs_record *records, const uint32_t *vals,
+                                  const uint32_t *tile_ranges, int64_t n, const fgs_camera *cams,
+                                  int n_views, const float *bg, const float *final_T,
+                                  const uint32_t *n_processed, const float *dL_dimages,
+                                  void *workspace, size_t workspace_bytes,
+                                  const fgs_options *opt, fgs_stream stream) {
   Views vs;
-  if (n < 0 || !build_views(cams, n_views, &vs)) return FGS_ERR_INVALID_ARG;
+  CallOpts co;
+  if (n < 0 || n > 0xffffffffLL || !build_views(cams, n_views, &vs) || !resolve_opts(opt, &co))
+    return FGS_ERR_INVALID_ARG;
   const int64_t R = (int64_t)n_views * n;
   if (R > 0xffffffffLL) return FGS_ERR_INVALID_ARG;
   if (!vals || !tile_ranges || !final_T || !n_processed || !dL_dimages || !workspace)
@@ -210,8 +235,18 @@ fgs_status fgs_backward_raster(const fgs_record *records, const uint32_t *vals,
   const float b0 = bg ? bg[0] : 0.f, b1 = bg ? bg[1] : 0.f, b2 = bg ? bg[2] : 0.f;
   return cuda_status(launch_raster_bwd(records, vals, tile_ranges, vs, b0, b1, b2, final_T,
                                        n_processed, dL_dimages, R,
-                                       reinterpret_cast<char *>(workspace), L,
+                                       reinterpret_cast<char *>(workspace), L, co,
                                        reinterpret_cast<cudaStream_t>(stream)));
+}
+
+fgs_status fgs_backward_raster(const fgs_record *records, const uint32_t *vals,
+                               const uint32_t *tile_ranges, int64_t n, const fgs_camera *cams,
+                               int n_views, const float *bg, const float *final_T,
+                               const uint32_t *n_processed, const float *dL_dimages,
+                               void *workspace, size_t workspace_bytes, fgs_stream stream) {
+  return fgs_backward_raster_ex(records, vals, tile_ranges, n, cams, n_views, bg, final_T,
+                                n_processed, dL_dimages, workspace, workspace_bytes, nullptr,
+                                stream);
 }
 
 fgs_status fgs_backward_preprocess(const fgs_gaussians *g, const fgs_camera *cams, int n_views,
@@ -236,6 +271,29 @@ fgs_status fgs_backward_preprocess(const fgs_gaussians *g, const fgs_camera *cam
                                            reinterpret_cast<cudaStream_t>(stream)));
 }
 
+fgs_status fgs_backward_ex(const fgs_gaussians *g, const fgs_camera *cams, int n_views,
+                           const fgs_record *records, const uint32_t *tiles_touched,
+                           const uint32_t *vals, const uint32_t *tile_ranges, const float *bg,
+                           const float *final_T, const uint32_t *n_processed,
+                           const float *dL_dimages, float *d_means, float *d_scales,
+                           float *d_quats, float *d_opacities, float *d_sh, void *workspace,
+                           size_t workspace_bytes, const fgs_options *opt, fgs_stream stream) {
+  if (!gauss_ok(g)) return FGS_ERR_INVALID_ARG;
+  // validate both halves before launching either
+  Views vs;
+  CallOpts co;
+  if (!build_views(cams, n_views, &vs) || !resolve_opts(opt, &co)) return FGS_ERR_INVALID_ARG;
+  if (g->n > 0 && (!records || !tiles_touched || !d_means || !d_scales || !d_quats ||
+                   !d_opacities || !d_sh))
+    return FGS_ERR_INVALID_ARG;
+  fgs_status s = fgs_backward_raster_ex(records, vals, tile_ranges, g->n, cams, n_views, bg,
+                                        final_T, n_processed, dL_dimages, workspace,
+                                        workspace_bytes, opt, stream);
+  if (s != FGS_OK) return s;
+  return fgs_backward_preprocess(g, cams, n_views, records, tiles_touched, d_means, d_scales,
+                                 d_quats, d_opacities, d_sh, workspace, workspace_bytes, stream);
+}
+
 fgs_status fgs_backward(const fgs_gaussians *g, const fgs_camera *cams, int n_views,
                         const fgs_record *records, const uint32_t *tiles_touched,
                         const uint32_t *vals, const uint32_t *tile_ranges, const float *bg,
@@ -243,19 +301,9 @@ fgs_status fgs_backward(const fgs_gaussians *g, const fgs_camera *cams, int n_vi
                         const float *dL_dimages, float *d_means, float *d_scales,
                         float *d_quats, float *d_opacities, float *d_sh, void *workspace,
                         size_t workspace_bytes, fgs_stream stream) {
-  if (!gauss_ok(g)) return FGS_ERR_INVALID_ARG;
-  // validate both halves before launching either
-  Views vs;
-  if (!build_views(cams, n_views, &vs)) return FGS_ERR_INVALID_ARG;
-  if (g->n > 0 && (!records || !tiles_touched || !d_means || !d_scales || !d_quats ||
-                   !d_opacities || !d_sh))
-    return FGS_ERR_INVALID_ARG;
-  fgs_status s = fgs_backward_raster(records, vals, tile_ranges, g->n, cams, n_views, bg,
-                                     final_T, n_processed, dL_dimages, workspace,
-                                     workspace_bytes, stream);
-  if (s != FGS_OK) return s;
-  return fgs_backward_preprocess(g, cams, n_views, records, tiles_touched, d_means, d_scales,
-                                 d_quats, d_opacities, d_sh, workspace, workspace_bytes, stream);
+  return fgs_backward_ex(g, cams, n_views, records, tiles_touched, vals, tile_ranges, bg,
+                         final_T, n_processed, dL_dimages, d_means, d_scales, d_quats,
+                         d_opacities, d_sh, workspace, workspace_bytes, nullptr, stream);
 }
 
 fgs_status fgs_read_status(const void *workspace, fgs_stream stream, int *status) {
@@ -266,17 +314,6 @@ fgs_status fgs_read_status(const void *workspace, fgs_stream stream, int *status
   if (cudaMemcpy(&v, workspace, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess)
     return FGS_ERR_CUDA;
   *status = (int)v;
-  return FGS_OK;
-}
-
-void fgs_set_instrumentation(int on) { g_instrument = on ? 1 : 0; }
-
-fgs_status fgs_set_raster_shape(int fwd_pixels_per_thread, int bwd_pixels_per_thread) {
-  auto ok = [](int v) { return v == 1 || v == 2 || v == 4; };
-  if (!ok(fwd_pixels_per_thread) || !(ok(bwd_pixels_per_thread) || bwd_pixels_per_thread == 8))
-    return FGS_ERR_INVALID_ARG;
-  g_raster_shape[0] = fwd_pixels_per_thread;
-  g_raster_shape[1] = bwd_pixels_per_thread;
   return FGS_OK;
 }
 

@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(EMIT_THREADS)
   __shared__ float4 s_con[ELLIPSE ? EMIT_CHUNK + 1 : 1];
   __shared__ uint32_t s_rc[ELLIPSE ? EMIT_CHUNK + 1 : 1];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (binning_timed_out(status)) return;
   const int64_t total = (int64_t)*n_cand;
   if (!SCATTER && blockIdx.x == 0 && tid == 0 && total > capacity) set_status(status, ST_CAPACITY);
   const int64_t n = min(total, capacity);
@@ -189,6 +190,7 @@ __global__ void __launch_bounds__(256)
                      int64_t n_per_view, Views vs, const uint32_t *__restrict__ vis_rec,
                      const unsigned long long *n_vis, const unsigned long long *n_cand,
                      int64_t capacity, uint32_t *ranges, uint32_t *status) {
+  if (binning_timed_out(status)) return;
   if ((int64_t)*n_cand > capacity) {
     if (blockIdx.x == 0 && threadIdx.x == 0) set_status(status, ST_CAPACITY);
     return;
@@ -227,8 +229,9 @@ __global__ void __launch_bounds__(256)
 template <bool ROWS>
 __global__ void __launch_bounds__(256)
     grid_scan_kernel(Views vs, int64_t n_lines, uint32_t *ranges,
-                     const unsigned long long *n_cand, int64_t capacity) {
-  if ((int64_t)*n_cand > capacity) return;
+                     const unsigned long long *n_cand, int64_t capacity,
+                     const uint32_t *status) {
+  if ((int64_t)*n_cand > capacity || binning_timed_out(status)) return;
   const int lane = threadIdx.x & 31;
   int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (g >= n_lines) return;
@@ -261,12 +264,14 @@ __global__ void __launch_bounds__(256)
 // over all tiles in global tile order, with decoupled look-back over partitions of TSCAN_PART
 // tiles. Writes tile_ranges[t] = (start, start) for every non-empty tile (the second word is
 // the scatter's cursor and ends as the tile's end) and appends the tile to the list of its
-// segment-size class; empty tiles keep (0, 0).
+// segment-size class; empty tiles keep (0, 0). It runs even after the record scan gave up (its
+// counts are then all zero), so that every partition publishes and no wait of its own look-back
+// depends on a partition that left early.
 __global__ void __launch_bounds__(256)
     tile_scan_kernel(uint32_t *ranges, int64_t total_tiles, uint64_t *lb,
                      uint32_t *part_counter, uint32_t *lists, uint32_t *seg_count,
                      const unsigned long long *n_cand, int64_t capacity, int64_t *n_int,
-                     uint32_t *status) {
+                     uint32_t *status, uint32_t wait_limit) {
   __shared__ uint32_t s_warp[8];
   __shared__ uint64_t s_prefix;
   __shared__ uint32_t s_part;
@@ -294,7 +299,7 @@ __global__ void __launch_bounds__(256)
       st_volatile_u64(lb, LB_INC | agg);
     } else {
       st_volatile_u64(lb + part, LB_AGG | agg);
-      prefix = look_back(lb, part, 1, status);
+      prefix = look_back(lb, part, 1, status, wait_limit);
       st_volatile_u64(lb + part, LB_INC | (prefix + agg));
     }
     s_prefix = prefix;
@@ -789,10 +794,11 @@ template <int NT, int IPT_LO, int CAP, int MIN_BLOCKS, bool CHUNKED>
 __global__ void __launch_bounds__(NT, MIN_BLOCKS)
     segsort_kernel(const uint32_t *__restrict__ list, const uint32_t *list_count,
                    const uint32_t *__restrict__ ranges, uint64_t *words, uint64_t *keys,
-                   uint32_t *vals, int64_t capacity) {
+                   uint32_t *vals, int64_t capacity, const uint32_t *status) {
   static_assert(NT * IPT_LO * 2 == CAP, "two word counts per class");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SegSmem<NT, CAP> &S = *reinterpret_cast<SegSmem<NT, CAP> *>(smem_raw);
+  if (binning_timed_out(status)) return;
   const uint32_t count = *list_count;
   for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
     const uint32_t t = __ldg(list + i);
@@ -812,7 +818,8 @@ __global__ void __launch_bounds__(NT, MIN_BLOCKS)
 template <int NT, int IPT_LO, int CAP, int MIN_BLOCKS, bool CHUNKED>
 cudaError_t launch_segsort(const uint32_t *list, const uint32_t *list_count,
                            const uint32_t *ranges, uint64_t *words, uint64_t *keys,
-                           uint32_t *vals, int64_t capacity, cudaStream_t st) {
+                           uint32_t *vals, int64_t capacity, const uint32_t *status,
+                           cudaStream_t st) {
   constexpr size_t smem = sizeof(SegSmem<NT, CAP>);
   static int occ = 0;
   if (occ == 0) {
@@ -825,7 +832,7 @@ cudaError_t launch_segsort(const uint32_t *list, const uint32_t *list_count,
     occ = a > 0 ? a : 1;
   }
   segsort_kernel<NT, IPT_LO, CAP, MIN_BLOCKS, CHUNKED><<<(unsigned)(sm_count() * occ), NT, smem, st>>>(
-      list, list_count, ranges, words, keys, vals, capacity);
+      list, list_count, ranges, words, keys, vals, capacity, status);
   return cudaGetLastError();
 }
 
@@ -834,7 +841,8 @@ cudaError_t launch_segsort(const uint32_t *list, const uint32_t *list_count,
 cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_touched,
                             int64_t n, const Views &vs, uint64_t *keys, uint32_t *vals,
                             int64_t capacity, uint32_t *tile_ranges, int64_t *n_int,
-                            char *ws, const WsLayout &L, uint32_t flags, cudaStream_t st) {
+                            char *ws, const WsLayout &L, uint32_t flags,
+                            const CallOpts &opt, cudaStream_t st) {
   cudaError_t e;
   WsHeader *hdr = reinterpret_cast<WsHeader *>(ws + L.header);
   uint64_t *scan_lb = reinterpret_cast<uint64_t *>(ws + L.scan_lb);
@@ -855,7 +863,8 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
 
   scan_kernel<<<(unsigned)L.scan_parts, EMIT_THREADS, 0, st>>>(
       tiles_touched, R, capacity, n_int, &hdr->n_candidates, &hdr->n_visible, scan_lb,
-      scan_lb + L.scan_parts, &hdr->scan_parts, vis_rec, vis_off, chunk_first, &hdr->status);
+      scan_lb + L.scan_parts, &hdr->scan_parts, vis_rec, vis_off, chunk_first, &hdr->status,
+      opt.wait_limit);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // two waves of the 8 CTAs an SM holds: the pair walks wait on record loads and returning
   // atomics, so more chunks in flight hide more of that latency
@@ -881,14 +890,14 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
                                                        &hdr->n_visible, &hdr->n_candidates,
                                                        capacity, tile_ranges, &hdr->status);
     grid_scan_kernel<true><<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(
-        vs, rows, tile_ranges, &hdr->n_candidates, capacity);
+        vs, rows, tile_ranges, &hdr->n_candidates, capacity, &hdr->status);
     grid_scan_kernel<false><<<(unsigned)((cols * 32 + 255) / 256), 256, 0, st>>>(
-        vs, cols, tile_ranges, &hdr->n_candidates, capacity);
+        vs, cols, tile_ranges, &hdr->n_candidates, capacity, &hdr->status);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   tile_scan_kernel<<<(unsigned)L.tile_parts, 256, 0, st>>>(
       tile_ranges, T, tile_lb, &hdr->tile_parts, lists, hdr->seg_count, &hdr->n_candidates,
-      capacity, n_int, &hdr->status);
+      capacity, n_int, &hdr->status, opt.wait_limit);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ellipse)
     pair_kernel<true, true><<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
@@ -900,11 +909,12 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
         tile_ranges, words, capacity, &hdr->status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_segsort<256, 2, SEG_CAP0, 6, false>(lists, &hdr->seg_count[0], tile_ranges,
-                                                       words, keys, vals, capacity, st)) !=
-      cudaSuccess)
+                                                       words, keys, vals, capacity,
+                                                       &hdr->status, st)) != cudaSuccess)
     return e;
   return launch_segsort<512, 8, SEG_CAP1, 1, true>(lists + T, &hdr->seg_count[1], tile_ranges,
-                                                   words, keys, vals, capacity, st);
+                                                   words, keys, vals, capacity, &hdr->status,
+                                                   st);
 }
 
 }  // namespace fgs

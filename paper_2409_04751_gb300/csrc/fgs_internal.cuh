@@ -32,8 +32,17 @@ constexpr uint32_t ST_TIMEOUT = FGS_ERR_TIMEOUT;
 
 // Bounded waits: polls before a wait gives up and reports FGS_ERR_TIMEOUT. A 48-byte bulk copy
 // lands within microseconds and a look-back predecessor publishes within one partition's work,
-// so these limits (about a second of polling) are only reached if something is broken.
+// so these limits (about a second of polling) are only reached if something is broken. The
+// look-back waits take their limit per call (fgs_options.wait_limit; 0 = give up at once).
 constexpr uint32_t SPIN_LIMIT = 1u << 20;
+
+// Options of one call, resolved from fgs_options (api.cu).
+struct CallOpts {
+  int fwd_ppt = 1;                   // pixels per thread of the forward rasterizer (1, 2, 4)
+  int bwd_ppt = 8;                   // of the backward rasterizer (1, 2, 4, 8)
+  bool instrument = false;           // count work into the workspace counters
+  uint32_t wait_limit = SPIN_LIMIT;  // polls of a look-back wait before it gives up
+};
 
 // ------------------------------------------------------------------------------------------
 // Per-view parameters, passed by value in the kernel parameter space (no device copy).
@@ -74,13 +83,14 @@ struct WsHeader {
   uint32_t spare[5];
   uint32_t raster_tiles;      // tile queue of the forward rasterizer
   uint32_t backward_tiles;    // tile queue of the backward rasterizer
-  // measurement counters, written only by instrumented launches (fgs_set_instrumentation):
+  // measurement counters, written only by instrumented launches (FGS_OPT_INSTRUMENT):
   // [0] forward (pixel, Gaussian) evaluations, [1] forward blends,
   // [2] backward evaluations, [3] backward contributions
   unsigned long long counters[4];
   unsigned long long n_visible;  // records with a non-empty rect (written by the scan)
   unsigned long long n_candidates;  // (record, tile) pairs of the rects (written by the scan)
-  uint32_t pad[40];
+  unsigned long long n_dropped;  // onesweep emission: pairs beyond their record's rect
+  uint32_t pad[38];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
 
@@ -155,6 +165,12 @@ inline WsLayout ws_layout(int64_t n_records, int64_t capacity, int64_t total_til
 
 __device__ __forceinline__ void set_status(uint32_t *status, uint32_t code) {
   atomicCAS(status, 0u, code);
+}
+
+// A look-back wait of an earlier kernel of the same binning gave up: its offsets are partial,
+// so the kernels after it leave their outputs alone (the status word keeps the error).
+__device__ __forceinline__ bool binning_timed_out(const uint32_t *status) {
+  return *(volatile const uint32_t *)status == ST_TIMEOUT;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -432,6 +448,16 @@ __device__ __forceinline__ bool in_field(int model, float x, float y, float z, f
   return z > COS_THETA_MAX * dist;
 }
 
+// The pinhole camera's guard band: its projected mean within 1.3 times the half image of the
+// principal point (the 1.3 tan(FOV/2) limit of the pinhole renderer the method is compared
+// with, applied as a cull; beyond it a Gaussian reaches the image only with the tail of an
+// ill-conditioned affine footprint).
+constexpr float PINHOLE_GUARD_HALF = 0.65f;  // 1.3 / 2
+__device__ __forceinline__ bool in_pinhole_guard(const View &V, float px, float py) {
+  return fabsf(px - V.cx) <= PINHOLE_GUARD_HALF * (float)V.width &&
+         fabsf(py - V.cy) <= PINHOLE_GUARD_HALF * (float)V.height;
+}
+
 // Projection of the mean and J (row-major 2x3) of view V at mu_c.
 __device__ __forceinline__ void project_mean(const View &V, float x, float y, float z, float l2,
                                              float &px, float &py, float (&J)[6]) {
@@ -576,8 +602,6 @@ struct GaussPtrs {
 };
 
 int sm_count();
-bool instrumented();
-int raster_shape(int which);  // pixels per thread: 0 = forward, 1 = backward
 // Per-view parameter table from the caller's cameras; false if any camera is invalid.
 bool build_views(const fgs_camera *cams, int n_views, Views *vs);
 
@@ -586,21 +610,23 @@ cudaError_t launch_preprocess_fwd(const GaussPtrs &g, const Views &vs, fgs_recor
 cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_touched,
                             int64_t n, const Views &vs, uint64_t *keys, uint32_t *vals,
                             int64_t capacity, uint32_t *tile_ranges, int64_t *n_int,
-                            char *ws, const WsLayout &L, uint32_t flags, cudaStream_t st);
+                            char *ws, const WsLayout &L, uint32_t flags,
+                            const CallOpts &opt, cudaStream_t st);
 cudaError_t launch_bin_sort_onesweep(const fgs_record *records, const uint32_t *tiles_touched,
                                      int64_t n, const Views &vs, uint64_t *keys,
                                      uint32_t *vals, int64_t capacity, uint32_t *tile_ranges,
                                      int64_t *n_int, char *ws, const WsLayout &L,
-                                     cudaStream_t st);
+                                     const CallOpts &opt, cudaStream_t st);
 cudaError_t launch_raster_fwd(const fgs_record *records, const uint32_t *vals,
                               const uint32_t *tile_ranges, const Views &vs, float bg0, float bg1,
                               float bg2, float *images, float *final_T, uint32_t *n_processed,
-                              char *ws, const WsLayout &L, cudaStream_t st);
+                              char *ws, const WsLayout &L, const CallOpts &opt,
+                              cudaStream_t st);
 cudaError_t launch_raster_bwd(const fgs_record *records, const uint32_t *vals,
                               const uint32_t *tile_ranges, const Views &vs, float bg0, float bg1,
                               float bg2, const float *final_T, const uint32_t *n_processed,
                               const float *dL_dimages, int64_t n_records, char *ws,
-                              const WsLayout &L, cudaStream_t st);
+                              const WsLayout &L, const CallOpts &opt, cudaStream_t st);
 cudaError_t launch_preprocess_bwd(const GaussPtrs &g, const Views &vs, const fgs_record *records,
                                   const uint32_t *tiles_touched, const float *g2d,
                                   float *d_means, float *d_scales, float *d_quats,

@@ -8,6 +8,10 @@
 //     by binary search in a shared-memory window and writes key = tile << 32 | depth bits,
 //     value = record, coalesced. The same pass counts the 8-bit digit histograms of every radix
 //     pass (warp-aggregated shared atomics), so the sort needs no separate histogram read.
+//     A pair beyond its record's rect (tiles_touched larger than the rect's area, or a rect
+//     outside its view's grid) gets the tile id total_tiles, one past the last tile: it sorts
+//     after every kept pair, no tile range takes it, and it is not counted in the result, so
+//     the output is the default sort's for such records too.
 //  3. onesweep_kernel (one launch per 8-bit digit): Adinets & Merrill's single-pass LSD radix
 //     sort: each partition of 4096 keys is ranked in shared memory (warp multi-split with
 //     match_any, stable), publishes its per-digit counts, resolves its global digit offsets by
@@ -29,20 +33,25 @@ __global__ void __launch_bounds__(EMIT_THREADS)
                 const uint32_t *__restrict__ chunk_first, const int64_t *n_int,
                 const unsigned long long *n_vis, uint64_t *__restrict__ keys,
                 uint32_t *__restrict__ vals, int64_t capacity, uint32_t *hist, int passes,
-                int idx_bits, int packed, uint32_t *status) {
+                int idx_bits, int packed, unsigned long long *n_dropped, uint32_t *status) {
   __shared__ uint64_t s_off[EMIT_CHUNK + 1];
   __shared__ uint32_t s_base[EMIT_CHUNK + 1];   // global tile id of the rect's corner (x0, y0)
   __shared__ uint32_t s_geom[EMIT_CHUNK + 1];   // rect width | view tiles_x << 16
+  __shared__ uint32_t s_rows[EMIT_CHUNK + 1];   // rect height (0: a rect outside the grid)
   __shared__ uint32_t s_depth[EMIT_CHUNK + 1];
   __shared__ uint32_t s_rec[EMIT_CHUNK + 1];
   __shared__ uint32_t s_hist[SORT_MAX_PASSES * 256];
+  __shared__ uint32_t s_drop;
   const int tid = threadIdx.x;
+  if (binning_timed_out(status)) return;
+  const uint32_t drop_tile = (uint32_t)vs.total_tiles;  // one past the last tile
   const int64_t total = *n_int;
   if (tid == 0 && total > capacity) set_status(status, ST_CAPACITY);
   const int64_t n = min(total, capacity);
   const int64_t nchunks = (n + EMIT_CHUNK - 1) / EMIT_CHUNK;
   const int64_t nv = (int64_t)*n_vis;
   for (int e = tid; e < passes * 256; e += EMIT_THREADS) s_hist[e] = 0u;
+  if (tid == 0) s_drop = 0u;
 
   for (int64_t ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
     const int64_t lo = ck * EMIT_CHUNK;
@@ -56,13 +65,15 @@ __global__ void __launch_bounds__(EMIT_THREADS)
     for (int i = tid; i < nw; i += EMIT_THREADS) {
       const uint32_t r = vis_rec[v0 + i];
       const uint4 w2 = __ldg(reinterpret_cast<const uint4 *>(rec + r) + 2);
-      const uint32_t x0 = w2.z & 0xffffu, y0 = w2.z >> 16, x1 = w2.w & 0xffffu;
+      const uint32_t x0 = w2.z & 0xffffu, y0 = w2.z >> 16, x1 = w2.w & 0xffffu, y1 = w2.w >> 16;
       const int v = (int)(r / (uint32_t)n_per_view);
-      const uint32_t tiles_x = (uint32_t)vs.v[v].tiles_x;
+      const uint32_t tiles_x = (uint32_t)vs.v[v].tiles_x, tiles_y = (uint32_t)vs.v[v].tiles_y;
+      const bool ok = x0 <= x1 && y0 <= y1 && x1 < tiles_x && y1 < tiles_y;
       s_off[i] = vis_off[v0 + i];
       s_rec[i] = r;
       s_base[i] = (uint32_t)vs.v[v].tile_offset + y0 * tiles_x + x0;
-      s_geom[i] = (x1 - x0 + 1u) | (tiles_x << 16);
+      s_geom[i] = (ok ? x1 - x0 + 1u : 1u) | (tiles_x << 16);
+      s_rows[i] = ok ? y1 - y0 + 1u : 0u;
       s_depth[i] = w2.y;
     }
     __syncthreads();
@@ -95,7 +106,9 @@ __global__ void __launch_bounds__(EMIT_THREADS)
         uint32_t dy = (uint32_t)((float)local * rcp_approx((float)w));
         if (dy * w > local) --dy;
         if ((dy + 1u) * w <= local) ++dy;
-        const uint32_t tile = s_base[a] + dy * tiles_x + (local - dy * w);
+        const bool kept = dy < s_rows[a];
+        const uint32_t tile = kept ? s_base[a] + dy * tiles_x + (local - dy * w) : drop_tile;
+        if (!kept) atomicAdd(&s_drop, 1u);
         key = ((uint64_t)tile << 32) | (uint64_t)s_depth[a];
         if (packed) {
           keys[j] = (key << idx_bits) | (uint64_t)s_rec[a];
@@ -117,6 +130,7 @@ __global__ void __launch_bounds__(EMIT_THREADS)
   __syncthreads();
   for (int e = tid; e < passes * 256; e += EMIT_THREADS)
     if (s_hist[e]) atomicAdd(hist + e, s_hist[e]);
+  if (tid == 0 && s_drop) atomicAdd(n_dropped, (unsigned long long)s_drop);
 }
 
 // Shared memory of one onesweep CTA: two input buffers filled by TMA bulk copies (the next
@@ -160,10 +174,13 @@ __global__ void __launch_bounds__(SORT_THREADS, KV ? 2 : 3)
                     uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
                     const int64_t *n_int, int64_t capacity, int shift, int idx_bits, int unpack,
                     const uint32_t *hist, uint64_t *lb, uint64_t *lb_next,
-                    uint32_t *part_counter, uint32_t *status) {
+                    uint32_t *part_counter, uint32_t *status, uint32_t wait_limit) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   SortSmem<KV> &S = *reinterpret_cast<SortSmem<KV> *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  // an earlier wait of the binning gave up: leave the keys alone (uniform over the launch, the
+  // word was set before it started)
+  if (binning_timed_out(status)) return;
   const int64_t n = min(*n_int, capacity);
   const int64_t nparts = (n + SORT_PART - 1) / SORT_PART;
 
@@ -259,7 +276,7 @@ __global__ void __launch_bounds__(SORT_THREADS, KV ? 2 : 3)
     S.local_start[d] = lstart;
     uint64_t prefix = 0;
     if (part > 0) {
-      prefix = look_back(lb + d, part, 256, status);
+      prefix = look_back(lb + d, part, 256, status, wait_limit);
       st_volatile_u64(my, LB_INC | (prefix + dcount));
     }
     S.global_base[d] = S.hist_excl[d] + (uint32_t)prefix;
@@ -303,7 +320,8 @@ __global__ void __launch_bounds__(SORT_THREADS, KV ? 2 : 3)
 // left undefined by a device-side error cannot steer a write out of bounds.
 __global__ void ranges_kernel(const uint64_t *__restrict__ keys, const int64_t *n_int,
                               int64_t capacity, int64_t total_tiles,
-                              uint32_t *__restrict__ ranges) {
+                              uint32_t *__restrict__ ranges, const uint32_t *status) {
+  if (binning_timed_out(status)) return;
   const int64_t n = min(*n_int, capacity);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -314,6 +332,14 @@ __global__ void ranges_kernel(const uint64_t *__restrict__ keys, const int64_t *
   }
 }
 
+// The pairs dropped at emission (beyond their record's rect) sorted to the end: the result
+// counts the kept pairs only, unless the candidates overflowed the capacity (the count then
+// stays the candidates', for the caller to grow the buffers).
+__global__ void drop_count_kernel(int64_t *n_int, int64_t capacity,
+                                  const unsigned long long *n_dropped, const uint32_t *status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && !binning_timed_out(status) && *n_int <= capacity)
+    *n_int -= (int64_t)*n_dropped;
+}
 
 }  // namespace
 
@@ -321,7 +347,7 @@ cudaError_t launch_bin_sort_onesweep(const fgs_record *records, const uint32_t *
                                      int64_t n, const Views &vs, uint64_t *keys,
                                      uint32_t *vals, int64_t capacity, uint32_t *tile_ranges,
                                      int64_t *n_int, char *ws, const WsLayout &L,
-                                     cudaStream_t st) {
+                                     const CallOpts &opt, cudaStream_t st) {
   cudaError_t e;
   WsHeader *hdr = reinterpret_cast<WsHeader *>(ws + L.header);
   uint64_t *scan_lb = reinterpret_cast<uint64_t *>(ws + L.scan_lb);
@@ -330,7 +356,11 @@ cudaError_t launch_bin_sort_onesweep(const fgs_record *records, const uint32_t *
   uint64_t *alt_keys = reinterpret_cast<uint64_t *>(ws + L.words);
   uint32_t *alt_vals = reinterpret_cast<uint32_t *>(ws + L.alt_vals);
   const int64_t R = (int64_t)vs.n * n;
-  const int passes = (32 + vs.tile_bits + 7) / 8;
+  // tile ids 0 .. total_tiles (the last one marks the pairs dropped at emission)
+  int sort_tile_bits = 0;
+  while (sort_tile_bits < 32 && ((int64_t)1 << sort_tile_bits) <= vs.total_tiles) ++sort_tile_bits;
+  const int passes = (32 + sort_tile_bits + 7) / 8;
+  unsigned long long *n_dropped = &hdr->n_dropped;
 
   if ((e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * SORT_MAX_PASSES * 256, st)) != cudaSuccess) return e;
@@ -345,7 +375,7 @@ cudaError_t launch_bin_sort_onesweep(const fgs_record *records, const uint32_t *
   // it writes.
   int idx_bits = 0;
   while (idx_bits < 32 && ((int64_t)1 << idx_bits) < R) ++idx_bits;
-  const bool packed = idx_bits + 32 + vs.tile_bits <= 64;
+  const bool packed = idx_bits + 32 + sort_tile_bits <= 64;
   uint64_t *k0, *k1;
   uint32_t *v0 = nullptr, *v1 = nullptr;
   if (packed) {
@@ -364,14 +394,15 @@ cudaError_t launch_bin_sort_onesweep(const fgs_record *records, const uint32_t *
   uint32_t *chunk_first = reinterpret_cast<uint32_t *>(ws + L.chunk_first);
   scan_kernel<<<(unsigned)L.scan_parts, EMIT_THREADS, 0, st>>>(
       tiles_touched, R, capacity, n_int, &hdr->n_candidates, &hdr->n_visible, scan_lb,
-      scan_lb + L.scan_parts, &hdr->scan_parts, vis_rec, vis_off, chunk_first, &hdr->status);
+      scan_lb + L.scan_parts, &hdr->scan_parts, vis_rec, vis_off, chunk_first, &hdr->status,
+      opt.wait_limit);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int64_t egrid = (int64_t)sm_count() * 4;
   if (egrid > L.chunks) egrid = L.chunks;
   if (egrid < 1) egrid = 1;
   emit_kernel<<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
       records, n, vs, vis_rec, vis_off, chunk_first, n_int, &hdr->n_visible, k0, v0, capacity,
-      hist, passes, idx_bits, packed ? 1 : 0, &hdr->status);
+      hist, passes, idx_bits, packed ? 1 : 0, n_dropped, &hdr->status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
   static int occ_kv = 0, occ_packed = 0;
@@ -406,8 +437,9 @@ cudaError_t launch_bin_sort_onesweep(const fgs_record *records, const uint32_t *
       int a6 = idx_bits + 8 * p, a7 = idx_bits, a8 = last ? 1 : 0;
       const uint32_t *a9 = hist + p * 256;
       uint32_t *a12 = &hdr->tile_parts, *a13 = &hdr->status;
+      uint32_t a14 = opt.wait_limit;
       void *args[] = {&a0, &a1, &a2, &a3, &n_int, &capacity, &a6, &a7, &a8, &a9, &lb, &lbn,
-                      &a12, &a13};
+                      &a12, &a13, &a14};
       e = cudaLaunchCooperativeKernel((const void *)onesweep_kernel<false>, dim3((unsigned)grid),
                                       dim3(SORT_THREADS), args, smem_packed, st);
       if (e != cudaSuccess) return e;
@@ -417,8 +449,9 @@ cudaError_t launch_bin_sort_onesweep(const fgs_record *records, const uint32_t *
       int a6 = 8 * p, a7 = 0, a8 = 0;
       const uint32_t *a9 = hist + p * 256;
       uint32_t *a12 = &hdr->tile_parts, *a13 = &hdr->status;
+      uint32_t a14 = opt.wait_limit;
       void *args[] = {&kin, &vin, &kout, &vout, &n_int, &capacity, &a6, &a7, &a8, &a9, &lb, &lbn,
-                      &a12, &a13};
+                      &a12, &a13, &a14};
       e = cudaLaunchCooperativeKernel((const void *)onesweep_kernel<true>, dim3((unsigned)grid),
                                       dim3(SORT_THREADS), args, smem_kv, st);
       if (e != cudaSuccess) return e;
@@ -427,7 +460,8 @@ cudaError_t launch_bin_sort_onesweep(const fgs_record *records, const uint32_t *
   }
   const int64_t rgrid = (int64_t)sm_count() * 8;
   ranges_kernel<<<(unsigned)rgrid, 256, 0, st>>>(keys, n_int, capacity, vs.total_tiles,
-                                                  tile_ranges);
+                                                  tile_ranges, &hdr->status);
+  drop_count_kernel<<<1, 32, 0, st>>>(n_int, capacity, n_dropped, &hdr->status);
   return cudaGetLastError();
 }
 

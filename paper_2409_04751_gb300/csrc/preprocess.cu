@@ -76,6 +76,10 @@ __global__ void __launch_bounds__(256)
     // mean (Sec. 3.2; other models Sec. 3.2 / Sec. 6) and Jacobian (Sec. 4.2)
     float px, py, J[6];
     project_mean(V, x, y, z, l2, px, py, J);
+    if (V.model == FGS_CAM_PINHOLE && !in_pinhole_guard(V, px, py)) {
+      tt[r] = 0u;
+      continue;
+    }
     const float J00 = J[0], J01 = J[1], J02 = J[2], J10 = J[3], J11 = J[4], J12 = J[5];
     // T = J W
     float T0[3], T1[3];

@@ -777,14 +777,15 @@ int occupancy_of(K kernel, int threads) {
 template <int PPT>
 cudaError_t fwd_launch(const fgs_record *records, const uint32_t *vals, const uint32_t *ranges,
                        const Views &vs, float bg0, float bg1, float bg2, float *images,
-                       float *final_T, uint32_t *n_processed, WsHeader *hdr, cudaStream_t st) {
+                       float *final_T, uint32_t *n_processed, WsHeader *hdr, bool instrument,
+                       cudaStream_t st) {
   constexpr int NT = TILE_PIX / PPT;
   static int occ = 0;
   if (occ == 0) occ = occupancy_of(raster_fwd_kernel<PPT, false>, NT);
   int64_t grid = (int64_t)sm_count() * occ;
   if (grid > vs.total_tiles) grid = vs.total_tiles;
   if (grid < 1) grid = 1;
-  if (instrumented())
+  if (instrument)
     raster_fwd_kernel<PPT, true><<<(unsigned)grid, NT, 0, st>>>(
         records, vals, ranges, vs, bg0, bg1, bg2, images, final_T, n_processed,
         &hdr->raster_tiles, &hdr->status, hdr->counters);
@@ -799,14 +800,14 @@ template <int PPT>
 cudaError_t bwd_launch(const fgs_record *records, const uint32_t *vals, const uint32_t *ranges,
                        const Views &vs, float bg0, float bg1, float bg2, const float *final_T,
                        const uint32_t *n_processed, const float *dL, float *g2d,
-                       const uint32_t *order, WsHeader *hdr, cudaStream_t st) {
+                       const uint32_t *order, WsHeader *hdr, bool instrument, cudaStream_t st) {
   constexpr int NT = TILE_PIX / PPT;
   static int occ = 0;
   if (occ == 0) occ = occupancy_of(raster_bwd_kernel<PPT, false>, NT);
   int64_t grid = (int64_t)sm_count() * occ;
   if (grid > vs.total_tiles) grid = vs.total_tiles;
   if (grid < 1) grid = 1;
-  if (instrumented())
+  if (instrument)
     raster_bwd_kernel<PPT, true><<<(unsigned)grid, NT, 0, st>>>(
         records, vals, ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL, g2d, order,
         &hdr->backward_tiles, &hdr->status, hdr->counters);
@@ -822,14 +823,16 @@ cudaError_t bwd_launch(const fgs_record *records, const uint32_t *vals, const ui
 cudaError_t launch_raster_fwd(const fgs_record *records, const uint32_t *vals,
                               const uint32_t *tile_ranges, const Views &vs, float bg0, float bg1,
                               float bg2, float *images, float *final_T, uint32_t *n_processed,
-                              char *ws, const WsLayout &L, cudaStream_t st) {
+                              char *ws, const WsLayout &L, const CallOpts &opt,
+                              cudaStream_t st) {
   WsHeader *hdr = reinterpret_cast<WsHeader *>(ws + L.header);
   cudaError_t e = cudaMemsetAsync(&hdr->raster_tiles, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
-  switch (raster_shape(0)) {
-    case 1: return fwd_launch<1>(records, vals, tile_ranges, vs, bg0, bg1, bg2, images, final_T, n_processed, hdr, st);
-    case 4: return fwd_launch<4>(records, vals, tile_ranges, vs, bg0, bg1, bg2, images, final_T, n_processed, hdr, st);
-    default: return fwd_launch<2>(records, vals, tile_ranges, vs, bg0, bg1, bg2, images, final_T, n_processed, hdr, st);
+  const bool ins = opt.instrument;
+  switch (opt.fwd_ppt) {
+    case 2: return fwd_launch<2>(records, vals, tile_ranges, vs, bg0, bg1, bg2, images, final_T, n_processed, hdr, ins, st);
+    case 4: return fwd_launch<4>(records, vals, tile_ranges, vs, bg0, bg1, bg2, images, final_T, n_processed, hdr, ins, st);
+    default: return fwd_launch<1>(records, vals, tile_ranges, vs, bg0, bg1, bg2, images, final_T, n_processed, hdr, ins, st);
   }
 }
 
@@ -837,7 +840,7 @@ cudaError_t launch_raster_bwd(const fgs_record *records, const uint32_t *vals,
                               const uint32_t *tile_ranges, const Views &vs, float bg0, float bg1,
                               float bg2, const float *final_T, const uint32_t *n_processed,
                               const float *dL_dimages, int64_t n_records, char *ws,
-                              const WsLayout &L, cudaStream_t st) {
+                              const WsLayout &L, const CallOpts &opt, cudaStream_t st) {
   WsHeader *hdr = reinterpret_cast<WsHeader *>(ws + L.header);
   float *g2d = reinterpret_cast<float *>(ws + L.g2d);
   uint32_t *order = reinterpret_cast<uint32_t *>(ws + L.tile_order);
@@ -855,11 +858,12 @@ cudaError_t launch_raster_bwd(const fgs_record *records, const uint32_t *vals,
         bucket, hist, hist + WORK_BUCKETS, vs.total_tiles, order);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  switch (raster_shape(1)) {
-    case 1: return bwd_launch<1>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, st);
-    case 8: return bwd_launch<8>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, st);
-    case 4: return bwd_launch<4>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, st);
-    default: return bwd_launch<2>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, st);
+  const bool ins = opt.instrument;
+  switch (opt.bwd_ppt) {
+    case 1: return bwd_launch<1>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, ins, st);
+    case 2: return bwd_launch<2>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, ins, st);
+    case 4: return bwd_launch<4>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, ins, st);
+    default: return bwd_launch<8>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, ins, st);
   }
 }
 

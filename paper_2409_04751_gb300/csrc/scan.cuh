@@ -43,12 +43,18 @@ __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *s_
 // Decoupled look-back: sums the values of partitions part-1, part-2, ... until an inclusive
 // entry is found, reading four predecessors per step so the walk costs a quarter of the L2
 // round trips, and backing off while a predecessor has not published yet. Bounded: gives up
-// (FGS_ERR_TIMEOUT) after SPIN_LIMIT empty polls.
+// (FGS_ERR_TIMEOUT) after `limit` empty polls, at once if limit = 0. The prefix it then
+// returns is partial (smaller than the true one), so every offset built from it stays inside
+// its buffer; the kernels after the scan see the status and do nothing.
 __device__ __forceinline__ uint64_t look_back(const uint64_t *lb, int64_t part, int64_t stride,
-                                              uint32_t *status) {
+                                              uint32_t *status, uint32_t limit) {
   uint64_t prefix = 0;
   uint32_t spins = 0;
   int64_t j = part - 1;
+  if (limit == 0u && j >= 0) {
+    set_status(status, ST_TIMEOUT);
+    return 0;
+  }
   while (j >= 0) {
     uint64_t st[4];
 #pragma unroll
@@ -66,7 +72,7 @@ __device__ __forceinline__ uint64_t look_back(const uint64_t *lb, int64_t part, 
     }
     if (done) break;
     if (used == 0) {
-      if (++spins > SPIN_LIMIT) {
+      if (++spins > limit) {
         set_status(status, ST_TIMEOUT);
         break;
       }
@@ -83,7 +89,7 @@ __global__ void __launch_bounds__(EMIT_THREADS)
                 uint64_t *lb_vis,
                 uint32_t *part_counter, uint32_t *__restrict__ vis_rec,
                 uint64_t *__restrict__ vis_off, uint32_t *__restrict__ chunk_first,
-                uint32_t *status) {
+                uint32_t *status, uint32_t wait_limit) {
   __shared__ uint32_t s_warp[8];
   __shared__ uint64_t s_prefix[2];
   __shared__ uint32_t s_part;
@@ -114,7 +120,7 @@ __global__ void __launch_bounds__(EMIT_THREADS)
       st_volatile_u64(lb, LB_INC | agg);
     } else {
       st_volatile_u64(lb + part, LB_AGG | agg);
-      prefix = look_back(lb, part, 1, status);
+      prefix = look_back(lb, part, 1, status, wait_limit);
       st_volatile_u64(lb + part, LB_INC | (prefix + agg));
     }
     s_prefix[tid == 0 ? 0 : 1] = prefix;

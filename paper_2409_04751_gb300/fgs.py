@@ -31,12 +31,15 @@ FGS_CAM_PINHOLE = 5
 # fgs_bin_sort_ex flags
 FGS_BIN_ELLIPSE = 1
 FGS_BIN_ONESWEEP = 2
+# fgs_options flags
+FGS_OPT_INSTRUMENT = 1
+FGS_OPT_NO_WAIT = 2
 
-EXPORTS = ["fgs_workspace_size", "fgs_workspace_size_ex", "fgs_total_tiles", "fgs_total_pixels", "fgs_preprocess",
-           "fgs_bin_sort", "fgs_rasterize", "fgs_backward", "fgs_backward_raster",
-           "fgs_backward_preprocess", "fgs_bin_sort_noalloc", "fgs_bin_sort_ex", "fgs_loss_l1",
-           "fgs_adam_step", "fgs_read_status",
-           "fgs_set_instrumentation", "fgs_read_counters", "fgs_set_raster_shape",
+EXPORTS = ["fgs_workspace_size", "fgs_workspace_size_ex", "fgs_total_tiles", "fgs_total_pixels",
+           "fgs_preprocess", "fgs_bin_sort", "fgs_bin_sort_ex", "fgs_rasterize",
+           "fgs_rasterize_ex", "fgs_backward", "fgs_backward_ex", "fgs_backward_raster",
+           "fgs_backward_raster_ex", "fgs_backward_preprocess", "fgs_bin_sort_noalloc",
+           "fgs_loss_l1", "fgs_adam_step", "fgs_read_status", "fgs_read_counters",
            "fgs_status_string"]
 
 
@@ -44,6 +47,22 @@ class FgsCamera(ctypes.Structure):
     _fields_ = [("W", ctypes.c_float * 9), ("b", ctypes.c_float * 3), ("fx", ctypes.c_float),
                 ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
                 ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("model", ctypes.c_int32)]
+
+
+class FgsOptions(ctypes.Structure):
+    _fields_ = [("fwd_pixels_per_thread", ctypes.c_int32), ("bwd_pixels_per_thread", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("wait_limit", ctypes.c_uint32)]
+
+
+def options(fwd=0, bwd=0, instrument=False, no_wait=False, wait_limit=0):
+    """fgs_options of one call: rasterizer work shapes (0 = the library's default), the
+    instrumented launches, and the bound of the binning's look-back waits."""
+    flags = (FGS_OPT_INSTRUMENT if instrument else 0) | (FGS_OPT_NO_WAIT if no_wait else 0)
+    return FgsOptions(int(fwd), int(bwd), flags, int(wait_limit))
+
+
+def _opt_ref(opts):
+    return None if opts is None else ctypes.byref(opts)
 
 
 class FgsGaussians(ctypes.Structure):
@@ -81,6 +100,7 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
         cam_p, g_p = ctypes.POINTER(FgsCamera), ctypes.POINTER(FgsGaussians)
+        o_p = ctypes.POINTER(FgsOptions)
         L.fgs_workspace_size.argtypes = [i64, cam_p, i32, i64, ctypes.POINTER(ctypes.c_size_t)]
         L.fgs_workspace_size_ex.argtypes = [i64, cam_p, i32, i64, ctypes.c_uint32,
                                             ctypes.POINTER(ctypes.c_size_t)]
@@ -96,25 +116,27 @@ def lib():
                                    ctypes.c_size_t, vp]
         L.fgs_rasterize.argtypes = [vp, vp, vp, cam_p, i32, vp, vp, vp, vp, vp,
                                     ctypes.c_size_t, vp]
+        L.fgs_rasterize_ex.argtypes = [vp, vp, vp, cam_p, i32, vp, vp, vp, vp, vp,
+                                       ctypes.c_size_t, o_p, vp]
         L.fgs_backward.argtypes = [g_p, cam_p, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                    vp, vp, vp, ctypes.c_size_t, vp]
+        L.fgs_backward_ex.argtypes = [g_p, cam_p, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                      vp, vp, vp, vp, ctypes.c_size_t, o_p, vp]
         L.fgs_backward_raster.argtypes = [vp, vp, vp, i64, cam_p, i32, vp, vp, vp, vp, vp,
                                           ctypes.c_size_t, vp]
+        L.fgs_backward_raster_ex.argtypes = [vp, vp, vp, i64, cam_p, i32, vp, vp, vp, vp, vp,
+                                             ctypes.c_size_t, o_p, vp]
         L.fgs_backward_preprocess.argtypes = [g_p, cam_p, i32, vp, vp, vp, vp, vp, vp, vp, vp,
                                               ctypes.c_size_t, vp]
         L.fgs_bin_sort_noalloc.argtypes = [vp, vp, i64, cam_p, i32, vp, vp, i64, vp, vp, vp, vp]
         L.fgs_bin_sort_ex.argtypes = [vp, vp, i64, cam_p, i32, vp, vp, i64, vp, vp, vp,
-                                      ctypes.c_size_t, ctypes.c_uint32, vp]
+                                      ctypes.c_size_t, ctypes.c_uint32, o_p, vp]
         L.fgs_read_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int)]
-        L.fgs_set_instrumentation.argtypes = [ctypes.c_int]
-        L.fgs_set_instrumentation.restype = None
         L.fgs_read_counters.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
-        L.fgs_set_raster_shape.argtypes = [ctypes.c_int, ctypes.c_int]
         L.fgs_status_string.argtypes = [ctypes.c_int]
         L.fgs_status_string.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("fgs_total_tiles", "fgs_total_pixels", "fgs_status_string",
-                            "fgs_set_instrumentation"):
+            if name not in ("fgs_total_tiles", "fgs_total_pixels", "fgs_status_string"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -201,13 +223,13 @@ def fgs_bin_sort(records, tiles_touched, n, cams, keys, vals, capacity, tile_ran
 
 
 def fgs_bin_sort_ex(records, tiles_touched, n, cams, keys, vals, capacity, tile_ranges,
-                    n_intersections, workspace, workspace_bytes, flags, stream=None):
+                    n_intersections, workspace, workspace_bytes, flags, stream=None, opts=None):
     """fgs_bin_sort with flags (FGS_BIN_ELLIPSE: keep only the pairs whose tile the alpha >=
-    1/255 ellipse reaches)."""
+    1/255 ellipse reaches; FGS_BIN_ONESWEEP: the device-wide radix sort) and options."""
     _check(lib().fgs_bin_sort_ex(_ptr(records), _ptr(tiles_touched), int(n), cams, len(cams),
                                  _ptr(keys), _ptr(vals), int(capacity), _ptr(tile_ranges),
                                  _ptr(n_intersections), _ptr(workspace), int(workspace_bytes),
-                                 int(flags), _stream(stream)), "fgs_bin_sort_ex")
+                                 int(flags), _opt_ref(opts), _stream(stream)), "fgs_bin_sort_ex")
 
 
 def fgs_loss_l1(images, targets, dL_dimages, n, scale, loss, stream=None):
@@ -245,35 +267,48 @@ def _bg_arg(bg):
 
 
 def fgs_rasterize(records, vals, tile_ranges, cams, bg, images, final_T, n_processed,
-                  workspace, workspace_bytes, stream=None):
+                  workspace, workspace_bytes, stream=None, opts=None):
+    """fgs_rasterize, or fgs_rasterize_ex when `opts` (options()) is given."""
     bgp, keep = _bg_arg(bg)
-    _check(lib().fgs_rasterize(_ptr(records), _ptr(vals), _ptr(tile_ranges), cams, len(cams),
-                               bgp, _ptr(images), _ptr(final_T), _ptr(n_processed),
-                               _ptr(workspace), int(workspace_bytes), _stream(stream)),
-           "fgs_rasterize")
+    args = (_ptr(records), _ptr(vals), _ptr(tile_ranges), cams, len(cams), bgp, _ptr(images),
+            _ptr(final_T), _ptr(n_processed), _ptr(workspace), int(workspace_bytes))
+    if opts is None:
+        _check(lib().fgs_rasterize(*args, _stream(stream)), "fgs_rasterize")
+    else:
+        _check(lib().fgs_rasterize_ex(*args, ctypes.byref(opts), _stream(stream)),
+               "fgs_rasterize_ex")
     del keep
 
 
 def fgs_backward(g, cams, records, tiles_touched, vals, tile_ranges, bg, final_T, n_processed,
                  dL_dimages, d_means, d_scales, d_quats, d_opacities, d_sh, workspace,
-                 workspace_bytes, stream=None):
+                 workspace_bytes, stream=None, opts=None):
+    """fgs_backward, or fgs_backward_ex when `opts` (options()) is given."""
     bgp, keep = _bg_arg(bg)
-    _check(lib().fgs_backward(ctypes.byref(g), cams, len(cams), _ptr(records),
-                              _ptr(tiles_touched), _ptr(vals), _ptr(tile_ranges), bgp,
-                              _ptr(final_T), _ptr(n_processed), _ptr(dL_dimages),
-                              _ptr(d_means), _ptr(d_scales), _ptr(d_quats), _ptr(d_opacities),
-                              _ptr(d_sh), _ptr(workspace), int(workspace_bytes),
-                              _stream(stream)), "fgs_backward")
+    args = (ctypes.byref(g), cams, len(cams), _ptr(records), _ptr(tiles_touched), _ptr(vals),
+            _ptr(tile_ranges), bgp, _ptr(final_T), _ptr(n_processed), _ptr(dL_dimages),
+            _ptr(d_means), _ptr(d_scales), _ptr(d_quats), _ptr(d_opacities), _ptr(d_sh),
+            _ptr(workspace), int(workspace_bytes))
+    if opts is None:
+        _check(lib().fgs_backward(*args, _stream(stream)), "fgs_backward")
+    else:
+        _check(lib().fgs_backward_ex(*args, ctypes.byref(opts), _stream(stream)),
+               "fgs_backward_ex")
     del keep
 
 
 def fgs_backward_raster(records, vals, tile_ranges, n, cams, bg, final_T, n_processed,
-                        dL_dimages, workspace, workspace_bytes, stream=None):
+                        dL_dimages, workspace, workspace_bytes, stream=None, opts=None):
+    """fgs_backward_raster, or fgs_backward_raster_ex when `opts` (options()) is given."""
     bgp, keep = _bg_arg(bg)
-    _check(lib().fgs_backward_raster(_ptr(records), _ptr(vals), _ptr(tile_ranges), int(n), cams,
-                                     len(cams), bgp, _ptr(final_T), _ptr(n_processed),
-                                     _ptr(dL_dimages), _ptr(workspace), int(workspace_bytes),
-                                     _stream(stream)), "fgs_backward_raster")
+    args = (_ptr(records), _ptr(vals), _ptr(tile_ranges), int(n), cams, len(cams), bgp,
+            _ptr(final_T), _ptr(n_processed), _ptr(dL_dimages), _ptr(workspace),
+            int(workspace_bytes))
+    if opts is None:
+        _check(lib().fgs_backward_raster(*args, _stream(stream)), "fgs_backward_raster")
+    else:
+        _check(lib().fgs_backward_raster_ex(*args, ctypes.byref(opts), _stream(stream)),
+               "fgs_backward_raster_ex")
     del keep
 
 
@@ -303,16 +338,7 @@ def fgs_read_status(workspace, stream=None) -> int:
     return int(out.value)
 
 
-def fgs_set_instrumentation(on: bool):
-    lib().fgs_set_instrumentation(1 if on else 0)
-
-
 def fgs_read_counters(workspace, stream=None):
     out = (ctypes.c_uint64 * 4)()
     _check(lib().fgs_read_counters(_ptr(workspace), _stream(stream), out), "fgs_read_counters")
     return [int(v) for v in out]
-
-
-def fgs_set_raster_shape(fwd_pixels_per_thread: int, bwd_pixels_per_thread: int):
-    _check(lib().fgs_set_raster_shape(int(fwd_pixels_per_thread), int(bwd_pixels_per_thread)),
-           "fgs_set_raster_shape")

@@ -21,7 +21,7 @@ _KEYS = ("means", "scales", "quats", "opacities", "sh")
 
 class HostPipeline:
     def __init__(self, n, sh_degree, cams_py, device="cuda", capacity=1 << 22, bg=None,
-                 backward=True, use_graph=True):
+                 backward=True, use_graph=True, shape=(0, 0)):
         self.device = torch.device(device)
         dev = self.device
         self.n, self.sh_degree = int(n), int(sh_degree)
@@ -37,7 +37,7 @@ class HostPipeline:
         self.dL = [z((3 * self.P,)) for _ in range(2)]
         self.img = [z((3 * self.P,)) for _ in range(2)]
         self.grad = [{k: z(shapes[k]) for k in _KEYS} for _ in range(2)]
-        self.renderer = FisheyeRenderer(dev, capacity=capacity)
+        self.renderer = FisheyeRenderer(dev, capacity=capacity, fwd_ppt=shape[0], bwd_ppt=shape[1])
         self.s_in = torch.cuda.Stream(dev)
         self.s_run = torch.cuda.Stream(dev)
         self.s_out = torch.cuda.Stream(dev)
@@ -87,11 +87,11 @@ class HostPipeline:
         fT, npr = r._bufs["final_T"], r._bufs["nproc"]
         fgs.fgs_preprocess(g, self.cams, rec, tt)
         fgs.fgs_bin_sort(rec, tt, self.n, self.cams, keys, vals, cap, rg, nint, ws, wsb)
-        fgs.fgs_rasterize(rec, vals, rg, self.cams, self.bg, img, fT, npr, ws, wsb)
+        fgs.fgs_rasterize(rec, vals, rg, self.cams, self.bg, img, fT, npr, ws, wsb, opts=r.opts)
         if self.backward:
             fgs.fgs_backward(g, self.cams, rec, tt, vals, rg, self.bg, fT, npr, dL,
                              grad["means"], grad["scales"], grad["quats"],
-                             grad["opacities"], grad["sh"], ws, wsb)
+                             grad["opacities"], grad["sh"], ws, wsb, opts=r.opts)
 
     def submit(self, host_inputs, host_dL, host_img, host_grads):
         """Queue one step: host_inputs (dict of pinned tensors) and host_dL in, host_img and

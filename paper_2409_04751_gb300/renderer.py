@@ -60,10 +60,14 @@ class FisheyeRenderer:
     binning: "rect" (the tile rect of each footprint, as the method bins) or "ellipse" (only
     the tiles the alpha >= 1/255 ellipse reaches; same images, shorter tile lists).
     sort: "tile" (the per-tile sort, default) or "onesweep" (the device-wide radix sort; rect
-    binning only); same keys."""
+    binning only); same keys.
+    fwd_ppt, bwd_ppt: pixels per thread of the two rasterizers (0 = the library's default);
+    images do not depend on them, gradients only through the order of their sums. They are
+    passed with every call (fgs_options), so renderers with different shapes can run side by
+    side."""
 
     def __init__(self, device="cuda", capacity=1 << 20, growth=1.25, binning="rect",
-                 sort="tile"):
+                 sort="tile", fwd_ppt=0, bwd_ppt=0):
         self.device = torch.device(device)
         self.capacity = int(capacity)
         self.growth = float(growth)
@@ -73,7 +77,13 @@ class FisheyeRenderer:
             raise ValueError("the onesweep sort bins by the rect")
         self.flags = ((fgs.FGS_BIN_ELLIPSE if binning == "ellipse" else 0) |
                       (fgs.FGS_BIN_ONESWEEP if sort == "onesweep" else 0))
+        self.set_shape(fwd_ppt, bwd_ppt)
         self._bufs = {}
+
+    def set_shape(self, fwd_ppt=0, bwd_ppt=0):
+        """Work shape of the rasterizers for this renderer's calls."""
+        self.shape = (int(fwd_ppt), int(bwd_ppt))
+        self.opts = fgs.options(fwd=self.shape[0], bwd=self.shape[1])
 
     def _buf(self, name, numel, dtype):
         b = self._bufs.get(name)
@@ -102,7 +112,7 @@ class FisheyeRenderer:
             nint = self._buf("nint", 1, torch.int64)
             ws = self._buf("ws", ws_bytes, torch.uint8)
             fgs.fgs_bin_sort_ex(records, tt, n, cams, keys, vals, cap, ranges, nint, ws,
-                                ws_bytes, self.flags, stream)
+                                ws_bytes, self.flags, stream, self.opts)
             if not check:
                 break
             st = fgs.fgs_read_status(ws, stream)
@@ -118,7 +128,7 @@ class FisheyeRenderer:
         nproc = self._buf("nproc", P, torch.int32)
         bgt = None if bg is None else tuple(float(v) for v in bg)
         fgs.fgs_rasterize(records, vals, ranges, cams, bgt, images, final_T, nproc, ws, ws_bytes,
-                          stream)
+                          stream, self.opts)
         if check:
             st = fgs.fgs_read_status(ws, stream)
             if st != fgs.FGS_OK:
@@ -135,7 +145,7 @@ class FisheyeRenderer:
         fgs.fgs_backward(g, frame.cams, frame.records, frame.tiles_touched, frame.vals,
                          frame.tile_ranges, frame.bg, frame.final_T, frame.n_processed,
                          dL_dimages, out["means"], out["scales"], out["quats"],
-                         out["opacities"], out["sh"], ws, ws.numel(), stream)
+                         out["opacities"], out["sh"], ws, ws.numel(), stream, self.opts)
         if check:
             st = fgs.fgs_read_status(ws, stream)
             if st != fgs.FGS_OK:

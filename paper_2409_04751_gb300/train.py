@@ -109,13 +109,14 @@ class Trainer:
         fgs.fgs_preprocess(self.g, cam, fr.records, fr.tiles_touched)
         fgs.fgs_bin_sort(fr.records, fr.tiles_touched, n, cam, fr.keys, fr.vals, cap,
                          fr.tile_ranges, fr.n_intersections, ws, wb)
+        opts = self.renderer.opts
         fgs.fgs_rasterize(fr.records, fr.vals, fr.tile_ranges, cam, self.bg, fr.images,
-                          fr.final_T, fr.n_processed, ws, wb)
+                          fr.final_T, fr.n_processed, ws, wb, opts=opts)
         fgs.fgs_loss_l1(fr.images, self.targets, self.dL, 3 * self.P, 1.0 / (3 * self.P), self.loss)
         g = self.grads
         fgs.fgs_backward(self.g, cam, fr.records, fr.tiles_touched, fr.vals, fr.tile_ranges,
                          self.bg, fr.final_T, fr.n_processed, self.dL, g["means"], g["scales"],
-                         g["quats"], g["opacities"], g["sh"], ws, wb)
+                         g["quats"], g["opacities"], g["sh"], ws, wb, opts=opts)
         if adam:
             fgs.fgs_adam_step(self.groups, self.betas[0], self.betas[1], self.eps,
                               self.step_count)

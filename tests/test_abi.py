@@ -98,6 +98,35 @@ def test_invalid_arguments_rejected_before_launch(lib):
     assert lib.fgs_workspace_size_ex(10, cams, 1, 10, 4, ctypes.byref(out)) == INV
     for fl in (4, fgs.FGS_BIN_ELLIPSE | fgs.FGS_BIN_ONESWEEP):
         assert lib.fgs_bin_sort_ex(256, 256, 10, cams, 1, 256, 256, 100, 256, 256, 256, 1 << 30,
-                                   fl, None) == INV
+                                   fl, None, None) == INV
     assert lib.fgs_bin_sort_ex(256, 256, 10, cams, 1, 256, 256, 100, 256, 256, 256, 1 << 12,
-                               fgs.FGS_BIN_ONESWEEP, None) == INV  # workspace too small
+                               fgs.FGS_BIN_ONESWEEP, None, None) == INV  # workspace too small
+    # more Gaussians than the 32-bit record index holds, bounded before any product with the
+    # view count
+    assert lib.fgs_bin_sort_ex(256, 256, 1 << 40, cams, 1, 256, 256, 100, 256, 256, 256,
+                               1 << 30, 0, None, None) == INV
+    assert lib.fgs_workspace_size(1 << 62, cams, 1, 10, ctypes.byref(out)) == INV
+
+
+def test_options_checked_before_launch(lib):
+    """fgs_options: work shapes outside the lists and unknown flag bits are refused by every
+    call that takes them, before anything is launched."""
+    cams = _cam()
+    INV = fgs.FGS_ERR_INVALID_ARG
+    bad = [fgs.options(fwd=3), fgs.options(fwd=8), fgs.options(bwd=16), fgs.options(bwd=-1),
+           fgs.FgsOptions(0, 0, 4, 0)]
+    g = fgs.FgsGaussians(16, 16, 16, 16, 16, 10, 3)
+    for o in bad:
+        r = ctypes.byref(o)
+        assert lib.fgs_rasterize_ex(256, 256, 256, cams, 1, None, 256, 256, 256, 256, 1 << 20,
+                                    r, None) == INV
+        assert lib.fgs_backward_raster_ex(256, 256, 256, 10, cams, 1, None, 256, 256, 256, 256,
+                                          1 << 20, r, None) == INV
+        assert lib.fgs_backward_ex(ctypes.byref(g), cams, 1, 256, 256, 256, 256, None, 256, 256,
+                                   256, 256, 256, 256, 256, 256, 256, 1 << 20, r, None) == INV
+        assert lib.fgs_bin_sort_ex(256, 256, 10, cams, 1, 256, 256, 100, 256, 256, 256, 1 << 30,
+                                   0, r, None) == INV
+    # null outputs are still refused when the options are fine
+    ok = ctypes.byref(fgs.options(fwd=1, bwd=8, wait_limit=5))
+    assert lib.fgs_rasterize_ex(256, 256, 256, cams, 1, None, 0, 256, 256, 256, 1 << 20, ok,
+                                None) == INV

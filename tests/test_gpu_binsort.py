@@ -52,7 +52,7 @@ def _records(rng, n, cams_py, p_empty=0.2, max_ext=3, tie_frac=0.3, big_frac=0.0
 SORTS = [0, fgs.FGS_BIN_ONESWEEP]  # the per-tile sort and the device-wide onesweep sort
 
 
-def _run(rec, tt, n, cams_py, capacity, flags=0):
+def _run(rec, tt, n, cams_py, capacity, flags=0, opts=None):
     dev = torch.device("cuda:0")
     cams = fgs.cameras(cams_py)
     R = rec.shape[0]
@@ -65,7 +65,8 @@ def _run(rec, tt, n, cams_py, capacity, flags=0):
     nint = torch.zeros(1, dtype=torch.int64, device=dev)
     wsb = fgs.fgs_workspace_size(n, cams, capacity, flags)
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
-    fgs.fgs_bin_sort_ex(records, ttd, n, cams, keys, vals, capacity, ranges, nint, ws, wsb, flags)
+    fgs.fgs_bin_sort_ex(records, ttd, n, cams, keys, vals, capacity, ranges, nint, ws, wsb, flags,
+                        opts=opts)
     st = fgs.fgs_read_status(ws)
     return dict(keys=keys.cpu().numpy().view(np.uint64), vals=vals.cpu().numpy().view(np.uint32),
                 ranges=ranges.cpu().numpy().view(np.uint32).reshape(-1, 2), n=int(nint.item()),
@@ -156,9 +157,8 @@ def test_binsort_tiles_touched_differs_from_rect(cuda_device, flags):
     are the first min(tiles_touched, w h) tiles of its rect in row-major order (a shorter count
     takes whole rows and part of the next; a longer one stops at the rect). The per-tile counts
     and the scattered pairs must agree exactly, so the keys, values and ranges are those of
-    that definition, written out here by brute force. (Longer counts only for the per-tile
-    sort: the device-wide sort's emission assumes tiles_touched = w h, as fgs_preprocess
-    writes it, and stays inside its buffers otherwise.)"""
+    that definition, written out here by brute force, for both sorts (the device-wide sort
+    drops the surplus pairs of a longer count at emission)."""
     cams_py = _cams([(160, 96), (64, 64)])
     rng = np.random.default_rng(21)
     n = 1500
@@ -169,9 +169,8 @@ def test_binsort_tiles_touched_differs_from_rect(cuda_device, flags):
     short = vis & (pick < 0.4)
     tt = tt.astype(np.int64)
     tt[short] = rng.integers(1, area[short] + 1)
-    if flags == 0:  # the device-wide sort emits tiles_touched pairs whatever the rect
-        longer = vis & (pick > 0.8)
-        tt[longer] = area[longer] + rng.integers(1, 4, int(longer.sum()))
+    longer = vis & (pick > 0.8)
+    tt[longer] = area[longer] + rng.integers(1, 4, int(longer.sum()))
     tt = tt.astype(np.uint32)
     cand = int(tt.astype(np.int64).sum())
     out = _run(rec, tt, n, cams_py, cand + 11, flags)
@@ -207,3 +206,73 @@ def test_binsort_tiles_touched_differs_from_rect(cuda_device, flags):
     starts = np.concatenate([[0], np.cumsum(cnt)[:-1]])
     nz = cnt > 0
     assert np.array_equal(rg[nz, 0], starts[nz])
+
+
+@pytest.mark.parametrize("n,size,flags", [
+    (9000, (256, 256), 0),                      # 3 record-scan partitions, 1 tile partition
+    (2000, (1752, 1168), 0),                    # 1 record-scan partition, 8 tile partitions
+    (9000, (256, 256), fgs.FGS_BIN_ONESWEEP),   # the record scan of the onesweep path
+    (2000, (1752, 1168), fgs.FGS_BIN_ONESWEEP),  # its radix passes (several key partitions)
+])
+def test_binsort_timeout_reports_status_and_recovers(cuda_device, n, size, flags):
+    """The timeout path of a real call: with FGS_OPT_NO_WAIT every decoupled look-back wait of
+    the binning gives up before its first poll. The call must report FGS_ERR_TIMEOUT, the
+    rasterizer must then draw the background only and the backward add nothing; the next call
+    at the normal wait bound is bit-exact again. Nothing waits on anything that never comes:
+    the waits give up by construction, and every kernel after the one that gave up leaves its
+    outputs alone."""
+    from paper_2409_04751_gb300 import scenes
+    from paper_2409_04751_gb300.renderer import gaussians_of, scene_to_device
+    dev = cuda_device
+    scene = scenes.shell_scene(n, seed=90, sh_degree=1)
+    cam = scenes.pose_camera(size[0], size[1], 180.0, seed=91)
+    gs = scene_to_device(scene, dev)
+    g = gaussians_of(gs)
+    cams = fgs.cameras([cam])
+    P = size[0] * size[1]
+    tiles = fgs.fgs_total_tiles(cams)
+    records = torch.empty(n * 12, dtype=torch.float32, device=dev)
+    tt = torch.empty(n, dtype=torch.int32, device=dev)
+    fgs.fgs_preprocess(g, cams, records, tt)
+    cap = int(tt.sum().item()) + 64
+    assert cap > 4096 + 64 or flags == 0  # several key partitions for the onesweep passes
+    wsb = fgs.fgs_workspace_size(n, cams, cap, flags)
+    bg = (0.25, 0.5, 0.75)
+
+    def frame(opts):
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        keys = torch.zeros(cap, dtype=torch.int64, device=dev)
+        vals = torch.zeros(cap + 4, dtype=torch.int32, device=dev)
+        ranges = torch.zeros(2 * tiles, dtype=torch.int32, device=dev)
+        nint = torch.zeros(1, dtype=torch.int64, device=dev)
+        fgs.fgs_bin_sort_ex(records, tt, n, cams, keys, vals, cap, ranges, nint, ws, wsb, flags,
+                            opts=opts)
+        st = fgs.fgs_read_status(ws)
+        img = torch.empty(3 * P, dtype=torch.float32, device=dev)
+        fT = torch.empty(P, dtype=torch.float32, device=dev)
+        npr = torch.empty(P, dtype=torch.int32, device=dev)
+        fgs.fgs_rasterize(records, vals, ranges, cams, bg, img, fT, npr, ws, wsb)
+        grads = {k: torch.full_like(gs[k], 7.0) for k in ("means", "scales", "quats",
+                                                           "opacities", "sh")}
+        dL = torch.ones(3 * P, dtype=torch.float32, device=dev)
+        fgs.fgs_backward(g, cams, records, tt, vals, ranges, bg, fT, npr, dL, grads["means"],
+                         grads["scales"], grads["quats"], grads["opacities"], grads["sh"], ws,
+                         wsb)
+        torch.cuda.synchronize()
+        return st, int(nint.item()), keys, vals, ranges, img, fT, npr, grads
+
+    ref = frame(None)
+    assert ref[0] == fgs.FGS_OK
+    st, _, _, _, _, img, fT, npr, grads = frame(fgs.options(no_wait=True))
+    assert st == fgs.FGS_ERR_TIMEOUT
+    img = img.view(3, -1)
+    for c in range(3):
+        assert torch.all(img[c] == bg[c])
+    assert torch.all(fT == 1.0) and torch.all(npr == 0)
+    for k, v in grads.items():
+        assert torch.all(v == 0), k
+    again = frame(fgs.options(wait_limit=0))  # the normal bound
+    assert again[0] == fgs.FGS_OK and again[1] == ref[1]
+    m = ref[1]
+    assert torch.equal(again[2][:m], ref[2][:m]) and torch.equal(again[3][:m], ref[3][:m])
+    assert torch.equal(again[4], ref[4]) and torch.equal(again[5], ref[5])

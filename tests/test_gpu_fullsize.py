@@ -1,7 +1,9 @@
 """Parity at the full benchmark workload (500k Gaussians, SH degree 3, one 1752x1168 view at
-180 degrees, random pose), in the launch configuration the benchmark times: sampled pixels
-rendered one by one by the oracle, the gradient of the loss restricted to those pixels, and
-properties of the sorted keys that hold at any size."""
+180 degrees, random pose), in the launch configuration the benchmark times (its rasterizer work
+shapes are 1 pixel per thread forward and 8 backward, the library's defaults, which its tuner
+confirms; every other shape is covered too): sampled pixels rendered one by one by the oracle,
+the gradient of the loss restricted to those pixels, and properties of the sorted keys that hold
+at any size."""
 import numpy as np
 import pytest
 import torch
@@ -19,10 +21,13 @@ def cfg1():
     scene, cams = scenes.config1()
     dev = torch.device("cuda:0")
     gs = scene_to_device(scene, dev)
-    r = FisheyeRenderer(dev, capacity=24_000_000)
+    r = FisheyeRenderer(dev, capacity=24_000_000, fwd_ppt=BENCH_SHAPE[0], bwd_ppt=BENCH_SHAPE[1])
     fr = r.forward(gs, cams)
     G = oracle.project(scene, cams[0])
     return scene, cams, gs, r, fr, G
+
+
+BENCH_SHAPE = (1, 8)  # pixels per thread of the forward and backward rasterizers
 
 
 def test_config1_sampled_pixels(cfg1):
@@ -74,9 +79,10 @@ def test_config1_keys_properties(cfg1):
     assert np.array_equal(vis[~near], (tt > 0)[~near])
 
 
-def test_config1_sampled_gradient(cfg1):
-    """dL/dimage nonzero only on sampled pixels: every gradient tensor against the oracle's
-    gradient of the same restricted loss."""
+@pytest.fixture(scope="module")
+def cfg1_grad(cfg1):
+    """dL/dimage nonzero only on 1500 sampled pixels, and the oracle's gradient of that
+    restricted loss (computed once)."""
     scene, cams, gs, r, fr, G = cfg1
     cam = cams[0]
     w, h = cam["width"], cam["height"]
@@ -87,8 +93,31 @@ def test_config1_sampled_gradient(cfg1):
     dL = np.zeros((3, h * w), np.float32)
     dL[:, idx] = gvals.T.astype(np.float32)
     ref = oracle.backward(G, scene, cam, pix, dL[:, idx].T.astype(np.float64))
-    g = r.backward(gs, fr, torch.as_tensor(dL.reshape(-1)).cuda())
-    parity.check_grads(g, ref, "config1 sampled")
+    return torch.as_tensor(dL.reshape(-1)).cuda(), ref
+
+
+@pytest.mark.parametrize("bwd", [8, 1, 2, 4])
+def test_config1_sampled_gradient(cfg1, cfg1_grad, bwd):
+    """Every gradient tensor against the oracle's gradient of the restricted loss, for the
+    benchmark's backward shape (8 pixels per thread) and every other one."""
+    scene, cams, gs, r, fr, G = cfg1
+    dL, ref = cfg1_grad
+    r2 = FisheyeRenderer(r.device, capacity=r.capacity, fwd_ppt=BENCH_SHAPE[0], bwd_ppt=bwd)
+    r2._bufs = r._bufs  # the same frame and workspace
+    g = r2.backward(gs, fr, dL)
+    parity.check_grads(g, ref, f"config1 sampled, backward shape {bwd}")
+
+
+@pytest.mark.parametrize("fwd", [2, 4])
+def test_config1_forward_shapes_identical(cfg1, fwd):
+    """The other forward work shapes give the benchmark shape's image, final T and processed
+    counts bit for bit at full size."""
+    scene, cams, gs, r, fr, G = cfg1
+    img0, T0, n0 = fr.images.clone(), fr.final_T.clone(), fr.n_processed.clone()
+    r2 = FisheyeRenderer(r.device, capacity=r.capacity, fwd_ppt=fwd, bwd_ppt=BENCH_SHAPE[1])
+    f2 = r2.forward(gs, cams)
+    assert torch.equal(f2.images, img0) and torch.equal(f2.final_T, T0)
+    assert torch.equal(f2.n_processed, n0)
 
 
 # ------------------------------------------------------------------------------------------

@@ -15,10 +15,10 @@ from tests import parity
 pytestmark = pytest.mark.gpu
 
 
-def _render(scene, cams, bg=None, capacity=1 << 16):
+def _render(scene, cams, bg=None, capacity=1 << 16, shape=(0, 0)):
     dev = torch.device("cuda:0")
     gs = scene_to_device(scene, dev)
-    r = FisheyeRenderer(dev, capacity=capacity)
+    r = FisheyeRenderer(dev, capacity=capacity, fwd_ppt=shape[0], bwd_ppt=shape[1])
     fr = r.forward(gs, cams, bg=bg)
     return r, gs, fr
 
@@ -147,9 +147,9 @@ def test_multiview_call_equals_single_view_calls(cuda_device):
         assert np.array_equal(f1.view_images([c])[0].cpu().numpy(), multi[k])
 
 
-def _grad_case(scene, cams, seed, bg=None, mask=None):
+def _grad_case(scene, cams, seed, bg=None, mask=None, shape=(0, 0)):
     dev = torch.device("cuda:0")
-    r, gs, fr = _render(scene, cams, bg=bg, capacity=1 << 20)
+    r, gs, fr = _render(scene, cams, bg=bg, capacity=1 << 20, shape=shape)
     P = sum(c["width"] * c["height"] for c in cams)
     dL = scenes.upstream_grad((3 * P,), 1.0, seed)
     g = r.backward(gs, fr, torch.as_tensor(dL).to(dev))
@@ -197,26 +197,88 @@ def test_gradients_near_axis_series_region(cuda_device):
     parity.check_grads(g, ref, "near-axis")
 
 
+FWD_SHAPES = (1, 2, 4)
+BWD_SHAPES = (1, 2, 4, 8)
+
+
 def test_work_shapes_agree(cuda_device):
-    """Every rasterizer work shape (pixels per thread 1, 2, 4) gives the same image, final T and
-    processed counts bit for bit, and the same gradients up to summation order."""
+    """Every rasterizer work shape (forward 1, 2, 4 and backward 1, 2, 4, 8 pixels per thread)
+    gives the same image, final T and processed counts bit for bit, and the same gradients up to
+    summation order. The shapes are passed per call (each renderer its own)."""
     scene = scenes.shell_scene(20_000, seed=80, sh_degree=3)
     cam = scenes.pose_camera(300, 200, 190.0, seed=81)
     dL = torch.as_tensor(scenes.upstream_grad((3 * 300 * 200,), 1.0, 82)).cuda()
     outs = []
-    try:
-        for s in (1, 2, 4):
-            fgs.fgs_set_raster_shape(s, s)
-            r, gs, fr = _render(scene, [cam], capacity=1 << 20)
-            g = r.backward(gs, fr, dL)
-            outs.append((fr.images.cpu().numpy().copy(), fr.final_T.cpu().numpy().copy(),
-                         fr.n_processed.cpu().numpy().copy(),
-                         {k: v.cpu().numpy().copy() for k, v in g.items()}))
-    finally:
-        fgs.fgs_set_raster_shape(2, 2)
+    for f, b in zip(FWD_SHAPES + (1,), BWD_SHAPES):
+        r, gs, fr = _render(scene, [cam], capacity=1 << 20, shape=(f, b))
+        g = r.backward(gs, fr, dL)
+        outs.append((fr.images.cpu().numpy().copy(), fr.final_T.cpu().numpy().copy(),
+                     fr.n_processed.cpu().numpy().copy(),
+                     {k: v.cpu().numpy().copy() for k, v in g.items()}))
     for o in outs[1:]:
         assert np.array_equal(o[0], outs[0][0])
         assert np.array_equal(o[1], outs[0][1])
         assert np.array_equal(o[2], outs[0][2])
         for k in o[3]:
             assert parity.rel_l2(o[3][k], outs[0][3][k]) < 1e-5, k
+
+
+@pytest.fixture(scope="module")
+def deg3_case():
+    """The SH-degree-3 gradient case (6000 Gaussians, 160 x 120 at 190 degrees, non-unit
+    quaternions, a background) with the oracle's gradient, computed once."""
+    scene = scenes.shell_scene(6000, seed=53, sh_degree=3)
+    scene["quats"] = scene["quats"] * np.float32(1.7)
+    cam = scenes.pose_camera(160, 120, 190.0, seed=503)
+    bg = (0.2, 0.3, 0.4)
+    dL = scenes.upstream_grad((3 * 160 * 120,), 1.0, 8)
+    G = oracle.project(scene, cam)
+    ref = oracle.backward(G, scene, cam, oracle.all_pixels(cam), dL.reshape(3, -1).T, bg)
+    return scene, cam, bg, dL, ref
+
+
+@pytest.mark.parametrize("bwd", BWD_SHAPES)
+def test_gradients_every_backward_shape_match_oracle(cuda_device, deg3_case, bwd):
+    """Whole-image gradients of every backward work shape, including the one-warp-per-tile
+    shape (8 pixels per thread) the benchmark's tuner picks, against the FP64 oracle."""
+    scene, cam, bg, dL, ref = deg3_case
+    r, gs, fr = _render(scene, [cam], bg=bg, capacity=1 << 20, shape=(1, bwd))
+    g = r.backward(gs, fr, torch.as_tensor(dL).cuda())
+    parity.check_grads(g, ref, f"backward shape {bwd}")
+
+
+def test_calls_with_different_shapes_run_side_by_side(cuda_device):
+    """The library keeps no process-wide setting: two renderers with different work shapes and
+    their own workspaces, running fwd + bwd on two streams at the same time, each give exactly
+    what they give alone (images bit for bit, gradients up to the order of their sums)."""
+    scene = scenes.shell_scene(20_000, seed=84, sh_degree=3)
+    cam = scenes.pose_camera(320, 240, 180.0, seed=85)
+    dev = torch.device("cuda:0")
+    gs = scene_to_device(scene, dev)
+    dL = torch.as_tensor(scenes.upstream_grad((3 * 320 * 240,), 1.0, 86)).to(dev)
+    shapes = [(1, 8), (4, 2)]
+    rs = [FisheyeRenderer(dev, capacity=1 << 20, fwd_ppt=f, bwd_ppt=b) for f, b in shapes]
+    alone = []
+    for r in rs:
+        fr = r.forward(gs, [cam])
+        g = r.backward(gs, fr, dL)
+        alone.append((fr.images.clone(), {k: v.clone() for k, v in g.items()}))
+    streams = [torch.cuda.Stream(dev) for _ in rs]
+    torch.cuda.synchronize()
+    together = []
+    for rep in range(3):
+        frs = []
+        for r, st in zip(rs, streams):
+            with torch.cuda.stream(st):
+                fr = r.forward(gs, [cam], check=False)
+                frs.append((fr, r.backward(gs, fr, dL, check=False)))
+        torch.cuda.synchronize()
+        together.append([(fr.images.clone(), {k: v.clone() for k, v in g.items()})
+                         for fr, g in frs])
+        for r in rs:
+            assert fgs.fgs_read_status(r._bufs["ws"]) == fgs.FGS_OK
+    for run in together:
+        for (img, g), (img0, g0) in zip(run, alone):
+            assert torch.equal(img, img0)
+            for k in g:
+                assert parity.rel_l2(g[k].cpu().numpy(), g0[k].cpu().numpy()) < 1e-5, k

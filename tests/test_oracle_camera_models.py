@@ -141,6 +141,31 @@ def test_field_limits():
     assert oracle.project(one([0.3, 0.2, -2.0]), cam_p)[0, 0] == 1    # behind: still seen
 
 
+def test_pinhole_guard_band():
+    """The pinhole culls a Gaussian whose projected mean lies beyond 1.3 times the half image
+    from the principal point: at 90 deg and 160 x 120 (f = 80, c = (80, 60)) the band is
+    |x_c / z_c| <= 1.3 and |y_c / z_c| <= 0.975, far inside its angular field (87.1 deg). The
+    Gaussians are large enough (footprints of about 100 px) to reach the image from there."""
+    one = lambda mu: dict(means=np.array([mu], np.float64), scales=np.full((1, 3), 0.5),
+                          quats=np.array([[1.0, 0, 0, 0]]), opacities=np.array([0.8]),
+                          sh=np.zeros((1, 1, 3)), sh_degree=0)
+    cam = scenes.fisheye_camera(160, 120, 90.0, model=oracle.CAM_PINHOLE)
+    assert abs(cam["fx"] - 80.0) < 1e-9 and cam["cx"] == 80.0 and cam["cy"] == 60.0
+    z = 2.0
+    for tx, ty, vis in [(1.299, 0.0, 1), (1.301, 0.0, 0), (-1.299, 0.5, 1), (-1.301, 0.5, 0),
+                        (0.3, 0.974, 1), (0.3, 0.976, 0), (0.0, -0.976, 0), (1.29, -0.97, 1)]:
+        G = oracle.project(one([tx * z, ty * z, z]), cam)
+        assert G[0, 0] == vis, (tx, ty)
+        if vis:
+            # the distance to the band (in tiles) is one of the decision margins
+            gap = min(104.0 - abs(G[0, oracle.F["xy"]] - 80.0),
+                      78.0 - abs(G[0, oracle.F["xy"] + 1] - 60.0)) / 16.0
+            assert G[0, oracle.F["rmargin"]] <= gap + 1e-12
+    # an equidistant camera of the same size keeps the point the pinhole culls
+    cam_e = scenes.fisheye_camera(160, 120, 90.0)
+    assert oracle.project(one([1.301 * z, 0.0, z]), cam_e)[0, 0] == 1
+
+
 def _tiny_scene(seed, n=7, degree=2):
     rng = np.random.default_rng(seed)
     means = rng.normal(size=(n, 3))

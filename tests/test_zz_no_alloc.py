@@ -88,6 +88,40 @@ def test_noalloc_matches_workspace_version_twice(cuda_device):
         assert np.array_equal(k0, k1) and np.array_equal(v0, v1) and np.array_equal(r0, r1)
 
 
+def test_noalloc_reports_capacity_overflow_like_the_workspace_version(cuda_device):
+    """A device-side error reaches the caller's status buffer: with fewer key slots than pairs
+    the call reports FGS_ERR_CAPACITY and the true pair count, as fgs_bin_sort does, and the
+    next call with room is correct again."""
+    dev = cuda_device
+    cams_py = _cams([(640, 480)])
+    n = 5000
+    rec, tt = _records(3, n, cams_py)
+    m = int(tt.astype(np.int64).sum())
+    cams = fgs.cameras(cams_py)
+    tiles = fgs.fgs_total_tiles(cams)
+    records = torch.as_tensor(rec.reshape(-1)).to(dev)
+    ttd = torch.as_tensor(tt.view(np.int32)).to(dev)
+    small = m // 2
+    ref = _buffers(small, tiles, dev)
+    wsb = fgs.fgs_workspace_size(n, cams, small)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    fgs.fgs_bin_sort(records, ttd, n, cams, ref["keys"], ref["vals"], small, ref["ranges"],
+                     ref["nint"], ws, wsb)
+    assert fgs.fgs_read_status(ws) == fgs.FGS_ERR_CAPACITY
+    got = _buffers(small, tiles, dev)
+    status = torch.full((1,), -1, dtype=torch.int32, device=dev)
+    fgs.fgs_bin_sort_noalloc(records, ttd, n, cams, got["keys"], got["vals"], small,
+                             got["ranges"], got["nint"], status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == fgs.FGS_ERR_CAPACITY
+    assert int(got["nint"].item()) == int(ref["nint"].item()) == m
+    big = _buffers(m + 8, tiles, dev)
+    fgs.fgs_bin_sort_noalloc(records, ttd, n, cams, big["keys"], big["vals"], m + 8,
+                             big["ranges"], big["nint"], status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == fgs.FGS_OK and int(big["nint"].item()) == m
+
+
 def test_noalloc_refuses_sizes_beyond_its_limits(cuda_device):
     L = fgs.lib()
     cams = fgs.cameras(_cams([(256, 256)]))
@@ -101,4 +135,12 @@ def test_noalloc_refuses_sizes_beyond_its_limits(cuda_device):
         fgs.FGS_ERR_INVALID_ARG
     # a missing status buffer
     assert L.fgs_bin_sort_noalloc(p, p, 10, cams, 1, p, p, 1024, p, p, None, None) == \
+        fgs.FGS_ERR_INVALID_ARG
+    # more tiles over all views than the fixed scratch holds (2^17): two views of 512 x 256
+    # tiles each
+    big = fgs.cameras(_cams([(8192, 4096), (8192, 4096)]))
+    assert L.fgs_bin_sort_noalloc(p, p, 10, big, 2, p, p, 1024, p, p, p, None) == \
+        fgs.FGS_ERR_INVALID_ARG
+    # a Gaussian count so large that it would overflow when multiplied by the view count
+    assert L.fgs_bin_sort_noalloc(p, p, 1 << 62, big, 2, p, p, 1024, p, p, p, None) == \
         fgs.FGS_ERR_INVALID_ARG

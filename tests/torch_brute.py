@@ -118,6 +118,9 @@ def render_and_grad(scene, cam, dLdC=None, bg=(0.0, 0.0, 0.0), grad=True):
         if not (float(dist) > 0.2 and in_field(muc) and float(opac[i]) >= 1 / 255):
             continue
         xy = phi(muc)
+        # the pinhole renderer's guard band 1.3 tan(FOV/2), as a cull of the projected mean
+        if model == 5 and (abs(float(xy[0]) - cx) > 0.65 * w or abs(float(xy[1]) - cy) > 0.65 * h):
+            continue
         J = torch.autograd.functional.jacobian(phi, muc, create_graph=True)
         R = _rot_from_quat(quats[i])
         M = R * scales[i][None, :]
