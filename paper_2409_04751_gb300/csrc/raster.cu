@@ -17,9 +17,10 @@
 // The backward replays each pixel's blend back to front from its final transmittance and the
 // number of list entries it processed (both written by the forward), recovering the
 // transmittance before each Gaussian by division; nothing per (pixel, Gaussian) is stored. Per
-// contributing pair it accumulates nine sums that depend on the pixel only: the moments
-// sum dL/dp (dx, dy, dx^2, dx dy, dy^2) of the exponent p = -0.5 d^T conic d, sum dL/dalpha
-// alpha_raw, and dL/drgb. Each thread first sums its own pixels; the warp then reduces two
+// list entry it needs nine sums over the pixels: the moments sum dL/dp (dx, dy, dx^2, dx dy,
+// dy^2) of the exponent p = -0.5 d^T conic d, sum dL/dalpha alpha_raw, and dL/drgb. Each thread
+// sums its own pixels into six local sums (the moments follow from sums of dL/dp weighted by
+// the pixel's row inside the thread) and forms the nine from them; the warp then reduces two
 // entries' eighteen sums with a transpose reduction (each exchange halves the values a lane
 // carries) and lanes add the totals to the records' accumulators. The preprocess backward turns
 // the moments into dL/dxy, dL/dconic and dL/dopacity with the record's conic and opacity. The
@@ -497,15 +498,22 @@ __device__ __forceinline__ float warp_transpose_sum16(const float (&a)[9], const
 
 // One (pixel, Gaussian) pair of the backward, back to front, its contribution decided by c:
 // recovers the transmittance in front of the Gaussian, updates the colour-behind sum GS and
-// adds the pixel's terms to the nine per-record sums v. A pixel that does not take part (not
+// adds the pixel's terms to the entry's six local sums a. A pixel that does not take part (not
 // yet reached back to front, or alpha below 1/255) gets alpha = 0 and 1/(1 - alpha) = 1 by
 // selection, so its transmittance, GS and sums stay exactly as they were. The backward calls
 // it for every pixel and entry without branching: the cull at staging leaves most evaluations
 // contributing, and straight-line code lets the compiler interleave the independent
 // transmittance chains of a thread's pixels, which hides the latency of each chain.
-__device__ __forceinline__ void bwd_contrib(bool c, float e, float r, float g, float b, float dx,
-                                            float dy, float G0, float G1, float G2, float &T,
-                                            float &GS, float (&v)[9]) {
+//
+// alpha = opacity exp(p), p = -0.5 d^T conic d, so dL/dp = dL/dalpha alpha where alpha is below
+// its cap, and the opacity term dL/dalpha alpha_raw equals dL/dp there: one sum serves both.
+// The moments of dL/dp over the pixel offsets (dx, dy) = (u + cx, v + cy) are not formed per
+// pixel: the thread's pixels share the column u and sit in rows v = v0 + k, k = 0 .. PPT - 1,
+// so a[0] = sum dL/dp, a[1] = sum k dL/dp and a[2] = sum k^2 dL/dp (k a constant once the
+// pixel loop is unrolled) determine all five (moments_of_local_sums). a[3..5] = sum dL/drgb.
+__device__ __forceinline__ void bwd_contrib(bool c, float e, float r, float g, float b, int k,
+                                            float G0, float G1, float G2, float &T, float &GS,
+                                            float (&a)[6]) {
   const float araw = c ? ex2_approx(e) : 0.f;
   const float alpha = fminf(ALPHA_MAX, araw);
   const float om = c ? rcp_approx(1.f - alpha) : 1.f;
@@ -515,21 +523,33 @@ __device__ __forceinline__ void bwd_contrib(bool c, float e, float r, float g, f
   // dL/dalpha = <dL/dC, colour T - behind / (1 - alpha)>
   const float dLda = fmaf(T, gc, -om * GS);
   GS = fmaf(gc, wgt, GS);
-  v[6] = fmaf(G0, wgt, v[6]);
-  v[7] = fmaf(G1, wgt, v[7]);
-  v[8] = fmaf(G2, wgt, v[8]);
-  // alpha = opacity exp(p), p = -0.5 d^T conic d: the moments of dL/dp over the pixel offsets
-  // and the opacity term, where alpha is below its cap; the conic and opacity are applied once
-  // per record in the preprocess backward
-  const bool free_ = araw < ALPHA_MAX;
-  const float dLdp = dLda * (free_ ? alpha : 0.f);
-  const float tx = dLdp * dx, ty = dLdp * dy;
-  v[0] += tx;
-  v[1] += ty;
-  v[2] = fmaf(tx, dx, v[2]);
-  v[3] = fmaf(tx, dy, v[3]);
-  v[4] = fmaf(ty, dy, v[4]);
-  v[5] = fmaf(dLda, free_ ? araw : 0.f, v[5]);
+  a[3] = fmaf(G0, wgt, a[3]);
+  a[4] = fmaf(G1, wgt, a[4]);
+  a[5] = fmaf(G2, wgt, a[5]);
+  const float d = dLda * (araw < ALPHA_MAX ? araw : 0.f);  // dL/dp
+  a[0] += d;
+  if (k > 0) {  // k is a constant in the unrolled pixel loop
+    a[1] = fmaf(d, (float)k, a[1]);
+    a[2] = fmaf(d, (float)(k * k), a[2]);
+  }
+}
+
+// The nine per-record sums of one entry from a thread's local sums: with w = v0 + cy (the first
+// row's offset from the mean) and dx = u + cx,
+//   sum dL/dp dx = dx S,  sum dL/dp dy = w S + S_k,  sum dL/dp dx^2 = dx^2 S,
+//   sum dL/dp dx dy = dx (w S + S_k),  sum dL/dp dy^2 = w^2 S + 2 w S_k + S_kk,
+// then the opacity term (S itself) and the three colour sums.
+__device__ __forceinline__ void moments_of_local_sums(const float (&a)[6], float dx, float w,
+                                                      float (&v)[9]) {
+  v[0] = dx * a[0];
+  v[1] = fmaf(w, a[0], a[1]);
+  v[2] = dx * v[0];
+  v[3] = dx * v[1];
+  v[4] = fmaf(w, v[1] + a[1], a[2]);
+  v[5] = a[0];
+  v[6] = a[3];
+  v[7] = a[4];
+  v[8] = a[5];
 }
 
 template <int PPT, bool COUNT>
@@ -646,13 +666,13 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
           const bool any_pos = pos_a < my_max;
           if (!__any_sync(0xffffffffu, any_pos)) continue;
           float va[9], vb[9];
-#pragma unroll
-          for (int q = 0; q < 9; ++q) va[q] = vb[q] = 0.f;
           bool ca = false, cb = false;
           {
             const PairTerms pt = pair_terms(cf[p][0], cf[p][1], cf[p][2], u2, uu2);
             const float4 qa = cf[p][3], qb = cf[p][4];
-            const float dxa = fu + qa.w, dxb = fu + qb.w;
+            float sa[6], sb[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) sa[q] = sb[q] = 0.f;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
               const bool in_a = pos_a < last[k], in_b = pos_b < last[k];
@@ -665,11 +685,11 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
               }
               cb = cb || cbk;
               ca = ca || cak;
-              bwd_contrib(cbk, e.y, qb.x, qb.y, qb.z, dxb, vk + qy.y, G0[k], G1[k], G2[k], T[k],
-                            GS[k], vb);
-              bwd_contrib(cak, e.x, qa.x, qa.y, qa.z, dxa, vk + qy.x, G0[k], G1[k], G2[k], T[k],
-                            GS[k], va);
+              bwd_contrib(cbk, e.y, qb.x, qb.y, qb.z, k, G0[k], G1[k], G2[k], T[k], GS[k], sb);
+              bwd_contrib(cak, e.x, qa.x, qa.y, qa.z, k, G0[k], G1[k], G2[k], T[k], GS[k], sa);
             }
+            moments_of_local_sums(sa, fu + qa.w, fv + qy.x, va);
+            moments_of_local_sums(sb, fu + qb.w, fv + qy.y, vb);
           }
           const bool any_a = __any_sync(0xffffffffu, ca), any_b = __any_sync(0xffffffffu, cb);
           if (any_a || any_b) {
