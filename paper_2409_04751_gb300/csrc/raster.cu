@@ -534,6 +534,36 @@ __device__ __forceinline__ void bwd_contrib(bool c, float e, float r, float g, f
   }
 }
 
+// bwd_contrib for two pixels of a thread (rows k and k + 1) and one entry at once. Their
+// transmittance chains are independent, so every FP32 add, multiply and fused multiply-add of
+// the pair is one paired instruction (add / mul / fma .rn.f32x2, each half rounded exactly as
+// the scalar operation); the selects, compares and MUFU operations stay per pixel. The local
+// sums a are kept as two partial sums (rows k and k + 1), folded after the pixel loop.
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+__device__ __forceinline__ void bwd_contrib2(bool c0, bool c1, float2 e, float r, float g,
+                                             float b, int k, float2 G0, float2 G1, float2 G2,
+                                             float2 &T, float2 &GS, float2 (&a)[6]) {
+  const float2 araw = make_float2(c0 ? ex2_approx(e.x) : 0.f, c1 ? ex2_approx(e.y) : 0.f);
+  const float2 alpha = make_float2(fminf(ALPHA_MAX, araw.x), fminf(ALPHA_MAX, araw.y));
+  const float2 oma = fadd2(dup2(1.f), make_float2(-alpha.x, -alpha.y));
+  const float2 om = make_float2(c0 ? rcp_approx(oma.x) : 1.f, c1 ? rcp_approx(oma.y) : 1.f);
+  T = fmul2(T, om);  // transmittance before this Gaussian
+  const float2 wgt = fmul2(alpha, T);
+  const float2 gc = ffma2(G2, dup2(b), ffma2(G1, dup2(g), fmul2(G0, dup2(r))));
+  const float2 dLda = ffma2(T, gc, fmul2(make_float2(-om.x, -om.y), GS));
+  GS = ffma2(gc, wgt, GS);
+  a[3] = ffma2(G0, wgt, a[3]);
+  a[4] = ffma2(G1, wgt, a[4]);
+  a[5] = ffma2(G2, wgt, a[5]);
+  const float2 d = fmul2(dLda, make_float2(araw.x < ALPHA_MAX ? araw.x : 0.f,
+                                            araw.y < ALPHA_MAX ? araw.y : 0.f));  // dL/dp
+  a[0] = fadd2(a[0], d);
+  a[1] = ffma2(d, make_float2((float)k, (float)(k + 1)), a[1]);
+  a[2] = ffma2(d, make_float2((float)(k * k), (float)((k + 1) * (k + 1))), a[2]);
+}
+
 // The nine per-record sums of one entry from a thread's local sums: with w = v0 + cy (the first
 // row's offset from the mean) and dx = u + cx,
 //   sum dL/dp dx = dx S,  sum dL/dp dy = w S + S_k,  sum dL/dp dx^2 = dx^2 S,
@@ -552,8 +582,10 @@ __device__ __forceinline__ void moments_of_local_sums(const float (&a)[6], float
   v[8] = a[5];
 }
 
+// 8 pixels per thread (one warp per tile): at most 128 registers, so that 16 one-warp CTAs fit
+// an SM (the paired pixel state would otherwise take 160 and leave 12)
 template <int PPT, bool COUNT>
-__global__ void __launch_bounds__(TILE_PIX / PPT)
+__global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 8 ? 16 : 1)
     raster_bwd_kernel(const fgs_record *__restrict__ rec, const uint32_t *__restrict__ vals,
                       const uint32_t *__restrict__ ranges, Views vs, float bg0, float bg1,
                       float bg2, const float *__restrict__ final_T,
@@ -671,22 +703,58 @@ __global__ void __launch_bounds__(TILE_PIX / PPT)
             const PairTerms pt = pair_terms(cf[p][0], cf[p][1], cf[p][2], u2, uu2);
             const float4 qa = cf[p][3], qb = cf[p][4];
             float sa[6], sb[6];
+            if constexpr (PPT == 1) {
 #pragma unroll
-            for (int q = 0; q < 6; ++q) sa[q] = sb[q] = 0.f;
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-              const bool in_a = pos_a < last[k], in_b = pos_b < last[k];
-              const float vk = fv + (float)k;
-              const float2 e = pair_exponent(pt, vk);
+              for (int q = 0; q < 6; ++q) sa[q] = sb[q] = 0.f;
+              const bool in_a = pos_a < last[0], in_b = pos_b < last[0];
+              const float2 e = pair_exponent(pt, fv);
               const bool cbk = in_b && e.y >= LOG2_ALPHA_MIN, cak = in_a && e.x >= LOG2_ALPHA_MIN;
               if (COUNT) {
                 n_eval += (in_a ? 1u : 0u) + (in_b ? 1u : 0u);
                 n_contrib += (cak ? 1u : 0u) + (cbk ? 1u : 0u);
               }
-              cb = cb || cbk;
-              ca = ca || cak;
-              bwd_contrib(cbk, e.y, qb.x, qb.y, qb.z, k, G0[k], G1[k], G2[k], T[k], GS[k], sb);
-              bwd_contrib(cak, e.x, qa.x, qa.y, qa.z, k, G0[k], G1[k], G2[k], T[k], GS[k], sa);
+              cb = cbk;
+              ca = cak;
+              bwd_contrib(cbk, e.y, qb.x, qb.y, qb.z, 0, G0[0], G1[0], G2[0], T[0], GS[0], sb);
+              bwd_contrib(cak, e.x, qa.x, qa.y, qa.z, 0, G0[0], G1[0], G2[0], T[0], GS[0], sa);
+            } else {
+              // pixels in pairs (rows k, k + 1): the exponents of one entry for both rows, then
+              // the paired contributions, entry b (behind) before entry a
+              float2 pa[6], pb[6];
+#pragma unroll
+              for (int q = 0; q < 6; ++q) pa[q] = pb[q] = dup2(0.f);
+              const float2 base_a = dup2(pt.base.x), base_b = dup2(pt.base.y);
+              const float2 slope_a = dup2(pt.slope.x), slope_b = dup2(pt.slope.y);
+              const float2 C_a = dup2(pt.C.x), C_b = dup2(pt.C.y);
+#pragma unroll
+              for (int k = 0; k < PPT; k += 2) {
+                const float2 vv = make_float2(fv + (float)k, fv + (float)(k + 1));
+                const float2 vsq = fmul2(vv, vv);
+                const float2 ea = ffma2(vsq, C_a, ffma2(vv, slope_a, base_a));
+                const float2 eb = ffma2(vsq, C_b, ffma2(vv, slope_b, base_b));
+                const bool ia0 = pos_a < last[k], ia1 = pos_a < last[k + 1];
+                const bool ib0 = pos_b < last[k], ib1 = pos_b < last[k + 1];
+                const bool ca0 = ia0 && ea.x >= LOG2_ALPHA_MIN, ca1 = ia1 && ea.y >= LOG2_ALPHA_MIN;
+                const bool cb0 = ib0 && eb.x >= LOG2_ALPHA_MIN, cb1 = ib1 && eb.y >= LOG2_ALPHA_MIN;
+                if (COUNT) {
+                  n_eval += (ia0 ? 1u : 0u) + (ia1 ? 1u : 0u) + (ib0 ? 1u : 0u) + (ib1 ? 1u : 0u);
+                  n_contrib += (ca0 ? 1u : 0u) + (ca1 ? 1u : 0u) + (cb0 ? 1u : 0u) + (cb1 ? 1u : 0u);
+                }
+                cb = cb || cb0 || cb1;
+                ca = ca || ca0 || ca1;
+                float2 Tp = make_float2(T[k], T[k + 1]), GSp = make_float2(GS[k], GS[k + 1]);
+                const float2 G0p = make_float2(G0[k], G0[k + 1]), G1p = make_float2(G1[k], G1[k + 1]);
+                const float2 G2p = make_float2(G2[k], G2[k + 1]);
+                bwd_contrib2(cb0, cb1, eb, qb.x, qb.y, qb.z, k, G0p, G1p, G2p, Tp, GSp, pb);
+                bwd_contrib2(ca0, ca1, ea, qa.x, qa.y, qa.z, k, G0p, G1p, G2p, Tp, GSp, pa);
+                T[k] = Tp.x; T[k + 1] = Tp.y;
+                GS[k] = GSp.x; GS[k + 1] = GSp.y;
+              }
+#pragma unroll
+              for (int q = 0; q < 6; ++q) {
+                sa[q] = pa[q].x + pa[q].y;
+                sb[q] = pb[q].x + pb[q].y;
+              }
             }
             moments_of_local_sums(sa, fu + qa.w, fv + qy.x, va);
             moments_of_local_sums(sb, fu + qb.w, fv + qy.y, vb);
