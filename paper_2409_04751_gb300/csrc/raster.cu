@@ -537,13 +537,14 @@ __device__ __forceinline__ void bwd_contrib(bool c, float e, float r, float g, f
 // bwd_contrib for two pixels of a thread (rows k and k + 1) and one entry at once. Their
 // transmittance chains are independent, so every FP32 add, multiply and fused multiply-add of
 // the pair is one paired instruction (add / mul / fma .rn.f32x2, each half rounded exactly as
-// the scalar operation); the selects, compares and MUFU operations stay per pixel. The local
-// sums a are kept as two partial sums (rows k and k + 1), folded after the pixel loop.
+// the scalar operation); the selects, compares and MUFU operations stay per pixel. a[0] sums
+// dL/dp and a[3..5] the colour terms for the two rows separately (folded after the pixel loop);
+// a[1] and a[2] are filled by the caller (suffix sums over the pixel pairs, see below).
 __device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
 __device__ __forceinline__ void bwd_contrib2(bool c0, bool c1, float2 e, float r, float g,
-                                             float b, int k, float2 G0, float2 G1, float2 G2,
+                                             float b, float2 G0, float2 G1, float2 G2,
                                              float2 &T, float2 &GS, float2 (&a)[6]) {
   const float2 araw = make_float2(c0 ? ex2_approx(e.x) : 0.f, c1 ? ex2_approx(e.y) : 0.f);
   const float2 alpha = make_float2(fminf(ALPHA_MAX, araw.x), fminf(ALPHA_MAX, araw.y));
@@ -560,8 +561,29 @@ __device__ __forceinline__ void bwd_contrib2(bool c0, bool c1, float2 e, float r
   const float2 d = fmul2(dLda, make_float2(araw.x < ALPHA_MAX ? araw.x : 0.f,
                                             araw.y < ALPHA_MAX ? araw.y : 0.f));  // dL/dp
   a[0] = fadd2(a[0], d);
-  a[1] = ffma2(d, make_float2((float)k, (float)(k + 1)), a[1]);
-  a[2] = ffma2(d, make_float2((float)(k * k), (float)((k + 1) * (k + 1))), a[2]);
+}
+
+// Row-weighted sums of a thread's pixels from suffix sums. The pixel pairs j = J-1 .. 0
+// (rows 2j, 2j + 1) are visited in descending order; after pair j is added to P = a[0],
+// Q = a[1] += P (j >= 1) and R = a[2] += Q (j >= 2), so that per half
+// Q = sum_j j d_j and R = sum_j j (j - 1) / 2 d_j. With rows k = 2j (x) and 2j + 1 (y):
+//   sum d = P.x + P.y,  sum k d = 2 (Q.x + Q.y) + P.y,
+//   sum k^2 d = 8 (R.x + R.y) + 4 (Q.x + Q.y) + 4 Q.y + P.y
+// (k^2 = 4 j^2 (+ 4 j + 1 for the odd row) and j^2 = 2 j (j - 1) / 2 + j). Only additions, no
+// per-row weights.
+__device__ __forceinline__ void suffix_step(int k, float2 (&a)[6]) {
+  if (k >= 2) a[1] = fadd2(a[1], a[0]);
+  if (k >= 4) a[2] = fadd2(a[2], a[1]);
+}
+
+__device__ __forceinline__ void fold_pairs(const float2 (&a)[6], float (&s)[6]) {
+  const float qs = a[1].x + a[1].y, rs = a[2].x + a[2].y;
+  s[0] = a[0].x + a[0].y;
+  s[1] = fmaf(2.f, qs, a[0].y);
+  s[2] = fmaf(8.f, rs, fmaf(4.f, qs + a[1].y, a[0].y));
+  s[3] = a[3].x + a[3].y;
+  s[4] = a[4].x + a[4].y;
+  s[5] = a[5].x + a[5].y;
 }
 
 // The nine per-record sums of one entry from a thread's local sums: with w = v0 + cy (the first
@@ -727,7 +749,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 8 ? 16 : 1)
               const float2 slope_a = dup2(pt.slope.x), slope_b = dup2(pt.slope.y);
               const float2 C_a = dup2(pt.C.x), C_b = dup2(pt.C.y);
 #pragma unroll
-              for (int k = 0; k < PPT; k += 2) {
+              for (int k = PPT - 2; k >= 0; k -= 2) {  // descending pairs: suffix sums
                 const float2 vv = make_float2(fv + (float)k, fv + (float)(k + 1));
                 const float2 vsq = fmul2(vv, vv);
                 const float2 ea = ffma2(vsq, C_a, ffma2(vv, slope_a, base_a));
@@ -745,16 +767,15 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 8 ? 16 : 1)
                 float2 Tp = make_float2(T[k], T[k + 1]), GSp = make_float2(GS[k], GS[k + 1]);
                 const float2 G0p = make_float2(G0[k], G0[k + 1]), G1p = make_float2(G1[k], G1[k + 1]);
                 const float2 G2p = make_float2(G2[k], G2[k + 1]);
-                bwd_contrib2(cb0, cb1, eb, qb.x, qb.y, qb.z, k, G0p, G1p, G2p, Tp, GSp, pb);
-                bwd_contrib2(ca0, ca1, ea, qa.x, qa.y, qa.z, k, G0p, G1p, G2p, Tp, GSp, pa);
+                bwd_contrib2(cb0, cb1, eb, qb.x, qb.y, qb.z, G0p, G1p, G2p, Tp, GSp, pb);
+                bwd_contrib2(ca0, ca1, ea, qa.x, qa.y, qa.z, G0p, G1p, G2p, Tp, GSp, pa);
+                suffix_step(k, pb);
+                suffix_step(k, pa);
                 T[k] = Tp.x; T[k + 1] = Tp.y;
                 GS[k] = GSp.x; GS[k + 1] = GSp.y;
               }
-#pragma unroll
-              for (int q = 0; q < 6; ++q) {
-                sa[q] = pa[q].x + pa[q].y;
-                sb[q] = pb[q].x + pb[q].y;
-              }
+              fold_pairs(pa, sa);
+              fold_pairs(pb, sb);
             }
             moments_of_local_sums(sa, fu + qa.w, fv + qy.x, va);
             moments_of_local_sums(sb, fu + qb.w, fv + qy.y, vb);
