@@ -919,9 +919,12 @@ def run_training(args, dev):
 
 
 def run_serving(args, dev):
-    """Continuous-batching server vs plain one-request-at-a-time serving: 4 resident scenes
+    """Continuous-batching server vs the same server without batching (one view per batch: the
+    gain of concurrent slots alone) vs plain one-request-at-a-time serving: 4 resident scenes
     (200k, 500k, 1M, 2M Gaussians, SH 3), Poisson arrivals, random pose, square resolution
-    U{512..2048 step 256}, FOV U(150, 200) deg, forward rendering."""
+    U{512..2048 step 256}, FOV U(150, 200) deg, forward rendering. Per rate: views/s, p50 and
+    p99 latency (ms), mean views per batch, overflow retries; for the batching server also the
+    histogram of views per batch and the number of batches holding several scenes."""
     import copy
     import torch
     from paper_2409_04751_gb300 import scenes
@@ -932,21 +935,38 @@ def run_serving(args, dev):
            for k, n in enumerate((200_000, 500_000, 1_000_000, 2_000_000))]
     out = {"workload": "fisheye-GS serving, 4 resident scenes (0.2M, 0.5M, 1M, 2M Gaussians, SH3), "
                        "Poisson arrivals, random pose, square 512..2048 px, FOV U(150,200) deg, fwd",
+           "server": dict(slots=args.serve_slots, max_batch_views=args.serve_batch,
+                          window_ms=args.serve_window_ms),
+           "columns": ["views_per_s", "p50_ms", "p99_ms", "views_per_batch", "retries"],
            "rates": {}}
-    calib = [[scenes.pose_camera(1024, 1024, 175.0, seed=7 + k)] for k in range(len(scs))]
+    # intersections per weighted pixel of each scene: the worst of a few poses and FOVs
+    calib = [[scenes.pose_camera(1024, 1024, fov, seed=7 + 10 * k + j)
+              for j, fov in enumerate((150.0, 175.0, 200.0, 200.0))] for k in range(len(scs))]
+
+    def row(sm):
+        return [round(sm["views_per_s"], 1), round(sm["p50_ms"], 3), round(sm["p99_ms"], 3),
+                round(sm["views_per_batch_mean"], 2), sm["retries"]]
+
     for rate in args.serve_rates:
         reqs = poisson_requests(float(rate), args.serve_seconds, len(scs), seed=int(rate))
-        srv = Server(scs, n_slots=args.serve_slots, max_batch_views=args.serve_batch,
-                     device=dev)
-        srv.calibrate(calib)
-        # warm both paths on a few requests (untimed)
-        Server(scs, n_slots=2, device=dev).run(copy.deepcopy(reqs[:8]))
-        serve_plain(scs, copy.deepcopy(reqs[:4]), device=dev)
+        res = {"requests": len(reqs)}
+        for name, views in (("batched", args.serve_batch), ("slots_only", 1)):
+            srv = Server(scs, n_slots=args.serve_slots, max_batch_views=views,
+                         window_ms=args.serve_window_ms if views > 1 else 0.0, device=dev)
+            srv.calibrate(calib)
+            srv.warm()  # every slot's buffers sized before the requests arrive (untimed)
+            Server(scs, n_slots=2, device=dev).run(copy.deepcopy(reqs[:8]))  # launch paths
+            torch.cuda.synchronize()
+            sm = srv.run(copy.deepcopy(reqs)).summary()
+            res[name] = row(sm)
+            if views > 1:
+                res["views_per_batch_hist"] = sm["views_per_batch_hist"]
+                res["multi_scene_batches"] = sm["multi_scene_batches"]
+                res["batches"] = sm["batches"]
         torch.cuda.synchronize()
-        a = srv.run(copy.deepcopy(reqs)).summary()
-        torch.cuda.synchronize()
-        b = serve_plain(scs, copy.deepcopy(reqs), device=dev).summary()
-        out["rates"][str(rate)] = {"requests": len(reqs), "batched": a, "plain": b}
+        res["plain"] = row(serve_plain(scs, copy.deepcopy(reqs), device=dev,
+                                       warm_size=2048).summary())
+        out["rates"][str(rate)] = res
     return out
 
 
@@ -971,10 +991,11 @@ def main():
     ap.add_argument("--no-training", action="store_true", help="skip the training-step timing")
     ap.add_argument("--train-views", type=int, default=8)
     ap.add_argument("--train-steps", type=int, default=20)
-    ap.add_argument("--serve-rates", type=int, nargs="*", default=[200, 500, 1000, 2000])
+    ap.add_argument("--serve-rates", type=int, nargs="*", default=[200, 500, 1000, 1500, 2000])
     ap.add_argument("--serve-seconds", type=float, default=1.0)
-    ap.add_argument("--serve-slots", type=int, default=3)
+    ap.add_argument("--serve-slots", type=int, default=2)
     ap.add_argument("--serve-batch", type=int, default=16)
+    ap.add_argument("--serve-window-ms", type=float, default=0.5)
     ap.add_argument("--batch-views", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--raster-shape", default="",

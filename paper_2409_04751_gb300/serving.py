@@ -1,18 +1,23 @@
 """Continuous-batching render server over device-resident scenes (forward rendering).
 
 Requests (scene, camera) arrive over time. The server keeps a few slots, each a CUDA stream with
-its own buffers; a free slot takes the oldest pending request plus every other pending request
-of the same scene that fits (at most `max_batch_views` views and the HBM budget left), and
-renders them in one call per stage. Slots run concurrently, so work of requests that arrive
-while others are on the GPU overlaps on the device. Completion is detected with CUDA events;
-latency = completion time - arrival time on the host clock.
+its own buffers. A free slot takes the pending requests in arrival order - of any scene and
+any size - while the batch stays within `max_batch_views` views and the HBM budget left, and
+renders them with one call per stage for each scene of the batch (all views of a scene in one
+multi-view call), on its stream. Slots run concurrently, so the work of requests that arrive
+while others are on the GPU overlaps on the device. When the device is idle a free slot starts
+at once; while other work is in flight it waits up to `window_ms` (or until a full batch is
+pending) so that requests arriving meanwhile join the batch: the device is busy anyway, and one
+call over several views costs less than one call per view. Completion is detected with CUDA
+events; latency = completion time - arrival time on the host clock.
 
 A request's image does not depend on which other views share its batch: every kernel treats
 views independently (tested).
 
-The intersection count of a batch is not known before it runs. Each slot sizes its key buffers
-from the intersections per pixel seen so far for that scene (times a margin); a batch whose
-count overflows is detected on completion (status word) and re-run with room to spare.
+The intersection count of a batch is not known before it runs. Each slot sizes the key buffers
+of a scene's views from the intersections per weighted pixel of that scene (calibrated on the
+worst of several poses, times a margin, decaying slowly); a group that still overflows is
+detected on completion (status word) and re-run with room to spare.
 """
 import collections
 import time
@@ -38,20 +43,36 @@ class Request:
     def pixels(self):
         return int(self.cam["width"]) * int(self.cam["height"])
 
+    @property
+    def tiles(self):
+        return ((int(self.cam["width"]) + 15) // 16) * ((int(self.cam["height"]) + 15) // 16)
+
+
+@dataclass
+class _Group:
+    """The views of one scene inside a batch: one multi-view call per stage, and an event
+    recorded after it, so that the group completes as soon as its own calls have run."""
+    scene: int
+    reqs: list
+    cap: int
+    bytes: int
+    frame: object = None
+    event: object = None
+    done: bool = False
+
 
 @dataclass
 class _Batch:
-    reqs: list
-    event: object
-    frame: object
+    groups: list
     bytes: int
     t_launch: float
+    views_done: int = 0
 
 
 @dataclass
 class _Slot:
     stream: object
-    renderer: FisheyeRenderer
+    renderers: dict = field(default_factory=dict)  # scene -> FisheyeRenderer (its buffers)
     batch: object = None
 
 
@@ -62,26 +83,35 @@ class ServeStats:
     batches: int = 0
     retries: int = 0
     wall_s: float = 0.0
+    batch_views: list = field(default_factory=list)   # views per completed batch
+    batch_scenes: list = field(default_factory=list)  # scenes per completed batch
 
     def summary(self):
         import numpy as np
         lat = np.asarray(self.latencies_ms) if self.latencies_ms else np.zeros(1)
+        hist = collections.Counter(self.batch_views)
         return dict(views=self.views, batches=self.batches, retries=self.retries,
                     views_per_s=self.views / max(self.wall_s, 1e-9),
                     p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
-                    mean_ms=float(lat.mean()), wall_s=self.wall_s)
+                    mean_ms=float(lat.mean()), wall_s=self.wall_s,
+                    views_per_batch_mean=self.views / max(self.batches, 1),
+                    views_per_batch_hist={int(k): int(v) for k, v in sorted(hist.items())},
+                    multi_scene_batches=int(sum(1 for n in self.batch_scenes if n > 1)))
 
 
 class Server:
-    def __init__(self, scenes_gs, n_slots=3, max_batch_views=16, hbm_budget_bytes=48 << 30,
-                 margin=1.6, keep_images=False, device="cuda"):
+    def __init__(self, scenes_gs, n_slots=2, max_batch_views=16, hbm_budget_bytes=48 << 30,
+                 margin=2.0, window_ms=0.5, max_group_records=8 << 20, keep_images=False,
+                 device="cuda"):
         self.scenes = scenes_gs
         self.device = torch.device(device)
-        self.slots = [_Slot(torch.cuda.Stream(self.device), FisheyeRenderer(self.device))
-                      for _ in range(n_slots)]
+        self.slots = [_Slot(torch.cuda.Stream(self.device)) for _ in range(n_slots)]
         self.max_batch_views = max_batch_views
         self.budget = int(hbm_budget_bytes)
         self.margin = margin
+        self.window_s = window_ms * 1e-3
+        # views of one scene per group: at most this many records (views x Gaussians)
+        self.max_group_records = int(max_group_records)
         self.keep_images = keep_images
         self.pending = collections.deque()
         self.in_flight_bytes = 0
@@ -91,11 +121,23 @@ class Server:
 
     # ---------------------------------------------------------------------------------------
     def _bytes(self, scene, reqs, capacity):
+        """Device bytes of one scene group: records and tiles_touched, keys and values, the
+        workspace, images, final T and processed counts."""
         n = int(self.scenes[scene]["means"].shape[0])
         R = n * len(reqs)
         P = sum(r.pixels for r in reqs)
         ws = fgs.fgs_workspace_size(n, fgs.cameras([r.cam for r in reqs]), capacity)
         return R * 52 + capacity * 12 + ws + P * 20
+
+    def _bytes_estimate(self, scene, reqs, capacity):
+        """_bytes without the library call (the workspace from its dominant regions: 60 bytes
+        per record, 8 per key slot, 16 per tile), for the budget checks while a batch is
+        formed."""
+        n = int(self.scenes[scene]["means"].shape[0])
+        R = n * len(reqs)
+        P = sum(r.pixels for r in reqs)
+        T = sum(r.tiles for r in reqs)
+        return R * (52 + 60) + capacity * (12 + 8) + T * 16 + P * 20 + 4096
 
     @staticmethod
     def _weight(reqs):
@@ -107,78 +149,144 @@ class Server:
         return min(int(self.ipp[scene] * self._weight(reqs) * self.margin) + 65536, (1 << 31) - 1)
 
     def calibrate(self, cams_by_scene):
-        """Render a view per scene to learn its intersections per weighted pixel."""
+        """Render the given views of each scene to learn its intersections per weighted pixel
+        (the largest over the views)."""
         for k, cams in enumerate(cams_by_scene):
             r = FisheyeRenderer(self.device, capacity=1 << 22)
-            fr = r.forward(self.scenes[k], cams, check=True)
-            w = self._weight([Request(0, k, c, 0.0) for c in cams])
-            self.ipp[k] = int(fr.n_intersections.item()) / max(w, 1e-9)
+            ipp = 0.0
+            for c in cams:
+                fr = r.forward(self.scenes[k], [c], check=True)
+                w = self._weight([Request(0, k, c, 0.0)])
+                ipp = max(ipp, int(fr.n_intersections.item()) / max(w, 1e-9))
+            self.ipp[k] = ipp
 
     def _form_batch(self):
-        first = self.pending[0]
-        scene = first.scene
-        picked = []
-        for r in list(self.pending):
-            if r.scene != scene:
-                continue
-            trial = picked + [r]
-            cap = self._capacity(scene, trial)
-            if picked and (len(trial) > self.max_batch_views or
-                           self.in_flight_bytes + self._bytes(scene, trial, cap) > self.budget):
+        """The pending requests in arrival order, of any scene, while the batch holds at most
+        max_batch_views views and (beside the work in flight) fits the HBM budget. Returns the
+        batch's scene groups (in order of first appearance) and their bytes, or None if the
+        oldest request does not fit beside the work in flight (an idle device always admits
+        it)."""
+        by = collections.OrderedDict()  # scene -> requests
+        est = {}                        # scene -> estimated bytes of its group
+        total, picked = 0, 0
+        for r in self.pending:
+            if picked + 1 > self.max_batch_views:
                 break
-            picked = trial
-        cap = self._capacity(scene, picked)
-        need = self._bytes(scene, picked, cap)
+            rs = by.get(r.scene, []) + [r]
+            if picked and len(rs) * int(self.scenes[r.scene]["means"].shape[0]) > self.max_group_records:
+                break
+            b = self._bytes_estimate(r.scene, rs, self._capacity(r.scene, rs))
+            t = total - est.get(r.scene, 0) + b
+            if picked and self.in_flight_bytes + t > self.budget:
+                break
+            by[r.scene], est[r.scene], total, picked = rs, b, t, picked + 1
+        groups = []
+        for scene, rs in by.items():
+            cap = self._capacity(scene, rs)
+            groups.append(_Group(scene, rs, cap, self._bytes(scene, rs, cap)))
+        need = sum(g.bytes for g in groups)
         if self.in_flight_bytes > 0 and self.in_flight_bytes + need > self.budget:
             return None  # wait for memory to free up
-        for r in picked:
-            self.pending.remove(r)
-        return scene, picked, cap, need
+        taken = {id(r) for g in groups for r in g.reqs}
+        self.pending = collections.deque(r for r in self.pending if id(r) not in taken)
+        return groups, need
 
-    def _launch(self, slot, scene, reqs, cap, need):
-        slot.renderer.capacity = cap
+    def _ready(self, now):
+        """Whether a free slot starts a batch now: at once on an idle device; while other
+        batches are in flight, when a full batch is pending or the oldest request has waited
+        the window."""
+        if not self.pending:
+            return False
+        if not any(s.batch is not None for s in self.slots):
+            return True
+        if len(self.pending) >= self.max_batch_views:
+            return True
+        return now - self.pending[0].t_arrival >= self.window_s
+
+    def warm(self, max_size=2048, fov=150.0):
+        """Size every slot's buffers for the largest group each scene can form (its most views
+        at max_size^2 and the narrowest FOV, whose longer focal length gives the largest key
+        capacity), before serving: the serving loop then reuses them instead of allocating
+        device memory between requests."""
+        for k, gs in enumerate(self.scenes):
+            n = int(gs["means"].shape[0])
+            views = max(1, min(self.max_batch_views, self.max_group_records // max(n, 1)))
+            reqs = [Request(0, k, _wide_camera(max_size, fov, j), 0.0) for j in range(views)]
+            cap = self._capacity(k, reqs)
+            for slot in self.slots:
+                r = self._renderer(slot, k)
+                r.capacity = cap
+                with torch.cuda.stream(slot.stream):
+                    r.forward(gs, [q.cam for q in reqs], check=False)
+        torch.cuda.synchronize(self.device)
+
+    def _renderer(self, slot, scene):
+        r = slot.renderers.get(scene)
+        if r is None:
+            r = slot.renderers[scene] = FisheyeRenderer(self.device)
+        return r
+
+    def _launch(self, slot, groups, need):
         with torch.cuda.stream(slot.stream):
-            fr = slot.renderer.forward(self.scenes[scene], [r.cam for r in reqs], check=False)
-            ev = torch.cuda.Event()
-            ev.record(slot.stream)
-        slot.batch = _Batch(reqs, ev, fr, need, time.perf_counter())
+            for g in groups:
+                r = self._renderer(slot, g.scene)
+                r.capacity = g.cap
+                g.frame = r.forward(self.scenes[g.scene], [q.cam for q in g.reqs], check=False)
+                g.event = torch.cuda.Event()
+                g.event.record(slot.stream)
+        slot.batch = _Batch(groups, need, time.perf_counter())
         self.in_flight_bytes += need
 
-    def _complete(self, slot, now):
-        b = slot.batch
-        slot.batch = None
-        self.in_flight_bytes -= b.bytes
-        st = fgs.fgs_read_status(slot.renderer._bufs["ws"], slot.stream)
-        n_int = int(b.frame.n_intersections.item())
-        scene = b.reqs[0].scene
-        w = max(self._weight(b.reqs), 1e-9)
-        self.ipp[scene] = max(0.95 * self.ipp[scene], n_int / w)
+    def _complete_group(self, slot, g, now):
+        """Results of one scene group whose calls have run: latencies, or a re-queue of its
+        requests if its key buffers overflowed."""
+        g.done = True
+        r = self._renderer(slot, g.scene)
+        st = fgs.fgs_read_status(r._bufs["ws"], slot.stream)
+        n_int = int(g.frame.n_intersections.item())
+        w = max(self._weight(g.reqs), 1e-9)
+        self.ipp[g.scene] = max(0.99 * self.ipp[g.scene], n_int / w)
         if st == fgs.FGS_ERR_CAPACITY:
-            self.ipp[scene] = max(self.ipp[scene], 1.2 * n_int / w)
-            for r in reversed(b.reqs):
-                r.retries += 1
-                self.pending.appendleft(r)
+            self.ipp[g.scene] = max(self.ipp[g.scene], 1.2 * n_int / w)
+            for q in reversed(g.reqs):
+                q.retries += 1
+                self.pending.appendleft(q)
             self.stats.retries += 1
-            return
+            return 0
         if st != fgs.FGS_OK:
             raise fgs.FgsError(st, "serving batch")
-        imgs = b.frame.view_images([r.cam for r in b.reqs]) if self.keep_images else None
-        for k, r in enumerate(b.reqs):
-            r.t_done = now
+        imgs = g.frame.view_images([q.cam for q in g.reqs]) if self.keep_images else None
+        for k, q in enumerate(g.reqs):
+            q.t_done = now
             if imgs is not None:
-                r.image = imgs[k].clone()
-            self.stats.latencies_ms.append(1e3 * (r.t_done - r.t_arrival))
-        self.stats.views += len(b.reqs)
-        self.stats.batches += 1
+                q.image = imgs[k].clone()
+            self.stats.latencies_ms.append(1e3 * (q.t_done - q.t_arrival))
+        return len(g.reqs)
+
+    def _retire(self, slot):
+        """Complete the finished groups of the slot's batch; free the slot when all are."""
+        b = slot.batch
+        for g in b.groups:
+            if not g.done and g.event.query():
+                b.views_done += self._complete_group(slot, g, time.perf_counter())
+        if all(g.done for g in b.groups):
+            slot.batch = None
+            self.in_flight_bytes -= b.bytes
+            done = b.views_done
+            if done:
+                self.stats.views += done
+                self.stats.batches += 1
+                self.stats.batch_views.append(done)
+                self.stats.batch_scenes.append(len(b.groups))
 
     def poll(self):
-        """Retire finished batches and start new ones on free slots. Returns True if any work is
-        pending or in flight."""
+        """Retire finished work and start new batches on free slots. Returns True if any work
+        is pending or in flight."""
         for slot in self.slots:
-            if slot.batch is not None and slot.batch.event.query():
-                self._complete(slot, time.perf_counter())
+            if slot.batch is not None:
+                self._retire(slot)
         for slot in self.slots:
-            if slot.batch is None and self.pending:
+            if slot.batch is None and self._ready(time.perf_counter()):
                 formed = self._form_batch()
                 if formed is None:
                     break
@@ -204,9 +312,18 @@ class Server:
         return self.stats
 
 
-def serve_plain(scenes_gs, requests, device="cuda", keep_images=False):
-    """One request at a time, one single-view call sequence each, in arrival order."""
+def _wide_camera(size, fov, seed):
+    from . import scenes as sc
+    return sc.pose_camera(size, size, fov, seed=seed)
+
+
+def serve_plain(scenes_gs, requests, device="cuda", keep_images=False, warm_size=0):
+    """One request at a time, one single-view call sequence each, in arrival order. warm_size
+    > 0 first renders one warm_size^2 view at 150 degrees of every scene (untimed), so that the
+    buffers are sized before the requests arrive."""
     r = FisheyeRenderer(torch.device(device), capacity=1 << 22)
+    for gs in (scenes_gs if warm_size else []):
+        r.forward(gs, [_wide_camera(warm_size, 150.0, 0)], check=True)
     stats = ServeStats()
     t0 = time.perf_counter()
     for q in requests:

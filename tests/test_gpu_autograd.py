@@ -48,3 +48,34 @@ def test_autograd_matches_oracle_chain(cuda_device):
         refi = oracle.render_image(oracle.project(used, c), c, bg=(0.1, 0.1, 0.1),
                                    impact_min=parity.IMPACT_MIN)
         parity.check_image(im.detach().cpu().numpy(), refi, "autograd")
+
+
+def test_renders_reuse_pooled_buffers_and_unchecked_renders_agree(cuda_device):
+    """A training loop's renders take their buffers from the pool and give them back in the
+    backward, so steps reuse the same device buffers; frames alive at the same time get
+    separate buffers; a render without the host-synchronising check gives the checked result."""
+    from paper_2409_04751_gb300 import autograd as ag, fgs
+    sc = scenes.shell_scene(4000, seed=97, sh_degree=1)
+    cam = [scenes.pose_camera(96, 80, 180.0, seed=971)]
+    dev = cuda_device
+    p = [torch.tensor(sc[k], device=dev, requires_grad=True)
+         for k in ("means", "scales", "quats", "opacities", "sh")]
+    ag._pool.pop(dev, None)
+    grads = []
+    for step in range(3):
+        for t in p:
+            t.grad = None
+        img = ag.render(*p, cam, 1, check=(step == 0))[0]
+        img.sum().backward()
+        grads.append([t.grad.clone() for t in p])
+    assert ag.last_status(dev) == fgs.FGS_OK
+    assert len(ag._pool[dev]) == 1  # one renderer, reused by every step
+    for g in grads[1:]:
+        for a, b in zip(g, grads[0]):
+            assert parity.rel_l2(a.cpu().numpy(), b.cpu().numpy()) < 1e-5
+    # two frames alive together hold two renderers
+    a = ag.render(*p, cam, 1)[0]
+    b = ag.render(*p, cam, 1)[0]
+    assert torch.equal(a, b)
+    (a.sum() + b.sum()).backward()
+    assert len(ag._pool[dev]) == 2

@@ -102,6 +102,11 @@ def _oracle(rect, depth, n, cams_py):
     (30000, [(32, 32)], 13, dict(max_ext=1, tie_frac=0.6)),
     # every pair at one depth: the order is the record order alone
     (9000, [(16, 16)], 14, dict(tie_frac=1.0)),
+    # many small tiles whose depths all tie: every one is too clustered for the one-warp bucket
+    # sort and goes to the large class's CTAs
+    (3000, [(256, 256)], 15, dict(max_ext=5, tie_frac=1.0)),
+    # a mix: half of the small tiles tie, half do not
+    (6000, [(640, 480)], 16, dict(max_ext=4, tie_frac=0.5)),
 ])
 @pytest.mark.parametrize("flags", SORTS)
 def test_binsort_bit_exact(cuda_device, n, sizes, seed, kw, flags):

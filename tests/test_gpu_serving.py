@@ -1,6 +1,6 @@
 """Continuous-batching server: every request's image equals the image of the same request
 rendered alone with a plain single-view call, bit for bit, while requests of several scenes
-and sizes arrive, overlap on the device and share batches."""
+and sizes arrive, overlap on the device and share batches (across scenes too)."""
 import numpy as np
 import pytest
 import torch
@@ -22,11 +22,13 @@ def test_served_results_equal_alone(cuda_device):
     stats = srv.run(reqs)
     assert stats.views == len(reqs)
     assert stats.batches < len(reqs)  # requests really were batched together
+    s = stats.summary()
+    assert s["multi_scene_batches"] >= 1  # and across scenes
+    assert sum(s["views_per_batch_hist"].values()) == stats.batches
     r = FisheyeRenderer("cuda", capacity=1 << 20)
     for q in reqs:
         fr = r.forward(scs[q.scene], [q.cam])
         assert torch.equal(fr.view_images([q.cam])[0], q.image), q.rid
-    s = stats.summary()
     assert s["p99_ms"] >= s["p50_ms"] > 0
 
 
