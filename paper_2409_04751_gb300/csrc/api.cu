@@ -228,8 +228,8 @@ fgs_status fgs_backward_raster_ex(const fgs_record *records, const uint32_t *val
     return FGS_ERR_INVALID_ARG;
   if (R > 0 && (!records || !aligned(records, 16))) return FGS_ERR_INVALID_ARG;
   if (!aligned(workspace, 256)) return FGS_ERR_INVALID_ARG;
-  // the header, the screen-space gradient region and the tile order precede every
-  // capacity-dependent region
+  // the header, the look-back arrays, the screen-space gradient region and the tile order
+  // precede every capacity-dependent region
   const WsLayout L = ws_layout(R, 1, vs.total_tiles);
   if (workspace_bytes < L.vis_rec) return FGS_ERR_INVALID_ARG;
   const float b0 = bg ? bg[0] : 0.f, b1 = bg ? bg[1] : 0.f, b2 = bg ? bg[2] : 0.f;
@@ -261,7 +261,7 @@ fgs_status fgs_backward_preprocess(const fgs_gaussians *g, const fgs_camera *cam
   if (g->n > 0 && (!records || !tiles_touched || !d_means || !d_scales || !d_quats ||
                    !d_opacities || !d_sh || !aligned(records, 16)))
     return FGS_ERR_INVALID_ARG;
-  const WsLayout L = ws_layout(R, 1, 1);
+  const WsLayout L = ws_layout(R, 1, vs.total_tiles);
   if (workspace_bytes < L.vis_rec) return FGS_ERR_INVALID_ARG;
   char *ws = reinterpret_cast<char *>(workspace);
   WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);

@@ -10,11 +10,13 @@
 //  1. scan_kernel: single-pass scan of tiles_touched with decoupled look-back (partitions of
 //     4096 records claimed in order through an atomic counter). For every record with pairs it
 //     writes its pair offset and its rank among such records (a compacted list), and for every
-//     1024-pair chunk the rank of the record holding the chunk's first pair.
-//  2. rect binning: rect_diff_kernel and grid_scan_kernel count the pairs of every tile from a
-//     2D difference grid of the records' rects (at most eight atomics per record). Exact
-//     (ellipse) binning: pair_kernel<false>, one CTA per 1024-pair chunk (the work per CTA is
-//     fixed however many tiles one Gaussian covers), counts them pair by pair.
+//     1024-pair chunk the rank of the record holding the chunk's first pair. For rect binning
+//     it also adds each visible record to a 2D difference grid of tile counts (at most eight
+//     atomics per record, rect_difference in scan.cuh).
+//  2. rect binning: grid_scan_kernel turns the difference grid into the pairs of every tile
+//     (row sums, then column sums). Exact (ellipse) binning: pair_kernel<false>, one CTA per
+//     1024-pair chunk (the work per CTA is fixed however many tiles one Gaussian covers), counts
+//     them pair by pair.
 //  3. tile_scan_kernel: exclusive scan of the tile counts (decoupled look-back) gives every
 //     tile's start; tiles are listed by segment size.
 //  4. pair_kernel<true>: the same walk over the pairs claims a slot in the pair's tile bucket and
@@ -175,54 +177,6 @@ __global__ void __launch_bounds__(EMIT_THREADS)
   }
 }
 
-// Rect binning's tile counts without a pass over the pairs. A record's pairs are the first
-// k = min(tiles_touched, w h) tiles of its w x h rect in row-major order (exactly what the pair
-// walk emits): fr = k / w full rows and a partial row of k - fr w tiles. Each such block adds
-// +1, -1, -1, +1 at the corners (x_lo, y_lo), (x_hi + 1, y_lo), (x_lo, y_hi + 1),
-// (x_hi + 1, y_hi + 1) of a 2D difference grid held in tile_ranges[2t] (corners past the
-// grid's edge are dropped: they only reach tiles beyond it); inclusive prefix sums along the
-// rows and then the columns of every view turn it into the per-tile pair counts. Eight
-// atomics per record at most, instead of one per pair. With more candidates than capacity the
-// counts stay zero and the capacity status is set (the outputs are then undefined, but every
-// later stage stays inside its buffers).
-__global__ void __launch_bounds__(256)
-    rect_diff_kernel(const fgs_record *__restrict__ rec, const uint32_t *__restrict__ tt,
-                     int64_t n_per_view, Views vs, const uint32_t *__restrict__ vis_rec,
-                     const unsigned long long *n_vis, const unsigned long long *n_cand,
-                     int64_t capacity, uint32_t *ranges, uint32_t *status) {
-  if (binning_timed_out(status)) return;
-  if ((int64_t)*n_cand > capacity) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) set_status(status, ST_CAPACITY);
-    return;
-  }
-  const int64_t nv = (int64_t)*n_vis;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nv;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t r = vis_rec[q];
-    const uint4 w2 = __ldg(reinterpret_cast<const uint4 *>(rec + r) + 2);
-    const uint32_t x0 = w2.z & 0xffffu, y0 = w2.z >> 16, x1 = w2.w & 0xffffu, y1 = w2.w >> 16;
-    const View &V = vs.v[(int)(r / (uint32_t)n_per_view)];
-    const uint32_t tiles_x = (uint32_t)V.tiles_x, tiles_y = (uint32_t)V.tiles_y;
-    if (!(x0 <= x1 && y0 <= y1 && x1 < tiles_x && y1 < tiles_y)) continue;  // as the pair walk
-    const uint32_t w = x1 - x0 + 1u, h = y1 - y0 + 1u;
-    const uint32_t k = (uint32_t)min((uint64_t)__ldg(tt + r), (uint64_t)w * h);
-    const uint32_t fr = k / w, rem = k - fr * w;
-    uint32_t *grid = ranges + 2 * V.tile_offset;
-    auto add = [&](uint32_t x, uint32_t y, uint32_t d) {
-      if (x < tiles_x && y < tiles_y) atomicAdd(grid + 2 * ((size_t)y * tiles_x + x), d);
-    };
-    if (fr > 0u) {
-      add(x0, y0, 1u); add(x1 + 1u, y0, 0xffffffffu);
-      add(x0, y0 + fr, 0xffffffffu); add(x1 + 1u, y0 + fr, 1u);
-    }
-    if (rem > 0u) {
-      const uint32_t y = y0 + fr;
-      add(x0, y, 1u); add(x0 + rem, y, 0xffffffffu);
-      add(x0, y + 1u, 0xffffffffu); add(x0 + rem, y + 1u, 1u);
-    }
-  }
-}
-
 // In-place inclusive prefix sums of the difference grid, one warp per line: ROWS = true sums
 // along every view's tile rows, false along its columns (run after the rows). Sums are
 // modulo 2^32, so the negative differences need no sign.
@@ -282,13 +236,17 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   const int64_t part = s_part;
   const int64_t base = part * TSCAN_PART;
+  // with more candidates than capacity the counts are not complete: read them as zero, and
+  // report the overflow (the caller grows the buffers from the candidate count)
+  const bool counts_ok = (int64_t)*n_cand <= capacity;
+  if (!counts_ok && part == 0 && tid == 0) set_status(status, ST_CAPACITY);
   constexpr int ITEMS = TSCAN_PART / 256;
   uint32_t c[ITEMS];
   uint32_t sum = 0;
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
     const int64_t t = base + tid * ITEMS + k;
-    c[k] = t < total_tiles ? ranges[2 * t] : 0u;
+    c[k] = t < total_tiles && counts_ok ? ranges[2 * t] : 0u;
     sum += c[k];
   }
   uint32_t agg;
@@ -855,23 +813,29 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
   const int64_t R = (int64_t)vs.n * n;
   const int64_t T = vs.total_tiles;
 
-  if ((e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return e;
+  // the header and both look-back arrays are adjacent: one memset
+  if ((e = cudaMemsetAsync(hdr, 0, L.g2d - L.header, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)T, st)) != cudaSuccess) return e;
   if (R == 0) return cudaMemsetAsync(n_int, 0, sizeof(int64_t), st);
-  if ((e = cudaMemsetAsync(scan_lb, 0, sizeof(uint64_t) * 2 * (size_t)L.scan_parts, st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(tile_lb, 0, sizeof(uint64_t) * (size_t)L.tile_parts, st)) != cudaSuccess) return e;
 
-  scan_kernel<<<(unsigned)L.scan_parts, EMIT_THREADS, 0, st>>>(
-      tiles_touched, R, capacity, n_int, &hdr->n_candidates, &hdr->n_visible, scan_lb,
-      scan_lb + L.scan_parts, &hdr->scan_parts, vis_rec, vis_off, chunk_first, &hdr->status,
-      opt.wait_limit);
+  const bool ellipse = (flags & FGS_BIN_ELLIPSE) != 0;
+  // rect binning: the record scan also builds the tile-count difference grid
+  if (ellipse)
+    scan_kernel<false><<<(unsigned)L.scan_parts, EMIT_THREADS, 0, st>>>(
+        tiles_touched, R, capacity, n_int, &hdr->n_candidates, &hdr->n_visible, scan_lb,
+        scan_lb + L.scan_parts, &hdr->scan_parts, vis_rec, vis_off, chunk_first, &hdr->status,
+        opt.wait_limit, records, n, vs, tile_ranges);
+  else
+    scan_kernel<true><<<(unsigned)L.scan_parts, EMIT_THREADS, 0, st>>>(
+        tiles_touched, R, capacity, n_int, &hdr->n_candidates, &hdr->n_visible, scan_lb,
+        scan_lb + L.scan_parts, &hdr->scan_parts, vis_rec, vis_off, chunk_first, &hdr->status,
+        opt.wait_limit, records, n, vs, tile_ranges);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // two waves of the 8 CTAs an SM holds: the pair walks wait on record loads and returning
   // atomics, so more chunks in flight hide more of that latency
   int64_t egrid = (int64_t)sm_count() * 16;
   if (egrid > L.chunks) egrid = L.chunks;
   if (egrid < 1) egrid = 1;
-  const bool ellipse = (flags & FGS_BIN_ELLIPSE) != 0;
   if (ellipse) {
     pair_kernel<false, true><<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
         records, n, vs, vis_rec, vis_off, chunk_first, &hdr->n_candidates, &hdr->n_visible,
@@ -882,13 +846,6 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
       rows += vs.v[v].tiles_y;
       cols += vs.v[v].tiles_x;
     }
-    int64_t dgrid = (int64_t)sm_count() * 4;
-    const int64_t need = (R + 255) / 256;
-    if (dgrid > need) dgrid = need;
-    if (dgrid < 1) dgrid = 1;
-    rect_diff_kernel<<<(unsigned)dgrid, 256, 0, st>>>(records, tiles_touched, n, vs, vis_rec,
-                                                       &hdr->n_visible, &hdr->n_candidates,
-                                                       capacity, tile_ranges, &hdr->status);
     grid_scan_kernel<true><<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(
         vs, rows, tile_ranges, &hdr->n_candidates, capacity, &hdr->status);
     grid_scan_kernel<false><<<(unsigned)((cols * 32 + 255) / 256), 256, 0, st>>>(

@@ -121,9 +121,10 @@ struct WsLayout {
 
 __host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Workspace layout. Regions that depend on the record count only come first, so the
-// rasterizer and the backward can locate them without knowing the key capacity or the tile
-// count; with_g2d = false leaves out the backward's accumulator (used by the sort-only variant);
+// Workspace layout. Regions that depend on the record and tile counts only come first, so the
+// backward can locate them without knowing the key capacity (the forward rasterizer uses the
+// header alone); with_g2d = false leaves out the backward's accumulator (used by the sort-only
+// variant);
 // with_onesweep adds the regions of the device-wide radix sort (onesweep.cu).
 constexpr WsLayout ws_layout_ex(int64_t n_records, int64_t capacity, int64_t total_tiles,
                                 bool with_g2d, bool with_onesweep = false) {
@@ -135,14 +136,15 @@ constexpr WsLayout ws_layout_ex(int64_t n_records, int64_t capacity, int64_t tot
   L.chunks = (capacity + EMIT_CHUNK - 1) / EMIT_CHUNK;
   L.total_tiles = T;
   size_t o = 0;
+  // header and both look-back arrays first: one memset clears them
   L.header = o; o += align256(256);
   L.scan_lb = o; o += align256(sizeof(uint64_t) * 2 * (size_t)(L.scan_parts > 0 ? L.scan_parts : 1));
+  L.tile_lb = o; o += align256(sizeof(uint64_t) * (size_t)L.tile_parts);
   L.g2d = o; if (with_g2d) o += align256(sizeof(float) * G2D_STRIDE * (size_t)R);
   // the backward's tile order: per-tile work bucket, tile ids by decreasing work, histogram
   L.tile_order = o; if (with_g2d) o += align256(sizeof(uint32_t) * (2 * (size_t)T + 2 * WORK_BUCKETS));
   L.vis_rec = o; o += align256(sizeof(uint32_t) * (size_t)R);
   L.vis_off = o; o += align256(sizeof(uint64_t) * (size_t)R);
-  L.tile_lb = o; o += align256(sizeof(uint64_t) * (size_t)L.tile_parts);
   L.seg_list = o; o += align256(sizeof(uint32_t) * 2 * (size_t)T);
   L.words = o; o += align256(sizeof(uint64_t) * (size_t)capacity);
   L.chunk_first = o; o += align256(sizeof(uint32_t) * ((size_t)L.chunks + 2));

@@ -33,3 +33,20 @@ def test_render_bytes_counts_every_buffer():
     tiles, pix = 4 * 2, 64 * 32
     ws = fgs.fgs_workspace_size(n, cams, m, 0)
     assert got == n * 52 + m * 12 + tiles * 8 + ws + pix * 20
+
+
+def test_compact_rounds_floats_only_and_keeps_structure():
+    line = dict(value=1239.228629294, n=7049570, ok=True, name="x",
+                nested=dict(a=[0.123456789, 2, None], b=(1.0 / 3.0,)))
+    out = bench.compact(line)
+    assert out["value"] == 1239.2 and out["n"] == 7049570 and out["ok"] is True
+    assert out["nested"]["a"] == [0.12346, 2, None] and out["nested"]["b"] == [0.33333]
+    assert list(out) == list(line)
+
+
+def test_fp32_units_from_device_properties():
+    class P:
+        multi_processor_count, major, minor = 152, 10, 3
+    assert bench.fp32_units(P()) == (152, 128)
+    P.major, P.minor, P.multi_processor_count = 8, 0, 108
+    assert bench.fp32_units(P()) == (108, 64)
