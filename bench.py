@@ -76,7 +76,7 @@ def render_bytes(fgs, n, cams_c, n_views, m, flags=0):
 
 
 # pixels per thread of the rasterizers when the tuner is off (the library's defaults)
-DEFAULT_SHAPE = (1, 8)
+DEFAULT_SHAPE = (4, 8)
 
 
 def fp32_units(props):
@@ -391,8 +391,14 @@ def run_gpu(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def stages(ev, with_bwd=True, opts=None):
-        opts = opts or r.opts
+    def stages(ev, with_bwd=True, opts=None, kev=None):
+        """One fwd(+bwd) step with events between the stages; kev = [(before, after) of the
+        forward rasterizer kernel, (before, after) of the backward rasterizer kernel] recorded
+        by the library around those two kernels alone."""
+        of = ob = opts or r.opts
+        if kev is not None:
+            of = fgs.options(fwd=r.shape[0], bwd=r.shape[1], events=kev[0])
+            ob = fgs.options(fwd=r.shape[0], bwd=r.shape[1], events=kev[1])
         ev[0].record(stream)
         fgs.fgs_preprocess(g, cam_c, fr.records, fr.tiles_touched)
         ev[1].record(stream)
@@ -400,11 +406,11 @@ def run_gpu(args):
                          fr.tile_ranges, fr.n_intersections, ws, wsb)
         ev[2].record(stream)
         fgs.fgs_rasterize(fr.records, fr.vals, fr.tile_ranges, cam_c, None, fr.images,
-                          fr.final_T, fr.n_processed, ws, wsb, opts=opts)
+                          fr.final_T, fr.n_processed, ws, wsb, opts=of)
         ev[3].record(stream)
         if with_bwd:
             fgs.fgs_backward_raster(fr.records, fr.vals, fr.tile_ranges, n, cam_c, None,
-                                    fr.final_T, fr.n_processed, dL, ws, wsb, opts=opts)
+                                    fr.final_T, fr.n_processed, dL, ws, wsb, opts=ob)
             ev[4].record(stream)
             fgs.fgs_backward_preprocess(g, cam_c, fr.records, fr.tiles_touched, grads["means"],
                                         grads["scales"], grads["quats"], grads["opacities"],
@@ -448,14 +454,17 @@ def run_gpu(args):
     barrier()
     sampler.start()
     time.sleep(0.3)
-    evs = []
+    evs, kevs = [], []
+    timing_event = lambda: torch.cuda.Event(enable_timing=True)
     barrier()
     t_wall = time.perf_counter()
     for _ in range(args.steps):
         flush.zero_()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
-        stages(ev)
+        ev = [timing_event() for _ in range(6)]
+        kev = [(timing_event(), timing_event()), (timing_event(), timing_event())]
+        stages(ev, kev=kev)
         evs.append(ev)
+        kevs.append(kev)
     barrier()
     t_wall = time.perf_counter() - t_wall
     stage_ms = np.zeros(5)
@@ -466,6 +475,9 @@ def run_gpu(args):
         step_ms.append(sum(d))
     stage_ms /= args.steps
     total_s = sum(step_ms) / 1e3
+    # the two rasterizer kernels alone (the library records these events right around them)
+    kernel_ms = dict(raster_fwd=float(np.mean([k[0][0].elapsed_time(k[0][1]) for k in kevs])),
+                     raster_bwd=float(np.mean([k[1][0].elapsed_time(k[1][1]) for k in kevs])))
 
     # forward only
     fevs = []
@@ -549,10 +561,14 @@ def run_gpu(args):
     kern = {}
     fwd_flops = counters[0] * FLOPS_FWD_EVAL + counters[1] * FLOPS_FWD_BLEND
     bwd_flops = counters[2] * FLOPS_BWD_EVAL + counters[3] * FLOPS_BWD_CONTRIB
-    kern["raster_fwd"] = dict(bound="alu", achieved=fwd_flops / (stage_ms[2] * 1e-3) / 1e12,
-                              peak=fp32_peak, unit="TFLOP/s")
-    kern["raster_bwd"] = dict(bound="alu", achieved=bwd_flops / (stage_ms[3] * 1e-3) / 1e12,
-                              peak=fp32_peak, unit="TFLOP/s")
+    # rasterizers: FLOPs over the kernel's own launch duration (kernel_ms); the stage, with its
+    # memsets and the backward's tile-order kernels, as stage_frac beside it
+    kern["raster_fwd"] = dict(bound="alu", achieved=fwd_flops / (kernel_ms["raster_fwd"] * 1e-3) / 1e12,
+                              peak=fp32_peak, unit="TFLOP/s",
+                              stage_frac=fwd_flops / (stage_ms[2] * 1e-3) / 1e12 / fp32_peak)
+    kern["raster_bwd"] = dict(bound="alu", achieved=bwd_flops / (kernel_ms["raster_bwd"] * 1e-3) / 1e12,
+                              peak=fp32_peak, unit="TFLOP/s",
+                              stage_frac=bwd_flops / (stage_ms[3] * 1e-3) / 1e12 / fp32_peak)
     vis = int((fr.tiles_touched > 0).sum().item())
     # bin + sort: tiles_touched, two reads of each visible record's rect and depth (count and
     # scatter walks), the bucket words written and read (8 + 8 B per pair), keys and values
@@ -620,6 +636,7 @@ def run_gpu(args):
         plain_fwd_views_per_s=job_rate(world, args.steps, fwd_s),
         mpix_per_s_fwd_bwd=value * P / 1e6,
         stage_ms=dict(zip(names, [round(float(x), 4) for x in stage_ms])),
+        kernel_ms={k: round(v, 4) for k, v in kernel_ms.items()},
         tuning_ms={k: round(v, 4) for k, v in shape.get("ms", {}).items()},
         intersections=m, visible=vis, pair_counters=counters,
         memory=dict(scene_mb=sum(gs[k].numel() * 4 for k in ("means", "scales", "quats",

@@ -126,7 +126,7 @@ typedef struct {
  * fgs_backward_raster_ex (HOST pointer, read during the call; NULL = every field 0 = the
  * defaults). None of them changes a result beyond the order of floating-point sums.
  *   fwd_pixels_per_thread  work shape of the forward rasterizer: 1, 2 or 4 pixels per thread
- *                          (a 16x16 tile runs on 256 / that many threads); 0 = 1.
+ *                          (a 16x16 tile runs on 256 / that many threads); 0 = 4.
  *   bwd_pixels_per_thread  the same for the backward rasterizer: 1, 2, 4 or 8 (8 = one warp
  *                          per tile); 0 = 8.
  *                          Images, final transmittances and processed counts do not depend on
@@ -143,6 +143,12 @@ typedef struct {
  *   wait_limit             polls after which one look-back wait gives up with FGS_ERR_TIMEOUT;
  *                          0 = 2^20 (about a second of polling). The waits of the rasterizers'
  *                          bulk copies keep their own bound of 2^20 polls.
+ *   main_kernel_events     a measurement hook: two cudaEvent_t (created by the caller) that
+ *                          fgs_rasterize_ex and fgs_backward_ex / fgs_backward_raster_ex record
+ *                          on `stream` immediately before and after the launch of the call's
+ *                          main kernel (the rasterizer, the backward rasterizer), so that its
+ *                          duration can be read apart from the call's small set-up kernels and
+ *                          memsets; NULL = none. Other calls ignore them.
  * Unknown flag bits or a shape outside the lists: FGS_ERR_INVALID_ARG before any launch. */
 #define FGS_OPT_INSTRUMENT 1u
 #define FGS_OPT_NO_WAIT 2u
@@ -151,6 +157,7 @@ typedef struct {
   int32_t bwd_pixels_per_thread;
   uint32_t flags;
   uint32_t wait_limit;
+  void *main_kernel_events[2];
 } fgs_options;
 
 /* Bytes of workspace needed by fgs_bin_sort, fgs_rasterize and fgs_backward for this set of

@@ -94,6 +94,9 @@ bool resolve_opts(const fgs_options *o, CallOpts *c) {
   c->instrument = (o->flags & FGS_OPT_INSTRUMENT) != 0;
   if (o->wait_limit) c->wait_limit = o->wait_limit;
   if (o->flags & FGS_OPT_NO_WAIT) c->wait_limit = 0;
+  if ((o->main_kernel_events[0] == nullptr) != (o->main_kernel_events[1] == nullptr)) return false;
+  c->ev_before = reinterpret_cast<cudaEvent_t>(o->main_kernel_events[0]);
+  c->ev_after = reinterpret_cast<cudaEvent_t>(o->main_kernel_events[1]);
   return true;
 }
 

@@ -38,10 +38,12 @@ constexpr uint32_t SPIN_LIMIT = 1u << 20;
 
 // Options of one call, resolved from fgs_options (api.cu).
 struct CallOpts {
-  int fwd_ppt = 1;                   // pixels per thread of the forward rasterizer (1, 2, 4)
+  int fwd_ppt = 4;                   // pixels per thread of the forward rasterizer (1, 2, 4)
   int bwd_ppt = 8;                   // of the backward rasterizer (1, 2, 4, 8)
   bool instrument = false;           // count work into the workspace counters
   uint32_t wait_limit = SPIN_LIMIT;  // polls of a look-back wait before it gives up
+  cudaEvent_t ev_before = nullptr;   // recorded around the call's main kernel (a measurement
+  cudaEvent_t ev_after = nullptr;    // hook; both or neither)
 };
 
 // ------------------------------------------------------------------------------------------

@@ -247,27 +247,39 @@ __device__ __forceinline__ float2 pair_exponent(const PairTerms &t, float v) {
   return ffma2(dup2(v * v), t.C, ffma2(dup2(v), t.slope, t.base));
 }
 
-// One list entry blended into one pixel without branches: the entry takes part if the pixel is
-// live and its exponent reaches 1/255; the pixel stops (and is left unchanged) if the blend
-// would take its transmittance below 1e-4. alpha is selected to 0 otherwise, which leaves T,
-// the colour and the processed count exactly as they were. q = (r, g, b, list position bits).
+// One list entry blended into two pixels of a thread (rows k and k + 1) at once, without
+// branches: an entry takes part at a pixel if the pixel is live and its exponent reaches 1/255;
+// the pixel stops (and is left unchanged) if the blend would take its transmittance below 1e-4;
+// alpha is selected to 0 otherwise, which leaves T, the colour and the processed count exactly
+// as they were. q = (r, g, b, list position bits). The two pixels' transmittance chains are
+// independent, so the FP32 products and fused multiply-adds of the pair
+// are paired instructions (fma / mul .rn.f32x2), the compares, selects and MUFU per pixel.
+// alpha is carried negated, na = max(-0.99, -2^e) = -min(0.99, 2^e) exactly, so that
+// T (1 - alpha) = fma(na, T, T) needs no negation, and the colour sums are kept negated,
+// Cn = -C: fma(rgb, na T, Cn) = -fma(rgb, alpha T, C) exactly (rounding to nearest is
+// symmetric), so the image is bit for bit the one of the scalar blend.
 template <bool COUNT>
-__device__ __forceinline__ void fwd_blend(bool &live, float e, const float4 &q, float &T,
-                                          float &C0, float &C1, float &C2, uint32_t &last,
-                                          uint32_t &n_blend) {
-  const bool c = live && e >= LOG2_ALPHA_MIN;
-  const float alpha = c ? fminf(ALPHA_MAX, ex2_approx(e)) : 0.f;
-  const bool stop = c && fmaf(-alpha, T, T) < T_MIN;
-  live = live && !stop;
-  const float a = stop ? 0.f : alpha;
-  const float wgt = a * T;
-  C0 = fmaf(q.x, wgt, C0);
-  C1 = fmaf(q.y, wgt, C1);
-  C2 = fmaf(q.z, wgt, C2);
-  T = fmaf(-a, T, T);
-  const bool blended = c && !stop;
-  last = blended ? __float_as_uint(q.w) + 1 : last;
-  if (COUNT && blended) ++n_blend;
+__device__ __forceinline__ void fwd_blend2(bool &live0, bool &live1, float e0, float e1,
+                                           const float4 &q, float2 &T, float2 &Cn0,
+                                           float2 &Cn1, float2 &Cn2, uint32_t &last0,
+                                           uint32_t &last1, uint32_t &n_blend) {
+  const bool c0 = live0 && e0 >= LOG2_ALPHA_MIN, c1 = live1 && e1 >= LOG2_ALPHA_MIN;
+  const float2 na = make_float2(c0 ? fmaxf(-ALPHA_MAX, -ex2_approx(e0)) : 0.f,
+                                c1 ? fmaxf(-ALPHA_MAX, -ex2_approx(e1)) : 0.f);
+  const float2 Tn = __ffma2_rn(na, T, T);
+  const bool stop0 = c0 && Tn.x < T_MIN, stop1 = c1 && Tn.y < T_MIN;
+  live0 = live0 && !stop0;
+  live1 = live1 && !stop1;
+  const float2 a = make_float2(stop0 ? 0.f : na.x, stop1 ? 0.f : na.y);
+  const float2 w = __fmul2_rn(a, T);  // -alpha T
+  Cn0 = __ffma2_rn(make_float2(q.x, q.x), w, Cn0);
+  Cn1 = __ffma2_rn(make_float2(q.y, q.y), w, Cn1);
+  Cn2 = __ffma2_rn(make_float2(q.z, q.z), w, Cn2);
+  T = __ffma2_rn(a, T, T);
+  const uint32_t pos1 = __float_as_uint(q.w) + 1;
+  last0 = c0 && !stop0 ? pos1 : last0;
+  last1 = c1 && !stop1 ? pos1 : last1;
+  if (COUNT) n_blend += (c0 && !stop0 ? 1u : 0u) + (c1 && !stop1 ? 1u : 0u);
 }
 
 template <int PPT, bool COUNT>
@@ -407,21 +419,46 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
           // several pixels per thread, blended without branches (alpha selected to 0 where a
           // pixel does not take part or has stopped), so that the compiler interleaves the
           // pixels' transmittance chains
+          // pixels in pairs (rows k, k + 1): the exponents per pixel (the same FMA sequence as
+          // every other shape), the blends paired over the two rows (fwd_blend2), with the
+          // colour sums kept negated until the tile is written
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            C0[k] = -C0[k];
+            C1[k] = -C1[k];
+            C2[k] = -C2[k];
+          }
           for (uint32_t p = 0; p < npairs && !done; ++p) {
             const PairTerms pt = pair_terms(cf[p][0], cf[p][1], cf[p][2], u2, uu2);
             const float4 qa = cf[p][3], qb = cf[p][4];
             const bool has_b = 2 * p + 1 < kept;
             bool any_live = false;
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-              const float2 e = pair_exponent(pt, fv + (float)k);
-              if (COUNT && live[k]) ++n_eval;
-              fwd_blend<COUNT>(live[k], e.x, qa, T[k], C0[k], C1[k], C2[k], last[k], n_blend);
-              if (COUNT && live[k] && has_b) ++n_eval;
-              fwd_blend<COUNT>(live[k], e.y, qb, T[k], C0[k], C1[k], C2[k], last[k], n_blend);
-              any_live = any_live || live[k];
+            for (int k = 0; k < PPT; k += 2) {
+              const float2 e0 = pair_exponent(pt, fv + (float)k);
+              const float2 e1 = pair_exponent(pt, fv + (float)(k + 1));
+              float2 Tp = make_float2(T[k], T[k + 1]);
+              float2 C0p = make_float2(C0[k], C0[k + 1]), C1p = make_float2(C1[k], C1[k + 1]);
+              float2 C2p = make_float2(C2[k], C2[k + 1]);
+              if (COUNT) n_eval += (live[k] ? 1u : 0u) + (live[k + 1] ? 1u : 0u);
+              fwd_blend2<COUNT>(live[k], live[k + 1], e0.x, e1.x, qa, Tp, C0p, C1p, C2p, last[k],
+                                last[k + 1], n_blend);
+              if (COUNT && has_b) n_eval += (live[k] ? 1u : 0u) + (live[k + 1] ? 1u : 0u);
+              fwd_blend2<COUNT>(live[k], live[k + 1], e0.y, e1.y, qb, Tp, C0p, C1p, C2p, last[k],
+                                last[k + 1], n_blend);
+              T[k] = Tp.x; T[k + 1] = Tp.y;
+              C0[k] = C0p.x; C0[k + 1] = C0p.y;
+              C1[k] = C1p.x; C1[k + 1] = C1p.y;
+              C2[k] = C2p.x; C2[k + 1] = C2p.y;
+              any_live = any_live || live[k] || live[k + 1];
             }
             done = !any_live;
+          }
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            C0[k] = -C0[k];
+            C1[k] = -C1[k];
+            C2[k] = -C2[k];
           }
         }
         if (__syncthreads_count(!done) == 0) {
@@ -938,11 +975,14 @@ cudaError_t launch_raster_fwd(const fgs_record *records, const uint32_t *vals,
   cudaError_t e = cudaMemsetAsync(&hdr->raster_tiles, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   const bool ins = opt.instrument;
+  if (opt.ev_before && (e = cudaEventRecord(opt.ev_before, st)) != cudaSuccess) return e;
   switch (opt.fwd_ppt) {
-    case 2: return fwd_launch<2>(records, vals, tile_ranges, vs, bg0, bg1, bg2, images, final_T, n_processed, hdr, ins, st);
-    case 4: return fwd_launch<4>(records, vals, tile_ranges, vs, bg0, bg1, bg2, images, final_T, n_processed, hdr, ins, st);
-    default: return fwd_launch<1>(records, vals, tile_ranges, vs, bg0, bg1, bg2, images, final_T, n_processed, hdr, ins, st);
+    case 2: e = fwd_launch<2>(records, vals, tile_ranges, vs, bg0, bg1, bg2, images, final_T, n_processed, hdr, ins, st); break;
+    case 4: e = fwd_launch<4>(records, vals, tile_ranges, vs, bg0, bg1, bg2, images, final_T, n_processed, hdr, ins, st); break;
+    default: e = fwd_launch<1>(records, vals, tile_ranges, vs, bg0, bg1, bg2, images, final_T, n_processed, hdr, ins, st); break;
   }
+  if (e == cudaSuccess && opt.ev_after) e = cudaEventRecord(opt.ev_after, st);
+  return e;
 }
 
 cudaError_t launch_raster_bwd(const fgs_record *records, const uint32_t *vals,
@@ -968,12 +1008,15 @@ cudaError_t launch_raster_bwd(const fgs_record *records, const uint32_t *vals,
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const bool ins = opt.instrument;
+  if (opt.ev_before && (e = cudaEventRecord(opt.ev_before, st)) != cudaSuccess) return e;
   switch (opt.bwd_ppt) {
-    case 1: return bwd_launch<1>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, ins, st);
-    case 2: return bwd_launch<2>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, ins, st);
-    case 4: return bwd_launch<4>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, ins, st);
-    default: return bwd_launch<8>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, ins, st);
+    case 1: e = bwd_launch<1>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, ins, st); break;
+    case 2: e = bwd_launch<2>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, ins, st); break;
+    case 4: e = bwd_launch<4>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, ins, st); break;
+    default: e = bwd_launch<8>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, ins, st); break;
   }
+  if (e == cudaSuccess && opt.ev_after) e = cudaEventRecord(opt.ev_after, st);
+  return e;
 }
 
 }  // namespace fgs

@@ -51,14 +51,27 @@ class FgsCamera(ctypes.Structure):
 
 class FgsOptions(ctypes.Structure):
     _fields_ = [("fwd_pixels_per_thread", ctypes.c_int32), ("bwd_pixels_per_thread", ctypes.c_int32),
-                ("flags", ctypes.c_uint32), ("wait_limit", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("wait_limit", ctypes.c_uint32),
+                ("main_kernel_events", ctypes.c_void_p * 2)]
 
 
-def options(fwd=0, bwd=0, instrument=False, no_wait=False, wait_limit=0):
+def options(fwd=0, bwd=0, instrument=False, no_wait=False, wait_limit=0, events=None):
     """fgs_options of one call: rasterizer work shapes (0 = the library's default), the
-    instrumented launches, and the bound of the binning's look-back waits."""
+    instrumented launches, the bound of the binning's look-back waits, and optionally two
+    torch.cuda.Event (timing) recorded around the call's main kernel."""
     flags = (FGS_OPT_INSTRUMENT if instrument else 0) | (FGS_OPT_NO_WAIT if no_wait else 0)
-    return FgsOptions(int(fwd), int(bwd), flags, int(wait_limit))
+    o = FgsOptions(int(fwd), int(bwd), flags, int(wait_limit))
+    if events is not None:
+        o.main_kernel_events[0] = _event_handle(events[0])
+        o.main_kernel_events[1] = _event_handle(events[1])
+    return o
+
+
+def _event_handle(ev):
+    """The cudaEvent_t of a torch.cuda.Event (created by recording it once)."""
+    if not ev.cuda_event:
+        ev.record()
+    return ev.cuda_event
 
 
 def _opt_ref(opts):

@@ -126,6 +126,11 @@ def test_options_checked_before_launch(lib):
                                    256, 256, 256, 256, 256, 256, 256, 1 << 20, r, None) == INV
         assert lib.fgs_bin_sort_ex(256, 256, 10, cams, 1, 256, 256, 100, 256, 256, 256, 1 << 30,
                                    0, r, None) == INV
+    # the measurement events come in pairs
+    half = fgs.options(fwd=1, bwd=8)
+    half.main_kernel_events[0] = 4096
+    assert lib.fgs_rasterize_ex(256, 256, 256, cams, 1, None, 256, 256, 256, 256, 1 << 20,
+                                ctypes.byref(half), None) == INV
     # null outputs are still refused when the options are fine
     ok = ctypes.byref(fgs.options(fwd=1, bwd=8, wait_limit=5))
     assert lib.fgs_rasterize_ex(256, 256, 256, cams, 1, None, 0, 256, 256, 256, 1 << 20, ok,
