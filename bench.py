@@ -187,10 +187,11 @@ def _traffic(kernel_name):
         f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
         if f.get("kernel") != kernel_name:
             continue
-        src = os.path.join(ROOT, "paper_2409_04751_gb300", "csrc", f.get("source", ""))
-        if not os.path.exists(src):
+        srcs = [os.path.join(ROOT, "paper_2409_04751_gb300", "csrc", x)
+                for x in f.get("source", "").split("+")]
+        if not all(os.path.exists(x) for x in srcs):
             return None
-        if code_hash(open(src).read()) != f.get("code"):
+        if code_hash("".join(open(x).read() for x in srcs)) != f.get("code"):
             return None
         return float(f["dram_bytes_per_launch"])
     return None
