@@ -28,6 +28,18 @@
  *    the wait bound are chosen per call (fgs_options). Calls on distinct workspaces are
  *    independent; calls sharing a workspace must not overlap in time (they share its
  *    counters).
+ *  - Checked build. The same sources compiled with -DFGS_CHECK=1 give libfgs_check.so, a
+ *    debugging build with the same ABI and the same results on valid inputs. In it, every
+ *    index a kernel reads from memory is compared with the size of the buffer it selects
+ *    before it is used: record indices from `vals` and from the binning's compacted record
+ *    list, tile ids from the binning's tile lists, sorted keys and the backward's tile order,
+ *    and [start, end) of every tile in `tile_ranges`. An index outside sets FGS_ERR_BOUNDS in
+ *    the status word and the access is skipped (the index taken as 0, the range as empty), so
+ *    a corrupted input or a kernel bug shows up as a status and not as an access out of
+ *    bounds. The rasterizers bound record indices and list ends by the record count and key
+ *    capacity that the last fgs_bin_sort / fgs_bin_sort_ex on the same workspace recorded
+ *    there (with no such binning, e.g. after fgs_bin_sort_noalloc, only start <= end is
+ *    checked). The product build (libfgs.so) has none of these comparisons.
  */
 #ifndef FGS_H
 #define FGS_H
@@ -46,7 +58,8 @@ typedef enum {
   FGS_ERR_INVALID_ARG = 1,
   FGS_ERR_CAPACITY = 2, /* more (Gaussian, tile) intersections than the key buffers hold */
   FGS_ERR_TIMEOUT = 3,  /* a bounded device-side wait gave up */
-  FGS_ERR_CUDA = 4
+  FGS_ERR_CUDA = 4,
+  FGS_ERR_BOUNDS = 5    /* checked build only: an index read from memory was out of range */
 } fgs_status;
 
 #define FGS_TILE 16        /* tiles are 16 x 16 pixels (Sec. 3.1 "Rendering") */

@@ -337,6 +337,7 @@ const char *fgs_status_string(int status) {
     case FGS_ERR_CAPACITY: return "more intersections than the key capacity";
     case FGS_ERR_TIMEOUT: return "a bounded device-side wait gave up";
     case FGS_ERR_CUDA: return "CUDA error";
+    case FGS_ERR_BOUNDS: return "an index read from memory was out of range (checked build)";
     default: return "unknown status";
   }
 }

@@ -78,11 +78,17 @@ __global__ void __launch_bounds__(EMIT_THREADS)
     // records spanned by the chunk: the owner of pair lo and at most EMIT_CHUNK more (the
     // last chunk of a capacity-truncated emission may list more; they own no pair below hi)
     const int nw = (int)min(v1 - v0 + 1, (int64_t)EMIT_CHUNK + 1);
+    // checked build: the chunk's records must lie in the compacted list (uniform per CTA)
+    if (FGS_CHECK && (v1 < v0 || !in_bounds((uint64_t)(v0 + nw - 1), (uint64_t)nv, status))) {
+      set_status(status, ST_BOUNDS);
+      continue;
+    }
     __syncthreads();
     for (int i = tid; i < EMIT_CHUNK; i += EMIT_THREADS) s_own[i] = 0;
     __syncthreads();
     for (int i = tid; i < nw; i += EMIT_THREADS) {
-      const uint32_t r = vis_rec[v0 + i];
+      uint32_t r = vis_rec[v0 + i];
+      if (!in_bounds(r, (uint64_t)n_per_view * vs.n, status)) r = 0u;
       const uint4 w2 = __ldg(reinterpret_cast<const uint4 *>(rec + r) + 2);
       const uint32_t x0 = w2.z & 0xffffu, y0 = w2.z >> 16, x1 = w2.w & 0xffffu, y1 = w2.w >> 16;
       const int v = (int)(r / (uint32_t)n_per_view);
@@ -169,6 +175,12 @@ __global__ void __launch_bounds__(EMIT_THREADS)
 #pragma unroll
       for (int k = 0; k < PER; ++k)
         pos[k] = tile[k] != 0xffffffffu ? atomicAdd(&ranges[2 * (size_t)tile[k] + 1], 1u) : 0xffffffffu;
+      // checked build: with complete counts every claimed slot lies below the capacity
+      if (FGS_CHECK && total <= capacity) {
+#pragma unroll
+        for (int k = 0; k < PER; ++k)
+          if (tile[k] != 0xffffffffu) in_bounds(pos[k], (uint64_t)capacity, status);
+      }
 #pragma unroll
       for (int k = 0; k < PER; ++k)
         if (tile[k] != 0xffffffffu && (int64_t)pos[k] < capacity)
@@ -752,17 +764,23 @@ template <int NT, int IPT_LO, int CAP, int MIN_BLOCKS, bool CHUNKED>
 __global__ void __launch_bounds__(NT, MIN_BLOCKS)
     segsort_kernel(const uint32_t *__restrict__ list, const uint32_t *list_count,
                    const uint32_t *__restrict__ ranges, uint64_t *words, uint64_t *keys,
-                   uint32_t *vals, int64_t capacity, const uint32_t *status) {
+                   uint32_t *vals, int64_t capacity, int64_t total_tiles, uint32_t *status) {
   static_assert(NT * IPT_LO * 2 == CAP, "two word counts per class");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SegSmem<NT, CAP> &S = *reinterpret_cast<SegSmem<NT, CAP> *>(smem_raw);
   if (binning_timed_out(status)) return;
-  const uint32_t count = *list_count;
+  uint32_t count = *list_count;
+  if (!in_bounds(count, (uint64_t)total_tiles + 1u, status)) count = 0u;
   for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
     const uint32_t t = __ldg(list + i);
+    if (!in_bounds(t, (uint64_t)total_tiles, status)) continue;
     const uint2 rg = __ldg(reinterpret_cast<const uint2 *>(ranges) + t);
-    // bounds of a bucket that a device-side error left inconsistent: skip it
-    if (rg.y <= rg.x || (int64_t)rg.y > capacity) continue;
+    // bounds of a bucket that a device-side error left inconsistent: skip it (a listed tile is
+    // never empty, so the checked build reports it)
+    if (rg.y <= rg.x || (int64_t)rg.y > capacity) {
+      if (FGS_CHECK) set_status(status, ST_BOUNDS);
+      continue;
+    }
     const uint32_t cnt = rg.y - rg.x;
     if (cnt <= (uint32_t)(NT * IPT_LO))
       sort_segment<NT, IPT_LO, CAP>(S, words + rg.x, cnt, t, keys + rg.x, vals + rg.x);
@@ -770,14 +788,16 @@ __global__ void __launch_bounds__(NT, MIN_BLOCKS)
       sort_segment<NT, 2 * IPT_LO, CAP>(S, words + rg.x, cnt, t, keys + rg.x, vals + rg.x);
     else if (CHUNKED)
       sort_segment_chunked<NT, 2 * IPT_LO, CAP>(S, words + rg.x, cnt, t, keys + rg.x, vals + rg.x);
+    else if (FGS_CHECK)
+      set_status(status, ST_BOUNDS);  // a long segment listed in the short class
   }
 }
 
 template <int NT, int IPT_LO, int CAP, int MIN_BLOCKS, bool CHUNKED>
 cudaError_t launch_segsort(const uint32_t *list, const uint32_t *list_count,
                            const uint32_t *ranges, uint64_t *words, uint64_t *keys,
-                           uint32_t *vals, int64_t capacity, const uint32_t *status,
-                           cudaStream_t st) {
+                           uint32_t *vals, int64_t capacity, int64_t total_tiles,
+                           uint32_t *status, cudaStream_t st) {
   constexpr size_t smem = sizeof(SegSmem<NT, CAP>);
   static int occ = 0;
   if (occ == 0) {
@@ -790,7 +810,7 @@ cudaError_t launch_segsort(const uint32_t *list, const uint32_t *list_count,
     occ = a > 0 ? a : 1;
   }
   segsort_kernel<NT, IPT_LO, CAP, MIN_BLOCKS, CHUNKED><<<(unsigned)(sm_count() * occ), NT, smem, st>>>(
-      list, list_count, ranges, words, keys, vals, capacity, status);
+      list, list_count, ranges, words, keys, vals, capacity, total_tiles, status);
   return cudaGetLastError();
 }
 
@@ -866,12 +886,12 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
         tile_ranges, words, capacity, &hdr->status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_segsort<256, 2, SEG_CAP0, 6, false>(lists, &hdr->seg_count[0], tile_ranges,
-                                                       words, keys, vals, capacity,
+                                                       words, keys, vals, capacity, T,
                                                        &hdr->status, st)) != cudaSuccess)
     return e;
   return launch_segsort<512, 8, SEG_CAP1, 1, true>(lists + T, &hdr->seg_count[1], tile_ranges,
-                                                   words, keys, vals, capacity, &hdr->status,
-                                                   st);
+                                                   words, keys, vals, capacity, T,
+                                                   &hdr->status, st);
 }
 
 }  // namespace fgs

@@ -29,6 +29,13 @@ constexpr float SERIES_T = 0.3f;                          // near-axis series be
 // Device status codes (same values as fgs_status).
 constexpr uint32_t ST_CAPACITY = FGS_ERR_CAPACITY;
 constexpr uint32_t ST_TIMEOUT = FGS_ERR_TIMEOUT;
+constexpr uint32_t ST_BOUNDS = FGS_ERR_BOUNDS;
+
+// Checked build: -DFGS_CHECK=1 compiles the index checks of in_bounds() in (libfgs_check.so);
+// the product build leaves them out.
+#ifndef FGS_CHECK
+#define FGS_CHECK 0
+#endif
 
 // Bounded waits: polls before a wait gives up and reports FGS_ERR_TIMEOUT. A 48-byte bulk copy
 // lands within microseconds and a look-back predecessor publishes within one partition's work,
@@ -92,9 +99,15 @@ struct WsHeader {
   unsigned long long n_visible;  // records with a non-empty rect (written by the scan)
   unsigned long long n_candidates;  // (record, tile) pairs of the rects (written by the scan)
   unsigned long long n_dropped;  // onesweep emission: pairs beyond their record's rect
-  uint32_t pad[38];
+  // checked build only, written by the binning for the rasterizers' index checks:
+  uint32_t bounds_magic;         // BOUNDS_MAGIC once a binning on this workspace set the two
+  uint32_t bounds_records;       // records of that binning (list entries must be below)
+  uint32_t bounds_pairs;         // its key capacity (list ends must not exceed it)
+  uint32_t pad[35];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
+static_assert(offsetof(WsHeader, status) == 0, "the status word starts the header");
+constexpr uint32_t BOUNDS_MAGIC = 0x4b434746u;
 
 constexpr int EMIT_THREADS = 256;
 constexpr int EMIT_ITEMS = 16;
@@ -169,6 +182,28 @@ inline WsLayout ws_layout(int64_t n_records, int64_t capacity, int64_t total_til
 
 __device__ __forceinline__ void set_status(uint32_t *status, uint32_t code) {
   atomicCAS(status, 0u, code);
+}
+
+// Index check of the checked build: true if i < n; otherwise FGS_ERR_BOUNDS is recorded and
+// the caller skips the access. Always true (and compiled away) in the product build.
+__device__ __forceinline__ bool in_bounds(uint64_t i, uint64_t n, uint32_t *status) {
+  if (!FGS_CHECK || i < n) return true;
+  set_status(status, ST_BOUNDS);
+  return false;
+}
+
+// Bounds of the rasterizers' index checks: the record count and key capacity recorded by the
+// binning on this workspace (the status word starts the header), or no bound when none did.
+struct ListBounds {
+  uint32_t records, pairs;
+};
+__device__ __forceinline__ ListBounds list_bounds(const uint32_t *status) {
+  ListBounds b{0xffffffffu, 0xffffffffu};
+  if (FGS_CHECK) {
+    const WsHeader *h = reinterpret_cast<const WsHeader *>(status);
+    if (h->bounds_magic == BOUNDS_MAGIC) b = ListBounds{h->bounds_records, h->bounds_pairs};
+  }
+  return b;
 }
 
 // A look-back wait of an earlier kernel of the same binning gave up: its offsets are partial,

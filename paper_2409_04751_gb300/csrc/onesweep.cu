@@ -61,9 +61,15 @@ __global__ void __launch_bounds__(EMIT_THREADS)
     // records spanned by the chunk: the owner of pair lo and at most EMIT_CHUNK more (the
     // last chunk of a capacity-truncated emission may list more; they own no pair below hi)
     const int nw = (int)min(v1 - v0 + 1, (int64_t)EMIT_CHUNK + 1);
+    // checked build: the chunk's records must lie in the compacted list (uniform per CTA)
+    if (FGS_CHECK && (v1 < v0 || !in_bounds((uint64_t)(v0 + nw - 1), (uint64_t)nv, status))) {
+      set_status(status, ST_BOUNDS);
+      continue;
+    }
     __syncthreads();
     for (int i = tid; i < nw; i += EMIT_THREADS) {
-      const uint32_t r = vis_rec[v0 + i];
+      uint32_t r = vis_rec[v0 + i];
+      if (!in_bounds(r, (uint64_t)n_per_view * vs.n, status)) r = 0u;
       const uint4 w2 = __ldg(reinterpret_cast<const uint4 *>(rec + r) + 2);
       const uint32_t x0 = w2.z & 0xffffu, y0 = w2.z >> 16, x1 = w2.w & 0xffffu, y1 = w2.w >> 16;
       const int v = (int)(r / (uint32_t)n_per_view);
@@ -320,13 +326,17 @@ __global__ void __launch_bounds__(SORT_THREADS, KV ? 2 : 3)
 // left undefined by a device-side error cannot steer a write out of bounds.
 __global__ void ranges_kernel(const uint64_t *__restrict__ keys, const int64_t *n_int,
                               int64_t capacity, int64_t total_tiles,
-                              uint32_t *__restrict__ ranges, const uint32_t *status) {
+                              uint32_t *__restrict__ ranges, uint32_t *status) {
   if (binning_timed_out(status)) return;
   const int64_t n = min(*n_int, capacity);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t t = keys[i] >> 32;
-    if (t >= (uint64_t)total_tiles) continue;
+    // the dropped pairs carry tile id total_tiles; any larger id is an error (checked build)
+    if (t >= (uint64_t)total_tiles) {
+      in_bounds(t, (uint64_t)total_tiles + 1u, status);
+      continue;
+    }
     if (i == 0 || (keys[i - 1] >> 32) != t) ranges[2 * t] = (uint32_t)i;
     if (i == n - 1 || (keys[i + 1] >> 32) != t) ranges[2 * t + 1] = (uint32_t)(i + 1);
   }

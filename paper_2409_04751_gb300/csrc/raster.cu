@@ -48,7 +48,8 @@ struct TileInfo {
 };
 
 __device__ __forceinline__ TileInfo tile_info(const Views &vs, int64_t t,
-                                              const uint32_t *__restrict__ ranges) {
+                                              const uint32_t *__restrict__ ranges,
+                                              const ListBounds &bd, uint32_t *status) {
   TileInfo ti;
   ti.v = view_of_tile(vs, t);
   const View &V = vs.v[ti.v];
@@ -58,6 +59,10 @@ __device__ __forceinline__ TileInfo tile_info(const Views &vs, int64_t t,
   const uint2 rg = __ldg(reinterpret_cast<const uint2 *>(ranges) + t);
   ti.start = rg.x;
   ti.count = rg.y > rg.x ? rg.y - rg.x : 0u;
+  // checked build: a range must not be inverted or end past the key capacity
+  if (FGS_CHECK && (!in_bounds(rg.x, (uint64_t)rg.y + 1u, status) ||
+                    !in_bounds(rg.y, (uint64_t)bd.pairs + 1u, status)))
+    ti.count = 0u;
   return ti;
 }
 
@@ -80,11 +85,13 @@ __device__ __forceinline__ void issue_batch(fgs_record *stage, uint64_t *bar,
 
 template <int NT, int PER>
 __device__ __forceinline__ void load_idx(const uint32_t *__restrict__ vals, uint32_t base,
-                                         uint32_t lo, uint32_t cnt, uint32_t (&idx)[PER]) {
+                                         uint32_t lo, uint32_t cnt, uint32_t (&idx)[PER],
+                                         const ListBounds &bd, uint32_t *status) {
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
     const uint32_t slot = threadIdx.x + k * NT;
     idx[k] = slot < cnt ? __ldg(vals + base + lo + slot) : 0u;
+    if (!in_bounds(idx[k], bd.records, status)) idx[k] = 0u;  // checked build only
   }
 }
 
@@ -311,6 +318,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
   const float2 u2 = dup2(fu), uu2 = dup2(fu * fu);
   // after a device-side error in the binning the lists are undefined: render background only
   const bool lists_ok = *(volatile const uint32_t *)status == 0u;
+  const ListBounds bd = list_bounds(status);
 
   for (;;) {
     if (tid == 0) s_tile = (int64_t)atomicAdd(tile_counter, 1u);
@@ -318,7 +326,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
     const int64_t t = s_tile;
     __syncthreads();
     if (t >= vs.total_tiles) break;
-    const TileInfo ti = tile_info(vs, t, ranges);
+    const TileInfo ti = tile_info(vs, t, ranges, bd, status);
     const View &V = vs.v[ti.v];
     const int px = ti.tx * TILE + lx;
     // tile centre (between pixel centres 7 and 8)
@@ -341,8 +349,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
 
     if (nb > 0) {
       uint32_t idx[PER], idx_next[PER];
-      load_idx<NT, PER>(vals, ti.start, 0, count, idx);
-      load_idx<NT, PER>(vals, ti.start, BATCH, count > BATCH ? count - BATCH : 0u, idx_next);
+      load_idx<NT, PER>(vals, ti.start, 0, count, idx, bd, status);
+      load_idx<NT, PER>(vals, ti.start, BATCH, count > BATCH ? count - BATCH : 0u, idx_next, bd, status);
       fence_proxy_async_smem();
       issue_batch<NT, PER>(raw[0], &bar[0], rec, idx, min(count, (uint32_t)BATCH));
       for (uint32_t b = 0; b < nb; ++b) {
@@ -354,7 +362,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
           issue_batch<NT, PER>(raw[s ^ 1], &bar[s ^ 1], rec, idx_next,
                                min((uint32_t)BATCH, count - lo - BATCH));
           const uint32_t lo2 = lo + 2 * BATCH;
-          load_idx<NT, PER>(vals, ti.start, lo2, count > lo2 ? count - lo2 : 0u, idx_next);
+          load_idx<NT, PER>(vals, ti.start, lo2, count > lo2 ? count - lo2 : 0u, idx_next, bd, status);
         }
         const bool ok = mbar_wait(&bar[s], s ? phase1 : phase0, status);
         if (s) phase1 ^= 1u; else phase0 ^= 1u;
@@ -676,17 +684,20 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 8 ? 16 : 1)
   const float2 u2 = dup2(fu), uu2 = dup2(fu * fu);
   // after a device-side error in the binning the lists are undefined: no gradient flows
   const bool lists_ok = *(volatile const uint32_t *)status == 0u;
+  const ListBounds bd = list_bounds(status);
 
   for (;;) {
     if (tid == 0) {  // tiles in decreasing order of work
       const uint32_t q = atomicAdd(tile_counter, 1u);
       s_tile = q < vs.total_tiles ? (int64_t)order[q] : vs.total_tiles;
+      // checked build: the order lists tiles only (an entry outside ends this CTA's work)
+      if (q < vs.total_tiles) in_bounds((uint64_t)s_tile, (uint64_t)vs.total_tiles, status);
       s_max = 0u;
     }
     __syncthreads();
     const int64_t t = s_tile;
     if (t >= vs.total_tiles) break;
-    const TileInfo ti = tile_info(vs, t, ranges);
+    const TileInfo ti = tile_info(vs, t, ranges, bd, status);
     const View &V = vs.v[ti.v];
     const int px = ti.tx * TILE + lx;
     const float tile_cx = (float)(ti.tx * TILE) + 0.5f * TILE, tile_cy = (float)(ti.ty * TILE) + 0.5f * TILE;
@@ -721,8 +732,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 8 ? 16 : 1)
       uint32_t idx[PER], idx_next[PER];
       {
         const uint32_t lo0 = (nb - 1) * BATCH;
-        load_idx<NT, PER>(vals, ti.start, lo0, max_last - lo0, idx);
-        if (nb >= 2) load_idx<NT, PER>(vals, ti.start, lo0 - BATCH, BATCH, idx_next);
+        load_idx<NT, PER>(vals, ti.start, lo0, max_last - lo0, idx, bd, status);
+        if (nb >= 2) load_idx<NT, PER>(vals, ti.start, lo0 - BATCH, BATCH, idx_next, bd, status);
         fence_proxy_async_smem();
         issue_batch<NT, PER>(raw[0], &bar[0], rec, idx, max_last - lo0);
 #pragma unroll
@@ -739,7 +750,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 8 ? 16 : 1)
           issue_batch<NT, PER>(raw[s ^ 1], &bar[s ^ 1], rec, idx_next, BATCH);
 #pragma unroll
           for (int k = 0; k < PER; ++k) mine[k] = idx_next[k];
-          if (b >= 2) load_idx<NT, PER>(vals, ti.start, lo - 2 * BATCH, BATCH, idx_next);
+          if (b >= 2) load_idx<NT, PER>(vals, ti.start, lo - 2 * BATCH, BATCH, idx_next, bd, status);
         }
         const bool ok = mbar_wait(&bar[s], s ? phase1 : phase0, status);
         if (s) phase1 ^= 1u; else phase0 ^= 1u;
@@ -852,7 +863,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 8 ? 16 : 1)
 // ones fill in at the end. Any order gives the same gradients up to the order of their sums.
 __global__ void __launch_bounds__(256)
     tile_work_kernel(const uint32_t *__restrict__ ranges, const uint32_t *__restrict__ n_processed,
-                     Views vs, const uint32_t *status, uint32_t *__restrict__ bucket,
+                     Views vs, uint32_t *status, uint32_t *__restrict__ bucket,
                      uint32_t *__restrict__ hist) {
   __shared__ uint32_t s_hist[WORK_BUCKETS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -860,7 +871,8 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   const int64_t t = (int64_t)blockIdx.x * 8 + warp;
   if (t < vs.total_tiles) {
-    const TileInfo ti = tile_info(vs, t, ranges);
+    const ListBounds bd = list_bounds(status);
+    const TileInfo ti = tile_info(vs, t, ranges, bd, status);
     const View &V = vs.v[ti.v];
     const bool lists_ok = *(volatile const uint32_t *)status == 0u;
     uint32_t m = 0;
@@ -887,7 +899,7 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(1024)
     tile_order_kernel(const uint32_t *__restrict__ bucket, const uint32_t *__restrict__ hist,
                       uint32_t *__restrict__ cursor, int64_t total_tiles,
-                      uint32_t *__restrict__ order) {
+                      uint32_t *__restrict__ order, uint32_t *status) {
   __shared__ uint32_t s_off[WORK_BUCKETS];
   if (threadIdx.x < 32) {  // start of each class: the tiles of all heavier classes come first
     const uint32_t h = hist[threadIdx.x];
@@ -910,7 +922,8 @@ __global__ void __launch_bounds__(1024)
   uint32_t base = 0;
   if (in && lane == leader) base = atomicAdd(&cursor[b], (uint32_t)__popc(peers));
   base = __shfl_sync(0xffffffffu, base, leader);
-  if (in) order[s_off[b] + base + __popc(peers & lanemask_lt())] = (uint32_t)t;
+  const uint32_t slot = s_off[b & (WORK_BUCKETS - 1)] + base + __popc(peers & lanemask_lt());
+  if (in && in_bounds(slot, (uint64_t)total_tiles, status)) order[slot] = (uint32_t)t;
 }
 
 template <typename K>
@@ -1004,7 +1017,7 @@ cudaError_t launch_raster_bwd(const fgs_record *records, const uint32_t *vals,
     tile_work_kernel<<<(unsigned)((vs.total_tiles + 7) / 8), 256, 0, st>>>(
         tile_ranges, n_processed, vs, &hdr->status, bucket, hist);
     tile_order_kernel<<<(unsigned)((vs.total_tiles + 1023) / 1024), 1024, 0, st>>>(
-        bucket, hist, hist + WORK_BUCKETS, vs.total_tiles, order);
+        bucket, hist, hist + WORK_BUCKETS, vs.total_tiles, order, &hdr->status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const bool ins = opt.instrument;

@@ -138,6 +138,12 @@ __global__ void __launch_bounds__(EMIT_THREADS)
   __syncthreads();
   const int64_t part = s_part;
   const int64_t base = part * EMIT_PART;
+  if (FGS_CHECK && part == 0 && tid == 0) {  // the rasterizers' index bounds (checked build)
+    WsHeader *h = reinterpret_cast<WsHeader *>(status);
+    h->bounds_records = (uint32_t)R;
+    h->bounds_pairs = (uint32_t)capacity;
+    h->bounds_magic = BOUNDS_MAGIC;
+  }
 
   uint32_t c[EMIT_ITEMS];
   uint32_t sum = 0, nv = 0;
@@ -185,7 +191,7 @@ __global__ void __launch_bounds__(EMIT_THREADS)
   uint64_t v = vbase + voff;
 #pragma unroll
   for (int k = 0; k < EMIT_ITEMS; ++k) {
-    if (c[k] > 0u) {
+    if (c[k] > 0u && in_bounds(v, (uint64_t)R, status)) {
       vis_rec[v] = (uint32_t)(base + tid * EMIT_ITEMS + k);
       vis_off[v] = o;
       // chunks whose first pair falls inside this record's pairs [o, o + c)

@@ -10,7 +10,11 @@ import os
 
 import torch
 
-from .build import LIB_PATH
+from .build import CHECK_LIB_PATH, LIB_PATH as PRODUCT_LIB_PATH
+
+# FGS_CHECKED_BUILD=1 in the environment loads the checked build (libfgs_check.so: the same ABI,
+# every index read from memory compared with its buffer's size, FGS_ERR_BOUNDS on a violation).
+LIB_PATH = CHECK_LIB_PATH if os.environ.get("FGS_CHECKED_BUILD") == "1" else PRODUCT_LIB_PATH
 
 RECORD_BYTES = 48
 TILE = 16
@@ -21,6 +25,7 @@ FGS_ERR_INVALID_ARG = 1
 FGS_ERR_CAPACITY = 2
 FGS_ERR_TIMEOUT = 3
 FGS_ERR_CUDA = 4
+FGS_ERR_BOUNDS = 5
 # camera models (fgs_camera_model)
 FGS_CAM_EQUIDISTANT = 0
 FGS_CAM_EQUISOLID = 1
@@ -104,7 +109,8 @@ _lib = None
 
 
 def lib():
-    """Load libfgs.so (built by __graft_entry__.build() / paper_2409_04751_gb300.build)."""
+    """Load libfgs.so, or libfgs_check.so under FGS_CHECKED_BUILD=1 (both built by
+    __graft_entry__.build() / paper_2409_04751_gb300.build)."""
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):

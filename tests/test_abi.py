@@ -36,6 +36,16 @@ def test_exports_every_declared_symbol(lib):
     assert sorted(names) == sorted(fgs.EXPORTS)
 
 
+def test_checked_build_exports_the_same_symbols():
+    # the debugging build (index checks compiled in) is a drop-in replacement of libfgs.so
+    cuda_build.build(check=True)
+    chk = ctypes.CDLL(cuda_build.CHECK_LIB_PATH)
+    for n in _declared():
+        assert hasattr(chk, n), n
+    chk.fgs_status_string.restype = ctypes.c_char_p
+    assert b"checked build" in chk.fgs_status_string(fgs.FGS_ERR_BOUNDS)
+
+
 def _cam(w=64, h=48):
     return fgs.cameras([dict(W=[1, 0, 0, 0, 1, 0, 0, 0, 1], b=[0, 0, 0], fx=20.0, fy=20.0,
                              cx=w / 2, cy=h / 2, width=w, height=h)])
