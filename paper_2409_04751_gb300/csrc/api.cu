@@ -28,7 +28,7 @@ bool build_views(const fgs_camera *cams, int n_views, Views *vs) {
   if (cams == nullptr || n_views < 1 || n_views > FGS_MAX_VIEWS) return false;
   memset(vs, 0, sizeof(Views));
   vs->n = n_views;
-  int64_t tiles = 0, pixels = 0;
+  int64_t tiles = 0, pixels = 0, cells = 0;
   for (int k = 0; k < n_views; ++k) {
     const fgs_camera &c = cams[k];
     if (c.width <= 0 || c.height <= 0) return false;
@@ -50,11 +50,15 @@ bool build_views(const fgs_camera *cams, int n_views, Views *vs) {
     if (V.tiles_x > 65535 || V.tiles_y > 65535) return false;
     V.tile_offset = tiles;
     V.pixel_offset = pixels;
+    V.cells_x = (V.tiles_x + CELL - 1) / CELL;
+    V.cell_offset = cells;
     tiles += (int64_t)V.tiles_x * V.tiles_y;
     pixels += (int64_t)c.width * c.height;
+    cells += (int64_t)V.cells_x * ((V.tiles_y + CELL - 1) / CELL);
   }
   vs->total_tiles = tiles;
   vs->total_pixels = pixels;
+  vs->total_cells = cells;
   int bits = 0;
   while (bits < 31 && ((int64_t)1 << bits) < tiles) ++bits;
   vs->tile_bits = bits;

@@ -3,30 +3,33 @@
 //
 // The result is the one the method defines: for every (record, tile) pair of a record's tile
 // rect, key = tile << 32 | depth bits and value = record, stably sorted by key, and each tile's
-// [start, end) in the sorted arrays. Instead of a device-wide radix sort over all key bits
-// (kept in onesweep.cu as the option FGS_BIN_ONESWEEP), the pairs are bucketed by tile first and
-// each tile's bucket is sorted on its own:
+// [start, end) in the sorted arrays. Instead of emitting every pair and sorting them all (the
+// device-wide radix sort over all key bits is kept in onesweep.cu as the option
+// FGS_BIN_ONESWEEP), the records are binned into cells of CELL x CELL tiles, each cell's short
+// list is sorted once by (depth, record), and every tile takes its pairs out of its cell's
+// sorted list in order:
 //
-//  1. scan_kernel: single-pass scan of tiles_touched with decoupled look-back (partitions of
-//     4096 records claimed in order through an atomic counter). For every record with pairs it
-//     writes its pair offset and its rank among such records (a compacted list), and for every
-//     1024-pair chunk the rank of the record holding the chunk's first pair. For rect binning
-//     it also adds each visible record to a 2D difference grid of tile counts (at most eight
-//     atomics per record, rect_difference in scan.cuh).
-//  2. rect binning: grid_scan_kernel turns the difference grid into the pairs of every tile
-//     (row sums, then column sums). Exact (ellipse) binning: pair_kernel<false>, one CTA per
-//     1024-pair chunk (the work per CTA is fixed however many tiles one Gaussian covers), counts
-//     them pair by pair.
-//  3. tile_scan_kernel: exclusive scan of the tile counts (decoupled look-back) gives every
-//     tile's start; tiles are listed by segment size.
-//  4. pair_kernel<true>: the same walk over the pairs claims a slot in the pair's tile bucket and
-//     writes depth bits << 32 | record there.
-//  5. segsort_kernel (one launch per size class): each tile's bucket is sorted in shared memory
+//  1. cell_count_kernel: the number of rect pairs and of visible records, and per cell the
+//     records with a pair in it. A warp numbers the cells of its 32 records and takes them 32
+//     at a time (the same work per lane however large the records); they are counted in shared
+//     memory, with one global atomic per CTA and cell.
+//  2. tile_scan_kernel over the cells: exclusive scan of the cell counts (decoupled look-back)
+//     gives every cell's start; cells are listed by size class.
+//  3. cell_scatter_kernel: the same walk writes depth bits << 32 | record into the record's
+//     cells (slots claimed per CTA and cell, then per entry in shared memory).
+//  4. cell_sort_kernel (one launch per size class): each cell's list is sorted in shared memory
 //     (a one-pass bucket sort on the depth bits, or LSD radix passes when the depths are too
-//     clustered for it) and written out as keys and values.
-// Moving 8-byte words through memory twice (bucket write, bucket read) replaces the five to
-// seven passes of a device-wide radix sort over (tile, depth) keys. The number of valid pairs
-// is read on the device, so nothing here needs a host sync.
+//     clustered for it), in place; then each entry gets the mask of the cell's tiles that hold
+//     one of its pairs (exact binning: whose pixels its alpha >= 1/255 ellipse reaches), and
+//     the cell's tiles get their pair counts.
+//  5. tile_scan_kernel over the tiles: exclusive scan of the tile counts gives every tile's
+//     [start, end) and the number of pairs.
+//  6. cell_emit_kernel: one CTA per cell stages the cell's sorted list in shared memory and
+//     one warp per tile keeps, in order, the entries whose mask has the tile's bit: the tile's
+//     pairs, already sorted; they are written out as keys and values.
+// A record's cells are about a seventh of its tiles on the 180-degree workloads, so the sort
+// handles a seventh of the pairs, no per-pair atomic is issued, and the pairs are written once.
+// The number of valid pairs is read on the device, so nothing here needs a host sync.
 #include "fgs_internal.cuh"
 #include "scan.cuh"
 
@@ -34,208 +37,277 @@ namespace fgs {
 
 namespace {
 
-// The (record, tile) pairs of one EMIT_CHUNK-pair chunk per CTA iteration, in pair order.
-// The CTA loads the few records its chunk spans into shared memory and marks the first pair of
-// each; a max-scan over the chunk then gives every pair its record. SCATTER = false: count the
-// pairs of every tile (tile_ranges[2t]). SCATTER = true: claim a slot in the tile's bucket
-// (tile_ranges[2t + 1] holds the bucket's next free slot) and write the word
-// depth_bits << 32 | record there. Both passes visit the same pairs in the same way, so every
-// bucket is filled exactly. Pairs whose tile falls outside their view's grid (a malformed
-// caller record) are skipped by both.
-template <bool SCATTER, bool ELLIPSE>
-__global__ void __launch_bounds__(EMIT_THREADS)
-    pair_kernel(const fgs_record *__restrict__ rec, int64_t n_per_view, Views vs,
-                const uint32_t *__restrict__ vis_rec, const uint64_t *__restrict__ vis_off,
-                const uint32_t *__restrict__ chunk_first, const unsigned long long *n_cand,
-                const unsigned long long *n_vis, uint32_t *ranges, uint64_t *__restrict__ words,
-                int64_t capacity, uint32_t *status) {
-  constexpr int PER = EMIT_CHUNK / EMIT_THREADS;  // pairs per thread and chunk
-  __shared__ uint32_t s_off[EMIT_CHUNK + 1];   // first pair of the record (clamped to hi)
-  __shared__ uint32_t s_base[EMIT_CHUNK + 1];  // global tile id of the rect's corner (x0, y0)
-  __shared__ uint32_t s_geom[EMIT_CHUNK + 1];  // rect width | rect height << 16 (0: skip)
-  __shared__ uint32_t s_tx[EMIT_CHUNK + 1];    // the view's tiles_x
-  __shared__ uint32_t s_depth[EMIT_CHUNK + 1];
-  __shared__ uint32_t s_rec[EMIT_CHUNK + 1];
-  __shared__ uint16_t s_own[EMIT_CHUNK];       // record (window slot) owning each pair
-  __shared__ uint32_t s_wmax[EMIT_THREADS / 32];
-  // exact mode: mean, conic, q* and the rect corner of each record of the window
-  __shared__ float2 s_mu[ELLIPSE ? EMIT_CHUNK + 1 : 1];
-  __shared__ float4 s_con[ELLIPSE ? EMIT_CHUNK + 1 : 1];
-  __shared__ uint32_t s_rc[ELLIPSE ? EMIT_CHUNK + 1 : 1];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  if (binning_timed_out(status)) return;
-  const int64_t total = (int64_t)*n_cand;
-  if (!SCATTER && blockIdx.x == 0 && tid == 0 && total > capacity) set_status(status, ST_CAPACITY);
-  const int64_t n = min(total, capacity);
-  const int64_t nchunks = (n + EMIT_CHUNK - 1) / EMIT_CHUNK;
-  const int64_t nv = (int64_t)*n_vis;
+constexpr int REC_THREADS = 256;
+constexpr int REC_PER_THREAD = 4;
+constexpr int REC_BLOCK = REC_THREADS * REC_PER_THREAD;  // records per CTA of the cell walks
+constexpr int SMEM_CELLS = 4096;  // cell counters a CTA keeps in shared memory (else global)
+constexpr int CELL_CAP0 = 4096;   // cells of at most this many entries: the smaller sort class
 
-  for (int64_t ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
-    const int64_t lo = ck * EMIT_CHUNK;
-    const int64_t hi = min(lo + (int64_t)EMIT_CHUNK, n);
-    const int64_t v0 = chunk_first[ck];
-    const int64_t v1 = ck + 1 < nchunks ? (int64_t)chunk_first[ck + 1] : nv - 1;
-    // records spanned by the chunk: the owner of pair lo and at most EMIT_CHUNK more (the
-    // last chunk of a capacity-truncated emission may list more; they own no pair below hi)
-    const int nw = (int)min(v1 - v0 + 1, (int64_t)EMIT_CHUNK + 1);
-    // checked build: the chunk's records must lie in the compacted list (uniform per CTA)
-    if (FGS_CHECK && (v1 < v0 || !in_bounds((uint64_t)(v0 + nw - 1), (uint64_t)nv, status))) {
-      set_status(status, ST_BOUNDS);
-      continue;
-    }
-    __syncthreads();
-    for (int i = tid; i < EMIT_CHUNK; i += EMIT_THREADS) s_own[i] = 0;
-    __syncthreads();
-    for (int i = tid; i < nw; i += EMIT_THREADS) {
-      uint32_t r = vis_rec[v0 + i];
-      if (!in_bounds(r, (uint64_t)n_per_view * vs.n, status)) r = 0u;
-      const uint4 w2 = __ldg(reinterpret_cast<const uint4 *>(rec + r) + 2);
-      const uint32_t x0 = w2.z & 0xffffu, y0 = w2.z >> 16, x1 = w2.w & 0xffffu, y1 = w2.w >> 16;
-      const int v = (int)(r / (uint32_t)n_per_view);
-      const uint32_t tiles_x = (uint32_t)vs.v[v].tiles_x, tiles_y = (uint32_t)vs.v[v].tiles_y;
-      const bool ok = x0 <= x1 && y0 <= y1 && x1 < tiles_x && y1 < tiles_y;
-      const uint64_t off = vis_off[v0 + i];
-      s_off[i] = (uint32_t)min(off, (uint64_t)hi);
-      s_rec[i] = r;
-      s_base[i] = (uint32_t)vs.v[v].tile_offset + y0 * tiles_x + x0;
-      s_geom[i] = ok ? (x1 - x0 + 1u) | ((y1 - y0 + 1u) << 16) : 0u;
-      s_tx[i] = tiles_x;
-      s_depth[i] = w2.y;
-      if (ELLIPSE) {
-        const float4 w0 = __ldg(reinterpret_cast<const float4 *>(rec + r));
-        const float4 w1 = __ldg(reinterpret_cast<const float4 *>(rec + r) + 1);
-        s_mu[i] = make_float2(w0.x, w0.y);
-        s_con[i] = make_float4(w0.z, w0.w, w1.x, fmaxf(2.f * logf(255.f * w1.y), 0.f));
-        s_rc[i] = x0 | (y0 << 16);
-      }
-      if (i > 0 && off < (uint64_t)hi) s_own[off - (uint64_t)lo] = (uint16_t)i;
-    }
-    __syncthreads();
-    // inclusive max-scan of the marks: thread t owns slots [PER t, PER t + PER)
-    {
-      uint32_t m[PER];
-      uint32_t run = 0;
-#pragma unroll
-      for (int k = 0; k < PER; ++k) {
-        run = max(run, (uint32_t)s_own[tid * PER + k]);
-        m[k] = run;
-      }
-      uint32_t x = run;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) x = max(x, __shfl_up_sync(0xffffffffu, x, o) * (lane >= o));
-      if (lane == 31) s_wmax[wid] = x;
-      uint32_t before = __shfl_up_sync(0xffffffffu, x, 1) * (lane >= 1);
-      __syncthreads();
-      for (int ww = 0; ww < wid; ++ww) before = max(before, s_wmax[ww]);
-#pragma unroll
-      for (int k = 0; k < PER; ++k) s_own[tid * PER + k] = (uint16_t)max(m[k], before);
-    }
-    __syncthreads();
-    // each thread takes pairs tid, tid + 256, ... of the chunk: all their tiles first, then
-    // all their atomics, so that a thread has several atomics in flight
-    uint32_t tile[PER], owner[PER];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int64_t j = lo + tid + k * EMIT_THREADS;
-      tile[k] = 0xffffffffu;
-      owner[k] = 0u;
-      if (j < hi) {
-        const uint32_t a = s_own[j - lo];
-        const uint32_t geom = s_geom[a];
-        const uint32_t local = (uint32_t)(j - lo) + (uint32_t)lo - s_off[a];
-        const uint32_t w = geom & 0xffffu, h = geom >> 16;
-        if (w != 0u) {
-          // row inside the rect: float quotient (local < 2^22 is exact in FP32), corrected by one
-          uint32_t dy = (uint32_t)((float)local * rcp_approx((float)w));
-          if (dy * w > local) --dy;
-          if ((dy + 1u) * w <= local) ++dy;
-          const uint32_t dx = local - dy * w;
-          // more pairs than the rect holds (a malformed record): skipped
-          bool keep = dy < h && dx < w;
-          if (ELLIPSE && keep) {
-            const float2 mu = s_mu[a];
-            const float4 cq = s_con[a];
-            const uint32_t rc = s_rc[a];
-            const float xl = (float)(((rc & 0xffffu) + dx) * TILE) + 0.5f;
-            const float yl = (float)(((rc >> 16) + dy) * TILE) + 0.5f;
-            keep = ellipse_reaches_tile(mu.x, mu.y, cq.x, cq.y, cq.z, cq.w, xl, xl + (TILE - 1),
-                                        yl, yl + (TILE - 1));
-          }
-          if (keep) tile[k] = s_base[a] + dy * s_tx[a] + dx;
-        }
-        owner[k] = a;
-      }
-    }
-    if (!SCATTER) {
-#pragma unroll
-      for (int k = 0; k < PER; ++k)
-        if (tile[k] != 0xffffffffu) atomicAdd(&ranges[2 * (size_t)tile[k]], 1u);
-    } else {
-      uint32_t pos[PER];
-#pragma unroll
-      for (int k = 0; k < PER; ++k)
-        pos[k] = tile[k] != 0xffffffffu ? atomicAdd(&ranges[2 * (size_t)tile[k] + 1], 1u) : 0xffffffffu;
-      // checked build: with complete counts every claimed slot lies below the capacity
-      if (FGS_CHECK && total <= capacity) {
-#pragma unroll
-        for (int k = 0; k < PER; ++k)
-          if (tile[k] != 0xffffffffu) in_bounds(pos[k], (uint64_t)capacity, status);
-      }
-#pragma unroll
-      for (int k = 0; k < PER; ++k)
-        if (tile[k] != 0xffffffffu && (int64_t)pos[k] < capacity)
-          words[pos[k]] = ((uint64_t)s_depth[owner[k]] << 32) | (uint64_t)s_rec[owner[k]];
-    }
-  }
+// The pairs of one record: the first k = min(tiles_touched, w h) tiles of its w x h rect in
+// row-major order, i.e. fr full rows from row y0 and the first rem tiles of the next row.
+struct PairSet {
+  uint32_t x0, y0, x1;
+  uint32_t fr, rem;
+  uint32_t k;
+};
+
+// false for a record with no pairs (tiles_touched = 0, or a rect outside its view's grid)
+__device__ __forceinline__ bool pair_set(uint4 w2, uint32_t tt, const View &V, PairSet &P) {
+  const uint32_t x0 = w2.z & 0xffffu, y0 = w2.z >> 16, x1 = w2.w & 0xffffu, y1 = w2.w >> 16;
+  if (tt == 0u || !(x0 <= x1 && y0 <= y1 && x1 < (uint32_t)V.tiles_x && y1 < (uint32_t)V.tiles_y))
+    return false;
+  const uint32_t w = x1 - x0 + 1u, h = y1 - y0 + 1u;
+  P.k = (uint32_t)min((uint64_t)tt, (uint64_t)w * h);
+  P.x0 = x0; P.y0 = y0; P.x1 = x1;
+  P.fr = P.k / w;
+  P.rem = P.k - P.fr * w;
+  return true;
 }
 
-// In-place inclusive prefix sums of the difference grid, one warp per line: ROWS = true sums
-// along every view's tile rows, false along its columns (run after the rows). Sums are
-// modulo 2^32, so the negative differences need no sign.
-template <bool ROWS>
-__global__ void __launch_bounds__(256)
-    grid_scan_kernel(Views vs, int64_t n_lines, uint32_t *ranges,
-                     const unsigned long long *n_cand, int64_t capacity,
-                     const uint32_t *status) {
-  if ((int64_t)*n_cand > capacity || binning_timed_out(status)) return;
+// The cells holding at least one of a record's pairs, numbered: first the cells of the full
+// rows (cols x rows, row-major from (cx0, cy0)), then the cells of the partial row (row cyB,
+// colsB cells from cx0) that the full rows' cells do not already cover. Each holds a pair, so
+// a record has at most as many cells as pairs.
+struct CellSet {
+  uint32_t cx0, cy0, cols, rows;
+  uint32_t cyB, colsB;
+  uint32_t n;
+};
+
+__device__ __forceinline__ CellSet cell_set(const PairSet &P) {
+  CellSet S;
+  S.cx0 = P.x0 / CELL;
+  S.cy0 = P.y0 / CELL;
+  S.cols = P.x1 / CELL - S.cx0 + 1u;
+  uint32_t last = 0xffffffffu;
+  S.rows = 0u;
+  if (P.fr > 0u) {
+    last = (P.y0 + P.fr - 1u) / CELL;
+    S.rows = last - S.cy0 + 1u;
+  }
+  S.cyB = (P.y0 + P.fr) / CELL;
+  S.colsB = P.rem > 0u && S.cyB != last ? (P.x0 + P.rem - 1u) / CELL - S.cx0 + 1u : 0u;
+  S.n = S.cols * S.rows + S.colsB;
+  return S;
+}
+
+// Walks the cells of 32 consecutive records [r0, r0 + 32) with one warp: lane l loads record
+// r0 + l, the warp numbers all their cells in record order and takes them 32 at a time, lane l
+// calling f(record, view, depth bits, cx, cy) for cell e0 + l. Every lane does the same work
+// however the cells are spread over the records.
+template <class F>
+__device__ __forceinline__ void warp_cells(const fgs_record *__restrict__ rec,
+                                           const uint32_t *__restrict__ tt, int64_t r0, int64_t R,
+                                           int64_t n_per_view, const Views &vs, F f) {
   const int lane = threadIdx.x & 31;
-  int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (g >= n_lines) return;
-  int v = 0;
-  for (; v < vs.n - 1; ++v) {
-    const int64_t lines = ROWS ? vs.v[v].tiles_y : vs.v[v].tiles_x;
-    if (g < lines) break;
-    g -= lines;
-  }
-  const View &V = vs.v[v];
-  const int64_t len = ROWS ? V.tiles_x : V.tiles_y;
-  const int64_t step = ROWS ? 2 : 2 * (int64_t)V.tiles_x;  // words between consecutive entries
-  uint32_t *p = ranges + 2 * (V.tile_offset + (ROWS ? g * V.tiles_x : g));
-  uint32_t carry = 0u;
-  for (int64_t c = 0; c < len; c += 32) {
-    const int64_t j = c + lane;
-    uint32_t x = j < len ? p[j * step] : 0u;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+  const int64_t r = r0 + lane;
+  CellSet S{};
+  int view = 0;
+  uint32_t depth = 0u;
+  if (r < R) {
+    const uint32_t t = tt[r];
+    if (t != 0u) {
+      view = (int)(r / n_per_view);
+      const uint4 w2 = __ldg(reinterpret_cast<const uint4 *>(rec + r) + 2);
+      PairSet P;
+      if (pair_set(w2, t, vs.v[view], P)) {
+        S = cell_set(P);
+        depth = w2.y;
+      }
     }
-    x += carry;
-    if (j < len) p[j * step] = x;
-    carry = __shfl_sync(0xffffffffu, x, 31);
+  }
+  uint32_t incl = S.n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  const uint32_t first = incl - S.n;
+  for (uint32_t e0 = 0; e0 < total; e0 += 32u) {
+    const uint32_t e = e0 + (uint32_t)lane;
+    // owner: the number of lanes whose cells all come before e
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const uint32_t v = __shfl_sync(0xffffffffu, incl, j + step - 1);
+      if (v <= e) j += step;
+    }
+    const uint32_t i = e - __shfl_sync(0xffffffffu, first, j);
+    const uint32_t cx0 = __shfl_sync(0xffffffffu, S.cx0, j);
+    const uint32_t cy0 = __shfl_sync(0xffffffffu, S.cy0, j);
+    const uint32_t cols = __shfl_sync(0xffffffffu, S.cols, j);
+    const uint32_t rows = __shfl_sync(0xffffffffu, S.rows, j);
+    const uint32_t cyB = __shfl_sync(0xffffffffu, S.cyB, j);
+    const int vj = __shfl_sync(0xffffffffu, view, j);
+    const uint32_t dj = __shfl_sync(0xffffffffu, depth, j);
+    if (e < total) {
+      const uint32_t nb = cols * rows;
+      uint32_t cx, cy;
+      if (i < nb) {
+        const uint32_t q = i / cols;
+        cy = cy0 + q;
+        cx = cx0 + (i - q * cols);
+      } else {
+        cy = cyB;
+        cx = cx0 + (i - nb);
+      }
+      f(r0 + j, vj, dj, cx, cy);
+    }
   }
 }
 
-// Exclusive scan of the per-tile pair counts (tile_ranges[2t], written by the counting pass)
-// over all tiles in global tile order, with decoupled look-back over partitions of TSCAN_PART
-// tiles. Writes tile_ranges[t] = (start, start) for every non-empty tile (the second word is
-// the scatter's cursor and ends as the tile's end) and appends the tile to the list of its
-// segment-size class; empty tiles keep (0, 0). It runs even after the record scan gave up (its
-// counts are then all zero), so that every partition publishes and no wait of its own look-back
-// depends on a partition that left early.
+// Bits lo - b .. hi - b of [lo, hi] clipped to the cell span [b, b + CELL) (0 if disjoint).
+__device__ __forceinline__ uint32_t span_bits(uint32_t lo, uint32_t hi, uint32_t b) {
+  const uint32_t l = max(lo, b), h = min(hi, b + (CELL - 1));
+  return l <= h ? (2u << (h - b)) - (1u << (l - b)) : 0u;
+}
+
+// The record's pairs inside the cell whose first tile is (bx, by): bit ly * CELL + lx for
+// the tile (bx + lx, by + ly).
+__device__ __forceinline__ uint32_t cell_mask(const PairSet &P, uint32_t bx, uint32_t by) {
+  uint32_t m = 0u;
+  if (P.fr > 0u) {
+    const uint32_t cols = span_bits(P.x0, P.x1, bx);
+    const uint32_t rows = span_bits(P.y0, P.y0 + P.fr - 1u, by);
+#pragma unroll
+    for (int ly = 0; ly < CELL; ++ly)
+      if ((rows >> ly) & 1u) m |= cols << (CELL * ly);
+  }
+  if (P.rem > 0u) {
+    const uint32_t y = P.y0 + P.fr;
+    if (y >= by && y < by + CELL) m |= span_bits(P.x0, P.x0 + P.rem - 1u, bx) << (CELL * (y - by));
+  }
+  return m;
+}
+
+__device__ __forceinline__ int64_t cell_id(const View &V, uint32_t cx, uint32_t cy) {
+  return V.cell_offset + (int64_t)cy * V.cells_x + cx;
+}
+
+// Step 1. Per-cell entry counts (cell_ranges[2c]), rect pairs (*n_cand) and visible records.
+__global__ void __launch_bounds__(REC_THREADS)
+    cell_count_kernel(const fgs_record *__restrict__ rec, const uint32_t *__restrict__ tt,
+                      int64_t R, int64_t n_per_view, Views vs, int64_t capacity,
+                      uint32_t *cell_ranges, unsigned long long *n_cand,
+                      unsigned long long *n_vis, uint32_t *status) {
+  __shared__ uint32_t s_cnt[SMEM_CELLS];
+  __shared__ unsigned long long s_sum[2];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const bool in_smem = vs.total_cells <= SMEM_CELLS;
+  if (FGS_CHECK && blockIdx.x == 0 && tid == 0) {  // the rasterizers' index bounds
+    WsHeader *h = reinterpret_cast<WsHeader *>(status);
+    h->bounds_records = (uint32_t)R;
+    h->bounds_pairs = (uint32_t)capacity;
+    h->bounds_magic = BOUNDS_MAGIC;
+  }
+  if (in_smem)
+    for (int c = tid; c < (int)vs.total_cells; c += REC_THREADS) s_cnt[c] = 0u;
+  if (tid < 2) s_sum[tid] = 0ull;
+  __syncthreads();
+  unsigned long long pairs = 0, vis = 0;
+  const int64_t base = (int64_t)blockIdx.x * REC_BLOCK;
+  // pairs and visible records, one record per thread
+  for (int i = 0; i < REC_PER_THREAD; ++i) {
+    const int64_t r = base + (int64_t)(i * (REC_THREADS / 32) + wid) * 32 + lane;
+    if (r >= R) break;
+    const uint32_t t = tt[r];
+    if (t == 0u) continue;
+    PairSet P;
+    if (!pair_set(__ldg(reinterpret_cast<const uint4 *>(rec + r) + 2), t,
+                  vs.v[(int)(r / n_per_view)], P))
+      continue;
+    pairs += P.k;
+    ++vis;
+  }
+  // cells, 32 records per warp walk
+  for (int i = 0; i < REC_PER_THREAD; ++i) {
+    const int64_t r0 = base + (int64_t)(i * (REC_THREADS / 32) + wid) * 32;
+    if (r0 >= R) break;
+    warp_cells(rec, tt, r0, R, n_per_view, vs, [&](int64_t, int v, uint32_t, uint32_t cx, uint32_t cy) {
+      const int64_t c = cell_id(vs.v[v], cx, cy);
+      if (in_smem) atomicAdd(&s_cnt[c], 1u);
+      else atomicAdd(&cell_ranges[2 * c], 1u);
+    });
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+    vis += __shfl_xor_sync(0xffffffffu, vis, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&s_sum[0], pairs);
+    atomicAdd(&s_sum[1], vis);
+  }
+  __syncthreads();
+  if (in_smem)
+    for (int c = tid; c < (int)vs.total_cells; c += REC_THREADS)
+      if (s_cnt[c]) atomicAdd(&cell_ranges[2 * c], s_cnt[c]);
+  if (tid == 0) {
+    if (s_sum[0]) atomicAdd(n_cand, s_sum[0]);
+    if (s_sum[1]) atomicAdd(n_vis, s_sum[1]);
+  }
+}
+
+// Step 3. Writes depth bits << 32 | record into every cell of every record (cell_ranges[2c + 1]
+// holds the cell's next free slot, set to its start by the cell scan). With the cell counters
+// in shared memory a CTA counts its entries per cell, claims a block of slots per cell with one
+// global atomic, and hands the slots out in shared memory; the order inside a cell is
+// irrelevant (the cell is sorted next).
+__global__ void __launch_bounds__(REC_THREADS)
+    cell_scatter_kernel(const fgs_record *__restrict__ rec, const uint32_t *__restrict__ tt,
+                        int64_t R, int64_t n_per_view, Views vs, uint32_t *cell_ranges,
+                        uint64_t *__restrict__ words, const unsigned long long *n_cand,
+                        int64_t capacity, uint32_t *status) {
+  __shared__ uint32_t s_cnt[SMEM_CELLS];
+  if (binning_timed_out(status) || (int64_t)*n_cand > capacity) return;
+  const int tid = threadIdx.x, wid = tid >> 5;
+  const bool in_smem = vs.total_cells <= SMEM_CELLS;
+  const int64_t base = (int64_t)blockIdx.x * REC_BLOCK;
+  if (in_smem) {
+    for (int c = tid; c < (int)vs.total_cells; c += REC_THREADS) s_cnt[c] = 0u;
+    __syncthreads();
+    for (int i = 0; i < REC_PER_THREAD; ++i) {
+      const int64_t r0 = base + (int64_t)(i * (REC_THREADS / 32) + wid) * 32;
+      if (r0 >= R) break;
+      warp_cells(rec, tt, r0, R, n_per_view, vs, [&](int64_t, int v, uint32_t, uint32_t cx, uint32_t cy) {
+        atomicAdd(&s_cnt[cell_id(vs.v[v], cx, cy)], 1u);
+      });
+    }
+    __syncthreads();
+    // the block's slots of each cell; s_cnt then holds the next one to hand out
+    for (int c = tid; c < (int)vs.total_cells; c += REC_THREADS)
+      if (s_cnt[c]) s_cnt[c] = atomicAdd(&cell_ranges[2 * c + 1], s_cnt[c]);
+    __syncthreads();
+  }
+  for (int i = 0; i < REC_PER_THREAD; ++i) {
+    const int64_t r0 = base + (int64_t)(i * (REC_THREADS / 32) + wid) * 32;
+    if (r0 >= R) break;
+    warp_cells(rec, tt, r0, R, n_per_view, vs, [&](int64_t r, int v, uint32_t depth, uint32_t cx, uint32_t cy) {
+      const int64_t c = cell_id(vs.v[v], cx, cy);
+      const uint32_t slot = in_smem ? atomicAdd(&s_cnt[c], 1u) : atomicAdd(&cell_ranges[2 * c + 1], 1u);
+      // a record's cells never outnumber its pairs, so the entries fit the capacity (checked
+      // build: verified)
+      if (in_bounds(slot, (uint64_t)capacity, status) && (int64_t)slot < capacity)
+        words[slot] = ((uint64_t)depth << 32) | (uint64_t)r;
+    });
+  }
+}
+
+// Steps 2 and 5. Exclusive scan of per-segment counts (ranges[2s], s a cell or a tile) in
+// segment order, with decoupled look-back over partitions of TSCAN_PART segments.
+// Cells (FINAL = false): writes ranges[s] = (start, start) for every non-empty cell (the second
+// word is the scatter's cursor and ends as the cell's end) and appends the cell to the list of
+// its size class (at most cls_cap entries: class 0). Tiles (FINAL = true): writes
+// ranges[s] = (start, end) for every non-empty tile and the number of pairs to *n_int (the rect
+// count instead when it exceeds the capacity, so the caller can grow the buffers). Empty
+// segments keep (0, 0). It runs even after a look-back of the binning gave up (its counts are
+// then all zero), so that every partition publishes and no wait of its own look-back depends on
+// a partition that left early.
+template <bool FINAL>
 __global__ void __launch_bounds__(256)
-    tile_scan_kernel(uint32_t *ranges, int64_t total_tiles, uint64_t *lb,
-                     uint32_t *part_counter, uint32_t *lists, uint32_t *seg_count,
+    tile_scan_kernel(uint32_t *ranges, int64_t total, uint64_t *lb, uint32_t *part_counter,
+                     uint32_t *lists, uint32_t *seg_count, uint32_t cls_cap,
                      const unsigned long long *n_cand, int64_t capacity, int64_t *n_int,
                      uint32_t *status, uint32_t wait_limit) {
   __shared__ uint32_t s_warp[8];
@@ -248,8 +320,8 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   const int64_t part = s_part;
   const int64_t base = part * TSCAN_PART;
-  // with more candidates than capacity the counts are not complete: read them as zero, and
-  // report the overflow (the caller grows the buffers from the candidate count)
+  // with more rect pairs than capacity nothing was binned: read the counts as zero, and report
+  // the overflow (the caller grows the buffers from the pair count)
   const bool counts_ok = (int64_t)*n_cand <= capacity;
   if (!counts_ok && part == 0 && tid == 0) set_status(status, ST_CAPACITY);
   constexpr int ITEMS = TSCAN_PART / 256;
@@ -257,8 +329,8 @@ __global__ void __launch_bounds__(256)
   uint32_t sum = 0;
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
-    const int64_t t = base + tid * ITEMS + k;
-    c[k] = t < total_tiles && counts_ok ? ranges[2 * t] : 0u;
+    const int64_t s = base + tid * ITEMS + k;
+    c[k] = s < total && counts_ok ? ranges[2 * s] : 0u;
     sum += c[k];
   }
   uint32_t agg;
@@ -273,40 +345,40 @@ __global__ void __launch_bounds__(256)
       st_volatile_u64(lb + part, LB_INC | (prefix + agg));
     }
     s_prefix = prefix;
-    // the pairs kept (fewer than the candidates in the exact mode); with more candidates than
-    // capacity the candidate count stays, so the caller can grow the buffers
-    if (base + TSCAN_PART >= total_tiles && (int64_t)*n_cand <= capacity)
-      *n_int = (int64_t)(prefix + agg);
+    if (FINAL && base + TSCAN_PART >= total)
+      *n_int = (int64_t)*n_cand <= capacity ? (int64_t)(prefix + agg) : (int64_t)*n_cand;
   }
-  // class ranks inside the CTA (order within a class list is irrelevant)
   uint32_t cls_rank[ITEMS];
+  if (!FINAL) {  // class ranks inside the CTA (order within a class list is irrelevant)
 #pragma unroll
-  for (int k = 0; k < ITEMS; ++k) {
-    const int cls = c[k] <= (uint32_t)SEG_CAP0 ? 0 : 1;
-    cls_rank[k] = c[k] > 0u ? atomicAdd(&s_cls[cls], 1u) : 0u;
+    for (int k = 0; k < ITEMS; ++k) {
+      const int cls = c[k] <= cls_cap ? 0 : 1;
+      cls_rank[k] = c[k] > 0u ? atomicAdd(&s_cls[cls], 1u) : 0u;
+    }
   }
   __syncthreads();
-  if (tid < 2) s_cls_base[tid] = s_cls[tid] ? atomicAdd(&seg_count[tid], s_cls[tid]) : 0u;
+  if (!FINAL && tid < 2) s_cls_base[tid] = s_cls[tid] ? atomicAdd(&seg_count[tid], s_cls[tid]) : 0u;
   __syncthreads();
   uint64_t o = s_prefix + off;
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
-    const int64_t t = base + tid * ITEMS + k;
+    const int64_t s = base + tid * ITEMS + k;
     if (c[k] > 0u) {
-      ranges[2 * t] = (uint32_t)o;
-      ranges[2 * t + 1] = (uint32_t)o;
-      const int cls = c[k] <= (uint32_t)SEG_CAP0 ? 0 : 1;
-      lists[(size_t)cls * (size_t)total_tiles + s_cls_base[cls] + cls_rank[k]] = (uint32_t)t;
+      ranges[2 * s] = (uint32_t)o;
+      ranges[2 * s + 1] = (uint32_t)(FINAL ? o + c[k] : o);
+      if (!FINAL) {
+        const int cls = c[k] <= cls_cap ? 0 : 1;
+        lists[(size_t)cls * (size_t)total + s_cls_base[cls] + cls_rank[k]] = (uint32_t)s;
+      }
     }
     o += c[k];
   }
 }
 
-// ------------------------------------------------------------------------------------------
-// Per-tile segment sort. A tile's bucket holds its words depth_bits << 32 | record in
-// arbitrary order; sorting the words as 64-bit integers orders them by depth and breaks depth
-// ties by record index, which is the order a stable sort of the keys (tile << 32 | depth) in
-// emission order gives. LSD radix passes over 8-bit digits, skipping digits that are equal in
+// Segment sort. A cell's list holds its words depth_bits << 32 | record in arbitrary order;
+// sorting the words as 64-bit integers orders them by depth and breaks depth ties by record
+// index, which is the order a stable sort of the keys (tile << 32 | depth) in emission order
+// gives inside every tile. LSD radix passes over 8-bit digits, skipping digits that are equal in
 // every word of the segment. A first attempt sorts the depth digits only; only a segment that
 // then shows two equal depths is sorted again over all digits.
 //
@@ -442,11 +514,11 @@ __device__ __forceinline__ void smem_pass(SegSmem<NT, CAP> &S, uint64_t (&x)[IPT
   }
 }
 
-// Sort one segment of cnt <= NT * IPT words in shared memory and write keys / values.
+// Sort one segment of cnt <= NT * IPT words in shared memory and write them to out (which
+// may be src: everything is read before the first write).
 template <int NT, int IPT, int CAP>
 __device__ __forceinline__ void sort_segment_smem(SegSmem<NT, CAP> &S, const uint64_t *src,
-                                                  uint32_t cnt, uint64_t tile,
-                                                  uint64_t *kout, uint32_t *vout) {
+                                                  uint32_t cnt, uint64_t *out) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   // the lane masks share storage with the bucket sort's counters: clear them first
   for (int e = threadIdx.x; e < (NT / 32) * 256; e += NT) (&S.rx.wmask[0][0])[e] = 0u;
@@ -480,11 +552,7 @@ __device__ __forceinline__ void sort_segment_smem(SegSmem<NT, CAP> &S, const uin
     for (int p = 0; p < 8; ++p)
       if ((varying >> (8 * p)) & 255u) smem_pass<NT, IPT, CAP>(S, x, cnt, 8 * p);
   }
-  for (uint32_t i = threadIdx.x; i < cnt; i += NT) {
-    const uint64_t v = S.buf[i];
-    kout[i] = (tile << 32) | (v >> 32);
-    vout[i] = (uint32_t)v;
-  }
+  for (uint32_t i = threadIdx.x; i < cnt; i += NT) out[i] = S.buf[i];
   __syncthreads();  // buf reused by the next segment
 }
 
@@ -501,8 +569,7 @@ constexpr uint32_t BUCKET_KMAX = 32;
 
 template <int NT, int IPT, int CAP>
 __device__ __forceinline__ bool bucket_sort_segment(SegSmem<NT, CAP> &S, const uint64_t *src,
-                                                    uint32_t cnt, uint64_t tile,
-                                                    uint64_t *kout, uint32_t *vout) {
+                                                    uint32_t cnt, uint64_t *out) {
   static_assert(NT * IPT <= CAP, "capacity");
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   // NB sub-buckets: CAP for the small class (fixed, so the counter loops unroll), else the
@@ -641,23 +708,19 @@ __device__ __forceinline__ bool bucket_sort_segment(SegSmem<NT, CAP> &S, const u
     if (li < cnt) S.buf[bs[k]] = x[k];
   }
   __syncthreads();
-  for (uint32_t i = tid; i < cnt; i += NT) {
-    const uint64_t v = S.buf[i];
-    kout[i] = (tile << 32) | (v >> 32);
-    vout[i] = (uint32_t)v;
-  }
+  for (uint32_t i = tid; i < cnt; i += NT) out[i] = S.buf[i];
   __syncthreads();  // buf and counters reused by the next segment
   return true;
 }
 
 // Sort one segment longer than NT * IPT through global memory: per digit, a histogram pass
 // over the segment, then the segment in chunks of NT * IPT words in order, each ranked in
-// shared memory and scattered to its place in the other buffer (words <-> the key output,
-// which serves as scratch). All digits with varying bits are sorted. The last step turns the
-// words into keys and values wherever the data ended (in place if that is the key output).
+// shared memory and scattered to its place in the other buffer (words <-> scratch). All digits
+// with varying bits are sorted. The last step copies the words back to `words` if they ended in
+// the scratch buffer.
 template <int NT, int IPT, int CAP>
-__device__ __noinline__ void sort_segment_chunked(SegSmem<NT, CAP> &S, uint64_t *words, uint32_t cnt,
-                                     uint64_t tile, uint64_t *kout, uint32_t *vout) {
+__device__ __noinline__ void sort_segment_chunked(SegSmem<NT, CAP> &S, uint64_t *words,
+                                                  uint32_t cnt, uint64_t *scratch) {
   constexpr uint32_t CH = NT * IPT;  // words per chunk
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   for (int e = tid; e < (NT / 32) * 256; e += NT) (&S.rx.wmask[0][0])[e] = 0u;
@@ -669,7 +732,7 @@ __device__ __noinline__ void sort_segment_chunked(SegSmem<NT, CAP> &S, uint64_t 
   }
   block_and_or<NT, IPT, CAP>(S, a, o);
   const uint64_t varying = a ^ o;
-  uint64_t *src = words, *dst = kout;
+  uint64_t *src = words, *dst = scratch;
   for (int p = 0; p < 8; ++p) {
     if (((varying >> (8 * p)) & 255u) == 0u) continue;
     const int shift = 8 * p;
@@ -727,91 +790,236 @@ __device__ __noinline__ void sort_segment_chunked(SegSmem<NT, CAP> &S, uint64_t 
     src = dst;
     dst = t;
   }
-  for (uint32_t i = tid; i < cnt; i += NT) {
-    const uint64_t v = src[i];
-    kout[i] = (tile << 32) | (v >> 32);
-    vout[i] = (uint32_t)v;
-  }
+  if (src != words)
+    for (uint32_t i = tid; i < cnt; i += NT) words[i] = src[i];
   __syncthreads();
 }
 
-// One CTA per listed tile of a size class, persistent over the class list.
-// The radix path kept out of line for the large class, where inlining it would raise the
+// The radix path kept out of line for the large classes, where inlining it would raise the
 // register needs of the bucket sort that every segment takes first.
 template <int NT, int IPT, int CAP>
 __device__ __noinline__ void sort_segment_smem_outlined(SegSmem<NT, CAP> &S, const uint64_t *src,
-                                                        uint32_t cnt, uint64_t tile,
-                                                        uint64_t *kout, uint32_t *vout) {
-  sort_segment_smem<NT, IPT, CAP>(S, src, cnt, tile, kout, vout);
+                                                        uint32_t cnt, uint64_t *out) {
+  sort_segment_smem<NT, IPT, CAP>(S, src, cnt, out);
 }
 
 // Sort one segment of cnt <= NT * IPT words in shared memory: the bucket sort, or the radix
 // passes if the bucket sort declines.
 template <int NT, int IPT, int CAP>
-__device__ __forceinline__ void sort_segment(SegSmem<NT, CAP> &S, uint64_t *words, uint32_t cnt,
-                                             uint64_t tile, uint64_t *kout, uint32_t *vout) {
-  if (bucket_sort_segment<NT, IPT, CAP>(S, words, cnt, tile, kout, vout)) return;
+__device__ __forceinline__ void sort_segment(SegSmem<NT, CAP> &S, uint64_t *words, uint32_t cnt) {
+  if (bucket_sort_segment<NT, IPT, CAP>(S, words, cnt, words)) return;
   if constexpr (CAP <= SEG_CAP0)
-    sort_segment_smem<NT, IPT, CAP>(S, words, cnt, tile, kout, vout);
+    sort_segment_smem<NT, IPT, CAP>(S, words, cnt, words);
   else
-    sort_segment_smem_outlined<NT, IPT, CAP>(S, words, cnt, tile, kout, vout);
+    sort_segment_smem_outlined<NT, IPT, CAP>(S, words, cnt, words);
 }
 
-// One CTA per listed tile of a size class, persistent over the class list. The number of words
-// per thread is picked per segment (the smallest of IPT_LO, 2 IPT_LO, ... that holds it), so a
-// segment costs in proportion to its own length, not the class's largest.
-template <int NT, int IPT_LO, int CAP, int MIN_BLOCKS, bool CHUNKED>
+// Step 4. One CTA per listed cell of a size class, persistent over the class list: sorts the
+// cell's words in place (the number of words per thread picked per cell, the smallest of IPT_LO
+// and 2 IPT_LO that holds it; cells longer than CAP sorted in chunks through the scratch
+// buffer), then writes each entry's tile mask and the pair count of each of the cell's tiles
+// (tile_ranges[2t]). The mask is exactly the entry's pairs in the cell; in the exact mode the
+// tiles its ellipse does not reach are taken out.
+template <int NT, int IPT_LO, int CAP, int MIN_BLOCKS, bool CHUNKED, bool ELLIPSE>
 __global__ void __launch_bounds__(NT, MIN_BLOCKS)
-    segsort_kernel(const uint32_t *__restrict__ list, const uint32_t *list_count,
-                   const uint32_t *__restrict__ ranges, uint64_t *words, uint64_t *keys,
-                   uint32_t *vals, int64_t capacity, int64_t total_tiles, uint32_t *status) {
+    cell_sort_kernel(const uint32_t *__restrict__ list, const uint32_t *list_count,
+                     const uint32_t *__restrict__ cell_ranges, uint64_t *words,
+                     uint16_t *__restrict__ masks, uint64_t *scratch, int64_t capacity,
+                     const fgs_record *__restrict__ rec, const uint32_t *__restrict__ tt,
+                     int64_t n_per_view, Views vs, uint32_t *tile_ranges,
+                     const unsigned long long *n_cand, uint32_t *status) {
   static_assert(NT * IPT_LO * 2 == CAP, "two word counts per class");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SegSmem<NT, CAP> &S = *reinterpret_cast<SegSmem<NT, CAP> *>(smem_raw);
-  if (binning_timed_out(status)) return;
+  __shared__ uint32_t s_cnt[NT / 32][CELL * CELL];
+  if (binning_timed_out(status) || (int64_t)*n_cand > capacity) return;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint64_t R = (uint64_t)n_per_view * vs.n;
   uint32_t count = *list_count;
-  if (!in_bounds(count, (uint64_t)total_tiles + 1u, status)) count = 0u;
+  if (!in_bounds(count, (uint64_t)vs.total_cells + 1u, status)) count = 0u;
   for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
-    const uint32_t t = __ldg(list + i);
-    if (!in_bounds(t, (uint64_t)total_tiles, status)) continue;
-    const uint2 rg = __ldg(reinterpret_cast<const uint2 *>(ranges) + t);
-    // bounds of a bucket that a device-side error left inconsistent: skip it (a listed tile is
-    // never empty, so the checked build reports it)
+    const uint32_t c = __ldg(list + i);
+    if (!in_bounds(c, (uint64_t)vs.total_cells, status)) continue;
+    const uint2 rg = __ldg(reinterpret_cast<const uint2 *>(cell_ranges) + c);
+    // a listed cell is never empty; bounds that a device-side error left inconsistent: skip
     if (rg.y <= rg.x || (int64_t)rg.y > capacity) {
       if (FGS_CHECK) set_status(status, ST_BOUNDS);
       continue;
     }
     const uint32_t cnt = rg.y - rg.x;
-    if (cnt <= (uint32_t)(NT * IPT_LO))
-      sort_segment<NT, IPT_LO, CAP>(S, words + rg.x, cnt, t, keys + rg.x, vals + rg.x);
-    else if (cnt <= (uint32_t)CAP)
-      sort_segment<NT, 2 * IPT_LO, CAP>(S, words + rg.x, cnt, t, keys + rg.x, vals + rg.x);
-    else if (CHUNKED)
-      sort_segment_chunked<NT, 2 * IPT_LO, CAP>(S, words + rg.x, cnt, t, keys + rg.x, vals + rg.x);
-    else if (FGS_CHECK)
-      set_status(status, ST_BOUNDS);  // a long segment listed in the short class
+    uint64_t *cw = words + rg.x;
+    if (cnt <= (uint32_t)(NT * IPT_LO)) {
+      sort_segment<NT, IPT_LO, CAP>(S, cw, cnt);
+    } else if (cnt <= (uint32_t)CAP) {
+      sort_segment<NT, 2 * IPT_LO, CAP>(S, cw, cnt);
+    } else if (CHUNKED) {
+      sort_segment_chunked<NT, 2 * IPT_LO, CAP>(S, cw, cnt, scratch + rg.x);
+    } else {
+      if (FGS_CHECK) set_status(status, ST_BOUNDS);  // a long cell listed in the short class
+      continue;
+    }
+    // masks: the sorted words are in shared memory (cells of at most CAP words) or, sorted in
+    // chunks, back in `words` (written by this CTA before the sort's last barrier: plain loads).
+    // Four words per thread per step, their records' loads issued together; the tile counts
+    // are summed by warp ballots.
+    const View &V = vs.v[view_of_cell(vs, c)];
+    const int64_t local = (int64_t)c - V.cell_offset;
+    const uint32_t cy = (uint32_t)(local / V.cells_x);
+    const uint32_t bx = (uint32_t)(local - (int64_t)cy * V.cells_x) * CELL, by = cy * CELL;
+    const bool in_smem = cnt <= (uint32_t)CAP;
+    uint32_t acc[CELL * CELL];
+#pragma unroll
+    for (int b = 0; b < CELL * CELL; ++b) acc[b] = 0u;
+    for (uint32_t j0 = 0; j0 < cnt; j0 += 4u * NT) {
+      uint32_t r[4];
+      uint4 g2[4];
+      uint32_t t4[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t j = j0 + (uint32_t)(q * NT + tid);
+        r[q] = 0xffffffffu;
+        if (j < cnt) {
+          r[q] = (uint32_t)(in_smem ? S.buf[j] : cw[j]);
+          if (!in_bounds(r[q], R, status)) r[q] = 0u;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (r[q] != 0xffffffffu) {
+          g2[q] = __ldg(reinterpret_cast<const uint4 *>(rec + r[q]) + 2);
+          t4[q] = __ldg(tt + r[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t m = 0u;
+        if (r[q] != 0xffffffffu) {
+          PairSet P;
+          m = pair_set(g2[q], t4[q], V, P) ? cell_mask(P, bx, by) : 0u;
+          if (ELLIPSE && m) {
+            const float4 w0 = __ldg(reinterpret_cast<const float4 *>(rec + r[q]));
+            const float4 w1 = __ldg(reinterpret_cast<const float4 *>(rec + r[q]) + 1);
+            const float qs = fmaxf(2.f * logf(255.f * w1.y), 0.f);
+            for (uint32_t rest = m; rest; rest &= rest - 1u) {
+              const uint32_t b = __ffs(rest) - 1;
+              const float xl = (float)((bx + b % CELL) * TILE) + 0.5f;
+              const float yl = (float)((by + b / CELL) * TILE) + 0.5f;
+              if (!ellipse_reaches_tile(w0.x, w0.y, w0.z, w0.w, w1.x, qs, xl, xl + (TILE - 1),
+                                        yl, yl + (TILE - 1)))
+                m &= ~(1u << b);
+            }
+          }
+          masks[rg.x + j0 + (uint32_t)(q * NT + tid)] = (uint16_t)m;
+        }
+#pragma unroll
+        for (int b = 0; b < CELL * CELL; ++b) acc[b] += __popc(__ballot_sync(0xffffffffu, (m >> b) & 1u));
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int b = 0; b < CELL * CELL; ++b) s_cnt[wid][b] = acc[b];
+    }
+    __syncthreads();
+    if (tid < CELL * CELL) {
+      uint32_t tot = 0;
+#pragma unroll
+      for (int w = 0; w < NT / 32; ++w) tot += s_cnt[w][tid];
+      const uint32_t tx = bx + tid % CELL, ty = by + tid / CELL;
+      if (tx < (uint32_t)V.tiles_x && ty < (uint32_t)V.tiles_y)
+        tile_ranges[2 * (V.tile_offset + (int64_t)ty * V.tiles_x + tx)] = tot;
+    }
+    __syncthreads();
   }
 }
 
-template <int NT, int IPT_LO, int CAP, int MIN_BLOCKS, bool CHUNKED>
-cudaError_t launch_segsort(const uint32_t *list, const uint32_t *list_count,
-                           const uint32_t *ranges, uint64_t *words, uint64_t *keys,
-                           uint32_t *vals, int64_t capacity, int64_t total_tiles,
-                           uint32_t *status, cudaStream_t st) {
+template <int NT, int IPT_LO, int CAP, int MIN_BLOCKS, bool CHUNKED, bool ELLIPSE>
+cudaError_t launch_cell_sort(const uint32_t *list, const uint32_t *list_count,
+                             const uint32_t *cell_ranges, uint64_t *words, uint16_t *masks,
+                             uint64_t *scratch, int64_t capacity, const fgs_record *rec,
+                             const uint32_t *tt, int64_t n_per_view, const Views &vs,
+                             uint32_t *tile_ranges, const unsigned long long *n_cand,
+                             uint32_t *status, cudaStream_t st) {
+  auto kernel = cell_sort_kernel<NT, IPT_LO, CAP, MIN_BLOCKS, CHUNKED, ELLIPSE>;
   constexpr size_t smem = sizeof(SegSmem<NT, CAP>);
   static int occ = 0;
   if (occ == 0) {
-    cudaError_t e = cudaFuncSetAttribute(segsort_kernel<NT, IPT_LO, CAP, MIN_BLOCKS, CHUNKED>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int a = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &a, segsort_kernel<NT, IPT_LO, CAP, MIN_BLOCKS, CHUNKED>, NT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, kernel, NT, smem);
     occ = a > 0 ? a : 1;
   }
-  segsort_kernel<NT, IPT_LO, CAP, MIN_BLOCKS, CHUNKED><<<(unsigned)(sm_count() * occ), NT, smem, st>>>(
-      list, list_count, ranges, words, keys, vals, capacity, total_tiles, status);
+  kernel<<<(unsigned)(sm_count() * occ), NT, smem, st>>>(list, list_count, cell_ranges, words, masks,
+                                                         scratch, capacity, rec, tt, n_per_view, vs,
+                                                         tile_ranges, n_cand, status);
   return cudaGetLastError();
+}
+
+// Step 6. One CTA of CELL x CELL warps per cell, persistent over the cells: the cell's sorted
+// entries are staged in shared memory (a cell longer than EMIT_SCAP is read from global memory
+// instead) and warp w takes the cell's tile w. It walks the entries 32 at a time and keeps those
+// whose mask has bit w; a ballot gives each kept entry its place, so the tile's pairs come out
+// in the cell's order, which is sorted, and are written as key tile << 32 | depth bits and
+// value record from the tile's start.
+constexpr int CEMIT_THREADS = 32 * CELL * CELL;
+constexpr int EMIT_SCAP = 4096;
+
+__global__ void __launch_bounds__(CEMIT_THREADS)
+    cell_emit_kernel(const uint32_t *__restrict__ tile_ranges,
+                     const uint32_t *__restrict__ cell_ranges, const uint64_t *__restrict__ words,
+                     const uint16_t *__restrict__ masks, Views vs, uint64_t *__restrict__ keys,
+                     uint32_t *__restrict__ vals, int64_t capacity,
+                     const unsigned long long *n_cand, uint32_t *status) {
+  __shared__ __align__(16) uint64_t s_w[EMIT_SCAP];
+  __shared__ __align__(16) uint16_t s_m[EMIT_SCAP];
+  if (binning_timed_out(status) || (int64_t)*n_cand > capacity) return;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t lt = lanemask_lt();
+  for (int64_t c = blockIdx.x; c < vs.total_cells; c += gridDim.x) {
+    const uint2 crg = __ldg(reinterpret_cast<const uint2 *>(cell_ranges) + c);
+    if (crg.y <= crg.x) continue;  // uniform over the CTA
+    if (!in_bounds(crg.y, (uint64_t)capacity + 1u, status) || (int64_t)crg.y > capacity) continue;
+    const uint32_t cnt = crg.y - crg.x;
+    const bool staged = cnt <= (uint32_t)EMIT_SCAP;
+    __syncthreads();  // the previous cell's entries are no longer read
+    if (staged) {
+      for (uint32_t i = tid; i < cnt; i += CEMIT_THREADS) {
+        s_w[i] = __ldg(words + crg.x + i);
+        s_m[i] = __ldg(masks + crg.x + i);
+      }
+    }
+    __syncthreads();
+    const View &V = vs.v[view_of_cell(vs, c)];
+    const int64_t local = c - V.cell_offset;
+    const uint32_t cy = (uint32_t)(local / V.cells_x);
+    const uint32_t tx = (uint32_t)(local - (int64_t)cy * V.cells_x) * CELL + wid % CELL;
+    const uint32_t ty = cy * CELL + wid / CELL;
+    if (tx >= (uint32_t)V.tiles_x || ty >= (uint32_t)V.tiles_y) continue;  // whole warp
+    const int64_t t = V.tile_offset + (int64_t)ty * V.tiles_x + tx;
+    const uint2 trg = __ldg(reinterpret_cast<const uint2 *>(tile_ranges) + t);
+    if (trg.y <= trg.x) continue;
+    if (!in_bounds(trg.y, (uint64_t)capacity + 1u, status) || (int64_t)trg.y > capacity) continue;
+    uint32_t o = trg.x;
+    for (uint32_t g = 0; g < cnt && o < trg.y; g += 32u) {
+      const uint32_t i = g + (uint32_t)lane;
+      uint64_t w = 0ull;
+      bool kept = false;
+      if (i < cnt) {
+        const uint32_t m = staged ? (uint32_t)s_m[i] : (uint32_t)__ldg(masks + crg.x + i);
+        kept = (m >> wid) & 1u;
+        if (kept) w = staged ? s_w[i] : __ldg(words + crg.x + i);
+      }
+      const uint32_t b = __ballot_sync(0xffffffffu, kept);
+      const uint32_t pos = o + __popc(b & lt);
+      if (kept && pos < trg.y) {
+        keys[pos] = ((uint64_t)t << 32) | (w >> 32);
+        vals[pos] = (uint32_t)w;
+      }
+      o += __popc(b);
+    }
+    // checked build: the tile received exactly its counted pairs
+    if (FGS_CHECK && lane == 0 && o != trg.y) set_status(status, ST_BOUNDS);
+  }
 }
 
 }  // namespace
@@ -823,75 +1031,67 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
                             const CallOpts &opt, cudaStream_t st) {
   cudaError_t e;
   WsHeader *hdr = reinterpret_cast<WsHeader *>(ws + L.header);
-  uint64_t *scan_lb = reinterpret_cast<uint64_t *>(ws + L.scan_lb);
   uint64_t *tile_lb = reinterpret_cast<uint64_t *>(ws + L.tile_lb);
+  uint64_t *cell_lb = reinterpret_cast<uint64_t *>(ws + L.cell_lb);
+  uint32_t *cell_ranges = reinterpret_cast<uint32_t *>(ws + L.cell_ranges);
   uint32_t *lists = reinterpret_cast<uint32_t *>(ws + L.seg_list);
   uint64_t *words = reinterpret_cast<uint64_t *>(ws + L.words);
-  uint32_t *vis_rec = reinterpret_cast<uint32_t *>(ws + L.vis_rec);
-  uint64_t *vis_off = reinterpret_cast<uint64_t *>(ws + L.vis_off);
-  uint32_t *chunk_first = reinterpret_cast<uint32_t *>(ws + L.chunk_first);
+  uint16_t *masks = reinterpret_cast<uint16_t *>(ws + L.masks);
   const int64_t R = (int64_t)vs.n * n;
-  const int64_t T = vs.total_tiles;
+  const int64_t T = vs.total_tiles, NC = vs.total_cells;
 
-  // the header and both look-back arrays are adjacent: one memset
+  // the header, both look-back arrays and the cell counters are adjacent: one memset
   if ((e = cudaMemsetAsync(hdr, 0, L.g2d - L.header, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)T, st)) != cudaSuccess) return e;
   if (R == 0) return cudaMemsetAsync(n_int, 0, sizeof(int64_t), st);
 
   const bool ellipse = (flags & FGS_BIN_ELLIPSE) != 0;
-  // rect binning: the record scan also builds the tile-count difference grid
-  if (ellipse)
-    scan_kernel<false><<<(unsigned)L.scan_parts, EMIT_THREADS, 0, st>>>(
-        tiles_touched, R, capacity, n_int, &hdr->n_candidates, &hdr->n_visible, scan_lb,
-        scan_lb + L.scan_parts, &hdr->scan_parts, vis_rec, vis_off, chunk_first, &hdr->status,
-        opt.wait_limit, records, n, vs, tile_ranges);
-  else
-    scan_kernel<true><<<(unsigned)L.scan_parts, EMIT_THREADS, 0, st>>>(
-        tiles_touched, R, capacity, n_int, &hdr->n_candidates, &hdr->n_visible, scan_lb,
-        scan_lb + L.scan_parts, &hdr->scan_parts, vis_rec, vis_off, chunk_first, &hdr->status,
-        opt.wait_limit, records, n, vs, tile_ranges);
+  const unsigned rgrid = (unsigned)((R + REC_BLOCK - 1) / REC_BLOCK);
+  cell_count_kernel<<<rgrid, REC_THREADS, 0, st>>>(records, tiles_touched, R, n, vs, capacity,
+                                                   cell_ranges, &hdr->n_candidates,
+                                                   &hdr->n_visible, &hdr->status);
+  tile_scan_kernel<false><<<(unsigned)((NC + TSCAN_PART - 1) / TSCAN_PART), 256, 0, st>>>(
+      cell_ranges, NC, cell_lb, &hdr->cell_parts, lists, hdr->seg_count, (uint32_t)CELL_CAP0,
+      &hdr->n_candidates, capacity, nullptr, &hdr->status, opt.wait_limit);
+  cell_scatter_kernel<<<rgrid, REC_THREADS, 0, st>>>(records, tiles_touched, R, n, vs, cell_ranges,
+                                                     words, &hdr->n_candidates, capacity,
+                                                     &hdr->status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // two waves of the 8 CTAs an SM holds: the pair walks wait on record loads and returning
-  // atomics, so more chunks in flight hide more of that latency
-  int64_t egrid = (int64_t)sm_count() * 16;
-  if (egrid > L.chunks) egrid = L.chunks;
-  if (egrid < 1) egrid = 1;
+  // the keys output serves as the chunked sort's scratch (it is written only by the last step)
   if (ellipse) {
-    pair_kernel<false, true><<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
-        records, n, vs, vis_rec, vis_off, chunk_first, &hdr->n_candidates, &hdr->n_visible,
-        tile_ranges, words, capacity, &hdr->status);
+    if ((e = launch_cell_sort<512, 4, CELL_CAP0, 2, false, true>(
+             lists, &hdr->seg_count[0], cell_ranges, words, masks, keys, capacity, records,
+             tiles_touched, n, vs, tile_ranges, &hdr->n_candidates, &hdr->status, st)) != cudaSuccess)
+      return e;
+    if ((e = launch_cell_sort<512, 8, SEG_CAP1, 1, true, true>(
+             lists + NC, &hdr->seg_count[1], cell_ranges, words, masks, keys, capacity, records,
+             tiles_touched, n, vs, tile_ranges, &hdr->n_candidates, &hdr->status, st)) != cudaSuccess)
+      return e;
   } else {
-    int64_t rows = 0, cols = 0;
-    for (int v = 0; v < vs.n; ++v) {
-      rows += vs.v[v].tiles_y;
-      cols += vs.v[v].tiles_x;
-    }
-    grid_scan_kernel<true><<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(
-        vs, rows, tile_ranges, &hdr->n_candidates, capacity, &hdr->status);
-    grid_scan_kernel<false><<<(unsigned)((cols * 32 + 255) / 256), 256, 0, st>>>(
-        vs, cols, tile_ranges, &hdr->n_candidates, capacity, &hdr->status);
+    if ((e = launch_cell_sort<512, 4, CELL_CAP0, 2, false, false>(
+             lists, &hdr->seg_count[0], cell_ranges, words, masks, keys, capacity, records,
+             tiles_touched, n, vs, tile_ranges, &hdr->n_candidates, &hdr->status, st)) != cudaSuccess)
+      return e;
+    if ((e = launch_cell_sort<512, 8, SEG_CAP1, 1, true, false>(
+             lists + NC, &hdr->seg_count[1], cell_ranges, words, masks, keys, capacity, records,
+             tiles_touched, n, vs, tile_ranges, &hdr->n_candidates, &hdr->status, st)) != cudaSuccess)
+      return e;
   }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  tile_scan_kernel<<<(unsigned)L.tile_parts, 256, 0, st>>>(
-      tile_ranges, T, tile_lb, &hdr->tile_parts, lists, hdr->seg_count, &hdr->n_candidates,
+  tile_scan_kernel<true><<<(unsigned)L.tile_parts, 256, 0, st>>>(
+      tile_ranges, T, tile_lb, &hdr->tile_parts, nullptr, nullptr, 0u, &hdr->n_candidates,
       capacity, n_int, &hdr->status, opt.wait_limit);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (ellipse)
-    pair_kernel<true, true><<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
-        records, n, vs, vis_rec, vis_off, chunk_first, &hdr->n_candidates, &hdr->n_visible,
-        tile_ranges, words, capacity, &hdr->status);
-  else
-    pair_kernel<true, false><<<(unsigned)egrid, EMIT_THREADS, 0, st>>>(
-        records, n, vs, vis_rec, vis_off, chunk_first, &hdr->n_candidates, &hdr->n_visible,
-        tile_ranges, words, capacity, &hdr->status);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = launch_segsort<256, 2, SEG_CAP0, 6, false>(lists, &hdr->seg_count[0], tile_ranges,
-                                                       words, keys, vals, capacity, T,
-                                                       &hdr->status, st)) != cudaSuccess)
-    return e;
-  return launch_segsort<512, 8, SEG_CAP1, 1, true>(lists + T, &hdr->seg_count[1], tile_ranges,
-                                                   words, keys, vals, capacity, T,
-                                                   &hdr->status, st);
+  static int eocc = 0;
+  if (eocc == 0) {
+    int a = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, cell_emit_kernel, CEMIT_THREADS, 0);
+    eocc = a > 0 ? a : 1;
+  }
+  int64_t egrid = (int64_t)sm_count() * eocc;
+  if (egrid > NC) egrid = NC;
+  cell_emit_kernel<<<(unsigned)(egrid > 0 ? egrid : 1), CEMIT_THREADS, 0, st>>>(
+      tile_ranges, cell_ranges, words, masks, vs, keys, vals, capacity, &hdr->n_candidates,
+      &hdr->status);
+  return cudaGetLastError();
 }
 
 }  // namespace fgs

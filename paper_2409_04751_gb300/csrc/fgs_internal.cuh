@@ -62,15 +62,21 @@ struct View {
   float cam_pos[3];  // camera centre -W^T b
   int32_t width, height, tiles_x, tiles_y;
   int32_t model;     // fgs_camera_model
+  int32_t cells_x;   // binning cells (CELL x CELL tiles) per row of the view
   int64_t tile_offset, pixel_offset;
+  int64_t cell_offset;  // first global cell id of the view
 };
 
 struct Views {
   int32_t n;
   int32_t tile_bits;
-  int64_t total_tiles, total_pixels;
+  int64_t total_tiles, total_pixels, total_cells;
   View v[FGS_MAX_VIEWS];
 };
+
+// The binning groups tiles into cells of CELL x CELL tiles (view-major, row-major inside a
+// view, the last row and column of a view ragged).
+constexpr int CELL = 4;
 
 // global tile -> view (views are few; binary search over the tile offsets)
 __device__ __forceinline__ int view_of_tile(const Views &vs, int64_t t) {
@@ -82,14 +88,25 @@ __device__ __forceinline__ int view_of_tile(const Views &vs, int64_t t) {
   return lo;
 }
 
+// global cell -> view
+__device__ __forceinline__ int view_of_cell(const Views &vs, int64_t c) {
+  int lo = 0, hi = vs.n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (vs.v[mid].cell_offset <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 // ------------------------------------------------------------------------------------------
 // Workspace layout (bytes from the workspace base; every region 256-byte aligned).
 struct WsHeader {
   uint32_t status;            // fgs_status of device-detected errors (first one wins)
   uint32_t scan_parts;        // partition counter of the tiles_touched scan
   uint32_t tile_parts;        // partition counter of the per-tile count scan
-  uint32_t seg_count[2];      // tiles in each segment-size class (filled by the tile scan)
-  uint32_t spare[5];
+  uint32_t seg_count[2];      // cells in each segment-size class (filled by the cell scan)
+  uint32_t cell_parts;        // partition counter of the per-cell count scan
+  uint32_t spare[4];
   uint32_t raster_tiles;      // tile queue of the forward rasterizer
   uint32_t backward_tiles;    // tile queue of the backward rasterizer
   // measurement counters, written only by instrumented launches (FGS_OPT_INSTRUMENT):
@@ -128,7 +145,8 @@ constexpr int SEG_CAP1 = 8192;
 constexpr int G2D_STRIDE = 12;                        // floats per record of screen-space grads
 
 struct WsLayout {
-  size_t header, scan_lb, g2d, tile_order, vis_rec, vis_off, tile_lb, seg_list, words, chunk_first;
+  size_t header, scan_lb, tile_lb, cell_lb, cell_ranges, g2d, tile_order, vis_rec, vis_off,
+      seg_list, words, masks, chunk_first;
   size_t sort_hist, sort_lb, alt_vals;  // the onesweep sort's regions (0 bytes unless requested)
   size_t total;
   int64_t scan_parts, tile_parts, chunks, total_tiles, sort_parts;
@@ -151,17 +169,23 @@ constexpr WsLayout ws_layout_ex(int64_t n_records, int64_t capacity, int64_t tot
   L.chunks = (capacity + EMIT_CHUNK - 1) / EMIT_CHUNK;
   L.total_tiles = T;
   size_t o = 0;
-  // header and both look-back arrays first: one memset clears them
+  // header, the look-back arrays and the per-cell counters first: one memset clears them (a
+  // view has at most as many cells as tiles, so tile counts bound the cell regions)
   L.header = o; o += align256(256);
   L.scan_lb = o; o += align256(sizeof(uint64_t) * 2 * (size_t)(L.scan_parts > 0 ? L.scan_parts : 1));
   L.tile_lb = o; o += align256(sizeof(uint64_t) * (size_t)L.tile_parts);
+  L.cell_lb = o; o += align256(sizeof(uint64_t) * (size_t)L.tile_parts);
+  L.cell_ranges = o; o += align256(sizeof(uint32_t) * 2 * (size_t)T);
   L.g2d = o; if (with_g2d) o += align256(sizeof(float) * G2D_STRIDE * (size_t)R);
   // the backward's tile order: per-tile work bucket, tile ids by decreasing work, histogram
   L.tile_order = o; if (with_g2d) o += align256(sizeof(uint32_t) * (2 * (size_t)T + 2 * WORK_BUCKETS));
   L.vis_rec = o; o += align256(sizeof(uint32_t) * (size_t)R);
   L.vis_off = o; o += align256(sizeof(uint64_t) * (size_t)R);
   L.seg_list = o; o += align256(sizeof(uint32_t) * 2 * (size_t)T);
-  L.words = o; o += align256(sizeof(uint64_t) * (size_t)capacity);
+  // cell entries (depth bits << 32 | record) and their tile masks; 4 entries of slack so that
+  // groups of 4 read from a multiple of 4 stay inside
+  L.words = o; o += align256(sizeof(uint64_t) * ((size_t)capacity + 4));
+  L.masks = o; o += align256(sizeof(uint16_t) * ((size_t)capacity + 4));
   L.chunk_first = o; o += align256(sizeof(uint32_t) * ((size_t)L.chunks + 2));
   L.sort_parts = (capacity + SORT_PART - 1) / SORT_PART;
   L.sort_hist = o;

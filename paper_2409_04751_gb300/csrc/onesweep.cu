@@ -402,10 +402,10 @@ cudaError_t launch_bin_sort_onesweep(const fgs_record *records, const uint32_t *
   uint32_t *vis_rec = reinterpret_cast<uint32_t *>(ws + L.vis_rec);
   uint64_t *vis_off = reinterpret_cast<uint64_t *>(ws + L.vis_off);
   uint32_t *chunk_first = reinterpret_cast<uint32_t *>(ws + L.chunk_first);
-  scan_kernel<false><<<(unsigned)L.scan_parts, EMIT_THREADS, 0, st>>>(
+  scan_kernel<<<(unsigned)L.scan_parts, EMIT_THREADS, 0, st>>>(
       tiles_touched, R, capacity, n_int, &hdr->n_candidates, &hdr->n_visible, scan_lb,
       scan_lb + L.scan_parts, &hdr->scan_parts, vis_rec, vis_off, chunk_first, &hdr->status,
-      opt.wait_limit, records, n, vs, tile_ranges);
+      opt.wait_limit);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int64_t egrid = (int64_t)sm_count() * 4;
   if (egrid > L.chunks) egrid = L.chunks;

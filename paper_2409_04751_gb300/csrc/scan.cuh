@@ -1,6 +1,6 @@
-// scan.cuh - the record scan shared by the two bin/sort paths (binsort.cu, onesweep.cu): a
-// single-pass scan of tiles_touched with decoupled look-back, and the helpers it and the
-// tile scan use. Included inside each file's anonymous namespace.
+// scan.cuh - the block scan and the bounded decoupled look-back shared by the bin/sort kernels
+// (binsort.cu, onesweep.cu), and the device-wide sort's record scan: a single-pass scan of
+// tiles_touched with decoupled look-back. Included inside each file's anonymous namespace.
 #pragma once
 
 #include "fgs_internal.cuh"
@@ -83,53 +83,15 @@ __device__ __forceinline__ uint64_t look_back(const uint64_t *lb, int64_t part, 
   return prefix;
 }
 
-// Rect binning's tile counts without a pass over the pairs. A record's pairs are the first
-// k = min(tiles_touched, w h) tiles of its w x h rect in row-major order (exactly what the pair
-// walk emits): fr = k / w full rows and a partial row of k - fr w tiles. Each such block adds
-// +1, -1, -1, +1 at the corners (x_lo, y_lo), (x_hi + 1, y_lo), (x_lo, y_hi + 1),
-// (x_hi + 1, y_hi + 1) of a 2D difference grid held in tile_ranges[2t] (corners past the
-// grid's edge are dropped: they only reach tiles beyond it); inclusive prefix sums along the
-// rows and then the columns of every view (grid_scan_kernel) turn it into the per-tile pair
-// counts. Eight atomics per record at most, instead of one per pair. A rect outside its view's
-// grid (a malformed caller record) adds nothing, as the pair walk skips it.
-__device__ __forceinline__ void rect_difference(const fgs_record *__restrict__ rec, uint32_t r,
-                                                uint32_t tt_r, int64_t n_per_view,
-                                                const Views &vs, uint32_t *ranges) {
-  const uint4 w2 = __ldg(reinterpret_cast<const uint4 *>(rec + r) + 2);
-  const uint32_t x0 = w2.z & 0xffffu, y0 = w2.z >> 16, x1 = w2.w & 0xffffu, y1 = w2.w >> 16;
-  const View &V = vs.v[(int)(r / (uint32_t)n_per_view)];
-  const uint32_t tiles_x = (uint32_t)V.tiles_x, tiles_y = (uint32_t)V.tiles_y;
-  if (!(x0 <= x1 && y0 <= y1 && x1 < tiles_x && y1 < tiles_y)) return;
-  const uint32_t w = x1 - x0 + 1u, h = y1 - y0 + 1u;
-  const uint32_t k = (uint32_t)min((uint64_t)tt_r, (uint64_t)w * h);
-  const uint32_t fr = k / w, rem = k - fr * w;
-  uint32_t *grid = ranges + 2 * V.tile_offset;
-  auto add = [&](uint32_t x, uint32_t y, uint32_t d) {
-    if (x < tiles_x && y < tiles_y) atomicAdd(grid + 2 * ((size_t)y * tiles_x + x), d);
-  };
-  if (fr > 0u) {
-    add(x0, y0, 1u); add(x1 + 1u, y0, 0xffffffffu);
-    add(x0, y0 + fr, 0xffffffffu); add(x1 + 1u, y0 + fr, 1u);
-  }
-  if (rem > 0u) {
-    const uint32_t y = y0 + fr;
-    add(x0, y, 1u); add(x0 + rem, y, 0xffffffffu);
-    add(x0, y + 1u, 0xffffffffu); add(x0 + rem, y + 1u, 1u);
-  }
-}
-
-// The record scan. DIFF = true (rect binning) also adds every visible record to the tile-count
-// difference grid (rect_difference) while its partition waits on the look-back; with more
-// candidates than capacity the counts are then not used (the tile scan reads them as zero).
-template <bool DIFF>
+// The record scan of the device-wide sort: pair offsets of the records (decoupled look-back),
+// the compacted list of records with pairs and the first record of every EMIT_CHUNK-pair chunk.
 __global__ void __launch_bounds__(EMIT_THREADS)
     scan_kernel(const uint32_t *__restrict__ tt, int64_t R, int64_t capacity, int64_t *n_int,
                 unsigned long long *n_cand, unsigned long long *n_vis, uint64_t *lb_pairs,
                 uint64_t *lb_vis,
                 uint32_t *part_counter, uint32_t *__restrict__ vis_rec,
                 uint64_t *__restrict__ vis_off, uint32_t *__restrict__ chunk_first,
-                uint32_t *status, uint32_t wait_limit, const fgs_record *__restrict__ rec,
-                int64_t n_per_view, Views vs, uint32_t *ranges) {
+                uint32_t *status, uint32_t wait_limit) {
   __shared__ uint32_t s_warp[8];
   __shared__ uint64_t s_prefix[2];
   __shared__ uint32_t s_part;
@@ -153,12 +115,6 @@ __global__ void __launch_bounds__(EMIT_THREADS)
     c[k] = r < R ? tt[r] : 0u;
     sum += c[k];
     nv += c[k] > 0u ? 1u : 0u;
-  }
-  if (DIFF) {
-#pragma unroll 4
-    for (int k = 0; k < EMIT_ITEMS; ++k)
-      if (c[k] > 0u)
-        rect_difference(rec, (uint32_t)(base + tid * EMIT_ITEMS + k), c[k], n_per_view, vs, ranges);
   }
   uint32_t cta_pairs, cta_vis;
   uint32_t off = block_excl_scan_256(sum, s_warp, &cta_pairs);

@@ -1,9 +1,11 @@
-"""GPU bin/sort (fgs_bin_sort: scan, per-tile pair count, tile scan, bucket scatter, per-tile
-segment sort; and fgs_bin_sort_ex with FGS_BIN_ONESWEEP: key emission and device-wide onesweep
-radix sort) against the oracle's key builder, bit for bit, on the same seeded synthetic
-records. The cases reach every segment-size class of the per-tile sort: buckets sorted in shared
-memory by 256- and 512-thread CTAs, and buckets longer than the largest shared-memory class,
-sorted in chunks through global memory."""
+"""GPU bin/sort (fgs_bin_sort: cell count, cell scan, cell scatter, per-cell sort with tile
+masks, tile scan, per-tile emission; and fgs_bin_sort_ex with FGS_BIN_ONESWEEP: key emission and
+device-wide onesweep radix sort) against the oracle's key builder, bit for bit, on the same
+seeded synthetic records. The cases reach every size class of the per-cell sort (cells sorted
+in shared memory at both word counts of the smaller class and in the larger class, and cells
+longer than the largest shared-memory class, sorted in chunks through global memory), the
+bucket sort and its radix fallback, and both ways the cell walks count (in shared memory, and
+with more cells than a CTA holds, in global memory)."""
 import numpy as np
 import pytest
 import torch
@@ -84,28 +86,27 @@ def _oracle(rect, depth, n, cams_py):
 
 @pytest.mark.parametrize("n,sizes,seed,kw", [
     (1, [(64, 48)], 0, {}),
-    (700, [(100, 90)], 1, {}),                                     # one scan partition
-    (9000, [(256, 256)], 2, dict(max_ext=6)),                      # several partitions
+    (700, [(100, 90)], 1, {}),                                     # four ragged cells
+    (9000, [(256, 256)], 2, dict(max_ext=6)),                      # sixteen full cells
     (3000, [(256, 256), (96, 40), (1752, 1168)], 3, dict(max_ext=4)),  # multi-view, ragged
     (20000, [(1752, 1168)], 4, dict(max_ext=10, big_frac=0.002)),  # ~1M pairs, huge rects
     (4000, [(16, 16)], 5, dict(tie_frac=0.9)),                     # one tile, heavy ties
     (3000, [(64, 64)], 6, dict(p_empty=1.0)),                      # nothing visible
-    # 10 views x 30k records, 80k tiles
+    # 10 views x 30k records, 80k tiles, 5320 cells: more than a CTA counts in shared memory
     (30000, [(1752, 1168)] * 10, 9, dict(max_ext=3, p_empty=0.5)),
-    # buckets of ~600, ~1000 and ~1200 pairs, across the smallest class limit (1024)
+    # one cell of three tiles with ~2200 entries (the smaller class's second word count)
     (2200, [(48, 16)], 10, dict(max_ext=2, tie_frac=0.0)),
-    # one tile with ~4800 pairs (512 x 16 shared-memory class)
+    # one cell with ~4800 entries (the larger class, in shared memory)
     (6000, [(16, 16)], 11, dict(tie_frac=0.0)),
-    # one tile with ~16000 pairs: longer than any shared-memory class, chunked sort
+    # one cell with ~16000 entries: longer than any shared-memory class, chunked sort
     (20000, [(16, 16)], 12, dict(tie_frac=0.0)),
-    # chunked sort with many equal depths, next to smaller buckets
+    # chunked sort with many equal depths
     (30000, [(32, 32)], 13, dict(max_ext=1, tie_frac=0.6)),
     # every pair at one depth: the order is the record order alone
     (9000, [(16, 16)], 14, dict(tie_frac=1.0)),
-    # many small tiles whose depths all tie: every one is too clustered for the one-warp bucket
-    # sort and goes to the large class's CTAs
+    # cells whose depths all tie: too clustered for the bucket sort, sorted by the radix passes
     (3000, [(256, 256)], 15, dict(max_ext=5, tie_frac=1.0)),
-    # a mix: half of the small tiles tie, half do not
+    # a mix: half of the entries tie, half do not
     (6000, [(640, 480)], 16, dict(max_ext=4, tie_frac=0.5)),
 ])
 @pytest.mark.parametrize("flags", SORTS)
@@ -214,8 +215,8 @@ def test_binsort_tiles_touched_differs_from_rect(cuda_device, flags):
 
 
 @pytest.mark.parametrize("n,size,flags", [
-    (9000, (256, 256), 0),                      # 3 record-scan partitions, 1 tile partition
-    (2000, (1752, 1168), 0),                    # 1 record-scan partition, 8 tile partitions
+    (9000, (4096, 2048), 0),                    # 2 cell-scan partitions, 32 tile partitions
+    (2000, (1752, 1168), 0),                    # 1 cell-scan partition, 8 tile partitions
     (9000, (256, 256), fgs.FGS_BIN_ONESWEEP),   # the record scan of the onesweep path
     (2000, (1752, 1168), fgs.FGS_BIN_ONESWEEP),  # its radix passes (several key partitions)
 ])
