@@ -92,13 +92,14 @@ __device__ __forceinline__ CellSet cell_set(const PairSet &P) {
 }
 
 // Walks the cells of 32 consecutive records [r0, r0 + 32) with one warp: lane l loads record
-// r0 + l, the warp numbers all their cells in record order and takes them 32 at a time, lane l
-// calling f(record, view, depth bits, cx, cy) for cell e0 + l. Every lane does the same work
+// r0 + l (calling g(pairs) if it has any), the warp numbers all their cells in record order
+// and takes them 32 at a time, lane l calling f(record, view, depth bits, cx, cy) for cell
+// e0 + l. Every lane does the same work
 // however the cells are spread over the records.
-template <class F>
+template <class G, class F>
 __device__ __forceinline__ void warp_cells(const fgs_record *__restrict__ rec,
                                            const uint32_t *__restrict__ tt, int64_t r0, int64_t R,
-                                           int64_t n_per_view, const Views &vs, F f) {
+                                           int64_t n_per_view, const Views &vs, G g, F f) {
   const int lane = threadIdx.x & 31;
   const int64_t r = r0 + lane;
   CellSet S{};
@@ -107,12 +108,13 @@ __device__ __forceinline__ void warp_cells(const fgs_record *__restrict__ rec,
   if (r < R) {
     const uint32_t t = tt[r];
     if (t != 0u) {
-      view = (int)(r / n_per_view);
+      view = (int)((uint32_t)r / (uint32_t)n_per_view);  // R < 2^32
       const uint4 w2 = __ldg(reinterpret_cast<const uint4 *>(rec + r) + 2);
       PairSet P;
       if (pair_set(w2, t, vs.v[view], P)) {
         S = cell_set(P);
         depth = w2.y;
+        g(P);
       }
     }
   }
@@ -207,28 +209,19 @@ __global__ void __launch_bounds__(REC_THREADS)
   __syncthreads();
   unsigned long long pairs = 0, vis = 0;
   const int64_t base = (int64_t)blockIdx.x * REC_BLOCK;
-  // pairs and visible records, one record per thread
-  for (int i = 0; i < REC_PER_THREAD; ++i) {
-    const int64_t r = base + (int64_t)(i * (REC_THREADS / 32) + wid) * 32 + lane;
-    if (r >= R) break;
-    const uint32_t t = tt[r];
-    if (t == 0u) continue;
-    PairSet P;
-    if (!pair_set(__ldg(reinterpret_cast<const uint4 *>(rec + r) + 2), t,
-                  vs.v[(int)(r / n_per_view)], P))
-      continue;
-    pairs += P.k;
-    ++vis;
-  }
-  // cells, 32 records per warp walk
   for (int i = 0; i < REC_PER_THREAD; ++i) {
     const int64_t r0 = base + (int64_t)(i * (REC_THREADS / 32) + wid) * 32;
     if (r0 >= R) break;
-    warp_cells(rec, tt, r0, R, n_per_view, vs, [&](int64_t, int v, uint32_t, uint32_t cx, uint32_t cy) {
-      const int64_t c = cell_id(vs.v[v], cx, cy);
-      if (in_smem) atomicAdd(&s_cnt[c], 1u);
-      else atomicAdd(&cell_ranges[2 * c], 1u);
-    });
+    warp_cells(rec, tt, r0, R, n_per_view, vs,
+               [&](const PairSet &P) {
+                 pairs += P.k;
+                 ++vis;
+               },
+               [&](int64_t, int v, uint32_t, uint32_t cx, uint32_t cy) {
+                 const int64_t c = cell_id(vs.v[v], cx, cy);
+                 if (in_smem) atomicAdd(&s_cnt[c], 1u);
+                 else atomicAdd(&cell_ranges[2 * c], 1u);
+               });
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -270,9 +263,10 @@ __global__ void __launch_bounds__(REC_THREADS)
     for (int i = 0; i < REC_PER_THREAD; ++i) {
       const int64_t r0 = base + (int64_t)(i * (REC_THREADS / 32) + wid) * 32;
       if (r0 >= R) break;
-      warp_cells(rec, tt, r0, R, n_per_view, vs, [&](int64_t, int v, uint32_t, uint32_t cx, uint32_t cy) {
-        atomicAdd(&s_cnt[cell_id(vs.v[v], cx, cy)], 1u);
-      });
+      warp_cells(rec, tt, r0, R, n_per_view, vs, [](const PairSet &) {},
+                 [&](int64_t, int v, uint32_t, uint32_t cx, uint32_t cy) {
+                   atomicAdd(&s_cnt[cell_id(vs.v[v], cx, cy)], 1u);
+                 });
     }
     __syncthreads();
     // the block's slots of each cell; s_cnt then holds the next one to hand out
@@ -283,7 +277,8 @@ __global__ void __launch_bounds__(REC_THREADS)
   for (int i = 0; i < REC_PER_THREAD; ++i) {
     const int64_t r0 = base + (int64_t)(i * (REC_THREADS / 32) + wid) * 32;
     if (r0 >= R) break;
-    warp_cells(rec, tt, r0, R, n_per_view, vs, [&](int64_t r, int v, uint32_t depth, uint32_t cx, uint32_t cy) {
+    warp_cells(rec, tt, r0, R, n_per_view, vs, [](const PairSet &) {},
+               [&](int64_t r, int v, uint32_t depth, uint32_t cx, uint32_t cy) {
       const int64_t c = cell_id(vs.v[v], cx, cy);
       const uint32_t slot = in_smem ? atomicAdd(&s_cnt[c], 1u) : atomicAdd(&cell_ranges[2 * c + 1], 1u);
       // a record's cells never outnumber its pairs, so the entries fit the capacity (checked
@@ -955,14 +950,20 @@ cudaError_t launch_cell_sort(const uint32_t *list, const uint32_t *list_count,
   return cudaGetLastError();
 }
 
-// Step 6. One CTA of CELL x CELL warps per cell, persistent over the cells: the cell's sorted
-// entries are staged in shared memory (a cell longer than EMIT_SCAP is read from global memory
-// instead) and warp w takes the cell's tile w. It walks the entries 32 at a time and keeps those
-// whose mask has bit w; a ballot gives each kept entry its place, so the tile's pairs come out
-// in the cell's order, which is sorted, and are written as key tile << 32 | depth bits and
-// value record from the tile's start.
+// Step 6. One CTA of CELL x CELL warps per cell, persistent over the cells. The cell's sorted
+// list is cut into groups of 32 entries; per group, one ballot per tile bit of the masks gives
+// the group's entries of each tile. (1) Every group's 16 ballots go to shared memory; (2) warp
+// b scans the popcounts of tile b's ballots over the groups, from the tile's start, so each
+// group knows where its entries of each tile go; (3) every group writes each of its entries
+// once per tile bit, at its group's place plus its rank in the ballot. A tile's pairs thus come
+// out in the cell's order, which is sorted, as key tile << 32 | depth bits and value record. A
+// cell of more than EMIT_GROUPS groups is emitted one tile per warp, walking the list in order.
 constexpr int CEMIT_THREADS = 32 * CELL * CELL;
-constexpr int EMIT_SCAP = 4096;
+constexpr int EMIT_GROUPS = 128;
+
+__device__ __forceinline__ int64_t cell_tile(const View &V, uint32_t bx, uint32_t by, int b) {
+  return V.tile_offset + (int64_t)(by + b / CELL) * V.tiles_x + bx + b % CELL;
+}
 
 __global__ void __launch_bounds__(CEMIT_THREADS)
     cell_emit_kernel(const uint32_t *__restrict__ tile_ranges,
@@ -970,8 +971,8 @@ __global__ void __launch_bounds__(CEMIT_THREADS)
                      const uint16_t *__restrict__ masks, Views vs, uint64_t *__restrict__ keys,
                      uint32_t *__restrict__ vals, int64_t capacity,
                      const unsigned long long *n_cand, uint32_t *status) {
-  __shared__ __align__(16) uint64_t s_w[EMIT_SCAP];
-  __shared__ __align__(16) uint16_t s_m[EMIT_SCAP];
+  __shared__ uint32_t s_bal[EMIT_GROUPS][CELL * CELL];  // group g's ballot of tile bit b
+  __shared__ uint32_t s_pre[EMIT_GROUPS][CELL * CELL];  // where group g's entries of tile b go
   if (binning_timed_out(status) || (int64_t)*n_cand > capacity) return;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t lt = lanemask_lt();
@@ -980,45 +981,101 @@ __global__ void __launch_bounds__(CEMIT_THREADS)
     if (crg.y <= crg.x) continue;  // uniform over the CTA
     if (!in_bounds(crg.y, (uint64_t)capacity + 1u, status) || (int64_t)crg.y > capacity) continue;
     const uint32_t cnt = crg.y - crg.x;
-    const bool staged = cnt <= (uint32_t)EMIT_SCAP;
-    __syncthreads();  // the previous cell's entries are no longer read
-    if (staged) {
-      for (uint32_t i = tid; i < cnt; i += CEMIT_THREADS) {
-        s_w[i] = __ldg(words + crg.x + i);
-        s_m[i] = __ldg(masks + crg.x + i);
-      }
-    }
-    __syncthreads();
+    const uint32_t G = (cnt + 31u) / 32u;
     const View &V = vs.v[view_of_cell(vs, c)];
     const int64_t local = c - V.cell_offset;
     const uint32_t cy = (uint32_t)(local / V.cells_x);
-    const uint32_t tx = (uint32_t)(local - (int64_t)cy * V.cells_x) * CELL + wid % CELL;
-    const uint32_t ty = cy * CELL + wid / CELL;
-    if (tx >= (uint32_t)V.tiles_x || ty >= (uint32_t)V.tiles_y) continue;  // whole warp
-    const int64_t t = V.tile_offset + (int64_t)ty * V.tiles_x + tx;
-    const uint2 trg = __ldg(reinterpret_cast<const uint2 *>(tile_ranges) + t);
-    if (trg.y <= trg.x) continue;
-    if (!in_bounds(trg.y, (uint64_t)capacity + 1u, status) || (int64_t)trg.y > capacity) continue;
-    uint32_t o = trg.x;
-    for (uint32_t g = 0; g < cnt && o < trg.y; g += 32u) {
-      const uint32_t i = g + (uint32_t)lane;
-      uint64_t w = 0ull;
-      bool kept = false;
-      if (i < cnt) {
-        const uint32_t m = staged ? (uint32_t)s_m[i] : (uint32_t)__ldg(masks + crg.x + i);
-        kept = (m >> wid) & 1u;
-        if (kept) w = staged ? s_w[i] : __ldg(words + crg.x + i);
+    const uint32_t bx = (uint32_t)(local - (int64_t)cy * V.cells_x) * CELL, by = cy * CELL;
+    const uint64_t *cw = words + crg.x;
+    const uint16_t *cm = masks + crg.x;
+    if (G <= (uint32_t)EMIT_GROUPS) {
+      __syncthreads();  // the previous cell's ballots are no longer read
+      for (uint32_t g = wid; g < G; g += CELL * CELL) {  // (1)
+        const uint32_t i = g * 32u + (uint32_t)lane;
+        const uint32_t m = i < cnt ? (uint32_t)__ldg(cm + i) : 0u;
+        uint32_t mine = 0u;
+#pragma unroll
+        for (int b = 0; b < CELL * CELL; ++b) {
+          const uint32_t bal = __ballot_sync(0xffffffffu, (m >> b) & 1u);
+          if (lane == b) mine = bal;
+        }
+        if (lane < CELL * CELL) s_bal[g][lane] = mine;
       }
-      const uint32_t b = __ballot_sync(0xffffffffu, kept);
-      const uint32_t pos = o + __popc(b & lt);
-      if (kept && pos < trg.y) {
-        keys[pos] = ((uint64_t)t << 32) | (w >> 32);
-        vals[pos] = (uint32_t)w;
+      __syncthreads();
+      {  // (2) warp b: exclusive scan over the groups, 4 consecutive groups per lane
+        const int b = wid;
+        const uint32_t tx = bx + b % CELL, ty = by + b / CELL;
+        uint32_t start = 0u, end = 0u;
+        if (tx < (uint32_t)V.tiles_x && ty < (uint32_t)V.tiles_y) {
+          const uint2 trg = __ldg(reinterpret_cast<const uint2 *>(tile_ranges) + cell_tile(V, bx, by, b));
+          start = trg.x;
+          end = trg.y;
+        }
+        uint32_t n4[4], sum = 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t g = 4u * lane + q;
+          n4[q] = g < G ? __popc(s_bal[g][b]) : 0u;
+          sum += n4[q];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        uint32_t run = start + incl - sum;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t g = 4u * lane + q;
+          if (g < G) s_pre[g][b] = run;
+          run += n4[q];
+        }
+        // checked build: the tile receives exactly its counted pairs
+        if (FGS_CHECK && lane == 31 && run != end) set_status(status, ST_BOUNDS);
       }
-      o += __popc(b);
+      __syncthreads();
+      for (uint32_t g = wid; g < G; g += CELL * CELL) {  // (3)
+        const uint32_t i = g * 32u + (uint32_t)lane;
+        const uint64_t w = i < cnt ? __ldg(cw + i) : 0ull;
+        const uint64_t kd = w >> 32;
+#pragma unroll
+        for (int b = 0; b < CELL * CELL; ++b) {
+          const uint32_t bal = s_bal[g][b];
+          if ((bal >> lane) & 1u) {
+            const uint32_t pos = s_pre[g][b] + __popc(bal & lt);
+            if (in_bounds(pos, (uint64_t)capacity, status) && (int64_t)pos < capacity) {
+              keys[pos] = ((uint64_t)cell_tile(V, bx, by, b) << 32) | kd;
+              vals[pos] = (uint32_t)w;
+            }
+          }
+        }
+      }
+    } else {
+      // a long cell: warp w walks the list for tile w
+      const uint32_t tx = bx + wid % CELL, ty = by + wid / CELL;
+      if (tx < (uint32_t)V.tiles_x && ty < (uint32_t)V.tiles_y) {
+        const int64_t t = cell_tile(V, bx, by, wid);
+        const uint2 trg = __ldg(reinterpret_cast<const uint2 *>(tile_ranges) + t);
+        if (trg.y > trg.x && in_bounds(trg.y, (uint64_t)capacity + 1u, status) &&
+            (int64_t)trg.y <= capacity) {
+          uint32_t o = trg.x;
+          for (uint32_t g = 0; g < cnt && o < trg.y; g += 32u) {
+            const uint32_t i = g + (uint32_t)lane;
+            const bool kept = i < cnt && ((__ldg(cm + i) >> wid) & 1u);
+            const uint32_t bal = __ballot_sync(0xffffffffu, kept);
+            const uint32_t pos = o + __popc(bal & lt);
+            if (kept && pos < trg.y) {
+              const uint64_t w = __ldg(cw + i);
+              keys[pos] = ((uint64_t)t << 32) | (w >> 32);
+              vals[pos] = (uint32_t)w;
+            }
+            o += __popc(bal);
+          }
+          if (FGS_CHECK && lane == 0 && o != trg.y) set_status(status, ST_BOUNDS);
+        }
+      }
     }
-    // checked build: the tile received exactly its counted pairs
-    if (FGS_CHECK && lane == 0 && o != trg.y) set_status(status, ST_BOUNDS);
   }
 }
 
