@@ -16,12 +16,12 @@
 //  2. tile_scan_kernel over the cells: exclusive scan of the cell counts (decoupled look-back)
 //     gives every cell's start; cells are listed by size class.
 //  3. cell_scatter_kernel: the same walk writes depth bits << 32 | record into the record's
-//     cells (slots claimed per CTA and cell, then per entry in shared memory).
+//     cells (slots claimed per CTA and cell, then per entry in shared memory), each with the
+//     mask of the cell's tiles that hold one of its pairs (exact binning: whose pixels its
+//     alpha >= 1/255 ellipse reaches).
 //  4. cell_sort_kernel (one launch per size class): each cell's list is sorted in shared memory
-//     (a one-pass bucket sort on the depth bits, or LSD radix passes when the depths are too
-//     clustered for it), in place; then each entry gets the mask of the cell's tiles that hold
-//     one of its pairs (exact binning: whose pixels its alpha >= 1/255 ellipse reaches), and
-//     the cell's tiles get their pair counts.
+//     with its masks (a one-pass bucket sort on the depth bits, or LSD radix passes when the
+//     depths are too clustered for it), in place, and the cell's tiles get their pair counts.
 //  5. tile_scan_kernel over the tiles: exclusive scan of the tile counts gives every tile's
 //     [start, end) and the number of pairs.
 //  6. cell_emit_kernel: one CTA per cell stages the cell's sorted list in shared memory and
@@ -93,8 +93,8 @@ __device__ __forceinline__ CellSet cell_set(const PairSet &P) {
 
 // Walks the cells of 32 consecutive records [r0, r0 + 32) with one warp: lane l loads record
 // r0 + l (calling g(pairs) if it has any), the warp numbers all their cells in record order
-// and takes them 32 at a time, lane l calling f(record, view, depth bits, cx, cy) for cell
-// e0 + l. Every lane does the same work
+// and takes them 32 at a time, lane l calling f(record, view, depth bits, cx, cy, pairs) for
+// cell e0 + l (pairs without k). Every lane does the same work
 // however the cells are spread over the records.
 template <class G, class F>
 __device__ __forceinline__ void warp_cells(const fgs_record *__restrict__ rec,
@@ -103,6 +103,7 @@ __device__ __forceinline__ void warp_cells(const fgs_record *__restrict__ rec,
   const int lane = threadIdx.x & 31;
   const int64_t r = r0 + lane;
   CellSet S{};
+  PairSet P{};
   int view = 0;
   uint32_t depth = 0u;
   if (r < R) {
@@ -110,7 +111,6 @@ __device__ __forceinline__ void warp_cells(const fgs_record *__restrict__ rec,
     if (t != 0u) {
       view = (int)((uint32_t)r / (uint32_t)n_per_view);  // R < 2^32
       const uint4 w2 = __ldg(reinterpret_cast<const uint4 *>(rec + r) + 2);
-      PairSet P;
       if (pair_set(w2, t, vs.v[view], P)) {
         S = cell_set(P);
         depth = w2.y;
@@ -143,6 +143,15 @@ __device__ __forceinline__ void warp_cells(const fgs_record *__restrict__ rec,
     const uint32_t cyB = __shfl_sync(0xffffffffu, S.cyB, j);
     const int vj = __shfl_sync(0xffffffffu, view, j);
     const uint32_t dj = __shfl_sync(0xffffffffu, depth, j);
+    PairSet Pj;
+    const uint32_t xy = __shfl_sync(0xffffffffu, P.x0 | (P.y0 << 16), j);
+    const uint32_t fr_rem = __shfl_sync(0xffffffffu, P.fr | (P.rem << 16), j);
+    Pj.x0 = xy & 0xffffu;
+    Pj.y0 = xy >> 16;
+    Pj.x1 = __shfl_sync(0xffffffffu, P.x1, j);
+    Pj.fr = fr_rem & 0xffffu;
+    Pj.rem = fr_rem >> 16;
+    Pj.k = 0u;
     if (e < total) {
       const uint32_t nb = cols * rows;
       uint32_t cx, cy;
@@ -154,7 +163,7 @@ __device__ __forceinline__ void warp_cells(const fgs_record *__restrict__ rec,
         cy = cyB;
         cx = cx0 + (i - nb);
       }
-      f(r0 + j, vj, dj, cx, cy);
+      f(r0 + j, vj, dj, cx, cy, Pj);
     }
   }
 }
@@ -179,6 +188,25 @@ __device__ __forceinline__ uint32_t cell_mask(const PairSet &P, uint32_t bx, uin
   if (P.rem > 0u) {
     const uint32_t y = P.y0 + P.fr;
     if (y >= by && y < by + CELL) m |= span_bits(P.x0, P.x0 + P.rem - 1u, bx) << (CELL * (y - by));
+  }
+  return m;
+}
+
+// Exact binning: the tiles of mask m (cell at tile (bx, by)) that the record's alpha >= 1/255
+// ellipse reaches.
+__device__ __forceinline__ uint32_t ellipse_mask(const fgs_record *rp, uint32_t m, uint32_t bx,
+                                                 uint32_t by) {
+  if (m == 0u) return 0u;
+  const float4 w0 = __ldg(reinterpret_cast<const float4 *>(rp));
+  const float4 w1 = __ldg(reinterpret_cast<const float4 *>(rp) + 1);
+  const float qs = fmaxf(2.f * logf(255.f * w1.y), 0.f);
+  for (uint32_t rest = m; rest; rest &= rest - 1u) {
+    const uint32_t b = __ffs(rest) - 1;
+    const float xl = (float)((bx + b % CELL) * TILE) + 0.5f;
+    const float yl = (float)((by + b / CELL) * TILE) + 0.5f;
+    if (!ellipse_reaches_tile(w0.x, w0.y, w0.z, w0.w, w1.x, qs, xl, xl + (TILE - 1), yl,
+                              yl + (TILE - 1)))
+      m &= ~(1u << b);
   }
   return m;
 }
@@ -217,7 +245,7 @@ __global__ void __launch_bounds__(REC_THREADS)
                  pairs += P.k;
                  ++vis;
                },
-               [&](int64_t, int v, uint32_t, uint32_t cx, uint32_t cy) {
+               [&](int64_t, int v, uint32_t, uint32_t cx, uint32_t cy, const PairSet &) {
                  const int64_t c = cell_id(vs.v[v], cx, cy);
                  if (in_smem) atomicAdd(&s_cnt[c], 1u);
                  else atomicAdd(&cell_ranges[2 * c], 1u);
@@ -243,15 +271,18 @@ __global__ void __launch_bounds__(REC_THREADS)
 }
 
 // Step 3. Writes depth bits << 32 | record into every cell of every record (cell_ranges[2c + 1]
-// holds the cell's next free slot, set to its start by the cell scan). With the cell counters
+// holds the cell's next free slot, set to its start by the cell scan), and beside it the mask
+// of the cell's tiles that hold one of the record's pairs (exact binning: those its alpha >=
+// 1/255 ellipse reaches; a mask can then be empty). With the cell counters
 // in shared memory a CTA counts its entries per cell, claims a block of slots per cell with one
 // global atomic, and hands the slots out in shared memory; the order inside a cell is
 // irrelevant (the cell is sorted next).
+template <bool ELLIPSE>
 __global__ void __launch_bounds__(REC_THREADS)
     cell_scatter_kernel(const fgs_record *__restrict__ rec, const uint32_t *__restrict__ tt,
                         int64_t R, int64_t n_per_view, Views vs, uint32_t *cell_ranges,
-                        uint64_t *__restrict__ words, const unsigned long long *n_cand,
-                        int64_t capacity, uint32_t *status) {
+                        uint64_t *__restrict__ words, uint16_t *__restrict__ masks,
+                        const unsigned long long *n_cand, int64_t capacity, uint32_t *status) {
   __shared__ uint32_t s_cnt[SMEM_CELLS];
   if (binning_timed_out(status) || (int64_t)*n_cand > capacity) return;
   const int tid = threadIdx.x, wid = tid >> 5;
@@ -264,7 +295,7 @@ __global__ void __launch_bounds__(REC_THREADS)
       const int64_t r0 = base + (int64_t)(i * (REC_THREADS / 32) + wid) * 32;
       if (r0 >= R) break;
       warp_cells(rec, tt, r0, R, n_per_view, vs, [](const PairSet &) {},
-                 [&](int64_t, int v, uint32_t, uint32_t cx, uint32_t cy) {
+                 [&](int64_t, int v, uint32_t, uint32_t cx, uint32_t cy, const PairSet &) {
                    atomicAdd(&s_cnt[cell_id(vs.v[v], cx, cy)], 1u);
                  });
     }
@@ -278,13 +309,18 @@ __global__ void __launch_bounds__(REC_THREADS)
     const int64_t r0 = base + (int64_t)(i * (REC_THREADS / 32) + wid) * 32;
     if (r0 >= R) break;
     warp_cells(rec, tt, r0, R, n_per_view, vs, [](const PairSet &) {},
-               [&](int64_t r, int v, uint32_t depth, uint32_t cx, uint32_t cy) {
+               [&](int64_t r, int v, uint32_t depth, uint32_t cx, uint32_t cy, const PairSet &P) {
       const int64_t c = cell_id(vs.v[v], cx, cy);
       const uint32_t slot = in_smem ? atomicAdd(&s_cnt[c], 1u) : atomicAdd(&cell_ranges[2 * c + 1], 1u);
+      const uint32_t bx = cx * CELL, by = cy * CELL;
+      uint32_t m = cell_mask(P, bx, by);
+      if (ELLIPSE) m = ellipse_mask(rec + r, m, bx, by);
       // a record's cells never outnumber its pairs, so the entries fit the capacity (checked
       // build: verified)
-      if (in_bounds(slot, (uint64_t)capacity, status) && (int64_t)slot < capacity)
+      if (in_bounds(slot, (uint64_t)capacity, status) && (int64_t)slot < capacity) {
         words[slot] = ((uint64_t)depth << 32) | (uint64_t)r;
+        masks[slot] = (uint16_t)m;
+      }
     });
   }
 }
@@ -384,6 +420,7 @@ __global__ void __launch_bounds__(256)
 template <int NT, int CAP>
 struct SegSmem {
   uint64_t buf[CAP];
+  uint16_t pay[CAP];  // each word's 16-bit payload (its tile mask), moved with it
   union {
     struct {
       uint32_t wcnt[NT / 32][256];   // per-warp digit counts -> per-warp offsets within a digit
@@ -487,8 +524,8 @@ __device__ __forceinline__ void block_and_or(SegSmem<NT, CAP> &S, uint64_t &a, u
 // One stable pass over the digit at `shift` of the segment held in registers (x) and shared
 // memory; leaves the result in both.
 template <int NT, int IPT, int CAP>
-__device__ __forceinline__ void smem_pass(SegSmem<NT, CAP> &S, uint64_t (&x)[IPT], uint32_t cnt,
-                                          int shift) {
+__device__ __forceinline__ void smem_pass(SegSmem<NT, CAP> &S, uint64_t (&x)[IPT],
+                                          uint32_t (&p)[IPT], uint32_t cnt, int shift) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t rank[IPT];
   rank_items<NT, IPT, CAP>(S, x, cnt, shift, rank);
@@ -498,7 +535,9 @@ __device__ __forceinline__ void smem_pass(SegSmem<NT, CAP> &S, uint64_t (&x)[IPT
     const uint32_t li = (uint32_t)(w * 32 * IPT + k * 32 + lane);
     if (li < cnt) {
       const uint32_t d = (uint32_t)(x[k] >> shift) & 255u;
-      S.buf[S.dstart[d] + S.rx.wcnt[w][d] + rank[k]] = x[k];
+      const uint32_t pos = S.dstart[d] + S.rx.wcnt[w][d] + rank[k];
+      S.buf[pos] = x[k];
+      S.pay[pos] = (uint16_t)p[k];
     }
   }
   __syncthreads();
@@ -506,24 +545,28 @@ __device__ __forceinline__ void smem_pass(SegSmem<NT, CAP> &S, uint64_t (&x)[IPT
   for (int k = 0; k < IPT; ++k) {
     const uint32_t li = (uint32_t)(w * 32 * IPT + k * 32 + lane);
     x[k] = li < cnt ? S.buf[li] : 0ull;
+    p[k] = li < cnt ? (uint32_t)S.pay[li] : 0u;
   }
 }
 
-// Sort one segment of cnt <= NT * IPT words in shared memory and write them to out (which
-// may be src: everything is read before the first write).
+// Sort one segment of cnt <= NT * IPT words with their payloads in shared memory and write
+// them to out / pout (which may be src / psrc: everything is read before the first write).
 template <int NT, int IPT, int CAP>
 __device__ __forceinline__ void sort_segment_smem(SegSmem<NT, CAP> &S, const uint64_t *src,
-                                                  uint32_t cnt, uint64_t *out) {
+                                                  const uint16_t *psrc, uint32_t cnt,
+                                                  uint64_t *out, uint16_t *pout) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   // the lane masks share storage with the bucket sort's counters: clear them first
   for (int e = threadIdx.x; e < (NT / 32) * 256; e += NT) (&S.rx.wmask[0][0])[e] = 0u;
   __syncthreads();
   uint64_t x[IPT];
+  uint32_t p[IPT];
   uint64_t a = ~0ull, o = 0ull;
 #pragma unroll
   for (int k = 0; k < IPT; ++k) {
     const uint32_t li = (uint32_t)(w * 32 * IPT + k * 32 + lane);
     x[k] = li < cnt ? src[li] : 0ull;
+    p[k] = li < cnt ? (uint32_t)psrc[li] : 0u;
     if (li < cnt) {
       S.buf[li] = x[k];
       a &= x[k];
@@ -533,8 +576,8 @@ __device__ __forceinline__ void sort_segment_smem(SegSmem<NT, CAP> &S, const uin
   block_and_or<NT, IPT, CAP>(S, a, o);
   const uint64_t varying = a ^ o;
 #pragma unroll
-  for (int p = 4; p < 8; ++p)
-    if ((varying >> (8 * p)) & 255u) smem_pass<NT, IPT, CAP>(S, x, cnt, 8 * p);
+  for (int d = 4; d < 8; ++d)
+    if ((varying >> (8 * d)) & 255u) smem_pass<NT, IPT, CAP>(S, x, p, cnt, 8 * d);
   // equal depths (the high halves) in adjacent slots: sort again over every digit
   bool tie = false;
 #pragma unroll
@@ -544,10 +587,20 @@ __device__ __forceinline__ void sort_segment_smem(SegSmem<NT, CAP> &S, const uin
   }
   if (__syncthreads_or(tie)) {
 #pragma unroll
-    for (int p = 0; p < 8; ++p)
-      if ((varying >> (8 * p)) & 255u) smem_pass<NT, IPT, CAP>(S, x, cnt, 8 * p);
+    for (int d = 0; d < 8; ++d)
+      if ((varying >> (8 * d)) & 255u) smem_pass<NT, IPT, CAP>(S, x, p, cnt, 8 * d);
   }
-  for (uint32_t i = threadIdx.x; i < cnt; i += NT) out[i] = S.buf[i];
+  // without a radix pass (one word) the payload is still in registers only
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    const uint32_t li = (uint32_t)(w * 32 * IPT + k * 32 + lane);
+    if (li < cnt) S.pay[li] = (uint16_t)p[k];
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < cnt; i += NT) {
+    out[i] = S.buf[i];
+    pout[i] = S.pay[i];
+  }
   __syncthreads();  // buf reused by the next segment
 }
 
@@ -564,7 +617,8 @@ constexpr uint32_t BUCKET_KMAX = 32;
 
 template <int NT, int IPT, int CAP>
 __device__ __forceinline__ bool bucket_sort_segment(SegSmem<NT, CAP> &S, const uint64_t *src,
-                                                    uint32_t cnt, uint64_t *out) {
+                                                    const uint16_t *psrc, uint32_t cnt,
+                                                    uint64_t *out, uint16_t *pout) {
   static_assert(NT * IPT <= CAP, "capacity");
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   // NB sub-buckets: CAP for the small class (fixed, so the counter loops unroll), else the
@@ -581,6 +635,7 @@ __device__ __forceinline__ bool bucket_sort_segment(SegSmem<NT, CAP> &S, const u
   for (int k = 0; k < IPT; ++k) {
     const uint32_t li = (uint32_t)(k * NT + tid);
     x[k] = li < cnt ? src[li] : 0ull;
+    if (li < cnt) S.pay[li] = psrc[li];  // staged by original slot, placed at the end
     if (li < cnt) {
       const uint32_t h = (uint32_t)(x[k] >> 32);
       kmin = min(kmin, h);
@@ -697,13 +752,26 @@ __device__ __forceinline__ bool bucket_sort_segment(SegSmem<NT, CAP> &S, const u
     }
   }
   __syncthreads();
+  uint32_t p[IPT];
 #pragma unroll
   for (int k = 0; k < IPT; ++k) {
     const uint32_t li = (uint32_t)(k * NT + tid);
-    if (li < cnt) S.buf[bs[k]] = x[k];
+    p[k] = li < cnt ? (uint32_t)S.pay[li] : 0u;
   }
   __syncthreads();
-  for (uint32_t i = tid; i < cnt; i += NT) out[i] = S.buf[i];
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    const uint32_t li = (uint32_t)(k * NT + tid);
+    if (li < cnt) {
+      S.buf[bs[k]] = x[k];
+      S.pay[bs[k]] = (uint16_t)p[k];
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = tid; i < cnt; i += NT) {
+    out[i] = S.buf[i];
+    pout[i] = S.pay[i];
+  }
   __syncthreads();  // buf and counters reused by the next segment
   return true;
 }
@@ -793,28 +861,29 @@ __device__ __noinline__ void sort_segment_chunked(SegSmem<NT, CAP> &S, uint64_t 
 // The radix path kept out of line for the large classes, where inlining it would raise the
 // register needs of the bucket sort that every segment takes first.
 template <int NT, int IPT, int CAP>
-__device__ __noinline__ void sort_segment_smem_outlined(SegSmem<NT, CAP> &S, const uint64_t *src,
-                                                        uint32_t cnt, uint64_t *out) {
-  sort_segment_smem<NT, IPT, CAP>(S, src, cnt, out);
+__device__ __noinline__ void sort_segment_smem_outlined(SegSmem<NT, CAP> &S, uint64_t *words,
+                                                        uint16_t *pay, uint32_t cnt) {
+  sort_segment_smem<NT, IPT, CAP>(S, words, pay, cnt, words, pay);
 }
 
 // Sort one segment of cnt <= NT * IPT words in shared memory: the bucket sort, or the radix
 // passes if the bucket sort declines.
 template <int NT, int IPT, int CAP>
-__device__ __forceinline__ void sort_segment(SegSmem<NT, CAP> &S, uint64_t *words, uint32_t cnt) {
-  if (bucket_sort_segment<NT, IPT, CAP>(S, words, cnt, words)) return;
+__device__ __forceinline__ void sort_segment(SegSmem<NT, CAP> &S, uint64_t *words, uint16_t *pay,
+                                             uint32_t cnt) {
+  if (bucket_sort_segment<NT, IPT, CAP>(S, words, pay, cnt, words, pay)) return;
   if constexpr (CAP <= SEG_CAP0)
-    sort_segment_smem<NT, IPT, CAP>(S, words, cnt, words);
+    sort_segment_smem<NT, IPT, CAP>(S, words, pay, cnt, words, pay);
   else
-    sort_segment_smem_outlined<NT, IPT, CAP>(S, words, cnt, words);
+    sort_segment_smem_outlined<NT, IPT, CAP>(S, words, pay, cnt);
 }
 
 // Step 4. One CTA per listed cell of a size class, persistent over the class list: sorts the
-// cell's words in place (the number of words per thread picked per cell, the smallest of IPT_LO
-// and 2 IPT_LO that holds it; cells longer than CAP sorted in chunks through the scratch
-// buffer), then writes each entry's tile mask and the pair count of each of the cell's tiles
-// (tile_ranges[2t]). The mask is exactly the entry's pairs in the cell; in the exact mode the
-// tiles its ellipse does not reach are taken out.
+// cell's words in place, each with its tile mask (the number of words per thread picked per
+// cell, the smallest of IPT_LO and 2 IPT_LO that holds it; cells longer than CAP are sorted in
+// chunks through the scratch buffer, and their masks found again from the records afterwards),
+// then writes the pair count of each of the cell's tiles (tile_ranges[2t]), summed from the
+// masks by warp ballots.
 template <int NT, int IPT_LO, int CAP, int MIN_BLOCKS, bool CHUNKED, bool ELLIPSE>
 __global__ void __launch_bounds__(NT, MIN_BLOCKS)
     cell_sort_kernel(const uint32_t *__restrict__ list, const uint32_t *list_count,
@@ -843,72 +912,46 @@ __global__ void __launch_bounds__(NT, MIN_BLOCKS)
     }
     const uint32_t cnt = rg.y - rg.x;
     uint64_t *cw = words + rg.x;
-    if (cnt <= (uint32_t)(NT * IPT_LO)) {
-      sort_segment<NT, IPT_LO, CAP>(S, cw, cnt);
-    } else if (cnt <= (uint32_t)CAP) {
-      sort_segment<NT, 2 * IPT_LO, CAP>(S, cw, cnt);
-    } else if (CHUNKED) {
-      sort_segment_chunked<NT, 2 * IPT_LO, CAP>(S, cw, cnt, scratch + rg.x);
-    } else {
-      if (FGS_CHECK) set_status(status, ST_BOUNDS);  // a long cell listed in the short class
-      continue;
-    }
-    // masks: the sorted words are in shared memory (cells of at most CAP words) or, sorted in
-    // chunks, back in `words` (written by this CTA before the sort's last barrier: plain loads).
-    // Four words per thread per step, their records' loads issued together; the tile counts
-    // are summed by warp ballots.
+    uint16_t *cm = masks + rg.x;
     const View &V = vs.v[view_of_cell(vs, c)];
     const int64_t local = (int64_t)c - V.cell_offset;
     const uint32_t cy = (uint32_t)(local / V.cells_x);
     const uint32_t bx = (uint32_t)(local - (int64_t)cy * V.cells_x) * CELL, by = cy * CELL;
-    const bool in_smem = cnt <= (uint32_t)CAP;
     uint32_t acc[CELL * CELL];
 #pragma unroll
     for (int b = 0; b < CELL * CELL; ++b) acc[b] = 0u;
-    for (uint32_t j0 = 0; j0 < cnt; j0 += 4u * NT) {
-      uint32_t r[4];
-      uint4 g2[4];
-      uint32_t t4[4];
+    if (cnt <= (uint32_t)CAP) {
+      // the words with their masks, sorted in shared memory; the tile counts from the masks
+      if (cnt <= (uint32_t)(NT * IPT_LO)) sort_segment<NT, IPT_LO, CAP>(S, cw, cm, cnt);
+      else sort_segment<NT, 2 * IPT_LO, CAP>(S, cw, cm, cnt);
+      for (uint32_t j0 = 0; j0 < cnt; j0 += NT) {
+        const uint32_t j = j0 + (uint32_t)tid;
+        const uint32_t m = j < cnt ? (uint32_t)S.pay[j] : 0u;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint32_t j = j0 + (uint32_t)(q * NT + tid);
-        r[q] = 0xffffffffu;
-        if (j < cnt) {
-          r[q] = (uint32_t)(in_smem ? S.buf[j] : cw[j]);
-          if (!in_bounds(r[q], R, status)) r[q] = 0u;
-        }
+        for (int b = 0; b < CELL * CELL; ++b) acc[b] += __popc(__ballot_sync(0xffffffffu, (m >> b) & 1u));
       }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (r[q] != 0xffffffffu) {
-          g2[q] = __ldg(reinterpret_cast<const uint4 *>(rec + r[q]) + 2);
-          t4[q] = __ldg(tt + r[q]);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
+    } else if (CHUNKED) {
+      // a long cell: the words sorted in chunks through the scratch buffer, then each entry's
+      // mask found again from its record (plain loads: this CTA wrote the words)
+      sort_segment_chunked<NT, 2 * IPT_LO, CAP>(S, cw, cnt, scratch + rg.x);
+      for (uint32_t j0 = 0; j0 < cnt; j0 += NT) {
+        const uint32_t j = j0 + (uint32_t)tid;
         uint32_t m = 0u;
-        if (r[q] != 0xffffffffu) {
+        if (j < cnt) {
+          uint32_t r = (uint32_t)cw[j];
+          if (!in_bounds(r, R, status)) r = 0u;
           PairSet P;
-          m = pair_set(g2[q], t4[q], V, P) ? cell_mask(P, bx, by) : 0u;
-          if (ELLIPSE && m) {
-            const float4 w0 = __ldg(reinterpret_cast<const float4 *>(rec + r[q]));
-            const float4 w1 = __ldg(reinterpret_cast<const float4 *>(rec + r[q]) + 1);
-            const float qs = fmaxf(2.f * logf(255.f * w1.y), 0.f);
-            for (uint32_t rest = m; rest; rest &= rest - 1u) {
-              const uint32_t b = __ffs(rest) - 1;
-              const float xl = (float)((bx + b % CELL) * TILE) + 0.5f;
-              const float yl = (float)((by + b / CELL) * TILE) + 0.5f;
-              if (!ellipse_reaches_tile(w0.x, w0.y, w0.z, w0.w, w1.x, qs, xl, xl + (TILE - 1),
-                                        yl, yl + (TILE - 1)))
-                m &= ~(1u << b);
-            }
-          }
-          masks[rg.x + j0 + (uint32_t)(q * NT + tid)] = (uint16_t)m;
+          if (pair_set(__ldg(reinterpret_cast<const uint4 *>(rec + r) + 2), __ldg(tt + r), V, P))
+            m = cell_mask(P, bx, by);
+          if (ELLIPSE) m = ellipse_mask(rec + r, m, bx, by);
+          cm[j] = (uint16_t)m;
         }
 #pragma unroll
         for (int b = 0; b < CELL * CELL; ++b) acc[b] += __popc(__ballot_sync(0xffffffffu, (m >> b) & 1u));
       }
+    } else {
+      if (FGS_CHECK) set_status(status, ST_BOUNDS);  // a long cell listed in the short class
+      continue;
     }
     if (lane == 0) {
 #pragma unroll
@@ -1110,9 +1153,14 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
   tile_scan_kernel<false><<<(unsigned)((NC + TSCAN_PART - 1) / TSCAN_PART), 256, 0, st>>>(
       cell_ranges, NC, cell_lb, &hdr->cell_parts, lists, hdr->seg_count, (uint32_t)CELL_CAP0,
       &hdr->n_candidates, capacity, nullptr, &hdr->status, opt.wait_limit);
-  cell_scatter_kernel<<<rgrid, REC_THREADS, 0, st>>>(records, tiles_touched, R, n, vs, cell_ranges,
-                                                     words, &hdr->n_candidates, capacity,
-                                                     &hdr->status);
+  if (ellipse)
+    cell_scatter_kernel<true><<<rgrid, REC_THREADS, 0, st>>>(
+        records, tiles_touched, R, n, vs, cell_ranges, words, masks, &hdr->n_candidates,
+        capacity, &hdr->status);
+  else
+    cell_scatter_kernel<false><<<rgrid, REC_THREADS, 0, st>>>(
+        records, tiles_touched, R, n, vs, cell_ranges, words, masks, &hdr->n_candidates,
+        capacity, &hdr->status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // the keys output serves as the chunked sort's scratch (it is written only by the last step)
   if (ellipse) {
