@@ -40,7 +40,8 @@ namespace {
 constexpr int REC_THREADS = 256;
 constexpr int REC_PER_THREAD = 4;
 constexpr int REC_BLOCK = REC_THREADS * REC_PER_THREAD;  // records per CTA of the cell walks
-constexpr int SMEM_CELLS = 4096;  // cell counters a CTA keeps in shared memory (else global)
+constexpr int SMEM_CELLS = CELL_WALK_SMEM;  // cell counters a CTA keeps in shared memory (else global)
+static_assert(REC_BLOCK == CELL_WALK_BLOCK, "the workspace sizes the count table by this block");
 constexpr int CELL_CAP0 = 4096;   // cells of at most this many entries: the smaller sort class
 
 // The pairs of one record: the first k = min(tiles_touched, w h) tiles of its w x h rect in
@@ -215,12 +216,13 @@ __device__ __forceinline__ int64_t cell_id(const View &V, uint32_t cx, uint32_t 
   return V.cell_offset + (int64_t)cy * V.cells_x + cx;
 }
 
-// Step 1. Per-cell entry counts (cell_ranges[2c]), rect pairs (*n_cand) and visible records.
+// Step 1. Per-cell entry counts (cell_ranges[2c]), rect pairs (*n_cand) and visible records;
+// with cta_counts, also each CTA's own counts per cell (row blockIdx of the table).
 __global__ void __launch_bounds__(REC_THREADS)
     cell_count_kernel(const fgs_record *__restrict__ rec, const uint32_t *__restrict__ tt,
                       int64_t R, int64_t n_per_view, Views vs, int64_t capacity,
-                      uint32_t *cell_ranges, unsigned long long *n_cand,
-                      unsigned long long *n_vis, uint32_t *status) {
+                      uint32_t *cell_ranges, uint32_t *__restrict__ cta_counts,
+                      unsigned long long *n_cand, unsigned long long *n_vis, uint32_t *status) {
   __shared__ uint32_t s_cnt[SMEM_CELLS];
   __shared__ unsigned long long s_sum[2];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -261,9 +263,14 @@ __global__ void __launch_bounds__(REC_THREADS)
     atomicAdd(&s_sum[1], vis);
   }
   __syncthreads();
-  if (in_smem)
-    for (int c = tid; c < (int)vs.total_cells; c += REC_THREADS)
-      if (s_cnt[c]) atomicAdd(&cell_ranges[2 * c], s_cnt[c]);
+  if (in_smem) {
+    uint32_t *row = cta_counts ? cta_counts + (size_t)blockIdx.x * vs.total_cells : nullptr;
+    for (int c = tid; c < (int)vs.total_cells; c += REC_THREADS) {
+      const uint32_t v = s_cnt[c];
+      if (v) atomicAdd(&cell_ranges[2 * c], v);
+      if (row) row[c] = v;  // this CTA's counts, for the scatter
+    }
+  }
   if (tid == 0) {
     if (s_sum[0]) atomicAdd(n_cand, s_sum[0]);
     if (s_sum[1]) atomicAdd(n_vis, s_sum[1]);
@@ -274,21 +281,28 @@ __global__ void __launch_bounds__(REC_THREADS)
 // holds the cell's next free slot, set to its start by the cell scan), and beside it the mask
 // of the cell's tiles that hold one of the record's pairs (exact binning: those its alpha >=
 // 1/255 ellipse reaches; a mask can then be empty). With the cell counters
-// in shared memory a CTA counts its entries per cell, claims a block of slots per cell with one
-// global atomic, and hands the slots out in shared memory; the order inside a cell is
-// irrelevant (the cell is sorted next).
+// in shared memory a CTA takes its entries per cell from the count table of the cell walk (or,
+// without the table, counts them again), claims a block of slots per cell with one global
+// atomic, and hands the slots out in shared memory; the order inside a cell is irrelevant (the
+// cell is sorted next).
 template <bool ELLIPSE>
 __global__ void __launch_bounds__(REC_THREADS)
     cell_scatter_kernel(const fgs_record *__restrict__ rec, const uint32_t *__restrict__ tt,
                         int64_t R, int64_t n_per_view, Views vs, uint32_t *cell_ranges,
                         uint64_t *__restrict__ words, uint16_t *__restrict__ masks,
+                        const uint32_t *__restrict__ cta_counts,
                         const unsigned long long *n_cand, int64_t capacity, uint32_t *status) {
   __shared__ uint32_t s_cnt[SMEM_CELLS];
   if (binning_timed_out(status) || (int64_t)*n_cand > capacity) return;
   const int tid = threadIdx.x, wid = tid >> 5;
   const bool in_smem = vs.total_cells <= SMEM_CELLS;
   const int64_t base = (int64_t)blockIdx.x * REC_BLOCK;
-  if (in_smem) {
+  if (in_smem && cta_counts) {
+    // the counts of this CTA's records, as the cell walk found them (same CTA-to-record map)
+    const uint32_t *row = cta_counts + (size_t)blockIdx.x * vs.total_cells;
+    for (int c = tid; c < (int)vs.total_cells; c += REC_THREADS) s_cnt[c] = row[c];
+    __syncthreads();
+  } else if (in_smem) {
     for (int c = tid; c < (int)vs.total_cells; c += REC_THREADS) s_cnt[c] = 0u;
     __syncthreads();
     for (int i = 0; i < REC_PER_THREAD; ++i) {
@@ -300,6 +314,8 @@ __global__ void __launch_bounds__(REC_THREADS)
                  });
     }
     __syncthreads();
+  }
+  if (in_smem) {
     // the block's slots of each cell; s_cnt then holds the next one to hand out
     for (int c = tid; c < (int)vs.total_cells; c += REC_THREADS)
       if (s_cnt[c]) s_cnt[c] = atomicAdd(&cell_ranges[2 * c + 1], s_cnt[c]);
@@ -1147,20 +1163,23 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
 
   const bool ellipse = (flags & FGS_BIN_ELLIPSE) != 0;
   const unsigned rgrid = (unsigned)((R + REC_BLOCK - 1) / REC_BLOCK);
+  // the per-CTA count table, when the cells fit shared memory and the table its region
+  uint32_t *cta_counts = NC <= SMEM_CELLS && (int64_t)rgrid * NC <= L.cell_count_entries
+                             ? reinterpret_cast<uint32_t *>(ws + L.cell_counts) : nullptr;
   cell_count_kernel<<<rgrid, REC_THREADS, 0, st>>>(records, tiles_touched, R, n, vs, capacity,
-                                                   cell_ranges, &hdr->n_candidates,
+                                                   cell_ranges, cta_counts, &hdr->n_candidates,
                                                    &hdr->n_visible, &hdr->status);
   tile_scan_kernel<false><<<(unsigned)((NC + TSCAN_PART - 1) / TSCAN_PART), 256, 0, st>>>(
       cell_ranges, NC, cell_lb, &hdr->cell_parts, lists, hdr->seg_count, (uint32_t)CELL_CAP0,
       &hdr->n_candidates, capacity, nullptr, &hdr->status, opt.wait_limit);
   if (ellipse)
     cell_scatter_kernel<true><<<rgrid, REC_THREADS, 0, st>>>(
-        records, tiles_touched, R, n, vs, cell_ranges, words, masks, &hdr->n_candidates,
-        capacity, &hdr->status);
+        records, tiles_touched, R, n, vs, cell_ranges, words, masks, cta_counts,
+        &hdr->n_candidates, capacity, &hdr->status);
   else
     cell_scatter_kernel<false><<<rgrid, REC_THREADS, 0, st>>>(
-        records, tiles_touched, R, n, vs, cell_ranges, words, masks, &hdr->n_candidates,
-        capacity, &hdr->status);
+        records, tiles_touched, R, n, vs, cell_ranges, words, masks, cta_counts,
+        &hdr->n_candidates, capacity, &hdr->status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // the keys output serves as the chunked sort's scratch (it is written only by the last step)
   if (ellipse) {

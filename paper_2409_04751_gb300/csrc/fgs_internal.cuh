@@ -143,13 +143,19 @@ constexpr int SORT_MAX_PASSES = 8;
 constexpr int SEG_CAP0 = 1024;
 constexpr int SEG_CAP1 = 8192;
 constexpr int G2D_STRIDE = 12;                        // floats per record of screen-space grads
+// the cell walks of the binning (binsort.cu): records per CTA, cell counters a CTA holds in
+// shared memory, and the bound of the per-CTA count table
+constexpr int CELL_WALK_BLOCK = 1024;
+constexpr int CELL_WALK_SMEM = 4096;
+constexpr int64_t CELL_COUNTS_MAX = (int64_t)1 << 22;
 
 struct WsLayout {
   size_t header, scan_lb, tile_lb, cell_lb, cell_ranges, g2d, tile_order, vis_rec, vis_off,
-      seg_list, words, masks, chunk_first;
+      seg_list, words, masks, chunk_first, cell_counts;
   size_t sort_hist, sort_lb, alt_vals;  // the onesweep sort's regions (0 bytes unless requested)
   size_t total;
   int64_t scan_parts, tile_parts, chunks, total_tiles, sort_parts;
+  int64_t cell_count_entries;  // capacity of cell_counts (per-CTA cell counts of the cell walk)
 };
 
 __host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -187,6 +193,15 @@ constexpr WsLayout ws_layout_ex(int64_t n_records, int64_t capacity, int64_t tot
   L.words = o; o += align256(sizeof(uint64_t) * ((size_t)capacity + 4));
   L.masks = o; o += align256(sizeof(uint16_t) * ((size_t)capacity + 4));
   L.chunk_first = o; o += align256(sizeof(uint32_t) * ((size_t)L.chunks + 2));
+  // each cell-walk CTA's counts per cell, kept for the scatter when they fit (views of at most
+  // CELL_WALK_SMEM cells; at most CELL_COUNTS_MAX entries)
+  {
+    const int64_t blocks = (n_records + CELL_WALK_BLOCK - 1) / CELL_WALK_BLOCK;
+    const int64_t cells = T < CELL_WALK_SMEM ? T : CELL_WALK_SMEM;
+    const int64_t want = blocks * cells;
+    L.cell_count_entries = want < CELL_COUNTS_MAX ? want : CELL_COUNTS_MAX;
+  }
+  L.cell_counts = o; o += align256(sizeof(uint32_t) * (size_t)(L.cell_count_entries + 1));
   L.sort_parts = (capacity + SORT_PART - 1) / SORT_PART;
   L.sort_hist = o;
   if (with_onesweep) o += align256(sizeof(uint32_t) * SORT_MAX_PASSES * 256);
