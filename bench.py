@@ -79,6 +79,17 @@ def render_bytes(fgs, n, cams_c, n_views, m, flags=0):
 DEFAULT_SHAPE = (4, 8)
 
 
+def cell_entries(records, tiles_touched, cell=4):
+    """Entries of the binning's cells: per record with pairs, the cells of 4 x 4 tiles its tile
+    rect covers (records whose tiles_touched is their rect's area, as fgs_preprocess writes)."""
+    import torch
+    r = records.view(-1, 12)[:, 10:12].contiguous().view(torch.int32).view(-1, 2)
+    x0, y0 = r[:, 0] & 0xffff, (r[:, 0] >> 16) & 0xffff
+    x1, y1 = r[:, 1] & 0xffff, (r[:, 1] >> 16) & 0xffff
+    n = (x1 // cell - x0 // cell + 1) * (y1 // cell - y0 // cell + 1)
+    return int(torch.where(tiles_touched > 0, n, torch.zeros_like(n)).sum().item())
+
+
 def fp32_units(props):
     """(SM count, FP32 lanes per SM) of a device: the count from its properties, the lanes
     from its compute capability (128 on every architecture from 8.6 on, 64 on 8.0 and 6.0)."""
@@ -571,10 +582,12 @@ def run_gpu(args):
                               peak=fp32_peak, unit="TFLOP/s",
                               stage_frac=bwd_flops / (stage_ms[3] * 1e-3) / 1e12 / fp32_peak)
     vis = int((fr.tiles_touched > 0).sum().item())
-    # bin + sort: tiles_touched, two reads of each visible record's rect and depth (count and
-    # scatter walks), the bucket words written and read (8 + 8 B per pair), keys and values
-    # written (12 B per pair)
-    sort_bytes = n * 4 + vis * 2 * 16 + m * (8 + 8 + 12)
+    ents = cell_entries(fr.records, fr.tiles_touched)
+    # bin + sort: tiles_touched and each visible record's rect and depth read by the two cell
+    # walks (count, scatter), every cell entry's word and mask (8 + 2 B) written by the scatter,
+    # read and written by the cell sort and read by the emission, keys and values written
+    # (12 B per pair)
+    sort_bytes = n * 2 * 4 + vis * 2 * 16 + ents * 4 * 10 + m * 12
     kern["bin_sort"] = dict(bound="hbm", achieved=sort_bytes / (stage_ms[1] * 1e-3) / 1e9,
                             peak=peaks["hbm_gbs"], unit="GB/s")
     pre_bytes = n * 16 + vis * (12 + 16 + 4 * 48 + 48) + n * 4
@@ -589,7 +602,7 @@ def run_gpu(args):
     roof["kernel"] = names[dom]
     roof["traffic"] = _traffic({"raster_bwd": "raster_bwd_kernel",
                                 "raster_fwd": "raster_fwd_kernel",
-                                "bin_sort": "segsort_kernel",
+                                "bin_sort": "cell_emit_kernel",
                                 "preprocess_fwd": "preprocess_fwd_kernel",
                                 "preprocess_bwd": "preprocess_bwd_kernel"}[names[dom]])
     roof["peak_source"] = (f"FP32: {sms} SMs (device properties) x {lanes} FP32 lanes per SM "

@@ -319,7 +319,7 @@ fgs_status fgs_adam_step(const fgs_adam_group *groups, int n_groups, double beta
  * Results are the same as fgs_bin_sort's for the same inputs.
  *  - Limits: n_views * n <= 2^19 records, capacity <= 2^19 key slots and at most 2^17 tiles
  *    over all views; larger sizes return FGS_ERR_INVALID_ARG before anything is launched.
- *    Every GPU that loads the library holds the array (about 12 MB) until the process exits.
+ *    Every GPU that loads the library holds the array (about 22 MB) until the process exits.
  *  - status: DEVICE pointer to one uint32 the call fills, in stream order, with the device
  *    status word (FGS_OK, FGS_ERR_CAPACITY or FGS_ERR_TIMEOUT) once the sort has run.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress);

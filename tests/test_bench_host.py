@@ -50,3 +50,15 @@ def test_fp32_units_from_device_properties():
     assert bench.fp32_units(P()) == (152, 128)
     P.major, P.minor, P.multi_processor_count = 8, 0, 108
     assert bench.fp32_units(P()) == (108, 64)
+
+
+def test_cell_entries_counts_the_cells_each_rect_covers():
+    import numpy as np
+    import torch
+    # rects (x0, y0, x1, y1) in tiles: one cell, four cells across a corner, three in a row, and
+    # a record without pairs
+    rects = np.array([[0, 0, 3, 3], [3, 3, 4, 4], [0, 0, 8, 0], [5, 5, 9, 9]], np.uint16)
+    tt = torch.tensor([16, 4, 9, 0], dtype=torch.int32)
+    rec = np.zeros((4, 12), np.float32)
+    rec[:, 10:12] = rects.reshape(4, 4).copy().view(np.float32).reshape(4, 2)
+    assert bench.cell_entries(torch.as_tensor(rec.reshape(-1)), tt) == 1 + 4 + 3
