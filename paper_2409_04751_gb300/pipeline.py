@@ -1,10 +1,13 @@
 """Rendering steps fed from and drained to host memory, with the copies overlapping the compute.
 
-A HostPipeline owns two device copies of the inputs (Gaussian parameters and dL/dimage) and of
-the outputs (images and parameter gradients), a copy-in stream, a compute stream and a copy-out
-stream. Step i copies its inputs into set i % 2 while step i - 1 computes on the other set, and
-its outputs leave set i % 2 while step i + 1 computes: the host link and the GPU work overlap,
-so a stream of steps runs at about the slower of the two instead of their sum. Each step is the
+A HostPipeline owns n_sets device copies (two by default) of the inputs (Gaussian parameters
+and dL/dimage) and of the outputs (images and parameter gradients), a copy-in stream, a compute
+stream and a copy-out stream. Step i copies its inputs into set i % n_sets while step i - 1
+computes on another set, and its outputs leave set i % n_sets while step i + 1 computes: the
+host link and the GPU work overlap, so a stream of steps runs at about the slower of the two
+instead of their sum. A set is reused n_sets steps later; on the bench workload the host link
+(about 160 GB/s each way with both directions busy) bounds the stream, and a third set gains
+nothing. Each step is the
 plain call sequence fgs_preprocess -> fgs_bin_sort -> fgs_rasterize -> fgs_backward on its own
 inputs, with the scratch buffers (records, keys, workspace) shared on the compute stream; events
 order the three streams, so every step's results equal those of the plain path. With
@@ -21,7 +24,7 @@ _KEYS = ("means", "scales", "quats", "opacities", "sh")
 
 class HostPipeline:
     def __init__(self, n, sh_degree, cams_py, device="cuda", capacity=1 << 22, bg=None,
-                 backward=True, use_graph=True, shape=(0, 0)):
+                 backward=True, use_graph=True, shape=(0, 0), n_sets=2):
         self.device = torch.device(device)
         dev = self.device
         self.n, self.sh_degree = int(n), int(sh_degree)
@@ -30,21 +33,25 @@ class HostPipeline:
         self.P = fgs.fgs_total_pixels(self.cams)
         self.bg = None if bg is None else tuple(float(v) for v in bg)
         self.backward = bool(backward)
+        self.n_sets = int(n_sets)
+        if self.n_sets < 2:
+            raise ValueError("n_sets >= 2")
         K = (self.sh_degree + 1) ** 2
         shapes = dict(means=(n, 3), scales=(n, 3), quats=(n, 4), opacities=(n,), sh=(n, K, 3))
         z = lambda s: torch.zeros(s, dtype=torch.float32, device=dev)
-        self.inp = [{k: z(shapes[k]) for k in _KEYS} for _ in range(2)]
-        self.dL = [z((3 * self.P,)) for _ in range(2)]
-        self.img = [z((3 * self.P,)) for _ in range(2)]
-        self.grad = [{k: z(shapes[k]) for k in _KEYS} for _ in range(2)]
+        S = self.n_sets
+        self.inp = [{k: z(shapes[k]) for k in _KEYS} for _ in range(S)]
+        self.dL = [z((3 * self.P,)) for _ in range(S)]
+        self.img = [z((3 * self.P,)) for _ in range(S)]
+        self.grad = [{k: z(shapes[k]) for k in _KEYS} for _ in range(S)]
         self.renderer = FisheyeRenderer(dev, capacity=capacity, fwd_ppt=shape[0], bwd_ppt=shape[1])
         self.s_in = torch.cuda.Stream(dev)
         self.s_run = torch.cuda.Stream(dev)
         self.s_out = torch.cuda.Stream(dev)
         E = lambda: torch.cuda.Event()
-        self.ev_in = [E(), E()]    # inputs of set k landed
-        self.ev_run = [E(), E()]   # compute on set k done
-        self.ev_out = [E(), E()]   # outputs of set k left
+        self.ev_in = [E() for _ in range(S)]    # inputs of set k landed
+        self.ev_run = [E() for _ in range(S)]   # compute on set k done
+        self.ev_out = [E() for _ in range(S)]   # outputs of set k left
         self.step = 0
         self.use_graph = bool(use_graph)
         self.graphs = None
@@ -66,7 +73,7 @@ class HostPipeline:
                 self._compute(0)
             self.s_run.synchronize()
             self.graphs = []
-            for k in range(2):
+            for k in range(self.n_sets):
                 g = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(g, stream=self.s_run):
                     self._compute(k)
@@ -97,7 +104,7 @@ class HostPipeline:
         """Queue one step: host_inputs (dict of pinned tensors) and host_dL in, host_img and
         host_grads (pinned) out. Asynchronous; the host buffers must stay untouched until
         `wait(handle)` returns. Returns a handle."""
-        k = self.step % 2
+        k = self.step % self.n_sets
         inp, dL, img, grad = self.inp[k], self.dL[k], self.img[k], self.grad[k]
         # copy in once the compute that last read set k is done
         self.s_in.wait_event(self.ev_run[k])
