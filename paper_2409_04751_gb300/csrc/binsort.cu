@@ -200,14 +200,13 @@ __device__ __forceinline__ uint32_t ellipse_mask(const fgs_record *rp, uint32_t 
   if (m == 0u) return 0u;
   const float4 w0 = __ldg(reinterpret_cast<const float4 *>(rp));
   const float4 w1 = __ldg(reinterpret_cast<const float4 *>(rp) + 1);
-  const float qs = fmaxf(2.f * logf(255.f * w1.y), 0.f);
+  const EllipseTest E = ellipse_test(w0.x, w0.y, w0.z, w0.w, w1.x,
+                                     fmaxf(2.f * logf(255.f * w1.y), 0.f));
   for (uint32_t rest = m; rest; rest &= rest - 1u) {
     const uint32_t b = __ffs(rest) - 1;
     const float xl = (float)((bx + b % CELL) * TILE) + 0.5f;
     const float yl = (float)((by + b / CELL) * TILE) + 0.5f;
-    if (!ellipse_reaches_tile(w0.x, w0.y, w0.z, w0.w, w1.x, qs, xl, xl + (TILE - 1), yl,
-                              yl + (TILE - 1)))
-      m &= ~(1u << b);
+    if (!ellipse_reaches_tile(E, xl, xl + (TILE - 1), yl, yl + (TILE - 1))) m &= ~(1u << b);
   }
   return m;
 }

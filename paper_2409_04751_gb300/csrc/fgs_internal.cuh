@@ -408,25 +408,39 @@ __device__ __forceinline__ FishG fisheye_g(float x, float y, float z) {
 // mean inside it, else it lies on an edge, where it is the 1D minimum in the free coordinate
 // clamped to the edge. The pair is kept when the minimum is at most q* (1 + 1e-3) + 1e-2, a
 // margin far above the rounding of the rasterizer's exponent, so no contributing pair is lost.
-__device__ __forceinline__ bool ellipse_reaches_tile(float mx, float my, float A, float B,
-                                                     float C, float qs, float xl, float xh,
+// The per-Gaussian part (threshold and the two reciprocals) is computed once and reused for
+// every tile the Gaussian's rect covers.
+struct EllipseTest {
+  float mx, my, A, B, C, thr, iA, iC;
+};
+
+__device__ __forceinline__ EllipseTest ellipse_test(float mx, float my, float A, float B, float C,
+                                                    float qs) {
+  EllipseTest E;
+  E.mx = mx; E.my = my; E.A = A; E.B = B; E.C = C;
+  E.thr = fmaf(qs, 1.001f, 1e-2f);
+  E.iA = 1.f / A;
+  E.iC = 1.f / C;
+  return E;
+}
+
+__device__ __forceinline__ bool ellipse_reaches_tile(const EllipseTest &E, float xl, float xh,
                                                      float yl, float yh) {
+  const float mx = E.mx, my = E.my, A = E.A, B = E.B, C = E.C;
   if (mx >= xl && mx <= xh && my >= yl && my <= yh) return true;
-  const float thr = fmaf(qs, 1.001f, 1e-2f);
-  const float iA = 1.f / A, iC = 1.f / C;
   float qmin = 3.0e38f;
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
     // vertical edge x = xl or xh: dy* = -B dx / C, clamped
     const float dx = (e ? xh : xl) - mx;
-    const float dy = fminf(fmaxf(-B * dx * iC, yl - my), yh - my);
+    const float dy = fminf(fmaxf(-B * dx * E.iC, yl - my), yh - my);
     qmin = fminf(qmin, fmaf(dx, fmaf(A, dx, 2.f * B * dy), C * dy * dy));
     // horizontal edge y = yl or yh: dx* = -B dy / A, clamped
     const float ey = (e ? yh : yl) - my;
-    const float ex = fminf(fmaxf(-B * ey * iA, xl - mx), xh - mx);
+    const float ex = fminf(fmaxf(-B * ey * E.iA, xl - mx), xh - mx);
     qmin = fminf(qmin, fmaf(ex, fmaf(A, ex, 2.f * B * ey), C * ey * ey));
   }
-  return qmin <= thr;
+  return qmin <= E.thr;
 }
 
 // ------------------------------------------------------------------------------------------
