@@ -211,10 +211,11 @@ def _traffic(kernel_name):
 # ------------------------------------------------------------------------------------------
 # CPU oracle (cpu_baseline leg and --impl reference)
 
-def _oracle_sample_rate(scene, cam, target_s, rng_seed=0):
-    """Time the FP64 oracle's fwd+bwd on a pixel sample sized for about target_s seconds and
-    extrapolate to views/s for the full view. The sample holds at least 256 pixels per thread,
-    so every OpenMP thread has work. Returns (views_per_s, seconds, sample_desc, threads)."""
+def _oracle_sample_rate(scene, cam, target_s, rng_seed=0, backward=True, min_per_thread=256):
+    """Time the FP64 oracle's fwd+bwd (forward only with backward=False) on a pixel sample sized
+    for about target_s seconds and extrapolate to views/s for the full view. The sample holds at
+    least min_per_thread pixels per thread, so every OpenMP thread has work. Returns
+    (views_per_s, seconds, sample_desc, threads)."""
     import oracle
     w, h = cam["width"], cam["height"]
     P = w * h
@@ -222,7 +223,7 @@ def _oracle_sample_rate(scene, cam, target_s, rng_seed=0):
     t0 = time.perf_counter()
     G = oracle.project(scene, cam)
     t_proj = time.perf_counter() - t0
-    n_pix = min(P, 256 * oracle.num_threads())
+    n_pix = min(P, min_per_thread * oracle.num_threads())
     spent = 0.0
     per_pix = None
     while True:
@@ -231,7 +232,8 @@ def _oracle_sample_rate(scene, cam, target_s, rng_seed=0):
         g = rng.normal(0, 1e-2, (n_pix, 3))
         t0 = time.perf_counter()
         oracle.render(G, pix)
-        oracle.backward(G, scene, cam, pix, g)
+        if backward:
+            oracle.backward(G, scene, cam, pix, g)
         dt = time.perf_counter() - t0
         spent += dt
         per_pix = dt / n_pix
@@ -239,8 +241,8 @@ def _oracle_sample_rate(scene, cam, target_s, rng_seed=0):
             break
         n_pix = int(min(P, max(n_pix * 2, (target_s - spent) / max(per_pix, 1e-9))))
     est = t_proj + per_pix * P
-    desc = (f"oracle fwd+bwd on {n_pix} random pixels of the {w}x{h} view "
-            f"(+ projection of all Gaussians), extrapolated to the full view")
+    desc = (f"oracle {'fwd+bwd' if backward else 'fwd'} on {n_pix} random pixels of the {w}x{h} "
+            f"view (+ projection of all Gaussians), extrapolated to the full view")
     return 1.0 / est, spent + t_proj, desc, oracle.num_threads()
 
 
@@ -270,6 +272,32 @@ def cpu_job(kind, target_s):
         fwd, both, thr = _oracle_full_view(scene, cams[0])
         return dict(threads=thr, fwd_s=fwd, fwd_bwd_s=both, fwd_views_per_s=1.0 / fwd,
                     fwd_bwd_views_per_s=1.0 / both)
+    if kind == "config2":  # 3M Gaussians, 2048^2 at 190 deg: the first pose, forward
+        scene, cams = scenes.config2(n_poses=1)
+        v, secs, desc, thr = _oracle_sample_rate(scene, cams[0], target_s, backward=False,
+                                                 min_per_thread=16)
+        return dict(threads=thr, fwd_views_per_s=v, seconds=secs, sample=desc)
+    if kind == "config3":  # 1M Gaussians, 64 mixed views: views 0 and 1, fwd+bwd
+        scene, cams = scenes.config3()
+        per_view, secs = [], 0.0
+        for cam in cams[:2]:
+            v, s_, desc, thr = _oracle_sample_rate(scene, cam, target_s / 2, min_per_thread=32)
+            per_view.append(1.0 / v)
+            secs += s_
+        return dict(threads=thr, fwd_bwd_views_per_s=len(per_view) / sum(per_view), seconds=secs,
+                    sample="views 0 and 1 of the 64 (" + desc.replace("the ", "each ", 1) + ")")
+    if kind == "config4":  # serving: one 1024^2 request on the 0.2M and on the 2M scene, forward
+        per_req, secs = [], 0.0
+        for k, n in ((0, 200_000), (3, 2_000_000)):
+            scene = scenes.shell_scene(n, seed=40 + k, sh_degree=3)
+            cam = scenes.pose_camera(1024, 1024, 180.0, seed=77 + k)
+            v, s_, desc, thr = _oracle_sample_rate(scene, cam, target_s / 2, backward=False,
+                                                   min_per_thread=32)
+            per_req.append(1.0 / v)
+            secs += s_
+        return dict(threads=thr, ms_per_request=[round(1e3 * t, 1) for t in per_req],
+                    seconds=secs, sample="a 1024x1024 request at 180 deg on the 0.2M and the 2M "
+                    "scene (" + desc.replace("the ", "each ", 1) + ")")
     scene, cams = scenes.config1()
     v, secs, desc, thr = _oracle_sample_rate(scene, cams[0], target_s)
     return dict(threads=thr, fwd_bwd_views_per_s=v, seconds=secs, sample=desc)
@@ -299,6 +327,10 @@ def cpu_baseline_legs(target_s):
         legs[tag] = dict(config0=run_cpu_job("config0", threads, target_s),
                          config1=run_cpu_job("config1", threads, target_s))
     allc = legs["all_cores"]
+    # the other configurations on subsets, every core, about a quarter of the time each
+    subsets = {k: run_cpu_job(k, 0, max(target_s / 4, 1.0)) for k in ("config2", "config3", "config4")}
+    for v in subsets.values():
+        v["seconds"] = round(v["seconds"], 2)
     return dict(value=allc["config1"]["fwd_bwd_views_per_s"], unit="views/s",
                 cores=allc["config1"]["threads"], kind="oracle",
                 sample=allc["config1"]["sample"], seconds=round(allc["config1"]["seconds"], 2),
@@ -313,9 +345,12 @@ def cpu_baseline_legs(target_s):
                                           fwd_bwd_views_per_s=l["config1"]["fwd_bwd_views_per_s"],
                                           seconds=round(l["config1"]["seconds"], 2))
                                 for tag, l in legs.items()},
+                config2_subset=subsets["config2"], config3_subset=subsets["config3"],
+                config4_subset=subsets["config4"],
                 note="value: the benchmark view (500k Gaussians, 1752x1168) on every core, "
                      "from a timed pixel sample; config0_full: the 10k-Gaussian 256x256 view "
-                     "rendered and differentiated at every pixel")
+                     "rendered and differentiated at every pixel; config2-4: pixel samples of "
+                     "one pose, two views and two requests, every core")
 
 
 def run_reference(args):
