@@ -108,6 +108,9 @@ def _oracle(rect, depth, n, cams_py):
     (3000, [(256, 256)], 15, dict(max_ext=5, tie_frac=1.0)),
     # a mix: half of the entries tie, half do not
     (6000, [(640, 480)], 16, dict(max_ext=4, tie_frac=0.5)),
+    # 4096 cells (all counted in shared memory) and 1075 record blocks: the per-block count
+    # table would exceed its bound, so the scatter counts its records again
+    (1_100_000, [(4096, 4096)], 17, dict(max_ext=1, p_empty=0.6, tie_frac=0.1)),
 ])
 @pytest.mark.parametrize("flags", SORTS)
 def test_binsort_bit_exact(cuda_device, n, sizes, seed, kw, flags):
