@@ -1029,8 +1029,9 @@ __global__ void __launch_bounds__(CEMIT_THREADS)
                      const uint16_t *__restrict__ masks, Views vs, uint64_t *__restrict__ keys,
                      uint32_t *__restrict__ vals, int64_t capacity,
                      const unsigned long long *n_cand, uint32_t *status) {
-  __shared__ uint32_t s_bal[EMIT_GROUPS][CELL * CELL];  // group g's ballot of tile bit b
-  __shared__ uint32_t s_pre[EMIT_GROUPS][CELL * CELL];  // where group g's entries of tile b go
+  // per group g and tile bit b: the group's ballot of the bit and where its entries of tile b go
+  __shared__ uint2 s_bp[EMIT_GROUPS][CELL * CELL];
+  __shared__ uint32_t s_tile[CELL * CELL];  // global tile id of each bit
   if (binning_timed_out(status) || (int64_t)*n_cand > capacity) return;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t lt = lanemask_lt();
@@ -1057,7 +1058,7 @@ __global__ void __launch_bounds__(CEMIT_THREADS)
           const uint32_t bal = __ballot_sync(0xffffffffu, (m >> b) & 1u);
           if (lane == b) mine = bal;
         }
-        if (lane < CELL * CELL) s_bal[g][lane] = mine;
+        if (lane < CELL * CELL) s_bp[g][lane].x = mine;
       }
       __syncthreads();
       {  // (2) warp b: exclusive scan over the groups, 4 consecutive groups per lane
@@ -1065,15 +1066,17 @@ __global__ void __launch_bounds__(CEMIT_THREADS)
         const uint32_t tx = bx + b % CELL, ty = by + b / CELL;
         uint32_t start = 0u, end = 0u;
         if (tx < (uint32_t)V.tiles_x && ty < (uint32_t)V.tiles_y) {
-          const uint2 trg = __ldg(reinterpret_cast<const uint2 *>(tile_ranges) + cell_tile(V, bx, by, b));
+          const int64_t t = cell_tile(V, bx, by, b);
+          const uint2 trg = __ldg(reinterpret_cast<const uint2 *>(tile_ranges) + t);
           start = trg.x;
           end = trg.y;
+          if (lane == 0) s_tile[b] = (uint32_t)t;
         }
         uint32_t n4[4], sum = 0u;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const uint32_t g = 4u * lane + q;
-          n4[q] = g < G ? __popc(s_bal[g][b]) : 0u;
+          n4[q] = g < G ? __popc(s_bp[g][b].x) : 0u;
           sum += n4[q];
         }
         uint32_t incl = sum;
@@ -1086,7 +1089,7 @@ __global__ void __launch_bounds__(CEMIT_THREADS)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const uint32_t g = 4u * lane + q;
-          if (g < G) s_pre[g][b] = run;
+          if (g < G) s_bp[g][b].y = run;
           run += n4[q];
         }
         // checked build: the tile receives exactly its counted pairs
@@ -1099,11 +1102,11 @@ __global__ void __launch_bounds__(CEMIT_THREADS)
         const uint64_t kd = w >> 32;
 #pragma unroll
         for (int b = 0; b < CELL * CELL; ++b) {
-          const uint32_t bal = s_bal[g][b];
-          if ((bal >> lane) & 1u) {
-            const uint32_t pos = s_pre[g][b] + __popc(bal & lt);
+          const uint2 bp = s_bp[g][b];
+          if ((bp.x >> lane) & 1u) {
+            const uint32_t pos = bp.y + __popc(bp.x & lt);
             if (in_bounds(pos, (uint64_t)capacity, status) && (int64_t)pos < capacity) {
-              keys[pos] = ((uint64_t)cell_tile(V, bx, by, b) << 32) | kd;
+              keys[pos] = ((uint64_t)s_tile[b] << 32) | kd;
               vals[pos] = (uint32_t)w;
             }
           }
