@@ -616,6 +616,12 @@ def run_gpu(args):
     kern["raster_bwd"] = dict(bound="alu", achieved=bwd_flops / (kernel_ms["raster_bwd"] * 1e-3) / 1e12,
                               peak=fp32_peak, unit="TFLOP/s",
                               stage_frac=bwd_flops / (stage_ms[3] * 1e-3) / 1e12 / fp32_peak)
+    # the records each rasterizer gathered into shared memory (48 B each, from the instrumented
+    # launch's counts) and the rate at which its timed launch moved them
+    for name, c in (("raster_fwd", counters[4]), ("raster_bwd", counters[5])):
+        kern[name]["gathered_mb"] = c * 48 / 1e6
+        kern[name]["gathered_per_pair"] = c / max(m, 1)
+        kern[name]["gather_gbs"] = c * 48 / (kernel_ms[name] * 1e-3) / 1e9
     vis = int((fr.tiles_touched > 0).sum().item())
     ents = cell_entries(fr.records, fr.tiles_touched)
     # bin + sort: tiles_touched and each visible record's rect and depth read by the two cell

@@ -364,9 +364,10 @@ fgs_status fgs_read_status(const void *workspace, fgs_stream stream, int *status
 
 /* Measurement hook (not part of the rendering path): after calls made with FGS_OPT_INSTRUMENT,
  * the workspace holds counters[0] = forward (pixel, Gaussian) evaluations, [1] = forward
- * blends, [2] = backward evaluations, [3] = backward contributions. The counters are reset by
- * fgs_bin_sort. fgs_read_counters synchronises `stream` and copies the four counters to host
- * memory. */
+ * blends, [2] = backward evaluations, [3] = backward contributions, [4] = records the forward
+ * rasterizer copied into shared memory (48 bytes each), [5] = the backward's. The counters are
+ * reset by fgs_bin_sort. fgs_read_counters synchronises `stream` and copies the six counters to
+ * host memory (counters: HOST uint64[6]). */
 fgs_status fgs_read_counters(const void *workspace, fgs_stream stream, uint64_t *counters);
 
 /* Static description of a status code. */

@@ -329,7 +329,7 @@ fgs_status fgs_read_counters(const void *workspace, fgs_stream stream, uint64_t 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (cudaStreamSynchronize(st) != cudaSuccess) return FGS_ERR_CUDA;
   if (cudaMemcpy(counters, reinterpret_cast<const char *>(workspace) + offsetof(WsHeader, counters),
-                 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+                 6 * sizeof(uint64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
     return FGS_ERR_CUDA;
   return FGS_OK;
 }

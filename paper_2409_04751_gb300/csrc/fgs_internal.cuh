@@ -111,8 +111,9 @@ struct WsHeader {
   uint32_t backward_tiles;    // tile queue of the backward rasterizer
   // measurement counters, written only by instrumented launches (FGS_OPT_INSTRUMENT):
   // [0] forward (pixel, Gaussian) evaluations, [1] forward blends,
-  // [2] backward evaluations, [3] backward contributions
-  unsigned long long counters[4];
+  // [2] backward evaluations, [3] backward contributions,
+  // [4] records the forward staged (copied into shared memory), [5] the backward's
+  unsigned long long counters[6];
   unsigned long long n_visible;  // records with a non-empty rect (written by the scan)
   unsigned long long n_candidates;  // (record, tile) pairs of the rects (written by the scan)
   unsigned long long n_dropped;  // onesweep emission: pairs beyond their record's rect
@@ -120,7 +121,7 @@ struct WsHeader {
   uint32_t bounds_magic;         // BOUNDS_MAGIC once a binning on this workspace set the two
   uint32_t bounds_records;       // records of that binning (list entries must be below)
   uint32_t bounds_pairs;         // its key capacity (list ends must not exceed it)
-  uint32_t pad[35];
+  uint32_t pad[31];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
 static_assert(offsetof(WsHeader, status) == 0, "the status word starts the header");

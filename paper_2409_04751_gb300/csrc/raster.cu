@@ -313,6 +313,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
   __syncthreads();
   uint32_t phase0 = 0, phase1 = 0;
   uint32_t n_eval = 0, n_blend = 0;
+  unsigned long long n_staged = 0;  // records copied in (thread 0 counts)
   const int lx = tid & (TILE - 1), ly0 = (tid / TILE) * PPT;
   const float fu = (float)lx - 7.5f, fv = (float)ly0 - 7.5f;
   const float2 u2 = dup2(fu), uu2 = dup2(fu * fu);
@@ -353,6 +354,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
       load_idx<NT, PER>(vals, ti.start, BATCH, count > BATCH ? count - BATCH : 0u, idx_next, bd, status);
       fence_proxy_async_smem();
       issue_batch<NT, PER>(raw[0], &bar[0], rec, idx, min(count, (uint32_t)BATCH));
+      if (COUNT && tid == 0) n_staged += min(count, (uint32_t)BATCH);
       for (uint32_t b = 0; b < nb; ++b) {
         const int s = b & 1;
         const uint32_t lo = b * BATCH;
@@ -361,6 +363,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
           fence_proxy_async_smem();
           issue_batch<NT, PER>(raw[s ^ 1], &bar[s ^ 1], rec, idx_next,
                                min((uint32_t)BATCH, count - lo - BATCH));
+          if (COUNT && tid == 0) n_staged += min((uint32_t)BATCH, count - lo - BATCH);
           const uint32_t lo2 = lo + 2 * BATCH;
           load_idx<NT, PER>(vals, ti.start, lo2, count > lo2 ? count - lo2 : 0u, idx_next, bd, status);
         }
@@ -496,6 +499,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
   if (COUNT) {
     atomicAdd(&counters[0], (unsigned long long)n_eval);
     atomicAdd(&counters[1], (unsigned long long)n_blend);
+    if (tid == 0) atomicAdd(&counters[4], n_staged);
   }
 }
 
@@ -679,6 +683,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 8 ? 16 : 1)
   __syncthreads();
   uint32_t phase0 = 0, phase1 = 0;
   uint32_t n_eval = 0, n_contrib = 0;
+  unsigned long long n_staged = 0;  // records copied in (thread 0 counts)
   const int lx = tid & (TILE - 1), ly0 = (tid / TILE) * PPT;
   const float fu = (float)lx - 7.5f, fv = (float)ly0 - 7.5f;
   const float2 u2 = dup2(fu), uu2 = dup2(fu * fu);
@@ -736,6 +741,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 8 ? 16 : 1)
         if (nb >= 2) load_idx<NT, PER>(vals, ti.start, lo0 - BATCH, BATCH, idx_next, bd, status);
         fence_proxy_async_smem();
         issue_batch<NT, PER>(raw[0], &bar[0], rec, idx, max_last - lo0);
+        if (COUNT && tid == 0) n_staged += max_last - lo0;
 #pragma unroll
         for (int k = 0; k < PER; ++k) xidx[tid + k * NT] = idx[k];
       }
@@ -748,6 +754,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 8 ? 16 : 1)
         if (b >= 1) {
           fence_proxy_async_smem();
           issue_batch<NT, PER>(raw[s ^ 1], &bar[s ^ 1], rec, idx_next, BATCH);
+          if (COUNT && tid == 0) n_staged += BATCH;
 #pragma unroll
           for (int k = 0; k < PER; ++k) mine[k] = idx_next[k];
           if (b >= 2) load_idx<NT, PER>(vals, ti.start, lo - 2 * BATCH, BATCH, idx_next, bd, status);
@@ -854,6 +861,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 8 ? 16 : 1)
   if (COUNT) {
     atomicAdd(&counters[2], (unsigned long long)n_eval);
     atomicAdd(&counters[3], (unsigned long long)n_contrib);
+    if (tid == 0) atomicAdd(&counters[5], n_staged);
   }
 }
 

@@ -358,6 +358,6 @@ def fgs_read_status(workspace, stream=None) -> int:
 
 
 def fgs_read_counters(workspace, stream=None):
-    out = (ctypes.c_uint64 * 4)()
+    out = (ctypes.c_uint64 * 6)()
     _check(lib().fgs_read_counters(_ptr(workspace), _stream(stream), out), "fgs_read_counters")
     return [int(v) for v in out]

@@ -282,3 +282,35 @@ def test_calls_with_different_shapes_run_side_by_side(cuda_device):
             assert torch.equal(img, img0)
             for k in g:
                 assert parity.rel_l2(g[k].cpu().numpy(), g0[k].cpu().numpy()) < 1e-5, k
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (2, 2), (4, 8)])
+def test_instrumented_launches_count_what_they_do(cuda_device, shape):
+    """The measurement launches (FGS_OPT_INSTRUMENT) render the same image and count their work
+    consistently: the backward's contributions are exactly the forward's blends (both passes
+    take the same alpha decisions), every evaluation count bounds its blend count, the backward
+    stages exactly the entries up to each tile's furthest processed one, and the forward stages
+    at least those and at most the tile's whole list."""
+    scene, cams = scenes.config0()
+    dev = cuda_device
+    gs = scene_to_device(scene, dev)
+    r = FisheyeRenderer(dev, capacity=1 << 16, fwd_ppt=shape[0], bwd_ppt=shape[1])
+    plain = r.forward(gs, cams).images.clone()
+    r.opts = fgs.options(fwd=shape[0], bwd=shape[1], instrument=True)
+    fr = r.forward(gs, cams)
+    assert torch.equal(fr.images, plain)
+    dL = torch.as_tensor(scenes.upstream_grad((3 * 256 * 256,), 1e-2, seed=3)).to(dev)
+    r.backward(gs, fr, dL)
+    c = fgs.fgs_read_counters(r._bufs["ws"])
+    m = int(fr.n_intersections.item())
+    assert c[1] == c[3] > 0
+    assert c[1] <= c[0] and c[3] <= c[2]
+    # per tile: the furthest list entry any of its pixels processed (clamped to the list)
+    rg = fr.tile_ranges.view(-1, 2).cpu().numpy().astype(np.int64)
+    npr = fr.n_processed.view(256, 256).cpu().numpy().astype(np.int64)
+    furthest = np.zeros(rg.shape[0], np.int64)
+    for t in range(rg.shape[0]):
+        ty, tx = divmod(t, 16)
+        furthest[t] = min(npr[16 * ty:16 * ty + 16, 16 * tx:16 * tx + 16].max(), rg[t, 1] - rg[t, 0])
+    assert c[5] == furthest.sum()
+    assert furthest.sum() <= c[4] <= m
