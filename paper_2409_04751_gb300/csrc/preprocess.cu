@@ -286,19 +286,37 @@ __global__ void __launch_bounds__(PRE_BWD_THREADS, 4)
     float Y[K], dY[K][3];
     sh_basis<D>(ux, uy, uz, Y);
     sh_basis_grad<D>(ux, uy, uz, dY);
+    // s_k = <SH row k, dL/drgb>, each over the channels in order 0, 1, 2; the coefficients
+    // come in as 16-byte loads where the rows allow it (the same sums either way)
+    float sk[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) sk[k] = 0.f;
+    if (VEC && (K3 % 4) == 0) {
+#pragma unroll
+      for (int q = 0; q < K3 / 4; ++q) {
+        const float4 w = __ldg(reinterpret_cast<const float4 *>(shp) + q);
+        const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int j = 4 * q + t;
+          sk[j / 3] = fmaf(wv[t], grgb[j % 3], sk[j / 3]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < K3; ++j) sk[j / 3] = fmaf(__ldg(shp + j), grgb[j % 3], sk[j / 3]);
+    }
     float dd0 = 0.f, dd1 = 0.f, dd2 = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      float s = 0.f;
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
         const int j = 3 * k + ch;
         my_dsh[j] = fmaf(Y[k], grgb[ch], first ? 0.f : my_dsh[j]);
-        s = fmaf(__ldg(shp + j), grgb[ch], s);
       }
-      dd0 = fmaf(s, dY[k][0], dd0);
-      dd1 = fmaf(s, dY[k][1], dd1);
-      dd2 = fmaf(s, dY[k][2], dd2);
+      dd0 = fmaf(sk[k], dY[k][0], dd0);
+      dd1 = fmaf(sk[k], dY[k][1], dd1);
+      dd2 = fmaf(sk[k], dY[k][2], dd2);
     }
     const float dot = ux * dd0 + uy * dd1 + uz * dd2;
     dmu[0] += (dd0 - ux * dot) * un;

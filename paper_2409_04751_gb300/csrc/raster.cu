@@ -606,7 +606,10 @@ __device__ __forceinline__ void bwd_contrib2(bool c0, bool c1, float2 e, float r
   const float2 araw = make_float2(c0 ? ex2_approx(e.x) : 0.f, c1 ? ex2_approx(e.y) : 0.f);
   const float2 alpha = make_float2(fminf(ALPHA_MAX, araw.x), fminf(ALPHA_MAX, araw.y));
   const float2 oma = fadd2(dup2(1.f), make_float2(-alpha.x, -alpha.y));
-  const float2 om = make_float2(c0 ? rcp_approx(oma.x) : 1.f, c1 ? rcp_approx(oma.y) : 1.f);
+  // a pixel that does not take part has alpha = 0 and 1 - alpha = 1, whose hardware
+  // reciprocal is exactly 1 (checked on sm_103a), so its transmittance is left as it was
+  // without a select
+  const float2 om = make_float2(rcp_approx(oma.x), rcp_approx(oma.y));
   T = fmul2(T, om);  // transmittance before this Gaussian
   const float2 wgt = fmul2(alpha, T);
   const float2 gc = ffma2(G2, dup2(b), ffma2(G1, dup2(g), fmul2(G0, dup2(r))));
