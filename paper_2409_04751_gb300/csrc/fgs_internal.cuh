@@ -108,7 +108,7 @@ struct WsHeader {
   uint32_t cell_parts;        // partition counter of the per-cell count scan
   uint32_t spare[4];
   uint32_t raster_tiles;      // tile queue of the forward rasterizer
-  uint32_t backward_tiles;    // tile queue of the backward rasterizer
+  uint32_t spare2;            // (the backward's tile queue sits with its tile order)
   // measurement counters, written only by instrumented launches (FGS_OPT_INSTRUMENT):
   // [0] forward (pixel, Gaussian) evaluations, [1] forward blends,
   // [2] backward evaluations, [3] backward contributions,
@@ -185,7 +185,7 @@ constexpr WsLayout ws_layout_ex(int64_t n_records, int64_t capacity, int64_t tot
   L.cell_ranges = o; o += align256(sizeof(uint32_t) * 2 * (size_t)T);
   L.g2d = o; if (with_g2d) o += align256(sizeof(float) * G2D_STRIDE * (size_t)R);
   // the backward's tile order: per-tile work bucket, tile ids by decreasing work, histogram
-  L.tile_order = o; if (with_g2d) o += align256(sizeof(uint32_t) * (2 * (size_t)T + 2 * WORK_BUCKETS));
+  L.tile_order = o; if (with_g2d) o += align256(sizeof(uint32_t) * (2 * (size_t)T + 2 * WORK_BUCKETS + 1));
   L.vis_rec = o; o += align256(sizeof(uint32_t) * (size_t)R);
   L.vis_off = o; o += align256(sizeof(uint64_t) * (size_t)R);
   L.seg_list = o; o += align256(sizeof(uint32_t) * 2 * (size_t)T);

@@ -25,6 +25,7 @@
 // carries) and lanes add the totals to the records' accumulators. The preprocess backward turns
 // the moments into dL/dxy, dL/dconic and dL/dopacity with the record's conic and opacity. The
 // backward takes its tiles longest first (tile_work_kernel, tile_order_kernel).
+#include <algorithm>
 #include "fgs_internal.cuh"
 
 namespace fgs {
@@ -880,13 +881,18 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 8 ? 16 : 1)
 // entries any of its pixels processed in the forward; tiles are ordered by the log2 class of
 // that work, most first, so that the persistent CTAs start the long tiles early and the short
 // ones fill in at the end. Any order gives the same gradients up to the order of their sums.
+// The same launch zeroes the records' gradient accumulators (16-byte stores over the grid),
+// which the backward rasterizer adds into next.
 __global__ void __launch_bounds__(256)
     tile_work_kernel(const uint32_t *__restrict__ ranges, const uint32_t *__restrict__ n_processed,
                      Views vs, uint32_t *status, uint32_t *__restrict__ bucket,
-                     uint32_t *__restrict__ hist) {
+                     uint32_t *__restrict__ hist, float4 *__restrict__ g2d4, int64_t n_g2d4) {
   __shared__ uint32_t s_hist[WORK_BUCKETS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x < WORK_BUCKETS) s_hist[threadIdx.x] = 0u;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_g2d4;
+       j += (int64_t)gridDim.x * blockDim.x)
+    g2d4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
   const int64_t t = (int64_t)blockIdx.x * 8 + warp;
   if (t < vs.total_tiles) {
@@ -978,7 +984,8 @@ template <int PPT>
 cudaError_t bwd_launch(const fgs_record *records, const uint32_t *vals, const uint32_t *ranges,
                        const Views &vs, float bg0, float bg1, float bg2, const float *final_T,
                        const uint32_t *n_processed, const float *dL, float *g2d,
-                       const uint32_t *order, WsHeader *hdr, bool instrument, cudaStream_t st) {
+                       const uint32_t *order, uint32_t *tile_counter, WsHeader *hdr,
+                       bool instrument, cudaStream_t st) {
   constexpr int NT = TILE_PIX / PPT;
   static int occ = 0;
   if (occ == 0) occ = occupancy_of(raster_bwd_kernel<PPT, false>, NT);
@@ -988,11 +995,11 @@ cudaError_t bwd_launch(const fgs_record *records, const uint32_t *vals, const ui
   if (instrument)
     raster_bwd_kernel<PPT, true><<<(unsigned)grid, NT, 0, st>>>(
         records, vals, ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL, g2d, order,
-        &hdr->backward_tiles, &hdr->status, hdr->counters);
+        tile_counter, &hdr->status, hdr->counters);
   else
     raster_bwd_kernel<PPT, false><<<(unsigned)grid, NT, 0, st>>>(
         records, vals, ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL, g2d, order,
-        &hdr->backward_tiles, &hdr->status, hdr->counters);
+        tile_counter, &hdr->status, hdr->counters);
   return cudaGetLastError();
 }
 
@@ -1026,26 +1033,34 @@ cudaError_t launch_raster_bwd(const fgs_record *records, const uint32_t *vals,
   float *g2d = reinterpret_cast<float *>(ws + L.g2d);
   uint32_t *order = reinterpret_cast<uint32_t *>(ws + L.tile_order);
   uint32_t *bucket = order + vs.total_tiles;
-  uint32_t *hist = bucket + vs.total_tiles;  // WORK_BUCKETS counts, then WORK_BUCKETS cursors
-  cudaError_t e = cudaMemsetAsync(&hdr->backward_tiles, 0, sizeof(uint32_t), st);
+  // WORK_BUCKETS class counts, WORK_BUCKETS cursors, then the persistent CTAs' tile counter:
+  // one memset clears the three
+  uint32_t *hist = bucket + vs.total_tiles;
+  uint32_t *tile_counter = hist + 2 * WORK_BUCKETS;
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (2 * WORK_BUCKETS + 1), st);
   if (e != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(g2d, 0, sizeof(float) * G2D_STRIDE * (size_t)n_records, st)) != cudaSuccess)
-    return e;
-  if ((e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 2 * WORK_BUCKETS, st)) != cudaSuccess) return e;
+  const size_t g2d_bytes = sizeof(float) * G2D_STRIDE * (size_t)n_records;
+  static_assert(G2D_STRIDE % 4 == 0, "gradient rows zeroed as float4");
   if (vs.total_tiles > 0) {
-    tile_work_kernel<<<(unsigned)((vs.total_tiles + 7) / 8), 256, 0, st>>>(
-        tile_ranges, n_processed, vs, &hdr->status, bucket, hist);
+    // a warp per tile, and enough CTAs that each thread zeroes at most eight float4
+    const int64_t n4 = (int64_t)(g2d_bytes / sizeof(float4));
+    const int64_t blocks = std::max((vs.total_tiles + 7) / 8, (n4 + 2047) / 2048);
+    tile_work_kernel<<<(unsigned)blocks, 256, 0, st>>>(tile_ranges, n_processed, vs, &hdr->status,
+                                                       bucket, hist,
+                                                       reinterpret_cast<float4 *>(g2d), n4);
     tile_order_kernel<<<(unsigned)((vs.total_tiles + 1023) / 1024), 1024, 0, st>>>(
         bucket, hist, hist + WORK_BUCKETS, vs.total_tiles, order, &hdr->status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else if ((e = cudaMemsetAsync(g2d, 0, g2d_bytes, st)) != cudaSuccess) {
+    return e;
   }
   const bool ins = opt.instrument;
   if (opt.ev_before && (e = cudaEventRecord(opt.ev_before, st)) != cudaSuccess) return e;
   switch (opt.bwd_ppt) {
-    case 1: e = bwd_launch<1>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, ins, st); break;
-    case 2: e = bwd_launch<2>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, ins, st); break;
-    case 4: e = bwd_launch<4>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, ins, st); break;
-    default: e = bwd_launch<8>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, hdr, ins, st); break;
+    case 1: e = bwd_launch<1>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, tile_counter, hdr, ins, st); break;
+    case 2: e = bwd_launch<2>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, tile_counter, hdr, ins, st); break;
+    case 4: e = bwd_launch<4>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, tile_counter, hdr, ins, st); break;
+    default: e = bwd_launch<8>(records, vals, tile_ranges, vs, bg0, bg1, bg2, final_T, n_processed, dL_dimages, g2d, order, tile_counter, hdr, ins, st); break;
   }
   if (e == cudaSuccess && opt.ev_after) e = cudaEventRecord(opt.ev_after, st);
   return e;
