@@ -344,18 +344,21 @@ __global__ void __launch_bounds__(REC_THREADS)
 // segment order, with decoupled look-back over partitions of TSCAN_PART segments.
 // Cells (FINAL = false): writes ranges[s] = (start, start) for every non-empty cell (the second
 // word is the scatter's cursor and ends as the cell's end) and appends the cell to the list of
-// its size class (at most cls_cap entries: class 0). Tiles (FINAL = true): writes
-// ranges[s] = (start, end) for every non-empty tile and the number of pairs to *n_int (the rect
-// count instead when it exceeds the capacity, so the caller can grow the buffers). Empty
-// segments keep (0, 0). It runs even after a look-back of the binning gave up (its counts are
-// then all zero), so that every partition publishes and no wait of its own look-back depends on
-// a partition that left early.
+// its size class (at most cls_cap entries: class 0); empty cells keep (0, 0). Tiles (FINAL =
+// true): writes ranges[s] = (start, end) for every tile, (0, 0) when empty, and the
+// number of pairs to *n_int (the rect count instead when it exceeds the capacity, so the caller
+// can grow the buffers). A tile's count was written by the sort of its cell, so the tiles of an
+// empty cell (cell_ranges (0, 0): no sort ran for it) count zero whatever their count word
+// holds, and the tile ranges need no clearing beforehand. It runs even after a look-back of
+// the binning gave up (its counts are then all zero), so that every partition publishes and no
+// wait of its own look-back depends on a partition that left early.
 template <bool FINAL>
 __global__ void __launch_bounds__(256)
     tile_scan_kernel(uint32_t *ranges, int64_t total, uint64_t *lb, uint32_t *part_counter,
                      uint32_t *lists, uint32_t *seg_count, uint32_t cls_cap,
                      const unsigned long long *n_cand, int64_t capacity, int64_t *n_int,
-                     uint32_t *status, uint32_t wait_limit) {
+                     uint32_t *status, uint32_t wait_limit, Views vs,
+                     const uint32_t *__restrict__ cell_ranges) {
   __shared__ uint32_t s_warp[8];
   __shared__ uint64_t s_prefix;
   __shared__ uint32_t s_part;
@@ -368,15 +371,26 @@ __global__ void __launch_bounds__(256)
   const int64_t base = part * TSCAN_PART;
   // with more rect pairs than capacity nothing was binned: read the counts as zero, and report
   // the overflow (the caller grows the buffers from the pair count)
-  const bool counts_ok = (int64_t)*n_cand <= capacity;
-  if (!counts_ok && part == 0 && tid == 0) set_status(status, ST_CAPACITY);
+  const bool fits = (int64_t)*n_cand <= capacity;
+  if (!fits && part == 0 && tid == 0) set_status(status, ST_CAPACITY);
+  // after a look-back of the binning gave up no sort wrote the tile counts: read them as zero
+  const bool counts_ok = fits && !(FINAL && binning_timed_out(status));
   constexpr int ITEMS = TSCAN_PART / 256;
   uint32_t c[ITEMS];
   uint32_t sum = 0;
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
     const int64_t s = base + tid * ITEMS + k;
-    c[k] = s < total && counts_ok ? ranges[2 * s] : 0u;
+    bool live = s < total && counts_ok;
+    if (FINAL && live) {  // the tile's cell was sorted (non-empty) or its count is zero
+      const View &V = vs.v[view_of_tile(vs, s)];
+      const int64_t local = s - V.tile_offset;
+      const int64_t ty = local / V.tiles_x, tx = local - ty * V.tiles_x;
+      const int64_t cell = V.cell_offset + (ty / CELL) * V.cells_x + tx / CELL;
+      const uint2 crg = __ldg(reinterpret_cast<const uint2 *>(cell_ranges) + cell);
+      live = crg.y > crg.x;
+    }
+    c[k] = live ? ranges[2 * s] : 0u;
     sum += c[k];
   }
   uint32_t agg;
@@ -409,6 +423,10 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
     const int64_t s = base + tid * ITEMS + k;
+    if (FINAL && s < total && c[k] == 0u) {  // an empty tile: (0, 0)
+      ranges[2 * s] = 0u;
+      ranges[2 * s + 1] = 0u;
+    }
     if (c[k] > 0u) {
       ranges[2 * s] = (uint32_t)o;
       ranges[2 * s + 1] = (uint32_t)(FINAL ? o + c[k] : o);
@@ -1160,8 +1178,10 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
 
   // the header, both look-back arrays and the cell counters are adjacent: one memset
   if ((e = cudaMemsetAsync(hdr, 0, L.g2d - L.header, st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)T, st)) != cudaSuccess) return e;
-  if (R == 0) return cudaMemsetAsync(n_int, 0, sizeof(int64_t), st);
+  if (R == 0) {  // no pairs: every tile range empty
+    if ((e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)T, st)) != cudaSuccess) return e;
+    return cudaMemsetAsync(n_int, 0, sizeof(int64_t), st);
+  }
 
   const bool ellipse = (flags & FGS_BIN_ELLIPSE) != 0;
   const unsigned rgrid = (unsigned)((R + REC_BLOCK - 1) / REC_BLOCK);
@@ -1173,7 +1193,7 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
                                                    &hdr->n_visible, &hdr->status);
   tile_scan_kernel<false><<<(unsigned)((NC + TSCAN_PART - 1) / TSCAN_PART), 256, 0, st>>>(
       cell_ranges, NC, cell_lb, &hdr->cell_parts, lists, hdr->seg_count, (uint32_t)CELL_CAP0,
-      &hdr->n_candidates, capacity, nullptr, &hdr->status, opt.wait_limit);
+      &hdr->n_candidates, capacity, nullptr, &hdr->status, opt.wait_limit, vs, nullptr);
   if (ellipse)
     cell_scatter_kernel<true><<<rgrid, REC_THREADS, 0, st>>>(
         records, tiles_touched, R, n, vs, cell_ranges, words, masks, cta_counts,
@@ -1205,7 +1225,7 @@ cudaError_t launch_bin_sort(const fgs_record *records, const uint32_t *tiles_tou
   }
   tile_scan_kernel<true><<<(unsigned)L.tile_parts, 256, 0, st>>>(
       tile_ranges, T, tile_lb, &hdr->tile_parts, nullptr, nullptr, 0u, &hdr->n_candidates,
-      capacity, n_int, &hdr->status, opt.wait_limit);
+      capacity, n_int, &hdr->status, opt.wait_limit, vs, cell_ranges);
   static int eocc = 0;
   if (eocc == 0) {
     int a = 0;

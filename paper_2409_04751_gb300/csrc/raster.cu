@@ -851,14 +851,15 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 8 ? 16 : 1)
           if (any_a || any_b) {
             float tot8;
             const float tot = warp_transpose_sum16(va, vb, lane, tot8);
-            const int q = lane >> 1;  // value index of this lane's total: 0..7 a, 8..15 b
-            const bool is_b = q >= 8;
-            if ((lane & 1) == 0 && (is_b ? any_b : any_a)) {
-              float *dst = g2d + (size_t)cidx[2 * p + (is_b ? 1 : 0)] * G2D_STRIDE;
-              atomicAdd(dst + (q & 7), tot);
+            // one atomic per lane at most: even lanes 2i add value i of (a[0..7], b[0..7]),
+            // lanes 1 and 17 the ninth value of a and of b
+            const bool even = (lane & 1) == 0;
+            const bool for_b = even ? lane >= 16 : lane == 17;
+            const bool act = (even || lane == 1 || lane == 17) && (for_b ? any_b : any_a);
+            if (act) {
+              float *dst = g2d + (size_t)cidx[2 * p + (for_b ? 1 : 0)] * G2D_STRIDE;
+              atomicAdd(dst + (even ? ((lane >> 1) & 7) : 8), even ? tot : tot8);
             }
-            if (lane == 0 && any_a) atomicAdd(g2d + (size_t)cidx[2 * p] * G2D_STRIDE + 8, tot8);
-            if (lane == 16 && any_b) atomicAdd(g2d + (size_t)cidx[2 * p + 1] * G2D_STRIDE + 8, tot8);
           }
         }
         __syncthreads();  // cf, xidx and cidx reused by the next batch
