@@ -479,13 +479,14 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
               const float2 Ta = __ffma2_rn(na_a[k / 2], Tp, Tp);
               const float2 Tb = __ffma2_rn(na_b[k / 2], Ta, Ta);
               would_stop = would_stop || Tb.x < T_MIN || Tb.y < T_MIN;
-              if (COUNT) n_eval += ((live[k] ? 1u : 0u) + (live[k + 1] ? 1u : 0u)) * (has_b ? 2u : 1u);
             }
             const uint32_t pa1 = __float_as_uint(qa.w) + 1, pb1 = __float_as_uint(qb.w) + 1;
             if (!__any_sync(0xffffffffu, would_stop)) {
               // no pixel of the warp stops: both blends without the stop's selects
 #pragma unroll
               for (int k = 0; k < PPT; k += 2) {
+                // (no pixel stops, so the live pixels evaluate both entries)
+                if (COUNT) n_eval += ((live[k] ? 1u : 0u) + (live[k + 1] ? 1u : 0u)) * (has_b ? 2u : 1u);
                 const float2 Tp = make_float2(T[k], T[k + 1]);
                 float2 C0p = make_float2(C0[k], C0[k + 1]), C1p = make_float2(C1[k], C1[k + 1]);
                 float2 C2p = make_float2(C2[k], C2[k + 1]);
@@ -517,8 +518,11 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
                 float2 Tp = make_float2(T[k], T[k + 1]);
                 float2 C0p = make_float2(C0[k], C0[k + 1]), C1p = make_float2(C1[k], C1[k + 1]);
                 float2 C2p = make_float2(C2[k], C2[k + 1]);
+                // a pixel that stops at entry a does not evaluate entry b
+                if (COUNT) n_eval += (live[k] ? 1u : 0u) + (live[k + 1] ? 1u : 0u);
                 fwd_blend2_na<COUNT>(live[k], live[k + 1], na_a[k / 2], qa, pa1, Tp, C0p, C1p, C2p,
                                      last[k], last[k + 1], n_blend);
+                if (COUNT && has_b) n_eval += (live[k] ? 1u : 0u) + (live[k + 1] ? 1u : 0u);
                 fwd_blend2_na<COUNT>(live[k], live[k + 1], na_b[k / 2], qb, pb1, Tp, C0p, C1p, C2p,
                                      last[k], last[k + 1], n_blend);
                 T[k] = Tp.x; T[k + 1] = Tp.y;

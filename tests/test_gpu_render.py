@@ -288,7 +288,8 @@ def test_calls_with_different_shapes_run_side_by_side(cuda_device):
 def test_instrumented_launches_count_what_they_do(cuda_device, shape):
     """The measurement launches (FGS_OPT_INSTRUMENT) render the same image and count their work
     consistently: the backward's contributions are exactly the forward's blends (both passes
-    take the same alpha decisions), every evaluation count bounds its blend count, the backward
+    take the same alpha decisions), every evaluation count bounds its blend count and every
+    forward shape counts the same evaluations and blends, the backward
     stages exactly the entries up to each tile's furthest processed one, and the forward stages
     at least those and at most the tile's whole list."""
     scene, cams = scenes.config0()
@@ -314,3 +315,10 @@ def test_instrumented_launches_count_what_they_do(cuda_device, shape):
         furthest[t] = min(npr[16 * ty:16 * ty + 16, 16 * tx:16 * tx + 16].max(), rg[t, 1] - rg[t, 0])
     assert c[5] == furthest.sum()
     assert furthest.sum() <= c[4] <= m
+    # every work shape evaluates the same (pixel, entry) pairs: a live pixel, an entry kept at
+    # staging, and no entry after the one that stopped the pixel
+    r1 = FisheyeRenderer(dev, capacity=1 << 16, fwd_ppt=1, bwd_ppt=shape[1])
+    r1.opts = fgs.options(fwd=1, bwd=shape[1], instrument=True)
+    r1.forward(gs, cams)
+    c1 = fgs.fgs_read_counters(r1._bufs["ws"])
+    assert c[0] == c1[0] and c[1] == c1[1]
