@@ -464,6 +464,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
             // (1 - a_b) is the smaller of the two transmittances, so T_b >= 1e-4 means neither
             // entry stops the pixel
             float2 na_a[PPT > 1 ? PPT / 2 : 1], na_b[PPT > 1 ? PPT / 2 : 1];
+            uint32_t last_n[PPT];  // the processed counts if no pixel stops
+            const uint32_t pa1 = __float_as_uint(qa.w) + 1, pb1 = __float_as_uint(qb.w) + 1;
             bool would_stop = false;
 #pragma unroll
             for (int k = 0; k < PPT; k += 2) {
@@ -479,8 +481,9 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
               const float2 Ta = __ffma2_rn(na_a[k / 2], Tp, Tp);
               const float2 Tb = __ffma2_rn(na_b[k / 2], Ta, Ta);
               would_stop = would_stop || Tb.x < T_MIN || Tb.y < T_MIN;
+              last_n[k] = cb0 ? pb1 : ca0 ? pa1 : last[k];
+              last_n[k + 1] = cb1 ? pb1 : ca1 ? pa1 : last[k + 1];
             }
-            const uint32_t pa1 = __float_as_uint(qa.w) + 1, pb1 = __float_as_uint(qb.w) + 1;
             if (!__any_sync(0xffffffffu, would_stop)) {
               // no pixel of the warp stops: both blends without the stop's selects
 #pragma unroll
@@ -500,8 +503,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, PPT == 1 ? 5 : 1)
                 C1p = __ffma2_rn(dup2(qb.y), wb, C1p);
                 C2p = __ffma2_rn(dup2(qb.z), wb, C2p);
                 const float2 Tb = __ffma2_rn(na_b[k / 2], Ta, Ta);
-                last[k] = na_b[k / 2].x != 0.f ? pb1 : na_a[k / 2].x != 0.f ? pa1 : last[k];
-                last[k + 1] = na_b[k / 2].y != 0.f ? pb1 : na_a[k / 2].y != 0.f ? pa1 : last[k + 1];
+                last[k] = last_n[k];
+                last[k + 1] = last_n[k + 1];
                 if (COUNT)
                   n_blend += (na_a[k / 2].x != 0.f) + (na_a[k / 2].y != 0.f) +
                              (na_b[k / 2].x != 0.f) + (na_b[k / 2].y != 0.f);
