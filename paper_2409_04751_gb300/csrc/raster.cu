@@ -11,8 +11,10 @@
 // (the exact binning's conservative test: the tile lists keep the rect binning of the method,
 // the blend skips what the rect over-covers) and writes the rest in pairs, so that one paired
 // FP32 FMA (fma.rn.f32x2) advances a pixel's exponent for two Gaussians; every kept entry
-// carries its list position. A warp whose pixels have all stopped skips the batch (warp
-// ballot); the CTA leaves the tile when all its pixels have stopped.
+// carries its list position. With several pixels per thread, a warp first checks whether a
+// pair of entries stops any of its pixels and, where none does (most pairs), blends both without
+// the stop test. A warp whose pixels have all stopped skips the batch (warp ballot); the CTA
+// leaves the tile when all its pixels have stopped.
 //
 // The backward replays each pixel's blend back to front from its final transmittance and the
 // number of list entries it processed (both written by the forward), recovering the
