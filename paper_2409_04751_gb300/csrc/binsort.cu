@@ -1041,7 +1041,8 @@ __device__ __forceinline__ int64_t cell_tile(const View &V, uint32_t bx, uint32_
   return V.tile_offset + (int64_t)(by + b / CELL) * V.tiles_x + bx + b % CELL;
 }
 
-__global__ void __launch_bounds__(CEMIT_THREADS)
+// four CTAs per SM: at most 32 registers a thread
+__global__ void __launch_bounds__(CEMIT_THREADS, 4)
     cell_emit_kernel(const uint32_t *__restrict__ tile_ranges,
                      const uint32_t *__restrict__ cell_ranges, const uint64_t *__restrict__ words,
                      const uint16_t *__restrict__ masks, Views vs, uint64_t *__restrict__ keys,
@@ -1121,13 +1122,18 @@ __global__ void __launch_bounds__(CEMIT_THREADS)
 #pragma unroll
         for (int b = 0; b < CELL * CELL; ++b) {
           const uint2 bp = s_bp[g][b];
-          if ((bp.x >> lane) & 1u) {
-            const uint32_t pos = bp.y + __popc(bp.x & lt);
-            if (in_bounds(pos, (uint64_t)capacity, status) && (int64_t)pos < capacity) {
-              keys[pos] = ((uint64_t)s_tile[b] << 32) | kd;
-              vals[pos] = (uint32_t)w;
-            }
-          }
+          const uint32_t pos = bp.y + __popc(bp.x & lt);
+          bool ok = (bp.x >> lane) & 1u;
+          if (FGS_CHECK && ok) ok = in_bounds(pos, (uint64_t)capacity, status);
+          ok = ok && (int64_t)pos < capacity;
+          // predicated stores (no branch per tile bit): the address is formed for every lane
+          // but only dereferenced where ok
+          const uint64_t key = ((uint64_t)s_tile[b] << 32) | kd;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.u32 p, %3, 0;\n"
+              " @p st.global.u64 [%0], %2;\n @p st.global.u32 [%1], %4;\n}"
+              :: "l"(keys + pos), "l"(vals + pos), "l"(key), "r"((uint32_t)ok), "r"((uint32_t)w)
+              : "memory");
         }
       }
     } else {
