@@ -23,7 +23,9 @@
  *    after a wait of the binning ran out its later kernels do nothing, and while the word is
  *    set fgs_rasterize draws the background only and fgs_backward's screen-space pass adds
  *    nothing.
- *  - Gradients are overwritten, not accumulated.
+ *  - Gradients are overwritten, not accumulated. The workspace and every output buffer may hold
+ *    anything before a call: each call clears or overwrites what it reads from them (the
+ *    backward zeroes its accumulators itself; fgs_bin_sort writes every tile range).
  *  - The library keeps no settings of its own: the work shape, the measurement counters and
  *    the wait bound are chosen per call (fgs_options). Calls on distinct workspaces are
  *    independent; calls sharing a workspace must not overlap in time (they share its
